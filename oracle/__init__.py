@@ -1,0 +1,241 @@
+"""CPU oracle for the projected Krylov verification path -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's ``cpu_baseline``
+/ ``--impl reference`` legs may import this package.  The product library never
+loads it and shares no code with it.
+
+The arithmetic lives in ``kv_oracle.c`` (plain FP64 C, optionally OpenMP);
+this module compiles it with gcc, marshals numpy arrays through ctypes, and
+strings the steps together in the paper's order:
+
+  1. fold b into the dynamics with a constant-1 variable (Sec. 2.1);
+  2. for every column E_j of the initial space (Sec. 3.2): beta0 = ||E_j||,
+     v1 = E_j / beta0, then Lanczos (symmetric A, Alg. 3/4) or Arnoldi (Alg. 1)
+     with P = C V accumulated in the loop (Sec. 3.1, Alg. 4);
+  3. basis[j][r][k] = beta0 * P[r,:] e^{H t_k} e_1 (Eq. approx-formula);
+  4. box-initial-set output interval, first violation, counter-example vertex
+     (the per-step LP of Sec. 2.1 in closed form).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Dict, List, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kv_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libkvoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BREAKDOWN_REL = 1e-12
+
+
+def build(force: bool = False) -> str:
+    """Compile kv_oracle.c into oracle/_build/libkvoracle.so (gcc, -fopenmp)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Op(C.Structure):
+    _fields_ = [("kind", C.c_int), ("ndim", C.c_int), ("dims", C.c_int64 * 3),
+                ("coef", C.c_double), ("h", C.c_double * 3), ("n", C.c_int64),
+                ("rp", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+                ("b", C.c_void_p), ("aug", C.c_int)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            lib.ora_num_threads.restype = C.c_int
+            lib.ora_dim.restype = C.c_int64
+            lib.ora_dim.argtypes = [C.POINTER(_Op)]
+            lib.ora_apply.argtypes = [C.POINTER(_Op), P, P]
+            for f in (lib.ora_lanczos, lib.ora_arnoldi):
+                f.restype = C.c_int
+                f.argtypes = [C.POINTER(_Op), P, C.c_int, C.c_int, P, P, P, P, P]
+            lib.ora_expm.argtypes = [C.c_int, P, P]
+            lib.ora_basis.argtypes = [C.c_int, C.c_int, P, C.c_int, P, C.c_double, C.c_double,
+                                      C.c_int, P]
+            lib.ora_bounds.restype = C.c_int
+            lib.ora_bounds.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P,
+                                       C.POINTER(C.c_int), C.POINTER(C.c_int), P,
+                                       C.POINTER(C.c_double)]
+            _lib = lib
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().ora_num_threads())
+
+
+class _OpHolder:
+    """Keeps the numpy arrays referenced by an ora_op alive."""
+
+    def __init__(self, system, aug: bool):
+        self.keep = []
+        op = _Op()
+        if hasattr(system, "dims"):
+            op.kind = 0
+            op.ndim = len(system.dims)
+            for a in range(3):
+                op.dims[a] = int(system.dims[a]) if a < op.ndim else 1
+                op.h[a] = float(system.h[a]) if a < op.ndim else 1.0
+            op.coef = float(system.coef)
+            op.n = int(np.prod(system.dims, dtype=np.int64))
+        else:
+            op.kind = 1
+            op.n = int(system.n)
+            rp = np.ascontiguousarray(system.row_ptr, dtype=np.int64)
+            col = np.ascontiguousarray(system.col, dtype=np.int32)
+            val = np.ascontiguousarray(system.val, dtype=np.float64)
+            self.keep += [rp, col, val]
+            op.rp, op.col, op.val = _p(rp), _p(col), _p(val)
+        b = getattr(system, "b", None)
+        if b is not None:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            self.keep.append(b)
+            op.b = _p(b)
+        op.aug = 1 if aug else 0
+        self.op = op
+
+    @property
+    def N(self) -> int:
+        return int(self.op.n) + int(self.op.aug)
+
+
+def apply(system, x: np.ndarray, aug: bool = False) -> np.ndarray:
+    """y = A x (or A' x with the constant variable appended when aug)."""
+    h = _OpHolder(system, aug)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert x.shape == (h.N,)
+    y = np.empty(h.N)
+    _load().ora_apply(C.byref(h.op), _p(x), _p(y))
+    return y
+
+
+def _c_arrays(C_row_ptr, C_col, C_val):
+    return (np.ascontiguousarray(C_row_ptr, dtype=np.int64),
+            np.ascontiguousarray(C_col, dtype=np.int64),
+            np.ascontiguousarray(C_val, dtype=np.float64))
+
+
+def krylov(system, v1: np.ndarray, m: int, C_row_ptr, C_col, C_val, *, method: str,
+           aug: bool = False):
+    """Lanczos (Alg. 3/4) or Arnoldi (Alg. 1) from the normalised v1.
+    Returns (H (m+1) x m, P o x m, number of valid columns)."""
+    h = _OpHolder(system, aug)
+    v1 = np.ascontiguousarray(v1, dtype=np.float64)
+    assert v1.shape == (h.N,)
+    crp, ccol, cval = _c_arrays(C_row_ptr, C_col, C_val)
+    o = len(crp) - 1
+    H = np.zeros((m + 1, m))
+    P = np.zeros((o, m))
+    f = _load().ora_lanczos if method == "lanczos" else _load().ora_arnoldi
+    used = f(C.byref(h.op), _p(v1), m, o, _p(crp), _p(ccol), _p(cval), _p(H), _p(P))
+    return H, P, int(used)
+
+
+def expm(A: np.ndarray) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    m = A.shape[0]
+    E = np.empty_like(A)
+    _load().ora_expm(m, _p(A), _p(E))
+    return E
+
+
+def basis(H: np.ndarray, P: np.ndarray, used: int, beta0: float, dt: float, steps: int) -> np.ndarray:
+    """o x (steps+1): beta0 * P[:, :used] e^{H_used t_k} e_1 for t_k = k dt."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    o = P.shape[0]
+    out = np.zeros((o, steps + 1))
+    if used == 0 or o == 0:
+        return out
+    _load().ora_basis(used, H.shape[1], _p(H), o, _p(P), float(beta0), float(dt), steps, _p(out))
+    return out
+
+
+def bounds(basis_all: np.ndarray, zlo, zhi, theta) -> Dict:
+    """basis_all: ncol x o x (steps+1).  Closed-form LP optimum per step."""
+    basis_all = np.ascontiguousarray(basis_all, dtype=np.float64)
+    ncol, o, S = basis_all.shape
+    zlo = np.ascontiguousarray(zlo, dtype=np.float64)
+    zhi = np.ascontiguousarray(zhi, dtype=np.float64)
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    lo = np.zeros((o, S))
+    hi = np.zeros((o, S))
+    vs, vr, ys = C.c_int(-1), C.c_int(-1), C.c_double(0.0)
+    zstar = np.zeros(ncol)
+    _load().ora_bounds(o, ncol, S - 1, _p(basis_all), _p(zlo), _p(zhi), _p(theta), _p(lo), _p(hi),
+                       C.byref(vs), C.byref(vr), _p(zstar), C.byref(ys))
+    unsafe = vs.value >= 0
+    return dict(lo=lo, hi=hi, viol_step=vs.value, viol_row=vr.value,
+                zstar=zstar if unsafe else None, ystar=ys.value if unsafe else None)
+
+
+def column_method(problem, col) -> str:
+    """Lanczos needs a symmetric operator: the system must be symmetric and the
+    column must not carry the constant variable (A' = [[A, b], [0, 0]] is not
+    symmetric, but it maps {x_const = 0} into itself as A does)."""
+    if problem.method in ("lanczos", "arnoldi"):
+        return problem.method
+    sym = bool(getattr(problem.system, "symmetric", False))
+    carries = problem.system.b is not None and col.is_fixed
+    return "lanczos" if (sym and not carries) else "arnoldi"
+
+
+def run(problem, *, columns: Optional[List[int]] = None, want_basis: bool = True) -> Dict:
+    """The whole path for one problem.  `columns` restricts the Krylov runs to
+    a subset of the initial-space columns (for sampled checks on large cases);
+    bounds are then only computed when every column was run."""
+    from workloads import column_dense
+
+    sysm = problem.system
+    n = int(sysm.n)
+    dims = getattr(sysm, "dims", None)
+    aug = sysm.b is not None
+    sel = list(range(problem.i)) if columns is None else list(columns)
+    Hs, Ps, used, beta0s, bases = {}, {}, {}, {}, {}
+    for j in sel:
+        col = problem.columns[j]
+        e = column_dense(col, n, dims)
+        if aug:
+            e = np.concatenate([e, [1.0 if col.is_fixed else 0.0]])
+        b0 = float(np.sqrt(np.dot(e, e)))
+        beta0s[j] = b0
+        if b0 == 0.0:
+            Hs[j] = np.zeros((problem.m + 1, problem.m))
+            Ps[j] = np.zeros((problem.o, problem.m))
+            used[j] = 0
+            bases[j] = np.zeros((problem.o, problem.steps + 1))
+            continue
+        H, P, u = krylov(sysm, e / b0, problem.m, problem.C_row_ptr, problem.C_col, problem.C_val,
+                         method=column_method(problem, col), aug=aug)
+        Hs[j], Ps[j], used[j] = H, P, u
+        if want_basis:
+            bases[j] = basis(H, P, u, b0, problem.dt, problem.steps)
+    out = dict(H=Hs, P=Ps, used=used, beta0=beta0s, basis=bases)
+    if want_basis and len(sel) == problem.i:
+        ball = np.stack([bases[j] for j in range(problem.i)])
+        zlo = [c.zlo for c in problem.columns]
+        zhi = [c.zhi for c in problem.columns]
+        out.update(bounds(ball, zlo, zhi, problem.theta))
+    return out

@@ -1,0 +1,357 @@
+"""Seeded synthetic inputs for the projected-Krylov verification path.
+
+This module only *describes* problems: grids, sparse matrices, initial-set
+columns, output rows and thresholds, drawn from fixed seeds.  It holds none of
+the method's arithmetic (no Krylov step, no exponential, no bound), so both the
+CPU oracle and the CUDA path can be fed from it without sharing any of the
+computation they are compared on.
+
+Workload shapes follow the paper's benchmarks:
+  * 2D / 3D heat diffusion on a uniform grid with a Dirichlet-0 boundary, a
+    heated block as a one-generator initial set and the temperature at the
+    centre as output (Sec. 6.3, "Symmetric 3D Heat Diffusion");
+  * a random sparse nonsymmetric system with a forcing term b, a box initial
+    set over a few variables and a couple of +-1 output rows, standing in for
+    the circuit benchmark of Sec. 6.1 (its matrix is not available);
+  * the timed harmonic oscillator worked example of Sec. 2.2.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------
+# descriptions
+# --------------------------------------------------------------------------
+@dataclass
+class GridSystem:
+    """dx/dt = coef * Laplacian_h(x) (+ b), Dirichlet-0 outside the grid.
+
+    dims are (nx, ny) or (nx, ny, nz); x varies fastest in the flat index
+    idx = (z*ny + y)*nx + x.  h holds the grid spacing per axis.
+    """
+    dims: Tuple[int, ...]
+    coef: float
+    h: Tuple[float, ...]
+    b: Optional[np.ndarray] = None
+
+    @property
+    def ndim(self) -> int:
+        return len(self.dims)
+
+    @property
+    def n(self) -> int:
+        return int(np.prod(self.dims, dtype=np.int64))
+
+    symmetric = True  # the Dirichlet Laplacian is symmetric
+
+
+@dataclass
+class CsrSystem:
+    """dx/dt = A x (+ b) with A in CSR form (row_ptr int64, col int32, val f64)."""
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    b: Optional[np.ndarray] = None
+    symmetric: bool = False
+
+
+@dataclass
+class Column:
+    """One column E_j of the initial-space matrix, x0 = sum_j E_j z_j.
+
+    kind = "box":    E_j = value on the grid cells lo <= idx < hi (per axis)
+    kind = "sparse": E_j[idx] = val
+    kind = "dense":  E_j = dense (length n)
+    is_fixed: z_j is pinned to 1 and the column carries the constant-1
+    variable used to fold b into the dynamics (Sec. 2.1).
+    """
+    kind: str
+    zlo: float
+    zhi: float
+    is_fixed: bool = False
+    box_lo: Tuple[int, ...] = ()
+    box_hi: Tuple[int, ...] = ()
+    value: float = 1.0
+    idx: Optional[np.ndarray] = None
+    val: Optional[np.ndarray] = None
+    dense: Optional[np.ndarray] = None
+
+
+@dataclass
+class Problem:
+    system: object
+    columns: List[Column]
+    C_row_ptr: np.ndarray
+    C_col: np.ndarray
+    C_val: np.ndarray
+    theta: np.ndarray          # per output row; +inf = no check
+    dt: float
+    steps: int
+    m: int                     # Krylov dimension (the paper's k)
+    method: str = "auto"       # auto | lanczos | arnoldi
+    precision: str = "fp64"    # fp64 | fp32
+    name: str = ""
+
+    @property
+    def o(self) -> int:
+        return len(self.C_row_ptr) - 1
+
+    @property
+    def i(self) -> int:
+        return len(self.columns)
+
+
+def _c_rows(rows: Sequence[Tuple[Sequence[int], Sequence[float]]]):
+    rp = [0]
+    cols: List[int] = []
+    vals: List[float] = []
+    for idx, val in rows:
+        cols.extend(int(c) for c in idx)
+        vals.extend(float(v) for v in val)
+        rp.append(len(cols))
+    return (np.asarray(rp, dtype=np.int64), np.asarray(cols, dtype=np.int64),
+            np.asarray(vals, dtype=np.float64))
+
+
+def grid_index(dims: Sequence[int], cell: Sequence[int]) -> int:
+    idx = 0
+    for ax in reversed(range(len(dims))):
+        idx = idx * int(dims[ax]) + int(cell[ax])
+    return idx
+
+
+# --------------------------------------------------------------------------
+# heat diffusion (Sec. 6.3 shapes; Dirichlet-0 boundary)
+# --------------------------------------------------------------------------
+def heat(dims: Sequence[int], *, coef: float = 0.01, block: Sequence[int],
+         output: str = "centre", theta: float = math.inf, dt: float,
+         steps: int, m: int, zlo: float = 0.9, zhi: float = 1.1,
+         precision: str = "fp64", method: str = "auto", name: str = "") -> Problem:
+    """Heat equation on a grid with spacing h = 1/(N+1) per axis.
+
+    Initial set: the corner block [0, block) per axis at temperature
+    u in [zlo, zhi] (one generator, one Krylov run); everything else 0.
+    output = "centre": the cell N//2 on every axis;
+    output = "centre8": the mean of the 2^ndim cells {N//2-1, N//2}^ndim.
+    """
+    dims = tuple(int(d) for d in dims)
+    h = tuple(1.0 / (d + 1) for d in dims)
+    sysm = GridSystem(dims=dims, coef=coef, h=h)
+    col = Column(kind="box", zlo=zlo, zhi=zhi, box_lo=tuple(0 for _ in dims),
+                 box_hi=tuple(int(b) for b in block), value=1.0)
+    if output == "centre":
+        cells = [tuple(d // 2 for d in dims)]
+    elif output == "centre8":
+        import itertools
+        cells = list(itertools.product(*[(d // 2 - 1, d // 2) for d in dims]))
+    else:
+        raise ValueError(output)
+    w = 1.0 / len(cells)
+    rp, cc, cv = _c_rows([([grid_index(dims, c) for c in cells], [w] * len(cells))])
+    return Problem(system=sysm, columns=[col], C_row_ptr=rp, C_col=cc, C_val=cv,
+                   theta=np.array([theta]), dt=dt, steps=steps, m=m,
+                   method=method, precision=precision, name=name)
+
+
+def heat2d_20(**kw) -> Problem:
+    """20x20 grid, 5x5 heated corner block, output at cell (10,10),
+    unsafe y >= 0.05, dt 0.1, 500 steps, Lanczos m = 30."""
+    args = dict(block=(5, 5), output="centre", theta=0.05, dt=0.1, steps=500, m=30,
+                name="heat2d-20x20")
+    args.update(kw)
+    return heat((20, 20), **args)
+
+
+def heat3d_100(**kw) -> Problem:
+    """100^3 grid, 10^3 heated corner block, mean of the 8 centre cells,
+    unsafe y >= 0.01, dt 0.02, 1000 steps, Lanczos m = 40."""
+    args = dict(block=(10, 10, 10), output="centre8", theta=0.01, dt=0.02, steps=1000,
+                m=40, name="heat3d-100^3")
+    args.update(kw)
+    return heat((100, 100, 100), **args)
+
+
+def heat3d_1000(**kw) -> Problem:
+    """1000^3 grid (n = 1e9), 100^3 heated corner block, centre cell output,
+    dt 0.02, 200 steps, Lanczos m = 30 (unsafe y >= 0.01)."""
+    args = dict(block=(100, 100, 100), output="centre", theta=0.01, dt=0.02, steps=200,
+                m=30, name="heat3d-1000^3")
+    args.update(kw)
+    return heat((1000, 1000, 1000), **args)
+
+
+def heat3d_truncated(full: Problem, side: int) -> Problem:
+    """The same heat problem on the sub-grid [0, side)^3 with the *same* h.
+
+    A Krylov vector after j steps is supported within j stencil hops of the
+    heated block, so while block + m < side - 1 the Lanczos coefficients and
+    projections on the truncated grid equal those of the full grid (the far
+    Dirichlet faces are never reached).  The output cell, if outside the
+    sub-grid, is dropped (its projection is exactly 0 on the full grid too).
+    """
+    s = full.system
+    dims = tuple(side for _ in s.dims)
+    sysm = GridSystem(dims=dims, coef=s.coef, h=s.h)
+    col = full.columns[0]
+    return Problem(system=sysm, columns=[col], C_row_ptr=np.array([0, 0], dtype=np.int64),
+                   C_col=np.zeros(0, dtype=np.int64), C_val=np.zeros(0), theta=np.array([math.inf]),
+                   dt=full.dt, steps=full.steps, m=full.m, method=full.method,
+                   precision=full.precision, name=full.name + f"-trunc{side}")
+
+
+# --------------------------------------------------------------------------
+# random sparse nonsymmetric system with forcing (stand-in for Sec. 6.1)
+# --------------------------------------------------------------------------
+def random_csr(n: int, nnz_per_row: int = 10, seed: int = 0, with_b: bool = True) -> CsrSystem:
+    """n x n, nnz_per_row distinct off-diagonal columns per row drawn uniformly
+    (never the row itself), values N(0,1)/sqrt(nnz_per_row), diagonal
+    -(row abs-sum + 0.1); b ~ U[-0.01, 0.01]."""
+    rng = np.random.default_rng(seed)
+    k = nnz_per_row
+    rows = np.arange(n, dtype=np.int64)
+    off = rng.integers(0, n - 1, size=(n, k), dtype=np.int64)
+    off = off + (off >= rows[:, None])
+    off.sort(axis=1)
+    while True:
+        dup = np.any(off[:, 1:] == off[:, :-1], axis=1)
+        if not dup.any():
+            break
+        bad = np.nonzero(dup)[0]
+        redraw = rng.integers(0, n - 1, size=(len(bad), k), dtype=np.int64)
+        redraw = redraw + (redraw >= bad[:, None])
+        redraw.sort(axis=1)
+        off[bad] = redraw
+    vals = rng.standard_normal((n, k)) / math.sqrt(k)
+    diag = -(np.abs(vals).sum(axis=1) + 0.1)
+    cols = np.concatenate([off, rows[:, None]], axis=1)
+    allv = np.concatenate([vals, diag[:, None]], axis=1)
+    order = np.argsort(cols, axis=1, kind="stable")
+    cols = np.take_along_axis(cols, order, axis=1)
+    allv = np.take_along_axis(allv, order, axis=1)
+    row_ptr = np.arange(n + 1, dtype=np.int64) * (k + 1)
+    b = rng.uniform(-0.01, 0.01, size=n) if with_b else None
+    return CsrSystem(n=n, row_ptr=row_ptr, col=cols.reshape(-1).astype(np.int32),
+                     val=allv.reshape(-1).astype(np.float64), b=b, symmetric=False)
+
+
+def random_csr_problem(n: int = 2_000_000, *, seed: int = 0, n_gen: int = 16, o: int = 2,
+                       c_width: int = 1000, dt: float = 0.01, steps: int = 2000, m: int = 60,
+                       theta: Optional[Sequence[float]] = None, precision: str = "fp64",
+                       with_b: bool = True, name: str = "") -> Problem:
+    """Box initial set on n_gen random variables each in [-1, 1] (one unit
+    generator per variable) plus the fixed centre column (zero state, constant
+    variable 1); C = o random +-1 rows over c_width distinct variables."""
+    sysm = random_csr(n, seed=seed, with_b=with_b)
+    rng = np.random.default_rng(seed + 7919)
+    gvars = rng.choice(n, size=n_gen, replace=False)
+    cols = [Column(kind="sparse", zlo=-1.0, zhi=1.0, idx=np.array([v], dtype=np.int64),
+                   val=np.array([1.0])) for v in gvars]
+    cols.append(Column(kind="sparse", zlo=1.0, zhi=1.0, is_fixed=True,
+                       idx=np.zeros(0, dtype=np.int64), val=np.zeros(0)))
+    rows = []
+    for _ in range(o):
+        cidx = np.sort(rng.choice(n, size=min(c_width, n), replace=False))
+        sgn = rng.choice([-1.0, 1.0], size=len(cidx))
+        rows.append((cidx, sgn))
+    rp, cc, cv = _c_rows(rows)
+    th = np.full(o, math.inf) if theta is None else np.asarray(theta, dtype=np.float64)
+    return Problem(system=sysm, columns=cols, C_row_ptr=rp, C_col=cc, C_val=cv, theta=th,
+                   dt=dt, steps=steps, m=m, method="auto", precision=precision,
+                   name=name or f"csr-{n}")
+
+
+# --------------------------------------------------------------------------
+# timed harmonic oscillator (Sec. 2.2)
+# --------------------------------------------------------------------------
+def oscillator(theta: float = 4.0) -> Problem:
+    """x' = y, y' = -x, t' = 1 as x' = A x + b with b = (0, 0, 1).
+    Initial set x0 = -5, y0 in [0, 1], t0 = 0: the fixed column (-5, 0, 0)
+    carries the constant variable, the generator (0, 1, 0) has z in [0, 1].
+    Output x, unsafe x >= theta, step pi/4, horizon pi (4 steps)."""
+    A_rp = np.array([0, 1, 2, 2], dtype=np.int64)
+    A_col = np.array([1, 0], dtype=np.int32)
+    A_val = np.array([1.0, -1.0])
+    sysm = CsrSystem(n=3, row_ptr=A_rp, col=A_col, val=A_val, b=np.array([0.0, 0.0, 1.0]),
+                     symmetric=False)
+    cols = [Column(kind="dense", zlo=0.0, zhi=1.0, dense=np.array([0.0, 1.0, 0.0])),
+            Column(kind="dense", zlo=1.0, zhi=1.0, is_fixed=True, dense=np.array([-5.0, 0.0, 0.0]))]
+    rp, cc, cv = _c_rows([([0], [1.0])])
+    return Problem(system=sysm, columns=cols, C_row_ptr=rp, C_col=cc, C_val=cv,
+                   theta=np.array([theta]), dt=math.pi / 4, steps=4, m=4, method="arnoldi",
+                   name="oscillator")
+
+
+# --------------------------------------------------------------------------
+# small random cases
+# --------------------------------------------------------------------------
+def random_symmetric_csr(n: int, nnz_per_row: int = 4, seed: int = 0) -> CsrSystem:
+    """Symmetric negative-definite sparse A = -(B + B^T)/2 - shift*I style:
+    random symmetric off-diagonal pattern, diagonal -(row abs-sum + 0.5)."""
+    rng = np.random.default_rng(seed)
+    pairs = set()
+    for r in range(n):
+        for c in rng.choice(n, size=min(nnz_per_row, n - 1), replace=False):
+            if c != r:
+                pairs.add((min(r, int(c)), max(r, int(c))))
+    dense = np.zeros((n, n))
+    for (r, c) in pairs:
+        v = rng.standard_normal() / math.sqrt(nnz_per_row)
+        dense[r, c] = v
+        dense[c, r] = v
+    dense[np.diag_indices(n)] = -(np.abs(dense).sum(axis=1) + 0.5)
+    return dense_to_csr(dense, symmetric=True)
+
+
+def dense_to_csr(dense: np.ndarray, b: Optional[np.ndarray] = None, symmetric: bool = False) -> CsrSystem:
+    n = dense.shape[0]
+    rp = [0]
+    cols: List[int] = []
+    vals: List[float] = []
+    for r in range(n):
+        nz = np.nonzero(dense[r])[0]
+        cols.extend(int(c) for c in nz)
+        vals.extend(float(dense[r, c]) for c in nz)
+        rp.append(len(cols))
+    return CsrSystem(n=n, row_ptr=np.asarray(rp, dtype=np.int64), col=np.asarray(cols, dtype=np.int32),
+                     val=np.asarray(vals, dtype=np.float64), b=b, symmetric=symmetric)
+
+
+def random_problem(sysm, *, seed: int, n_cols: int = 2, o: int = 2, dt: float = 0.05,
+                   steps: int = 40, m: int = 10, theta=None, fixed_last: bool = False,
+                   method: str = "auto", precision: str = "fp64") -> Problem:
+    """Random dense columns and dense random output rows for small systems."""
+    rng = np.random.default_rng(seed)
+    n = sysm.n
+    cols = []
+    for j in range(n_cols):
+        fixed = fixed_last and j == n_cols - 1
+        lo, hi = (1.0, 1.0) if fixed else (float(-rng.uniform(0, 1)), float(rng.uniform(0, 1)))
+        cols.append(Column(kind="dense", zlo=lo, zhi=hi, is_fixed=fixed, dense=rng.standard_normal(n)))
+    rows = [(np.arange(n), rng.standard_normal(n)) for _ in range(o)]
+    rp, cc, cv = _c_rows(rows)
+    th = np.full(o, math.inf) if theta is None else np.asarray(theta, dtype=np.float64)
+    return Problem(system=sysm, columns=cols, C_row_ptr=rp, C_col=cc, C_val=cv, theta=th,
+                   dt=dt, steps=steps, m=m, method=method, precision=precision,
+                   name=f"random-{n}-{seed}")
+
+
+def column_dense(col: Column, n: int, dims: Optional[Sequence[int]] = None) -> np.ndarray:
+    """Materialise one column as a dense vector (input handling only)."""
+    v = np.zeros(n)
+    if col.kind == "dense":
+        v[:] = col.dense
+    elif col.kind == "sparse":
+        v[np.asarray(col.idx, dtype=np.int64)] = col.val
+    elif col.kind == "box":
+        assert dims is not None
+        sl = tuple(slice(lo, hi) for lo, hi in zip(reversed(col.box_lo), reversed(col.box_hi)))
+        v.reshape(tuple(reversed(dims)))[sl] = col.value
+    else:
+        raise ValueError(col.kind)
+    return v
