@@ -1,0 +1,221 @@
+/*
+ * kv.h -- C ABI of libkv, a GB300 (sm_103a) library for the projected Krylov
+ * safety check of affine systems x' = A x + b from "Numerical Verification of
+ * Affine Systems with up to a Billion Dimensions" (Bak, Tran, Johnson).
+ *
+ * What one problem computes (all on the GPU):
+ *   1. b is folded into the dynamics by a constant-1 variable: A' = [[A, b],
+ *      [0, 0]] (Sec. 2.1).  Columns that carry the constant (is_fixed) run on
+ *      A'; the others run on A.
+ *   2. For every column E_j of the initial-space matrix (Sec. 3.2, x0 = E z):
+ *      a Krylov simulation from v = E_j / ||E_j|| -- Lanczos for symmetric A
+ *      (Alg. 3), Arnoldi otherwise (Alg. 1) -- with the output projection
+ *      P = C V taken inside the loop so the basis is never stored for Lanczos
+ *      (Alg. 4, Sec. 4.3).
+ *   3. The basis matrix C e^{A t_k} E_j ~ ||E_j|| P e^{H t_k} e_1 for every
+ *      step t_k = k dt, k = 0..steps (Eq. approx-formula, Sec. 4.2), with a
+ *      batched FP64 Pade-13 scaling-and-squaring exponential of H.
+ *   4. Per step and output row r, the interval [lo, hi] of y_r = C_r x over
+ *      the box z_j in [zlo_j, zhi_j], the first step whose upper bound reaches
+ *      the unsafe half-space y_r >= theta_r, and the maximising box vertex as
+ *      counter-example (the per-step LP of Sec. 2.1, solved in closed form for
+ *      a box and one half-space per row).
+ *
+ * Conventions for every entry point:
+ *   - Return value: KV_OK (0) or a KV_E* code; no exception crosses the ABI.
+ *     kv_last_error() returns a message for the calling thread's last error.
+ *   - Host pointers are read during the call only (copied to the device);
+ *     the caller keeps ownership.  Pointers documented as device pointers are
+ *     borrowed for the duration of the call.
+ *   - Objects (kv_ctx, kv_sys, kv_prob) are owned by the caller and freed
+ *     with the matching *_destroy.  A system must outlive its problems; a
+ *     context must outlive everything created from it.
+ *   - A kv_ctx is not thread-safe: use one per host thread.
+ *   - Device memory comes from the context's pool (an arena over one device
+ *     buffer); an allocation beyond it fails with KV_ENOMEM, never by trying
+ *     the device allocator until it fails.
+ *   - Index layout of grid systems: x fastest, idx = (z*ny + y)*nx + x.
+ */
+#ifndef KV_H
+#define KV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define KV_OK 0
+#define KV_EINVAL 1     /* bad argument (sizes, indices, flags, malformed CSR) */
+#define KV_ENOMEM 2     /* the context's device pool cannot hold the request */
+#define KV_ECUDA 3      /* a CUDA runtime call failed */
+#define KV_ETIMEOUT 4   /* a device-side wait gave up (status word set by the kernel) */
+#define KV_EBUSY 5      /* no free serving slot */
+#define KV_ENOTREADY 6  /* a submitted problem has not finished */
+
+/* storage precision of A's values and the Krylov vectors */
+#define KV_FP64 0       /* IEEE double storage and arithmetic */
+#define KV_FP32 1       /* float storage and stencil/SpMV arithmetic; every dot
+                           product and norm is accumulated error-free in float
+                           pairs and summed in double; H, the exponential and
+                           the bounds are double */
+
+/* Krylov method */
+#define KV_AUTO 0       /* Lanczos when the system is symmetric and the column
+                           does not carry the constant variable, else Arnoldi */
+#define KV_LANCZOS 1
+#define KV_ARNOLDI 2
+
+/* initial-space column kinds */
+#define KV_COL_BOX 0    /* value on the grid box box_lo <= idx < box_hi */
+#define KV_COL_SPARSE 1 /* (idx[e], val[e]) host arrays of nnz entries */
+#define KV_COL_DENSE 2  /* host array of n entries */
+
+/* how e^{H t_k} e_1 is formed for k = 0..steps */
+#define KV_EXPM_PER_STEP 0   /* one Pade-13 scaling-and-squaring exponential per step */
+#define KV_EXPM_PROPAGATE 1  /* M = e^{H dt} once, then u_k = M u_{k-1} */
+
+typedef struct kv_ctx kv_ctx;
+typedef struct kv_sys kv_sys;
+typedef struct kv_prob kv_prob;
+
+/* One column E_j of the initial-space matrix, with its box z_j in [zlo, zhi]
+ * (Sec. 3.2).  is_fixed: z_j = 1 (zlo = zhi = 1 required) and the column
+ * carries the constant-1 variable that folds b into the dynamics (Sec. 2.1,
+ * "fixed" initial values, Fig. 2(c)). */
+typedef struct {
+    int32_t kind;           /* KV_COL_* */
+    int32_t is_fixed;       /* 0 or 1 */
+    double zlo, zhi;        /* zlo <= zhi */
+    int64_t box_lo[3];      /* BOX: inclusive lower corner (x, y, z) */
+    int64_t box_hi[3];      /* BOX: exclusive upper corner */
+    double value;           /* BOX: value of E_j on the box */
+    int64_t nnz;            /* SPARSE: entries */
+    const int64_t *idx;     /* SPARSE: host, distinct, in [0, n) */
+    const double *val;      /* SPARSE: host */
+    const double *dense;    /* DENSE: host, n entries */
+} kv_column;
+
+/* A verification problem over one system (Sec. 2): initial set E z with a
+ * box on z, outputs y = C x with C in CSR form over the n state variables
+ * (Sec. 3.1), unsafe set y_r >= theta_r (theta_r = +inf: row not checked),
+ * step dt and steps + 1 check points t_k = k dt (k = 0 included), Krylov
+ * dimension krylov_m (the paper's k, 1 <= krylov_m <= KV_MAX_M). */
+typedef struct {
+    int32_t i;                  /* number of columns, >= 1 */
+    const kv_column *cols;      /* host, i entries */
+    int32_t o;                  /* number of output rows, >= 1 */
+    const int64_t *c_row_ptr;   /* host, o+1 */
+    const int64_t *c_col;       /* host, c_row_ptr[o] entries in [0, n) */
+    const double *c_val;        /* host */
+    const double *theta;        /* host, o */
+    double dt;                  /* > 0 */
+    int32_t steps;              /* >= 0 */
+    int32_t krylov_m;
+    int32_t method;             /* KV_AUTO | KV_LANCZOS | KV_ARNOLDI */
+    int32_t expm_mode;          /* KV_EXPM_PER_STEP | KV_EXPM_PROPAGATE */
+    int32_t batched;            /* CSR: 1 = all Arnoldi columns share one SpMM */
+} kv_problem_desc;
+
+#define KV_MAX_M 64
+
+/* Results copied to the host.  lo and hi are required; every other array is
+ * optional (NULL = not copied).  Layouts are row-major:
+ *   lo, hi   o x (steps+1)                 [r][k]
+ *   basis    i x o x (steps+1)             [j][r][k]: C e^{A t_k} E_j
+ *   H        i x (krylov_m+1) x krylov_m   [j][row][col], Hessenberg /
+ *                                          tridiagonal, the extra row kept
+ *   P        i x o x krylov_m              [j][r][l] = C v_l
+ *   beta0    i                             ||E_j|| (with the constant entry)
+ *   m_used   i                             valid columns of H and P
+ *   z_star   i                             counter-example z (unsafe only) */
+typedef struct {
+    double *lo;
+    double *hi;
+    double *basis;
+    double *H;
+    double *P;
+    double *beta0;
+    int32_t *m_used;
+    double *z_star;
+    int32_t first_violation_step;   /* -1: safe */
+    int32_t violation_row;          /* -1: safe */
+    double y_star;                  /* hi_r(k) at the violation */
+} kv_result;
+
+/* Library version string (static storage). */
+const char *kv_version(void);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *kv_last_error(void);
+
+/* Create a context on CUDA device `device`.  pool: a device buffer of
+ * pool_bytes the context sub-allocates from (borrowed until kv_destroy; must
+ * be 256-byte aligned), or NULL to let the context allocate pool_bytes itself
+ * once.  stream: a cudaStream_t to launch on, or NULL for a stream the
+ * context creates.  Errors: KV_EINVAL, KV_ENOMEM, KV_ECUDA. */
+int kv_create(kv_ctx **ctx, int device, void *pool, size_t pool_bytes, void *stream);
+int kv_destroy(kv_ctx *ctx);
+
+/* Bytes of the pool in use and in total. */
+int kv_pool_stats(const kv_ctx *ctx, size_t *in_use, size_t *total);
+
+/* Matrix-free grid system: A = coef * discrete Laplacian with spacing h[a]
+ * per axis and a Dirichlet-0 boundary (semi-finite-difference heat model,
+ * Sec. 6.3).  ndim = 2 or 3; dims[ndim..2] are ignored; b: host, n entries,
+ * or NULL.  The Laplacian is symmetric, so KV_AUTO picks Lanczos for columns
+ * without the constant variable. */
+int kv_system_stencil(kv_ctx *ctx, kv_sys **out, int ndim, const int64_t dims[3], double coef,
+                      const double h[3], const double *b);
+
+/* Sparse system in CSR form (row_ptr n+1 int64 starting at 0 and
+ * non-decreasing, col int32 in [0, n), sorted within a row, val).  When
+ * on_device is 0 the three arrays are host memory and are copied; when 1 they
+ * are device pointers copied device-to-device.  value_precision (KV_FP64 or
+ * KV_FP32) is the storage of the values and must match the precision of the
+ * problems run on the system.  symmetric: the caller's promise that A is
+ * symmetric (enables Lanczos).  b: host, n entries, or NULL. */
+int kv_system_csr(kv_ctx *ctx, kv_sys **out, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                  const double *val, const double *b, int symmetric, int value_precision,
+                  int on_device);
+int kv_sys_destroy(kv_sys *sys);
+
+/* Create a problem on a system: validates the description, reserves its
+ * device memory from the pool (KV_ENOMEM if it does not fit) and uploads the
+ * initial-space columns and C.  precision: KV_FP64 or KV_FP32 storage of
+ * the Krylov vectors. */
+int kv_problem(kv_ctx *ctx, kv_prob **out, const kv_sys *sys, const kv_problem_desc *desc,
+               int precision);
+int kv_prob_destroy(kv_prob *prob);
+
+/* Device bytes kv_problem would reserve (the memory model of Sec. 5 for this
+ * implementation: two n-vectors for Lanczos, m+1 for Arnoldi, plus the
+ * o x i x (steps+1) basis of Eq. memory_basis and small state). */
+int kv_problem_bytes(const kv_sys *sys, const kv_problem_desc *desc, int precision, size_t *bytes);
+
+/* Enqueue the whole path on the context stream and return; results stay on
+ * the device until kv_fetch. */
+int kv_enqueue(kv_prob *prob);
+
+/* Wait for the problem's work and copy its results to the host. */
+int kv_fetch(kv_prob *prob, kv_result *res);
+
+/* kv_enqueue + kv_fetch. */
+int kv_run(kv_prob *prob, kv_result *res);
+
+/* Per-kernel timing with CUDA events on the context stream.  enable != 0
+ * starts recording every launch (clearing earlier records); kv_profile_read
+ * synchronises and reports, for the kernel family `name`, the number of
+ * launches and their summed duration in milliseconds. */
+int kv_profile_enable(kv_ctx *ctx, int enable);
+int kv_profile_read(kv_ctx *ctx, const char *name, int64_t *launches, double *total_ms);
+
+/* Number of kernel launches the context has issued since creation. */
+int kv_launch_count(const kv_ctx *ctx, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KV_H */

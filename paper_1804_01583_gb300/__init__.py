@@ -1,0 +1,329 @@
+"""Python binding of libkv (include/kv.h): argument marshalling only.
+
+Every step of the verification path runs in the CUDA library; this module
+packs Python/numpy arguments into the C structures, calls the entry point of
+the same name and unpacks the results.  PyTorch, when used, only provides the
+device pool and the stream.  There is no fallback: if libkv.so is missing the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkv.so")
+
+KV_OK, KV_EINVAL, KV_ENOMEM, KV_ECUDA, KV_ETIMEOUT, KV_EBUSY, KV_ENOTREADY = range(7)
+KV_FP64, KV_FP32 = 0, 1
+KV_AUTO, KV_LANCZOS, KV_ARNOLDI = 0, 1, 2
+KV_COL_BOX, KV_COL_SPARSE, KV_COL_DENSE = 0, 1, 2
+KV_EXPM_PER_STEP, KV_EXPM_PROPAGATE = 0, 1
+KV_MAX_M = 64
+
+_PREC = {"fp64": KV_FP64, "fp32": KV_FP32}
+_METH = {"auto": KV_AUTO, "lanczos": KV_LANCZOS, "arnoldi": KV_ARNOLDI}
+_EXPM = {"per_step": KV_EXPM_PER_STEP, "propagate": KV_EXPM_PROPAGATE}
+
+
+class KvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"kv error {code}: {msg}")
+        self.code = code
+
+
+class kv_column(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("is_fixed", C.c_int32), ("zlo", C.c_double), ("zhi", C.c_double),
+                ("box_lo", C.c_int64 * 3), ("box_hi", C.c_int64 * 3), ("value", C.c_double),
+                ("nnz", C.c_int64), ("idx", C.c_void_p), ("val", C.c_void_p), ("dense", C.c_void_p)]
+
+
+class kv_problem_desc(C.Structure):
+    _fields_ = [("i", C.c_int32), ("cols", C.POINTER(kv_column)), ("o", C.c_int32),
+                ("c_row_ptr", C.c_void_p), ("c_col", C.c_void_p), ("c_val", C.c_void_p),
+                ("theta", C.c_void_p), ("dt", C.c_double), ("steps", C.c_int32),
+                ("krylov_m", C.c_int32), ("method", C.c_int32), ("expm_mode", C.c_int32),
+                ("batched", C.c_int32)]
+
+
+class kv_result(C.Structure):
+    _fields_ = [("lo", C.c_void_p), ("hi", C.c_void_p), ("basis", C.c_void_p), ("H", C.c_void_p),
+                ("P", C.c_void_p), ("beta0", C.c_void_p), ("m_used", C.c_void_p), ("z_star", C.c_void_p),
+                ("first_violation_step", C.c_int32), ("violation_row", C.c_int32), ("y_star", C.c_double)]
+
+
+EXPORTED = ["kv_version", "kv_last_error", "kv_create", "kv_destroy", "kv_pool_stats", "kv_system_stencil",
+            "kv_system_csr", "kv_sys_destroy", "kv_problem", "kv_prob_destroy", "kv_problem_bytes",
+            "kv_enqueue", "kv_fetch", "kv_run", "kv_profile_enable", "kv_profile_read", "kv_launch_count"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: Optional[str] = None):
+    """Load libkv.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libkv.so not found at {p}: run __graft_entry__.build() first "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        lib = C.CDLL(p)
+        V = C.c_void_p
+        I = C.c_int
+        lib.kv_version.restype = C.c_char_p
+        lib.kv_last_error.restype = C.c_char_p
+        lib.kv_create.argtypes = [C.POINTER(V), I, V, C.c_size_t, V]
+        lib.kv_destroy.argtypes = [V]
+        lib.kv_pool_stats.argtypes = [V, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        lib.kv_system_stencil.argtypes = [V, C.POINTER(V), I, C.POINTER(C.c_int64), C.c_double,
+                                          C.POINTER(C.c_double), V]
+        lib.kv_system_csr.argtypes = [V, C.POINTER(V), C.c_int64, V, V, V, V, I, I, I]
+        lib.kv_sys_destroy.argtypes = [V]
+        lib.kv_problem.argtypes = [V, C.POINTER(V), V, C.POINTER(kv_problem_desc), I]
+        lib.kv_prob_destroy.argtypes = [V]
+        lib.kv_problem_bytes.argtypes = [V, C.POINTER(kv_problem_desc), I, C.POINTER(C.c_size_t)]
+        lib.kv_enqueue.argtypes = [V]
+        lib.kv_fetch.argtypes = [V, C.POINTER(kv_result)]
+        lib.kv_run.argtypes = [V, C.POINTER(kv_result)]
+        lib.kv_profile_enable.argtypes = [V, I]
+        lib.kv_profile_read.argtypes = [V, C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+        lib.kv_launch_count.argtypes = [V, C.POINTER(C.c_int64)]
+        for name in EXPORTED:
+            f = getattr(lib, name)
+            if f.restype is None and name not in ("kv_version", "kv_last_error"):
+                f.restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != KV_OK:
+        raise KvError(rc, last_error())
+
+
+def version() -> str:
+    return load().kv_version().decode()
+
+
+def last_error() -> str:
+    return load().kv_last_error().decode()
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# --------------------------------------------------------------------------
+class Context:
+    """kv_create / kv_destroy.  pool: None (library allocates pool_bytes once)
+    or a torch CUDA tensor used as the pool; stream: None or a torch stream."""
+
+    def __init__(self, pool_bytes: int, device: int = 0, pool=None, stream=None):
+        self._lib = load()
+        self._pool = pool
+        h = C.c_void_p()
+        pool_ptr = None if pool is None else C.c_void_p(pool.data_ptr())
+        if pool is not None:
+            pool_bytes = pool.numel() * pool.element_size()
+        stream_ptr = None if stream is None else C.c_void_p(stream.cuda_stream)
+        _check(self._lib.kv_create(C.byref(h), device, pool_ptr, pool_bytes, stream_ptr))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._lib.kv_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pool_stats(self):
+        a, b = C.c_size_t(), C.c_size_t()
+        _check(self._lib.kv_pool_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        _check(self._lib.kv_launch_count(self.h, C.byref(n)))
+        return n.value
+
+    def profile_enable(self, on: bool = True):
+        _check(self._lib.kv_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, name: str):
+        n, t = C.c_int64(), C.c_double()
+        _check(self._lib.kv_profile_read(self.h, name.encode(), C.byref(n), C.byref(t)))
+        return n.value, t.value
+
+
+class System:
+    """kv_system_stencil / kv_system_csr / kv_sys_destroy for a workloads system."""
+
+    def __init__(self, ctx: Context, system, precision: str = "fp64"):
+        self.ctx = ctx
+        lib = ctx._lib
+        h = C.c_void_p()
+        b = getattr(system, "b", None)
+        bb = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+        if hasattr(system, "dims"):
+            nd = len(system.dims)
+            dims = (C.c_int64 * 3)(*[int(system.dims[a]) if a < nd else 1 for a in range(3)])
+            hh = (C.c_double * 3)(*[float(system.h[a]) if a < nd else 1.0 for a in range(3)])
+            _check(lib.kv_system_stencil(ctx.h, C.byref(h), nd, dims, float(system.coef), hh, _ptr(bb)))
+        else:
+            rp = np.ascontiguousarray(system.row_ptr, dtype=np.int64)
+            col = np.ascontiguousarray(system.col, dtype=np.int32)
+            val = np.ascontiguousarray(system.val, dtype=np.float64)
+            _check(lib.kv_system_csr(ctx.h, C.byref(h), int(system.n), _ptr(rp), _ptr(col), _ptr(val), _ptr(bb),
+                                     1 if system.symmetric else 0, _PREC[precision], 0))
+        self.h = h
+        self.n = int(system.n)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.ctx._lib.kv_sys_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _desc(problem, expm_mode: str, batched: bool, keep: list) -> kv_problem_desc:
+    cols = (kv_column * problem.i)()
+    for j, c in enumerate(problem.columns):
+        cc = cols[j]
+        cc.is_fixed = 1 if c.is_fixed else 0
+        cc.zlo, cc.zhi = float(c.zlo), float(c.zhi)
+        if c.kind == "box":
+            cc.kind = KV_COL_BOX
+            for a in range(3):
+                cc.box_lo[a] = int(c.box_lo[a]) if a < len(c.box_lo) else 0
+                cc.box_hi[a] = int(c.box_hi[a]) if a < len(c.box_hi) else 1
+            cc.value = float(c.value)
+        elif c.kind == "sparse":
+            cc.kind = KV_COL_SPARSE
+            ix = np.ascontiguousarray(c.idx, dtype=np.int64)
+            vv = np.ascontiguousarray(c.val, dtype=np.float64)
+            keep += [ix, vv]
+            cc.nnz = len(ix)
+            cc.idx, cc.val = _ptr(ix), _ptr(vv)
+        elif c.kind == "dense":
+            cc.kind = KV_COL_DENSE
+            dd = np.ascontiguousarray(c.dense, dtype=np.float64)
+            keep.append(dd)
+            cc.dense = _ptr(dd)
+        else:
+            raise ValueError(c.kind)
+    rp = np.ascontiguousarray(problem.C_row_ptr, dtype=np.int64)
+    cc_ = np.ascontiguousarray(problem.C_col, dtype=np.int64)
+    cv = np.ascontiguousarray(problem.C_val, dtype=np.float64)
+    th = np.ascontiguousarray(problem.theta, dtype=np.float64)
+    keep += [cols, rp, cc_, cv, th]
+    d = kv_problem_desc()
+    d.i = problem.i
+    d.cols = C.cast(cols, C.POINTER(kv_column))
+    d.o = problem.o
+    d.c_row_ptr, d.c_col, d.c_val, d.theta = _ptr(rp), _ptr(cc_), _ptr(cv), _ptr(th)
+    d.dt = float(problem.dt)
+    d.steps = int(problem.steps)
+    d.krylov_m = int(problem.m)
+    d.method = _METH[problem.method]
+    d.expm_mode = _EXPM[expm_mode]
+    d.batched = 1 if batched else 0
+    return d
+
+
+class ProblemHandle:
+    """kv_problem / kv_enqueue / kv_fetch / kv_run / kv_prob_destroy."""
+
+    def __init__(self, ctx: Context, sysh: System, problem, *, expm_mode: str = "per_step",
+                 batched: bool = False):
+        self.ctx = ctx
+        self.sysh = sysh
+        self.problem = problem
+        self._keep: list = []
+        self.desc = _desc(problem, expm_mode, batched, self._keep)
+        h = C.c_void_p()
+        _check(ctx._lib.kv_problem(ctx.h, C.byref(h), sysh.h, C.byref(self.desc), _PREC[problem.precision]))
+        self.h = h
+
+    def enqueue(self):
+        _check(self.ctx._lib.kv_enqueue(self.h))
+
+    def fetch(self, full: bool = True) -> Dict:
+        p = self.problem
+        S = p.steps + 1
+        out = dict(lo=np.zeros((p.o, S)), hi=np.zeros((p.o, S)))
+        if full:
+            out.update(basis=np.zeros((p.i, p.o, S)), H=np.zeros((p.i, p.m + 1, p.m)),
+                       P=np.zeros((p.i, p.o, p.m)), beta0=np.zeros(p.i), m_used=np.zeros(p.i, dtype=np.int32))
+        out["zstar"] = np.zeros(p.i)
+        r = kv_result()
+        r.lo, r.hi = _ptr(out["lo"]), _ptr(out["hi"])
+        if full:
+            r.basis, r.H, r.P = _ptr(out["basis"]), _ptr(out["H"]), _ptr(out["P"])
+            r.beta0, r.m_used = _ptr(out["beta0"]), _ptr(out["m_used"])
+        r.z_star = _ptr(out["zstar"])
+        _check(self.ctx._lib.kv_fetch(self.h, C.byref(r)))
+        out["viol_step"] = int(r.first_violation_step)
+        out["viol_row"] = int(r.violation_row)
+        if out["viol_step"] < 0:
+            out["zstar"] = None
+            out["ystar"] = None
+        else:
+            out["ystar"] = float(r.y_star)
+        return out
+
+    def run(self, full: bool = True) -> Dict:
+        self.enqueue()
+        return self.fetch(full)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.ctx._lib.kv_prob_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def problem_bytes(sysh: System, problem, *, expm_mode: str = "per_step", batched: bool = False) -> int:
+    keep: list = []
+    d = _desc(problem, expm_mode, batched, keep)
+    n = C.c_size_t()
+    _check(sysh.ctx._lib.kv_problem_bytes(sysh.h, C.byref(d), _PREC[problem.precision], C.byref(n)))
+    return n.value
+
+
+def solve(problem, ctx: Optional[Context] = None, *, pool_bytes: int = 1 << 30, expm_mode: str = "per_step",
+          batched: bool = False) -> Dict:
+    """Convenience: system + problem + run on a (new) context."""
+    own = ctx is None
+    if own:
+        ctx = Context(pool_bytes)
+    sysh = System(ctx, problem.system, problem.precision)
+    ph = ProblemHandle(ctx, sysh, problem, expm_mode=expm_mode, batched=batched)
+    try:
+        return ph.run()
+    finally:
+        ph.close()
+        sysh.close()
+        if own:
+            ctx.close()

@@ -1,0 +1,287 @@
+// k_expm.cu -- batched FP64 exponential of the small Krylov matrix H and the
+// basis-matrix rows C e^{A t_k} E_j ~ ||E_j|| P e^{H t_k} e_1 (Eq.
+// approx-formula, Sec. 4.2).
+//
+// The exponential is the [13/13] Pade approximant with scaling and squaring
+// (the off-the-shelf method named in Sec. 4.1; degree-13 coefficients
+// b_j = (26-j)! / (j! (13-j)!) and the threshold theta_13 = 5.371920351148152
+// from Higham, SIAM J. Matrix Anal. Appl. 26(4), 2005).  One CTA owns one
+// matrix in shared memory; all arithmetic is double.
+//
+// Two schedules (kv_problem_desc.expm_mode):
+//   PER_STEP   one CTA per (column, step): e^{H t_k} for every k.
+//   PROPAGATE  one CTA per column: M = e^{H dt}, u_0 = e_1, u_k = M u_{k-1};
+//              the same vectors in exact arithmetic, s matrix-vector products
+//              instead of s exponentials.
+#include <math.h>
+
+#include "kv_internal.h"
+
+namespace kv {
+
+constexpr int ENT = 256;
+
+__constant__ double c_pade13[14];
+
+// C = A B for n x n row-major matrices in shared memory (ld = n); C must not
+// alias A or B.  Ends with a barrier.
+__device__ void smm(int n, const double* A, const double* B, double* C) {
+    const int nn = n * n;
+    for (int e = threadIdx.x; e < nn; e += ENT) {
+        const int i = e / n, j = e - i * n;
+        double s = 0.0;
+        const double* a = A + i * n;
+        for (int k = 0; k < n; ++k) s = fma(a[k], B[k * n + j], s);
+        C[e] = s;
+    }
+    __syncthreads();
+}
+
+// Solve Q X = R in place (X left in R), Gaussian elimination with partial
+// pivoting.  piv / fac are shared scratch of n entries.  Ends with a barrier.
+__device__ void ssolve(int n, double* Q, double* R, double* fac, int* piv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < n; ++k) {
+        if (warp == 0) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + lane; i < n; i += 32) {
+                const double a = fabs(Q[i * n + k]);
+                if (a > best) { best = a; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) *piv = bi;
+        }
+        __syncthreads();
+        const int p = *piv;
+        if (p != k) {
+            for (int c = threadIdx.x; c < 2 * n; c += ENT) {
+                double* M = c < n ? Q : R;
+                const int cc = c < n ? c : c - n;
+                const double t = M[k * n + cc];
+                M[k * n + cc] = M[p * n + cc];
+                M[p * n + cc] = t;
+            }
+            __syncthreads();
+        }
+        const double dk = Q[k * n + k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += ENT) fac[i] = Q[i * n + k] / dk;
+        __syncthreads();
+        const int rows = n - k - 1;
+        const int cols = 2 * n;  // Q columns k+1..n-1 and all of R (waste on Q's left part is skipped)
+        for (int e = threadIdx.x; e < rows * cols; e += ENT) {
+            const int i = k + 1 + e / cols, c = e % cols;
+            const double f = fac[i];
+            if (c < n) {
+                if (c > k) Q[i * n + c] = fma(-f, Q[k * n + c], Q[i * n + c]);
+            } else {
+                const int cc = c - n;
+                R[i * n + cc] = fma(-f, R[k * n + cc], R[i * n + cc]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        for (int c = threadIdx.x; c < n; c += ENT) {
+            double s = R[k * n + c];
+            for (int i = k + 1; i < n; ++i) s = fma(-Q[k * n + i], R[i * n + c], s);
+            R[k * n + c] = s / Q[k * n + k];
+        }
+        __syncthreads();
+    }
+}
+
+// exp(X) for the n x n matrix in buf[0]; six n x n buffers buf[0..5].
+// Returns the index of the buffer holding the result.
+__device__ int sexpm(int n, double* buf[6], double* fac, int* piv, double* red) {
+    double *X = buf[0], *X2 = buf[1], *X4 = buf[2], *X6 = buf[3], *T = buf[4], *U = buf[5];
+    const double* b = c_pade13;
+    // 1-norm (max column abs sum)
+    double cmax = 0.0;
+    for (int j = threadIdx.x; j < n; j += ENT) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += fabs(X[i * n + j]);
+        cmax = fmax(cmax, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cmax;
+    __syncthreads();
+    double norm1 = 0.0;
+    for (int w = 0; w < ENT / 32; ++w) norm1 = fmax(norm1, red[w]);
+    const double theta13 = 5.371920351148152;
+    // squarings; a non-finite or absurd norm (> theta13 * 2^200) gets no
+    // scaling so the result is NaN/inf instead of an unbounded loop
+    int s = 0;
+    if (norm1 > theta13 && norm1 < theta13 * 1.6e60) s = (int)ceil(log2(norm1 / theta13));
+    if (s > 0) {
+        const double sc = ldexp(1.0, -s);
+        for (int e = threadIdx.x; e < n * n; e += ENT) X[e] *= sc;
+    }
+    __syncthreads();
+    smm(n, X, X, X2);
+    smm(n, X2, X2, X4);
+    smm(n, X4, X2, X6);
+    for (int e = threadIdx.x; e < n * n; e += ENT) T[e] = b[13] * X6[e] + b[11] * X4[e] + b[9] * X2[e];
+    __syncthreads();
+    smm(n, X6, T, U);
+    for (int e = threadIdx.x; e < n * n; e += ENT) {
+        U[e] += b[7] * X6[e] + b[5] * X4[e] + b[3] * X2[e];
+        if (e / n == e % n) U[e] += b[1];
+    }
+    __syncthreads();
+    smm(n, X, U, T);  // T = odd part
+    for (int e = threadIdx.x; e < n * n; e += ENT) U[e] = b[12] * X6[e] + b[10] * X4[e] + b[8] * X2[e];
+    __syncthreads();
+    smm(n, X6, U, X);  // X = X6 (...)
+    for (int e = threadIdx.x; e < n * n; e += ENT) {
+        X[e] += b[6] * X6[e] + b[4] * X4[e] + b[2] * X2[e];
+        if (e / n == e % n) X[e] += b[0];
+    }
+    __syncthreads();
+    // Q = V - U into X2, R = V + U into X4
+    for (int e = threadIdx.x; e < n * n; e += ENT) {
+        X2[e] = X[e] - T[e];
+        X4[e] = X[e] + T[e];
+    }
+    __syncthreads();
+    ssolve(n, X2, X4, fac, piv);
+    int cur = 2, spare = 3;
+    for (int q = 0; q < s; ++q) {
+        smm(n, buf[cur], buf[cur], buf[spare]);
+        const int t = cur;
+        cur = spare;
+        spare = t;
+    }
+    return cur;
+}
+
+struct ExpmArgs {
+    const double* H;       // i x (m+1) x m
+    const double* P;       // i x o x m
+    const ColState* st;    // i
+    double* basis;         // i x o x (steps+1)
+    int m, o, steps;
+    double dt;
+};
+
+__device__ void load_scaled_H(const ExpmArgs& a, int j, int mu, double t, double* X) {
+    const double* H = a.H + (int64_t)j * (a.m + 1) * a.m;
+    for (int e = threadIdx.x; e < mu * mu; e += ENT) {
+        const int r = e / mu, c = e - r * mu;
+        X[e] = H[(int64_t)r * a.m + c] * t;
+    }
+    __syncthreads();
+}
+
+// out[r] = beta0 * P[r, 0:mu] . u  (u has stride `stride`), one warp per row
+__device__ void project_rows(const ExpmArgs& a, int j, int mu, const double* u, int stride, int k) {
+    const double* P = a.P + (int64_t)j * a.o * a.m;
+    const double b0 = a.st[j].beta0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < a.o; r += ENT / 32) {
+        double s = 0.0;
+        for (int l = lane; l < mu; l += 32) s = fma(P[(int64_t)r * a.m + l], u[l * stride], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) a.basis[((int64_t)j * a.o + r) * (a.steps + 1) + k] = b0 * s;
+    }
+}
+
+__global__ void __launch_bounds__(ENT) k_expm_per_step(ExpmArgs a) {
+    extern __shared__ double smem[];
+    __shared__ double fac[KV_MAX_M];
+    __shared__ int piv;
+    __shared__ double red[ENT / 32];
+    const int j = blockIdx.y;
+    const int mu = a.st[j].m_used;
+    for (int k = blockIdx.x; k <= a.steps; k += gridDim.x) {
+        if (mu <= 0) {
+            for (int r = threadIdx.x; r < a.o; r += ENT) a.basis[((int64_t)j * a.o + r) * (a.steps + 1) + k] = 0.0;
+            continue;
+        }
+        double* buf[6];
+        for (int q = 0; q < 6; ++q) buf[q] = smem + q * mu * mu;
+        load_scaled_H(a, j, mu, (double)k * a.dt, buf[0]);
+        const int res = sexpm(mu, buf, fac, &piv, red);
+        project_rows(a, j, mu, buf[res], mu, k);  // first column: stride mu
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(ENT) k_expm_propagate(ExpmArgs a) {
+    extern __shared__ double smem[];
+    __shared__ double fac[KV_MAX_M];
+    __shared__ int piv;
+    __shared__ double red[ENT / 32];
+    const int j = blockIdx.x;
+    const int mu = a.st[j].m_used;
+    if (mu <= 0) {
+        for (int e = threadIdx.x; e < a.o * (a.steps + 1); e += ENT) a.basis[(int64_t)j * a.o * (a.steps + 1) + e] = 0.0;
+        return;
+    }
+    double* buf[6];
+    for (int q = 0; q < 6; ++q) buf[q] = smem + q * mu * mu;
+    load_scaled_H(a, j, mu, a.dt, buf[0]);
+    const int res = sexpm(mu, buf, fac, &piv, red);
+    const double* M = buf[res];
+    double* u = buf[(res + 1) % 6];
+    double* v = buf[(res + 2) % 6];
+    for (int l = threadIdx.x; l < mu; l += ENT) u[l] = (l == 0) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k <= a.steps; ++k) {
+        project_rows(a, j, mu, u, 1, k);
+        if (k == a.steps) break;
+        for (int l = threadIdx.x; l < mu; l += ENT) {
+            double s = 0.0;
+            for (int q = 0; q < mu; ++q) s = fma(M[l * mu + q], u[q], s);
+            v[l] = s;
+        }
+        __syncthreads();
+        double* t = u;
+        u = v;
+        v = t;
+    }
+}
+
+static bool g_coeffs_ready[64] = {false};
+
+static int upload_coeffs(int device) {
+    if (device >= 0 && device < 64 && g_coeffs_ready[device]) return KV_OK;
+    double b[14];
+    for (int j = 0; j <= 13; ++j) {
+        // (26-j)!/(13-j)! = product of the 13 integers 14-j .. 26-j; divide by j!
+        unsigned long long num = 1ULL, den = 1ULL;
+        for (int k = 14 - j; k <= 26 - j; ++k) num *= (unsigned long long)k;
+        for (int k = 2; k <= j; ++k) den *= (unsigned long long)k;
+        b[j] = (double)(num / den);
+    }
+    KV_CHECK_CUDA(cudaMemcpyToSymbol(c_pade13, b, sizeof(b)));
+    if (device >= 0 && device < 64) g_coeffs_ready[device] = true;
+    return KV_OK;
+}
+
+int launch_expm_basis(Prob* p) {
+    int rc = upload_coeffs(p->ctx->device);
+    if (rc != KV_OK) return rc;
+    ExpmArgs a{p->d_H, p->d_P, p->d_state, p->d_basis, p->m, p->o, p->steps, p->dt};
+    const size_t smem = (size_t)6 * p->m * p->m * sizeof(double);
+    if (p->expm_mode == KV_EXPM_PROPAGATE) {
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LaunchScope ls(p->ctx, "expm_propagate");
+        k_expm_propagate<<<p->i, ENT, smem, p->ctx->stream>>>(a);
+    } else {
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_per_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int gx = p->steps + 1;
+        if (gx > 65535 * 16) gx = 65535 * 16;
+        dim3 grd((unsigned)gx, (unsigned)p->i);
+        LaunchScope ls(p->ctx, "expm_per_step");
+        k_expm_per_step<<<grd, ENT, smem, p->ctx->stream>>>(a);
+    }
+    KV_CHECK_CUDA(cudaGetLastError());
+    return KV_OK;
+}
+
+}  // namespace kv

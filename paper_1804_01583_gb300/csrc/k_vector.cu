@@ -1,0 +1,111 @@
+// k_vector.cu -- initial Krylov vector for sparse and dense columns.
+//
+// The column E_j (with the constant-1 entry appended when the column carries
+// the constant variable, Sec. 2.1) is written into the first Krylov buffer
+// unnormalised; k_init_norm reduces ||E_j||^2 deterministically and its last
+// block sets beta0, the read scale s[0] = 1/beta0 and P[:, 0] = C v_0.
+#include "kv_internal.h"
+#include "reduce.cuh"
+
+namespace kv {
+
+constexpr int VNT = 256;
+
+template <typename T>
+__global__ void k_scatter(T* __restrict__ B, const int64_t* __restrict__ idx, const double* __restrict__ val,
+                          int64_t nnz) {
+    for (int64_t e = (int64_t)blockIdx.x * VNT + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * VNT)
+        B[idx[e]] = (T)val[e];
+}
+
+template <typename T>
+__global__ void k_convert(T* __restrict__ B, const double* __restrict__ src, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * VNT + threadIdx.x; e < n; e += (int64_t)gridDim.x * VNT)
+        B[e] = (T)src[e];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VNT) k_init_norm(const T* __restrict__ B, int64_t N, ColState* st, double* P,
+                                                   CDesc cd, int m, Reduce red) {
+    __shared__ double sh[VNT / 32];
+    __shared__ int flag;
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * VNT + threadIdx.x; e < N; e += (int64_t)gridDim.x * VNT) {
+        const double v = (double)B[e];
+        acc = fma(v, v, acc);
+    }
+    const double part = block_sum<VNT>(acc, sh);
+    if (!grid_arrive(part, red.partials, red.counter, blockIdx.x, gridDim.x, &flag)) return;
+    const double tot = grid_finish<VNT>(red.partials, gridDim.x, red.counter, sh);
+    __shared__ double s0;
+    if (threadIdx.x == 0) {
+        const double b0 = sqrt(tot);
+        st->beta0 = b0;
+        st->m_used = m;
+        st->status = 0;
+        if (!(b0 > 0.0) || !isfinite(b0)) {
+            st->done = 1;
+            st->m_used = 0;
+            s0 = 0.0;
+        } else {
+            st->done = 0;
+            st->s[0] = 1.0 / b0;
+            s0 = 1.0 / b0;
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < cd.o; ++r) {
+        double v = 0.0;
+        for (int64_t e = cd.rp[r] + threadIdx.x; e < cd.rp[r + 1]; e += VNT)
+            v += cd.val[e] * (double)__ldcg(B + cd.col[e]);
+        v = block_sum<VNT>(v, sh);
+        if (threadIdx.x == 0) P[(int64_t)r * m] = s0 * v;
+    }
+}
+
+static int grid_for(int64_t n) {
+    int64_t b = (n + VNT - 1) / VNT;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)(b < 1 ? 1 : b);
+}
+
+int launch_scatter(Prob* p, int j, void* B) {
+    const size_t es = elem_size(p->prec);
+    KV_CHECK_CUDA(cudaMemsetAsync(B, 0, (size_t)p->N * es, p->ctx->stream));
+    const kv_column& c = p->cols[j];
+    int64_t nnz = c.nnz + (p->aug[j] ? 1 : 0);
+    if (nnz == 0) return KV_OK;
+    LaunchScope ls(p->ctx, "scatter");
+    if (p->prec == KV_FP32)
+        k_scatter<float><<<grid_for(nnz), VNT, 0, p->ctx->stream>>>((float*)B, p->d_sidx[j], p->d_sval[j], nnz);
+    else
+        k_scatter<double><<<grid_for(nnz), VNT, 0, p->ctx->stream>>>((double*)B, p->d_sidx[j], p->d_sval[j], nnz);
+    KV_CHECK_CUDA(cudaGetLastError());
+    return KV_OK;
+}
+
+int launch_dense_to(Prob* p, int j, void* B) {
+    LaunchScope ls(p->ctx, "dense_init");
+    if (p->prec == KV_FP32)
+        k_convert<float><<<grid_for(p->N), VNT, 0, p->ctx->stream>>>((float*)B, p->d_dense[j], p->N);
+    else
+        k_convert<double><<<grid_for(p->N), VNT, 0, p->ctx->stream>>>((double*)B, p->d_dense[j], p->N);
+    KV_CHECK_CUDA(cudaGetLastError());
+    return KV_OK;
+}
+
+int launch_init_norm(Prob* p, int j, void* B) {
+    LaunchScope ls(p->ctx, "init_norm");
+    const int g = grid_for(p->N);
+    CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval};
+    ColState* st = p->d_state + j;
+    double* P = p->d_P + (int64_t)j * p->o * p->m;
+    if (p->prec == KV_FP32)
+        k_init_norm<float><<<g, VNT, 0, p->ctx->stream>>>((const float*)B, p->N, st, P, cd, p->m, p->red);
+    else
+        k_init_norm<double><<<g, VNT, 0, p->ctx->stream>>>((const double*)B, p->N, st, P, cd, p->m, p->red);
+    KV_CHECK_CUDA(cudaGetLastError());
+    return KV_OK;
+}
+
+}  // namespace kv

@@ -1,0 +1,740 @@
+// kv_abi.cu -- the C ABI of include/kv.h: contexts, the device-memory arena,
+// systems, problems and the enqueue of the whole path on one stream.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kv_internal.h"
+
+namespace kv {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+// ------------------------------------------------------------------- arena
+static const size_t kAlign = 256;
+
+void Arena::init(char* base, size_t size) {
+    base_ = base;
+    size_ = size;
+    in_use_ = 0;
+    free_.clear();
+    used_.clear();
+    if (size) free_[0] = size;
+}
+
+void* Arena::alloc(size_t bytes) {
+    if (bytes == 0) bytes = 1;
+    bytes = (bytes + kAlign - 1) / kAlign * kAlign;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+        if (it->second >= bytes) {
+            const size_t off = it->first, sz = it->second;
+            free_.erase(it);
+            if (sz > bytes) free_[off + bytes] = sz - bytes;
+            used_[off] = bytes;
+            in_use_ += bytes;
+            return base_ + off;
+        }
+    }
+    return nullptr;
+}
+
+void Arena::free(void* p) {
+    if (!p) return;
+    const size_t off = (size_t)((char*)p - base_);
+    auto it = used_.find(off);
+    if (it == used_.end()) return;
+    size_t sz = it->second;
+    used_.erase(it);
+    in_use_ -= sz;
+    size_t start = off;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && nx->first == off + sz) {
+        sz += nx->second;
+        free_.erase(nx);
+    }
+    auto pv = free_.lower_bound(off);
+    if (pv != free_.begin()) {
+        --pv;
+        if (pv->first + pv->second == off) {
+            start = pv->first;
+            sz += pv->second;
+            free_.erase(pv);
+        }
+    }
+    free_[start] = sz;
+}
+
+size_t Arena::largest_free() const {
+    size_t b = 0;
+    for (auto& kv : free_) b = std::max(b, kv.second);
+    return b;
+}
+
+// ----------------------------------------------------------- launch scope
+LaunchScope::LaunchScope(Ctx* c, const char* name) : ctx(c) {
+    ctx->launches++;
+    if (!ctx->profiling) return;
+    Ctx::Rec r;
+    r.name = name;
+    for (int q = 0; q < 2; ++q) {
+        cudaEvent_t e;
+        if (!ctx->spare_events.empty()) {
+            e = ctx->spare_events.back();
+            ctx->spare_events.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            return;
+        }
+        (q == 0 ? r.a : r.b) = e;
+    }
+    cudaEventRecord(r.a, ctx->stream);
+    ctx->recs.push_back(r);
+    rec = (int)ctx->recs.size() - 1;
+}
+
+LaunchScope::~LaunchScope() {
+    if (rec >= 0) cudaEventRecord(ctx->recs[rec].b, ctx->stream);
+}
+
+static void clear_profile(Ctx* c) {
+    for (auto& r : c->recs) {
+        c->spare_events.push_back(r.a);
+        c->spare_events.push_back(r.b);
+    }
+    c->recs.clear();
+}
+
+// ------------------------------------------------------------- helpers
+template <typename T>
+static int dalloc(Prob* p, T** out, size_t count) {
+    void* q = p->ctx->arena.alloc(count * sizeof(T));
+    if (!q) {
+        return fail(KV_ENOMEM, "device pool exhausted: need %zu more bytes (largest free block %zu of %zu)",
+                    count * sizeof(T), p->ctx->arena.largest_free(), p->ctx->arena.total());
+    }
+    p->allocs.push_back(q);
+    *out = (T*)q;
+    return KV_OK;
+}
+
+static int upload(Ctx* c, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return KV_OK;
+    KV_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return KV_OK;
+}
+
+static int with_device(int device) {
+    KV_CHECK_CUDA(cudaSetDevice(device));
+    return KV_OK;
+}
+
+int64_t reduce_slots_needed(const Prob* p) {
+    int64_t nb = 152 * 8;
+    if (p->sys->kind == 0) {
+        StencilGeom g;
+        g.nx = p->sys->dims[0];
+        g.ny = p->sys->ndim >= 2 ? p->sys->dims[1] : 1;
+        g.nz = p->sys->ndim >= 3 ? p->sys->dims[2] : 1;
+        int zc;
+        nb = std::max<int64_t>(nb, stencil_blocks(g, &zc));
+    }
+    return nb * (int64_t)(p->m + 2);
+}
+
+}  // namespace kv
+
+using namespace kv;
+
+struct kv_ctx : public Ctx {};
+struct kv_sys : public Sys {};
+struct kv_prob : public Prob {};
+
+extern "C" {
+
+const char* kv_version(void) { return "kv 0.1 (sm_103a)"; }
+
+const char* kv_last_error(void) { return g_err.c_str(); }
+
+int kv_create(kv_ctx** out, int device, void* pool, size_t pool_bytes, void* stream) {
+    if (!out) return fail(KV_EINVAL, "kv_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    KV_CHECK_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(KV_EINVAL, "kv_create: device %d of %d", device, ndev);
+    if (pool && ((uintptr_t)pool % 256) != 0) return fail(KV_EINVAL, "kv_create: pool must be 256-byte aligned");
+    if (pool_bytes < 4096) return fail(KV_EINVAL, "kv_create: pool_bytes too small");
+    int rc = with_device(device);
+    if (rc) return rc;
+    kv_ctx* c = new (std::nothrow) kv_ctx();
+    if (!c) return fail(KV_ENOMEM, "kv_create: host allocation");
+    c->device = device;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(KV_ECUDA, "kv_create: cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    if (pool) {
+        c->pool = pool;
+    } else {
+        cudaError_t e = cudaMalloc(&c->pool, pool_bytes);
+        if (e != cudaSuccess) {
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            delete c;
+            return fail(KV_ENOMEM, "kv_create: cudaMalloc(%zu) failed: %s", pool_bytes, cudaGetErrorString(e));
+        }
+        c->own_pool = true;
+    }
+    c->arena.init((char*)c->pool, pool_bytes);
+    *out = c;
+    return KV_OK;
+}
+
+int kv_destroy(kv_ctx* c) {
+    if (!c) return KV_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    clear_profile(c);
+    for (auto e : c->spare_events) cudaEventDestroy(e);
+    if (c->own_pool) cudaFree(c->pool);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return KV_OK;
+}
+
+int kv_pool_stats(const kv_ctx* c, size_t* in_use, size_t* total) {
+    if (!c) return fail(KV_EINVAL, "kv_pool_stats: ctx is NULL");
+    if (in_use) *in_use = c->arena.in_use();
+    if (total) *total = c->arena.total();
+    return KV_OK;
+}
+
+int kv_launch_count(const kv_ctx* c, int64_t* launches) {
+    if (!c || !launches) return fail(KV_EINVAL, "kv_launch_count: NULL argument");
+    *launches = c->launches;
+    return KV_OK;
+}
+
+int kv_system_stencil(kv_ctx* c, kv_sys** out, int ndim, const int64_t dims[3], double coef, const double h[3],
+                      const double* b) {
+    if (!c || !out || !dims || !h) return fail(KV_EINVAL, "kv_system_stencil: NULL argument");
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return fail(KV_EINVAL, "kv_system_stencil: ndim must be 2 or 3");
+    int64_t n = 1;
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] < 1 || dims[a] > (int64_t)1 << 31) return fail(KV_EINVAL, "kv_system_stencil: dims[%d]", a);
+        if (!(h[a] > 0) || !isfinite(h[a])) return fail(KV_EINVAL, "kv_system_stencil: h[%d]", a);
+        if (n > ((int64_t)1 << 62) / dims[a]) return fail(KV_EINVAL, "kv_system_stencil: grid too large");
+        n *= dims[a];
+    }
+    if (!isfinite(coef)) return fail(KV_EINVAL, "kv_system_stencil: coef");
+    // launch-shape limits of the grid kernels: ceil(ny/8) and ceil(nz/8) blocks
+    if (dims[1] > 524280 || (ndim == 3 && dims[2] > 524280))
+        return fail(KV_EINVAL, "kv_system_stencil: ny and nz must be <= 524280");
+    int rc = with_device(c->device);
+    if (rc) return rc;
+    kv_sys* s = new (std::nothrow) kv_sys();
+    if (!s) return fail(KV_ENOMEM, "host allocation");
+    s->ctx = c;
+    s->kind = 0;
+    s->ndim = ndim;
+    for (int a = 0; a < 3; ++a) {
+        s->dims[a] = a < ndim ? dims[a] : 1;
+        s->h[a] = a < ndim ? h[a] : 1.0;
+    }
+    s->coef = coef;
+    s->n = n;
+    s->symmetric = true;
+    if (b) {
+        s->d_b = (double*)c->arena.alloc((size_t)n * sizeof(double));
+        if (!s->d_b) {
+            delete s;
+            return fail(KV_ENOMEM, "kv_system_stencil: pool cannot hold b");
+        }
+        rc = upload(c, s->d_b, b, (size_t)n * sizeof(double));
+        if (rc) {
+            c->arena.free(s->d_b);
+            delete s;
+            return rc;
+        }
+    }
+    *out = s;
+    return KV_OK;
+}
+
+int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                  const double* val, const double* b, int symmetric, int value_precision, int on_device) {
+    if (!c || !out || !row_ptr || !col || !val) return fail(KV_EINVAL, "kv_system_csr: NULL argument");
+    *out = nullptr;
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(KV_EINVAL, "kv_system_csr: n out of range");
+    if (value_precision != KV_FP64 && value_precision != KV_FP32)
+        return fail(KV_EINVAL, "kv_system_csr: value_precision");
+    int rc = with_device(c->device);
+    if (rc) return rc;
+    std::vector<int64_t> hrp;
+    const int64_t* rp = row_ptr;
+    if (on_device) {
+        hrp.resize((size_t)n + 1);
+        KV_CHECK_CUDA(cudaMemcpy(hrp.data(), row_ptr, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        rp = hrp.data();
+    }
+    if (rp[0] != 0) return fail(KV_EINVAL, "kv_system_csr: row_ptr[0] != 0");
+    for (int64_t r = 0; r < n; ++r)
+        if (rp[r + 1] < rp[r]) return fail(KV_EINVAL, "kv_system_csr: row_ptr decreases at row %lld", (long long)r);
+    const int64_t nnz = rp[n];
+    if (!on_device) {
+        for (int64_t r = 0; r < n; ++r) {
+            for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+                if (col[e] < 0 || col[e] >= n)
+                    return fail(KV_EINVAL, "kv_system_csr: col[%lld] = %d out of range", (long long)e, col[e]);
+                if (e > rp[r] && col[e] <= col[e - 1])
+                    return fail(KV_EINVAL, "kv_system_csr: row %lld columns not strictly increasing", (long long)r);
+            }
+        }
+    }
+    kv_sys* s = new (std::nothrow) kv_sys();
+    if (!s) return fail(KV_ENOMEM, "host allocation");
+    s->ctx = c;
+    s->kind = 1;
+    s->n = n;
+    s->nnz = nnz;
+    s->symmetric = symmetric != 0;
+    s->val_prec = value_precision;
+    const size_t vb = (size_t)nnz * elem_size(value_precision);
+    s->d_rp = (int64_t*)c->arena.alloc((size_t)(n + 1) * sizeof(int64_t));
+    s->d_col = (int32_t*)c->arena.alloc((size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t));
+    s->d_val = c->arena.alloc(std::max<size_t>(vb, 8));
+    if (b) s->d_b = (double*)c->arena.alloc((size_t)n * sizeof(double));
+    if (!s->d_rp || !s->d_col || !s->d_val || (b && !s->d_b)) {
+        c->arena.free(s->d_rp);
+        c->arena.free(s->d_col);
+        c->arena.free(s->d_val);
+        c->arena.free(s->d_b);
+        delete s;
+        return fail(KV_ENOMEM, "kv_system_csr: pool cannot hold the matrix (%lld nnz)", (long long)nnz);
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(s->d_rp, row_ptr, (size_t)(n + 1) * sizeof(int64_t), kind, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_col, col, (size_t)nnz * sizeof(int32_t), kind, c->stream);
+    if (e == cudaSuccess) {
+        if (value_precision == KV_FP64) {
+            e = cudaMemcpyAsync(s->d_val, val, (size_t)nnz * sizeof(double), kind, c->stream);
+        } else if (!on_device) {
+            std::vector<float> f((size_t)nnz);
+            for (int64_t q = 0; q < nnz; ++q) f[q] = (float)val[q];
+            e = cudaMemcpyAsync(s->d_val, f.data(), (size_t)nnz * sizeof(float), kind, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        } else {
+            e = cudaErrorInvalidValue;
+        }
+    }
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(s->d_b, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->arena.free(s->d_rp);
+        c->arena.free(s->d_col);
+        c->arena.free(s->d_val);
+        c->arena.free(s->d_b);
+        delete s;
+        return fail(KV_ECUDA, "kv_system_csr: upload failed: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return KV_OK;
+}
+
+int kv_sys_destroy(kv_sys* s) {
+    if (!s) return KV_OK;
+    Ctx* c = s->ctx;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    c->arena.free(s->d_rp);
+    c->arena.free(s->d_col);
+    c->arena.free(s->d_val);
+    c->arena.free(s->d_b);
+    delete s;
+    return KV_OK;
+}
+
+// ---------------------------------------------------------------- problems
+static int validate(const Sys* s, const kv_problem_desc* d, int precision) {
+    if (!d) return fail(KV_EINVAL, "problem description is NULL");
+    if (precision != KV_FP64 && precision != KV_FP32) return fail(KV_EINVAL, "precision");
+    if (s->kind == 1 && s->val_prec != precision)
+        return fail(KV_EINVAL, "problem precision must match the CSR value precision");
+    if (d->i < 1 || !d->cols) return fail(KV_EINVAL, "need at least one column");
+    if (d->o < 1 || !d->c_row_ptr || !d->theta) return fail(KV_EINVAL, "need at least one output row");
+    if (!(d->dt > 0) || !isfinite(d->dt)) return fail(KV_EINVAL, "dt must be positive and finite");
+    if (d->steps < 0) return fail(KV_EINVAL, "steps must be >= 0");
+    if (d->krylov_m < 1 || d->krylov_m > KV_MAX_M) return fail(KV_EINVAL, "krylov_m must be in [1, %d]", KV_MAX_M);
+    if ((int64_t)(d->steps + 1) * d->o >= ((int64_t)1 << 31) - 1) return fail(KV_EINVAL, "o * (steps+1) too large");
+    if (d->method < KV_AUTO || d->method > KV_ARNOLDI) return fail(KV_EINVAL, "method");
+    if (d->expm_mode != KV_EXPM_PER_STEP && d->expm_mode != KV_EXPM_PROPAGATE) return fail(KV_EINVAL, "expm_mode");
+    const int64_t n = s->n;
+    if (d->c_row_ptr[0] != 0) return fail(KV_EINVAL, "c_row_ptr[0] != 0");
+    for (int r = 0; r < d->o; ++r) {
+        if (d->c_row_ptr[r + 1] < d->c_row_ptr[r]) return fail(KV_EINVAL, "c_row_ptr decreases");
+        if (isnan(d->theta[r])) return fail(KV_EINVAL, "theta[%d] is NaN", r);
+    }
+    const int64_t cnnz = d->c_row_ptr[d->o];
+    if (cnnz > 0 && (!d->c_col || !d->c_val)) return fail(KV_EINVAL, "C arrays are NULL");
+    for (int64_t e = 0; e < cnnz; ++e) {
+        if (d->c_col[e] < 0 || d->c_col[e] >= n) return fail(KV_EINVAL, "c_col[%lld] out of range", (long long)e);
+        if (!isfinite(d->c_val[e])) return fail(KV_EINVAL, "c_val[%lld] not finite", (long long)e);
+    }
+    for (int j = 0; j < d->i; ++j) {
+        const kv_column& c = d->cols[j];
+        if (!(c.zlo <= c.zhi) || !isfinite(c.zlo) || !isfinite(c.zhi)) return fail(KV_EINVAL, "column %d: zlo > zhi", j);
+        if (c.is_fixed && (c.zlo != 1.0 || c.zhi != 1.0)) return fail(KV_EINVAL, "column %d: fixed needs z = 1", j);
+        if (c.kind == KV_COL_BOX) {
+            if (s->kind != 0) return fail(KV_EINVAL, "column %d: box columns need a grid system", j);
+            for (int a = 0; a < s->ndim; ++a)
+                if (c.box_lo[a] < 0 || c.box_hi[a] > s->dims[a] || c.box_lo[a] > c.box_hi[a])
+                    return fail(KV_EINVAL, "column %d: box out of the grid on axis %d", j, a);
+            if (!isfinite(c.value)) return fail(KV_EINVAL, "column %d: value", j);
+        } else if (c.kind == KV_COL_SPARSE) {
+            if (c.nnz < 0 || (c.nnz > 0 && (!c.idx || !c.val))) return fail(KV_EINVAL, "column %d: sparse arrays", j);
+            std::vector<int64_t> ix(c.idx, c.idx + c.nnz);
+            std::sort(ix.begin(), ix.end());
+            for (int64_t e = 0; e < c.nnz; ++e) {
+                if (ix[e] < 0 || ix[e] >= n) return fail(KV_EINVAL, "column %d: index out of range", j);
+                if (e > 0 && ix[e] == ix[e - 1]) return fail(KV_EINVAL, "column %d: duplicate index", j);
+                if (!isfinite(c.val[e])) return fail(KV_EINVAL, "column %d: value not finite", j);
+            }
+        } else if (c.kind == KV_COL_DENSE) {
+            if (!c.dense) return fail(KV_EINVAL, "column %d: dense is NULL", j);
+        } else {
+            return fail(KV_EINVAL, "column %d: kind", j);
+        }
+        const bool carries = s->d_b != nullptr && c.is_fixed;
+        if (carries && s->kind == 0) return fail(KV_EINVAL, "column %d: forcing term on grid systems is not supported", j);
+        if (d->method == KV_LANCZOS && (carries || !s->symmetric))
+            return fail(KV_EINVAL, "column %d: Lanczos needs a symmetric operator", j);
+        if (s->kind == 0 && d->method == KV_ARNOLDI)
+            return fail(KV_EINVAL, "Arnoldi on grid systems is not supported; grids are symmetric (use Lanczos)");
+    }
+    return KV_OK;
+}
+
+static void plan_methods(const Sys* s, const kv_problem_desc* d, Prob* p) {
+    p->method.resize(d->i);
+    p->aug.resize(d->i);
+    for (int j = 0; j < d->i; ++j) {
+        const bool carries = s->d_b != nullptr && d->cols[j].is_fixed != 0;
+        p->aug[j] = carries ? 1 : 0;
+        int m = d->method;
+        if (m == KV_AUTO) m = (s->symmetric && !carries) ? KV_LANCZOS : KV_ARNOLDI;
+        p->method[j] = m;
+    }
+}
+
+static int vectors_needed(const Sys* s, const Prob* p) {
+    int nv = 0;
+    for (int j = 0; j < p->i; ++j) {
+        int need = 0;
+        if (p->method[j] == KV_LANCZOS) need = s->kind == 0 ? 2 : 3;
+        else need = p->m + 1;
+        nv = std::max(nv, need);
+    }
+    return nv;
+}
+
+static void free_prob(Prob* p) {
+    for (void* q : p->allocs) p->ctx->arena.free(q);
+    p->allocs.clear();
+    if (p->done_ev) cudaEventDestroy(p->done_ev);
+    p->done_ev = nullptr;
+}
+
+int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, size_t* bytes) {
+    if (!s || !d || !bytes) return fail(KV_EINVAL, "kv_problem_bytes: NULL argument");
+    int rc = validate(s, d, precision);
+    if (rc) return rc;
+    Prob tmp;
+    tmp.sys = s;
+    tmp.i = d->i;
+    tmp.o = d->o;
+    tmp.m = d->krylov_m;
+    tmp.steps = d->steps;
+    plan_methods(s, d, &tmp);
+    const int64_t N = s->n + (std::count(tmp.aug.begin(), tmp.aug.end(), 1) ? 1 : 0);
+    const int nv = vectors_needed(s, &tmp);
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t t = 0;
+    t += r256((size_t)nv * N * elem_size(precision));
+    t += r256((size_t)d->i * d->o * (d->steps + 1) * sizeof(double));  // basis (Eq. memory_basis)
+    t += 2 * r256((size_t)d->o * (d->steps + 1) * sizeof(double));      // lo, hi
+    t += r256((size_t)d->i * (d->krylov_m + 1) * d->krylov_m * sizeof(double));
+    t += r256((size_t)d->i * d->o * d->krylov_m * sizeof(double));
+    t += r256((size_t)d->i * sizeof(ColState));
+    t += r256((size_t)reduce_slots_needed(&tmp) * sizeof(double)) + 256;
+    t += r256((size_t)(d->o + 1) * 8) + 2 * r256((size_t)d->c_row_ptr[d->o] * 8) + r256((size_t)d->o * 8);
+    t += 3 * r256((size_t)d->i * 8) + 2 * 256;
+    for (int j = 0; j < d->i; ++j) {
+        const kv_column& c = d->cols[j];
+        if (c.kind == KV_COL_SPARSE) t += r256((size_t)(c.nnz + 1) * 8) * 2;
+        if (c.kind == KV_COL_DENSE) t += r256((size_t)N * 8);
+    }
+    *bytes = t;
+    return KV_OK;
+}
+
+int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc* d, int precision) {
+    if (!c || !out || !s) return fail(KV_EINVAL, "kv_problem: NULL argument");
+    *out = nullptr;
+    if (s->ctx != c) return fail(KV_EINVAL, "kv_problem: system belongs to another context");
+    int rc = validate(s, d, precision);
+    if (rc) return rc;
+    rc = with_device(c->device);
+    if (rc) return rc;
+    kv_prob* p = new (std::nothrow) kv_prob();
+    if (!p) return fail(KV_ENOMEM, "host allocation");
+    p->ctx = c;
+    p->sys = s;
+    p->prec = precision;
+    p->i = d->i;
+    p->o = d->o;
+    p->m = d->krylov_m;
+    p->steps = d->steps;
+    p->dt = d->dt;
+    p->expm_mode = d->expm_mode;
+    p->batched = d->batched;
+    plan_methods(s, d, p);
+    p->N = s->n + (std::count(p->aug.begin(), p->aug.end(), 1) ? 1 : 0);
+    p->nvec = vectors_needed(s, p);
+    p->cols.assign(d->cols, d->cols + d->i);
+    const int64_t S = d->steps + 1;
+    const int64_t cnnz = d->c_row_ptr[d->o];
+#define TRY(x)               \
+    do {                     \
+        rc = (x);            \
+        if (rc) goto failed; \
+    } while (0)
+    {
+        TRY(dalloc(p, (char**)&p->d_vec, (size_t)p->nvec * p->N * elem_size(precision)));
+        TRY(dalloc(p, &p->d_basis, (size_t)p->i * p->o * S));
+        TRY(dalloc(p, &p->d_lo, (size_t)p->o * S));
+        TRY(dalloc(p, &p->d_hi, (size_t)p->o * S));
+        TRY(dalloc(p, &p->d_H, (size_t)p->i * (p->m + 1) * p->m));
+        TRY(dalloc(p, &p->d_P, (size_t)p->i * p->o * p->m));
+        TRY(dalloc(p, &p->d_state, (size_t)p->i));
+        p->red_slots = (int)reduce_slots_needed(p);
+        TRY(dalloc(p, &p->red.partials, (size_t)p->red_slots));
+        TRY(dalloc(p, &p->red.counter, 1));
+        TRY(dalloc(p, &p->d_crp, (size_t)p->o + 1));
+        TRY(dalloc(p, &p->d_ccol, (size_t)std::max<int64_t>(cnnz, 1)));
+        TRY(dalloc(p, &p->d_cval, (size_t)std::max<int64_t>(cnnz, 1)));
+        TRY(dalloc(p, &p->d_theta, (size_t)p->o));
+        TRY(dalloc(p, &p->d_zlo, (size_t)p->i));
+        TRY(dalloc(p, &p->d_zhi, (size_t)p->i));
+        TRY(dalloc(p, &p->d_zstar, (size_t)p->i));
+        TRY(dalloc(p, &p->d_ystar, 1));
+        TRY(dalloc(p, &p->d_viol, 1));
+        TRY(upload(c, p->d_crp, d->c_row_ptr, (size_t)(p->o + 1) * 8));
+        TRY(upload(c, p->d_ccol, d->c_col, (size_t)cnnz * 8));
+        TRY(upload(c, p->d_cval, d->c_val, (size_t)cnnz * 8));
+        TRY(upload(c, p->d_theta, d->theta, (size_t)p->o * 8));
+        std::vector<double> zl(p->i), zh(p->i);
+        for (int j = 0; j < p->i; ++j) {
+            zl[j] = d->cols[j].zlo;
+            zh[j] = d->cols[j].zhi;
+        }
+        TRY(upload(c, p->d_zlo, zl.data(), (size_t)p->i * 8));
+        TRY(upload(c, p->d_zhi, zh.data(), (size_t)p->i * 8));
+        KV_CHECK_CUDA(cudaMemsetAsync(p->red.counter, 0, sizeof(unsigned), c->stream));
+        KV_CHECK_CUDA(cudaMemsetAsync(p->d_H, 0, (size_t)p->i * (p->m + 1) * p->m * 8, c->stream));
+        KV_CHECK_CUDA(cudaMemsetAsync(p->d_P, 0, (size_t)p->i * p->o * p->m * 8, c->stream));
+        p->d_sidx.assign(p->i, nullptr);
+        p->d_sval.assign(p->i, nullptr);
+        p->d_dense.assign(p->i, nullptr);
+        for (int j = 0; j < p->i; ++j) {
+            const kv_column& col = d->cols[j];
+            kv_column& hc = p->cols[j];
+            hc.idx = nullptr;
+            hc.val = nullptr;
+            hc.dense = nullptr;
+            if (col.kind == KV_COL_SPARSE) {
+                const int64_t nn = col.nnz + (p->aug[j] ? 1 : 0);
+                std::vector<int64_t> ix(col.idx, col.idx + col.nnz);
+                std::vector<double> vv(col.val, col.val + col.nnz);
+                if (p->aug[j]) {
+                    ix.push_back(s->n);
+                    vv.push_back(1.0);
+                }
+                TRY(dalloc(p, &p->d_sidx[j], (size_t)std::max<int64_t>(nn, 1)));
+                TRY(dalloc(p, &p->d_sval[j], (size_t)std::max<int64_t>(nn, 1)));
+                TRY(upload(c, p->d_sidx[j], ix.data(), (size_t)nn * 8));
+                TRY(upload(c, p->d_sval[j], vv.data(), (size_t)nn * 8));
+                KV_CHECK_CUDA(cudaStreamSynchronize(c->stream));  // host vectors go out of scope
+            } else if (col.kind == KV_COL_DENSE) {
+                TRY(dalloc(p, &p->d_dense[j], (size_t)p->N));
+                TRY(upload(c, p->d_dense[j], col.dense, (size_t)s->n * 8));
+                if (p->N > s->n) {
+                    static const double one = 1.0, zero = 0.0;
+                    TRY(upload(c, p->d_dense[j] + s->n, p->aug[j] ? &one : &zero, 8));
+                }
+            }
+        }
+        if (cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+            rc = fail(KV_ECUDA, "event creation failed");
+            goto failed;
+        }
+        KV_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+    }
+#undef TRY
+    *out = p;
+    return KV_OK;
+failed:
+    cudaStreamSynchronize(c->stream);
+    free_prob(p);
+    delete p;
+    return rc;
+}
+
+int kv_prob_destroy(kv_prob* p) {
+    if (!p) return KV_OK;
+    cudaSetDevice(p->ctx->device);
+    cudaStreamSynchronize(p->ctx->stream);
+    free_prob(p);
+    delete p;
+    return KV_OK;
+}
+
+static int run_column(Prob* p, int j) {
+    const Sys* s = p->sys;
+    const size_t es = elem_size(p->prec);
+    char* base = (char*)p->d_vec;
+    auto vec = [&](int q) { return (void*)(base + (size_t)q * p->N * es); };
+    int rc;
+    const kv_column& c = p->cols[j];
+    if (c.kind == KV_COL_BOX) {
+        rc = launch_stencil_init_box(p, j, vec(0));
+    } else {
+        rc = c.kind == KV_COL_SPARSE ? launch_scatter(p, j, vec(0)) : launch_dense_to(p, j, vec(0));
+        if (!rc) rc = launch_init_norm(p, j, vec(0));
+    }
+    if (rc) return rc;
+    if (p->method[j] == KV_LANCZOS && s->kind == 0) {
+        for (int it = 0; it < p->m; ++it) {
+            void* B = vec(it & 1);
+            void* A = vec((it + 1) & 1);
+            rc = launch_stencil_alpha(p, j, it, B);
+            if (!rc) rc = launch_stencil_update(p, j, it, B, A);
+            if (rc) return rc;
+        }
+        return KV_OK;
+    }
+    return launch_arnoldi_column(p, j, p->d_vec);
+}
+
+int kv_enqueue(kv_prob* p) {
+    if (!p) return fail(KV_EINVAL, "kv_enqueue: NULL problem");
+    int rc = with_device(p->ctx->device);
+    if (rc) return rc;
+    for (int j = 0; j < p->i; ++j) {
+        rc = run_column(p, j);
+        if (rc) return rc;
+    }
+    rc = launch_expm_basis(p);
+    if (rc) return rc;
+    rc = launch_bounds(p);
+    if (rc) return rc;
+    KV_CHECK_CUDA(cudaEventRecord(p->done_ev, p->ctx->stream));
+    return KV_OK;
+}
+
+int kv_fetch(kv_prob* p, kv_result* r) {
+    if (!p || !r || !r->lo || !r->hi) return fail(KV_EINVAL, "kv_fetch: NULL argument");
+    int rc = with_device(p->ctx->device);
+    if (rc) return rc;
+    KV_CHECK_CUDA(cudaEventSynchronize(p->done_ev));
+    const size_t S = (size_t)p->steps + 1;
+    KV_CHECK_CUDA(cudaMemcpy(r->lo, p->d_lo, (size_t)p->o * S * 8, cudaMemcpyDeviceToHost));
+    KV_CHECK_CUDA(cudaMemcpy(r->hi, p->d_hi, (size_t)p->o * S * 8, cudaMemcpyDeviceToHost));
+    if (r->basis) KV_CHECK_CUDA(cudaMemcpy(r->basis, p->d_basis, (size_t)p->i * p->o * S * 8, cudaMemcpyDeviceToHost));
+    if (r->H) KV_CHECK_CUDA(cudaMemcpy(r->H, p->d_H, (size_t)p->i * (p->m + 1) * p->m * 8, cudaMemcpyDeviceToHost));
+    if (r->P) KV_CHECK_CUDA(cudaMemcpy(r->P, p->d_P, (size_t)p->i * p->o * p->m * 8, cudaMemcpyDeviceToHost));
+    std::vector<ColState> st(p->i);
+    KV_CHECK_CUDA(cudaMemcpy(st.data(), p->d_state, (size_t)p->i * sizeof(ColState), cudaMemcpyDeviceToHost));
+    int status = 0;
+    for (int j = 0; j < p->i; ++j) {
+        if (r->beta0) r->beta0[j] = st[j].beta0;
+        if (r->m_used) r->m_used[j] = st[j].m_used;
+        status |= st[j].status;
+    }
+    int key = 0;
+    KV_CHECK_CUDA(cudaMemcpy(&key, p->d_viol, sizeof(int), cudaMemcpyDeviceToHost));
+    if (key == 0x7f7f7f7f) {
+        r->first_violation_step = -1;
+        r->violation_row = -1;
+        r->y_star = 0.0;
+    } else {
+        r->first_violation_step = key / p->o;
+        r->violation_row = key % p->o;
+        KV_CHECK_CUDA(cudaMemcpy(&r->y_star, p->d_ystar, sizeof(double), cudaMemcpyDeviceToHost));
+        if (r->z_star) KV_CHECK_CUDA(cudaMemcpy(r->z_star, p->d_zstar, (size_t)p->i * 8, cudaMemcpyDeviceToHost));
+    }
+    if (status) return fail(KV_ETIMEOUT, "a device-side wait gave up (status %d)", status);
+    return KV_OK;
+}
+
+int kv_run(kv_prob* p, kv_result* r) {
+    int rc = kv_enqueue(p);
+    if (rc) return rc;
+    return kv_fetch(p, r);
+}
+
+int kv_profile_enable(kv_ctx* c, int enable) {
+    if (!c) return fail(KV_EINVAL, "kv_profile_enable: NULL ctx");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    clear_profile(c);
+    c->profiling = enable != 0;
+    return KV_OK;
+}
+
+int kv_profile_read(kv_ctx* c, const char* name, int64_t* launches, double* total_ms) {
+    if (!c || !name || !launches || !total_ms) return fail(KV_EINVAL, "kv_profile_read: NULL argument");
+    KV_CHECK_CUDA(cudaSetDevice(c->device));
+    KV_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+    int64_t n = 0;
+    double t = 0.0;
+    for (auto& r : c->recs) {
+        if (r.name != name) continue;
+        float ms = 0.f;
+        KV_CHECK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        n++;
+        t += ms;
+    }
+    *launches = n;
+    *total_ms = t;
+    return KV_OK;
+}
+
+}  // extern "C"

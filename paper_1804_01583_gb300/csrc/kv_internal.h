@@ -1,0 +1,185 @@
+// kv_internal.h -- host/device declarations shared by the libkv translation
+// units (not part of the public ABI; see include/kv.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/kv.h"
+
+namespace kv {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+#define KV_CHECK_CUDA(call)                                                        \
+    do {                                                                           \
+        cudaError_t _e = (call);                                                   \
+        if (_e != cudaSuccess) {                                                   \
+            ::kv::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), \
+                            __FILE__, __LINE__);                                   \
+            return KV_ECUDA;                                                       \
+        }                                                                          \
+    } while (0)
+
+// ------------------------------------------------------------------- arena
+// First-fit allocator over one device buffer; 256-byte granularity.  All
+// device memory of a context comes from here, so admission is a bookkeeping
+// question (does the request fit?) rather than a cudaMalloc that may fail.
+class Arena {
+  public:
+    void init(char* base, size_t size);
+    // returns nullptr when the request does not fit
+    void* alloc(size_t bytes);
+    void free(void* p);
+    size_t in_use() const { return in_use_; }
+    size_t total() const { return size_; }
+    size_t largest_free() const;
+
+  private:
+    char* base_ = nullptr;
+    size_t size_ = 0, in_use_ = 0;
+    std::map<size_t, size_t> free_;  // offset -> size
+    std::map<size_t, size_t> used_;  // offset -> size
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* pool = nullptr;
+    bool own_pool = false;
+    Arena arena;
+    int64_t launches = 0;
+    bool profiling = false;
+    struct Rec {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> spare_events;
+};
+
+// Records one launch: bumps the launch counter and, when profiling, brackets
+// the launch with events on the context stream.
+struct LaunchScope {
+    LaunchScope(Ctx* c, const char* name);
+    ~LaunchScope();
+    Ctx* ctx;
+    int rec = -1;
+};
+
+struct Sys {
+    Ctx* ctx = nullptr;
+    int kind = 0;  // 0 grid, 1 csr
+    int ndim = 0;
+    int64_t dims[3] = {1, 1, 1};
+    double coef = 0, h[3] = {1, 1, 1};
+    int64_t n = 0, nnz = 0;
+    int64_t* d_rp = nullptr;
+    int32_t* d_col = nullptr;
+    void* d_val = nullptr;  // double or float
+    int val_prec = KV_FP64;
+    double* d_b = nullptr;
+    bool symmetric = false;
+};
+
+// --------------------------------------------------------------- device state
+// Per-column Krylov state kept on the device so the iteration needs no host
+// round trip: the stored buffer holding v_j is scaled by s[j] on read (lazy
+// normalisation), beta0 = ||E_j||, done = breakdown or zero column.
+struct ColState {
+    double beta0;
+    int done;
+    int m_used;
+    int status;
+    int pad;
+    double s[KV_MAX_M + 2];
+};
+
+struct CDesc {  // output matrix C in CSR form on the device
+    int o;
+    const int64_t* rp;
+    const int64_t* col;
+    const double* val;
+};
+
+struct Reduce {  // scratch of one deterministic grid reduction
+    double* partials;
+    unsigned* counter;
+};
+
+struct StencilGeom {
+    int64_t nx, ny, nz;
+    double kx, ky, kz, kc;  // kc = -2 (kx + ky + kz)
+};
+
+struct Prob {
+    Ctx* ctx = nullptr;
+    const Sys* sys = nullptr;
+    int prec = KV_FP64;
+    int i = 0, o = 0, m = 0, steps = 0;
+    double dt = 0;
+    int expm_mode = KV_EXPM_PER_STEP;
+    int batched = 0;
+    std::vector<int> method;     // per column: KV_LANCZOS | KV_ARNOLDI
+    std::vector<int> aug;        // per column: runs on A' (carries the constant)
+    std::vector<kv_column> cols; // host copy (pointers cleared)
+    std::vector<int64_t*> d_sidx;
+    std::vector<double*> d_sval;
+    std::vector<double*> d_dense;
+    // device arrays
+    int64_t* d_crp = nullptr;
+    int64_t* d_ccol = nullptr;
+    double* d_cval = nullptr;
+    double* d_theta = nullptr;
+    double* d_zlo = nullptr;
+    double* d_zhi = nullptr;
+    ColState* d_state = nullptr;
+    double* d_H = nullptr;
+    double* d_P = nullptr;
+    double* d_basis = nullptr;
+    double* d_lo = nullptr;
+    double* d_hi = nullptr;
+    double* d_zstar = nullptr;
+    double* d_ystar = nullptr;
+    int* d_viol = nullptr;
+    void* d_vec = nullptr;  // Krylov vectors
+    int64_t N = 0;          // vector length (n, or n+1 if any column is augmented)
+    int nvec = 0;           // vectors of length N reserved
+    Reduce red{};
+    int red_slots = 0;
+    std::vector<void*> allocs;
+    cudaEvent_t done_ev = nullptr;
+};
+
+// ------------------------------------------------------------ launchers
+// grid stencil (k_stencil.cu)
+int stencil_blocks(const StencilGeom& g, int* zc);
+int launch_stencil_init_box(Prob* p, int j, void* B);
+int launch_stencil_alpha(Prob* p, int j, int it, const void* B);
+int launch_stencil_update(Prob* p, int j, int it, const void* B, void* A);
+
+// generic vectors (k_vector.cu)
+int launch_init_norm(Prob* p, int j, void* B);
+int launch_scatter(Prob* p, int j, void* B);
+int launch_dense_to(Prob* p, int j, void* B);
+
+// CSR (k_csr.cu)
+int launch_arnoldi_column(Prob* p, int j, void* V);
+
+// exponential + basis (k_expm.cu)
+int launch_expm_basis(Prob* p);
+
+// bounds (k_bounds.cu)
+int launch_bounds(Prob* p);
+
+// number of reduction partial slots a problem needs
+int64_t reduce_slots_needed(const Prob* p);
+
+inline size_t elem_size(int prec) { return prec == KV_FP32 ? 4 : 8; }
+
+}  // namespace kv

@@ -1,0 +1,50 @@
+"""Host-side checks that need no GPU: the library builds, loads and exports
+every entry point declared in include/kv.h; host-side validation and the
+memory model."""
+import os
+import re
+
+import pytest
+
+import paper_1804_01583_gb300 as kv
+from paper_1804_01583_gb300 import build as kvbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(kv_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    kvbuild.build()
+    return kv.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_entry_points()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+    assert set(kv.EXPORTED) <= set(names)
+
+
+def test_version_and_error_string(lib):
+    assert "sm_103a" in kv.version()
+    assert isinstance(kv.last_error(), str)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(kv.KvError) as ei:
+        kv.Context(1 << 20)
+    assert ei.value.code in (kv.KV_ECUDA, kv.KV_EINVAL)
