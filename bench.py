@@ -1,0 +1,299 @@
+#!/usr/bin/env python3
+"""Benchmark of the projected-Krylov verification path on GB300.
+
+One *step* is one whole verification query of the workload (initial vector,
+krylov_m Lanczos iterations with the on-the-fly output projection, the batched
+exponential for every time step, the bounds and the first-violation scan).
+
+Default workload: 3D heat on a 1000^3 grid (n = 1e9), 7-point matrix-free
+Laplacian, Dirichlet-0, coefficient 0.01, h = 1/1001, a 100^3 heated corner
+block (one generator, u in [0.9, 1.1]), centre-cell output, dt = 0.02,
+200 steps, Lanczos m = 30.
+
+metric: Lanczos-step GB/s = algorithmic bytes of the Lanczos iterations
+(read v_j, read v_{j-1}, write v_{j+1}: 3 vectors of n elements per
+iteration) / time per query.  The vectors (8 GB FP64, 4 GB FP32) are far
+larger than the 126 MB L2, so no flush is needed between iterations.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "Lanczos-step HBM GB/s (1e9-dim heat); queries/s + p99 at <=1e-6 rel bound error"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name: str, precision: str):
+    if name == "heat3d-1000":
+        return W.heat3d_1000(precision=precision)
+    if name == "heat3d-100":
+        return W.heat3d_100(precision=precision)
+    if name == "heat2d-20":
+        return W.heat2d_20(precision=precision)
+    raise ValueError(name)
+
+
+def bytes_per_iteration(p) -> float:
+    es = 8 if p.precision == "fp64" else 4
+    return 3.0 * es * p.system.n
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline(p, iters: int = 4):
+    """The oracle's Lanczos (Alg. 3/4, plain FP64 C with OpenMP) on the same
+    grid for a bounded number of iterations; same byte model as the GPU."""
+    import oracle
+    n = p.system.n
+    e = W.column_dense(p.columns[0], n, p.system.dims)
+    b0 = float(np.sqrt(np.dot(e, e)))
+    e /= b0
+    t0 = time.perf_counter()
+    oracle.krylov(p.system, e, iters, p.C_row_ptr, p.C_col, p.C_val, method="lanczos")
+    t = time.perf_counter() - t0
+    del e
+    gbs = iters * 3.0 * 8 * n / t / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{iters} Lanczos iterations of the FP64 oracle on the full {p.name} grid "
+                      f"(n={n}), {t:.1f} s"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank: int, world: int):
+    import torch
+    import paper_1804_01583_gb300 as kv
+    from paper_1804_01583_gb300 import build as kvbuild
+
+    kvbuild.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    p = workload(args.workload, args.precision)
+    pool_bytes = max(kv_bytes_guess(p), 1 << 30)
+    stream = torch.cuda.Stream()
+    ctx = kv.Context(pool_bytes, device=dev, stream=stream)
+    sysh = kv.System(ctx, p.system, p.precision)
+    ph = kv.ProblemHandle(ctx, sysh, p, expm_mode=args.expm)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        ph.enqueue()
+    torch.cuda.synchronize()
+    # timed region (device events on the library stream)
+    launches0 = ctx.launch_count()
+    ctx.profile_enable(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ph.enqueue()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    kern = {}
+    for name in ["stencil_update", "stencil_alpha", "stencil_init", "expm_per_step", "expm_propagate",
+                 "bounds", "bounds_finish"]:
+        nl, tms = ctx.profile_read(name)
+        if nl:
+            kern[name] = (nl, tms)
+    ctx.profile_enable(False)
+    res = ph.fetch(full=False)
+    ph.close()
+    sysh.close()
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    bpi = bytes_per_iteration(p)
+    gbs = world * p.m * bpi / (ms_step * 1e-3) / 1e9
+
+    # end to end through the public API with host inputs: system + problem
+    # creation (host -> device), run, result fetch (device -> host)
+    e2e_ms = []
+    for q in range(max(2, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = kv.System(ctx, p.system, p.precision)
+        h2 = kv.ProblemHandle(ctx, s2, p, expm_mode=args.expm)
+        out = h2.run(full=False)
+        t1 = time.perf_counter()
+        h2.close()
+        s2.close()
+        if q > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e = statistics.median(e2e_ms)
+    h2d = 8 * (p.o + 1) + 8 * len(p.C_col) * 2 + 8 * p.o + 16 * p.i + 64 * p.i
+    d2h = 8 * 2 * p.o * (p.steps + 1) + 8 * p.i + 16
+    out_e2e = {"value": world * p.m * bpi / (e2e * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peak, peak_kind = peaks()
+    dom = "stencil_update"
+    nl, tms = kern.get(dom, (0, 0.0))
+    achieved = (bpi / (tms / nl * 1e-3) / 1e9) if nl else None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": bpi, "traffic": None}
+    kernels = {k: {"launches": v[0], "avg_ms": v[1] / v[0], "share": v[1] / ms_total} for k, v in kern.items()}
+    line = {
+        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if p.precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": p.name, "n": p.system.n, "krylov_m": p.m, "steps_per_query": p.steps,
+                   "precision": p.precision, "expm": args.expm, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "queries_per_s": world * 1e3 / ms_step,
+        "roofline": roof, "kernels": kernels, "e2e": out_e2e, "gpu_launches": launches,
+        "clocks": clk, "first_violation_step": res["viol_step"],
+    }
+    ctx.close()
+    return line, p
+
+
+def kv_bytes_guess(p) -> int:
+    es = 8 if p.precision == "fp64" else 4
+    return int(2 * p.system.n * es * 1.02) + (256 << 20)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kv", choices=["kv", "reference"])
+    ap.add_argument("--workload", default="heat3d-1000", choices=["heat3d-1000", "heat3d-100", "heat2d-20"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--expm", default="per_step", choices=["per_step", "propagate"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=4)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        p = workload(args.workload, "fp64")
+        vals = []
+        cb = None
+        for _ in range(args.warmup + args.steps):
+            cb = cpu_baseline(p, iters=args.cpu_iters)
+            vals.append(cb["value"])
+        v = statistics.median(vals[args.warmup:]) if args.steps else vals[-1]
+        cb["value"] = v
+        line = {"metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 0, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": p.m * bytes_per_iteration(p) / v / 1e6,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": p.name, "n": p.system.n, "krylov_m": p.m, "precision": "fp64",
+                           "sample": cb["sample"]},
+                "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line, p = run_gpu(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(workload(args.workload, "fp64"), iters=args.cpu_iters)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -117,7 +117,12 @@ typedef struct {
     int32_t method;             /* KV_AUTO | KV_LANCZOS | KV_ARNOLDI */
     int32_t expm_mode;          /* KV_EXPM_PER_STEP | KV_EXPM_PROPAGATE */
     int32_t batched;            /* CSR: 1 = all Arnoldi columns share one SpMM */
+    int32_t flags;              /* KV_FLAG_* bits, 0 = defaults */
 } kv_problem_desc;
+
+/* kv_problem_desc.flags */
+#define KV_FLAG_TWO_PASS 1      /* grid Lanczos: use the two-pass kernels even where
+                                   the single-pass TMA iteration applies */
 
 #define KV_MAX_M 64
 

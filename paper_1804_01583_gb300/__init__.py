@@ -25,6 +25,7 @@ KV_AUTO, KV_LANCZOS, KV_ARNOLDI = 0, 1, 2
 KV_COL_BOX, KV_COL_SPARSE, KV_COL_DENSE = 0, 1, 2
 KV_EXPM_PER_STEP, KV_EXPM_PROPAGATE = 0, 1
 KV_MAX_M = 64
+KV_FLAG_TWO_PASS = 1
 
 _PREC = {"fp64": KV_FP64, "fp32": KV_FP32}
 _METH = {"auto": KV_AUTO, "lanczos": KV_LANCZOS, "arnoldi": KV_ARNOLDI}
@@ -48,7 +49,7 @@ class kv_problem_desc(C.Structure):
                 ("c_row_ptr", C.c_void_p), ("c_col", C.c_void_p), ("c_val", C.c_void_p),
                 ("theta", C.c_void_p), ("dt", C.c_double), ("steps", C.c_int32),
                 ("krylov_m", C.c_int32), ("method", C.c_int32), ("expm_mode", C.c_int32),
-                ("batched", C.c_int32)]
+                ("batched", C.c_int32), ("flags", C.c_int32)]
 
 
 class kv_result(C.Structure):
@@ -202,7 +203,7 @@ class System:
             pass
 
 
-def _desc(problem, expm_mode: str, batched: bool, keep: list) -> kv_problem_desc:
+def _desc(problem, expm_mode: str, batched: bool, keep: list, flags: int = 0) -> kv_problem_desc:
     cols = (kv_column * problem.i)()
     for j, c in enumerate(problem.columns):
         cc = cols[j]
@@ -244,6 +245,7 @@ def _desc(problem, expm_mode: str, batched: bool, keep: list) -> kv_problem_desc
     d.method = _METH[problem.method]
     d.expm_mode = _EXPM[expm_mode]
     d.batched = 1 if batched else 0
+    d.flags = int(flags)
     return d
 
 
@@ -251,12 +253,12 @@ class ProblemHandle:
     """kv_problem / kv_enqueue / kv_fetch / kv_run / kv_prob_destroy."""
 
     def __init__(self, ctx: Context, sysh: System, problem, *, expm_mode: str = "per_step",
-                 batched: bool = False):
+                 batched: bool = False, flags: int = 0):
         self.ctx = ctx
         self.sysh = sysh
         self.problem = problem
         self._keep: list = []
-        self.desc = _desc(problem, expm_mode, batched, self._keep)
+        self.desc = _desc(problem, expm_mode, batched, self._keep, flags)
         h = C.c_void_p()
         _check(ctx._lib.kv_problem(ctx.h, C.byref(h), sysh.h, C.byref(self.desc), _PREC[problem.precision]))
         self.h = h
@@ -304,22 +306,23 @@ class ProblemHandle:
             pass
 
 
-def problem_bytes(sysh: System, problem, *, expm_mode: str = "per_step", batched: bool = False) -> int:
+def problem_bytes(sysh: System, problem, *, expm_mode: str = "per_step", batched: bool = False,
+                  flags: int = 0) -> int:
     keep: list = []
-    d = _desc(problem, expm_mode, batched, keep)
+    d = _desc(problem, expm_mode, batched, keep, flags)
     n = C.c_size_t()
     _check(sysh.ctx._lib.kv_problem_bytes(sysh.h, C.byref(d), _PREC[problem.precision], C.byref(n)))
     return n.value
 
 
 def solve(problem, ctx: Optional[Context] = None, *, pool_bytes: int = 1 << 30, expm_mode: str = "per_step",
-          batched: bool = False) -> Dict:
+          batched: bool = False, flags: int = 0) -> Dict:
     """Convenience: system + problem + run on a (new) context."""
     own = ctx is None
     if own:
         ctx = Context(pool_bytes)
     sysh = System(ctx, problem.system, problem.precision)
-    ph = ProblemHandle(ctx, sysh, problem, expm_mode=expm_mode, batched=batched)
+    ph = ProblemHandle(ctx, sysh, problem, expm_mode=expm_mode, batched=batched, flags=flags)
     try:
         return ph.run()
     finally:

@@ -161,6 +161,7 @@ int64_t reduce_slots_needed(const Prob* p) {
         g.nz = p->sys->ndim >= 3 ? p->sys->dims[2] : 1;
         int zc;
         nb = std::max<int64_t>(nb, stencil_blocks(g, &zc));
+        if (p->fused) nb = std::max<int64_t>(nb, 2 * (int64_t)fused_tma_blocks(p, &zc));
     }
     return nb * (int64_t)(p->m + 2);
 }
@@ -458,7 +459,7 @@ static int vectors_needed(const Sys* s, const Prob* p) {
     int nv = 0;
     for (int j = 0; j < p->i; ++j) {
         int need = 0;
-        if (p->method[j] == KV_LANCZOS) need = s->kind == 0 ? 2 : 3;
+        if (p->method[j] == KV_LANCZOS) need = (s->kind == 0 && !p->fused) ? 2 : 3;
         else need = p->m + 1;
         nv = std::max(nv, need);
     }
@@ -482,7 +483,10 @@ int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, s
     tmp.o = d->o;
     tmp.m = d->krylov_m;
     tmp.steps = d->steps;
+    tmp.prec = precision;
+    tmp.flags = d->flags;
     plan_methods(s, d, &tmp);
+    tmp.fused = !(d->flags & KV_FLAG_TWO_PASS) && fused_tma_supported(&tmp);
     const int64_t N = s->n + (std::count(tmp.aug.begin(), tmp.aug.end(), 1) ? 1 : 0);
     const int nv = vectors_needed(s, &tmp);
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -525,7 +529,9 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
     p->dt = d->dt;
     p->expm_mode = d->expm_mode;
     p->batched = d->batched;
+    p->flags = d->flags;
     plan_methods(s, d, p);
+    p->fused = !(d->flags & KV_FLAG_TWO_PASS) && fused_tma_supported(p);
     p->N = s->n + (std::count(p->aug.begin(), p->aug.end(), 1) ? 1 : 0);
     p->nvec = vectors_needed(s, p);
     p->cols.assign(d->cols, d->cols + d->i);
@@ -640,6 +646,17 @@ static int run_column(Prob* p, int j) {
         if (!rc) rc = launch_init_norm(p, j, vec(0));
     }
     if (rc) return rc;
+    if (p->method[j] == KV_LANCZOS && s->kind == 0 && p->fused) {
+        // alpha_0 by one read pass, then one fused pass per iteration over
+        // three rotating buffers (v_{j-1}, v_j, w)
+        rc = launch_stencil_alpha(p, j, 0, vec(0));
+        if (rc) return rc;
+        for (int it = 0; it < p->m; ++it) {
+            rc = launch_lanczos_fused(p, j, it, vec(it % 3), vec((it + 2) % 3), vec((it + 1) % 3));
+            if (rc) return rc;
+        }
+        return KV_OK;
+    }
     if (p->method[j] == KV_LANCZOS && s->kind == 0) {
         for (int it = 0; it < p->m; ++it) {
             void* B = vec(it & 1);

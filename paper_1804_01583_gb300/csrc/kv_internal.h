@@ -125,6 +125,8 @@ struct Prob {
     double dt = 0;
     int expm_mode = KV_EXPM_PER_STEP;
     int batched = 0;
+    int flags = 0;
+    bool fused = false;          // single-pass TMA Lanczos iterations on the grid
     std::vector<int> method;     // per column: KV_LANCZOS | KV_ARNOLDI
     std::vector<int> aug;        // per column: runs on A' (carries the constant)
     std::vector<kv_column> cols; // host copy (pointers cleared)
@@ -162,6 +164,11 @@ int stencil_blocks(const StencilGeom& g, int* zc);
 int launch_stencil_init_box(Prob* p, int j, void* B);
 int launch_stencil_alpha(Prob* p, int j, int it, const void* B);
 int launch_stencil_update(Prob* p, int j, int it, const void* B, void* A);
+
+// single-pass TMA Lanczos iteration, FP32 grids (k_stencil_tma.cu)
+bool fused_tma_supported(const Prob* p);
+int fused_tma_blocks(const Prob* p, int* zc);
+int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, void* W);
 
 // generic vectors (k_vector.cu)
 int launch_init_norm(Prob* p, int j, void* B);

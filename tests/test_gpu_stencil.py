@@ -138,24 +138,54 @@ def test_deterministic(ctx):
     assert np.array_equal(a["H"], b["H"]) and np.array_equal(a["hi"], b["hi"])
 
 
+PATHS = {"fused": 0, "two_pass": 1}  # 1 = KV_FLAG_TWO_PASS
+
+
+@pytest.mark.parametrize("path", ["fused", "two_pass"])
 @pytest.mark.parametrize("theta", [0.05, 0.01])
-def test_fp32_storage_heat2d(ctx, theta):
+def test_fp32_storage_heat2d(ctx, theta, path):
     """FP32 vectors, error-free float dot products summed in double: bounds
-    within 1e-6 of the FP64 oracle and the same violation step."""
+    within 1e-6 of the FP64 oracle and the same violation step, through the
+    single-pass TMA iteration and through the two-pass kernels."""
     p = W.heat2d_20(theta=theta, precision="fp32")
-    got = run_gpu(ctx, p)
+    got = run_gpu(ctx, p, flags=PATHS[path])
     ref = oracle.run(W.heat2d_20(theta=theta))
     e = bound_error(got, ref)
     assert e <= 1e-6, e
     assert got["viol_step"] == ref["viol_step"]
 
 
-def test_fp32_storage_3d(ctx):
-    p = W.heat((37, 19, 23), block=(5, 4, 3), output="centre8", dt=0.01, steps=120, m=25, precision="fp32")
-    got = run_gpu(ctx, p)
-    p64 = W.heat((37, 19, 23), block=(5, 4, 3), output="centre8", dt=0.01, steps=120, m=25)
-    e = bound_error(got, oracle.run(p64))
+@pytest.mark.parametrize("dims", [(37, 19, 23), (36, 19, 23), (260, 33, 40)])
+@pytest.mark.parametrize("path", ["fused", "two_pass"])
+def test_fp32_storage_3d(ctx, dims, path):
+    """Partial tiles in x, y and z (the fused path needs nx % 4 == 0 and falls
+    back to the two-pass kernels otherwise)."""
+    kw = dict(block=(5, 4, 3), output="centre8", dt=0.01, steps=120, m=25)
+    got = run_gpu(ctx, W.heat(dims, precision="fp32", **kw), flags=PATHS[path])
+    ref = oracle.run(W.heat(dims, **kw))
+    e = bound_error(got, ref)
     assert e <= 1e-6, e
+    for j in range(1):
+        eh, _ = krylov_error(got, ref, j)
+        assert eh <= 1e-5, eh
+
+
+@pytest.mark.parametrize("path", ["fused", "two_pass"])
+def test_fp32_output_within_reach_100(ctx, path):
+    """100^3 with a nearby output cell: non-zero bounds at full size in FP32."""
+    p = W.heat3d_100(m=40, steps=400, precision="fp32")
+    cell = W.grid_index((100, 100, 100), (12, 12, 12))
+    for q in (p,):
+        q.C_row_ptr = np.array([0, 1], dtype=np.int64)
+        q.C_col = np.array([cell], dtype=np.int64)
+        q.C_val = np.array([1.0])
+        q.theta = np.array([0.05])
+    got = run_gpu(ctx, p, flags=PATHS[path])
+    p64 = W.heat3d_100(m=40, steps=400)
+    p64.C_row_ptr, p64.C_col, p64.C_val, p64.theta = p.C_row_ptr, p.C_col, p.C_val, p.theta
+    ref = oracle.run(p64)
+    assert bound_error(got, ref) <= 1e-6
+    assert got["viol_step"] == ref["viol_step"]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
