@@ -178,7 +178,7 @@ def run_gpu(args, rank: int, world: int):
     ms_total = ev0.elapsed_time(ev1)
     launches = ctx.launch_count() - launches0
     kern = {}
-    for name in ["stencil_update", "stencil_alpha", "stencil_init", "expm_per_step", "expm_propagate",
+    for name in ["lanczos_fused", "stencil_update", "stencil_alpha", "stencil_init", "expm_per_step", "expm_propagate",
                  "bounds", "bounds_finish"]:
         nl, tms = ctx.profile_read(name)
         if nl:
@@ -241,7 +241,7 @@ def run_gpu(args, rank: int, world: int):
 
 def kv_bytes_guess(p) -> int:
     es = 8 if p.precision == "fp64" else 4
-    return int(2 * p.system.n * es * 1.02) + (256 << 20)
+    return int(3 * p.system.n * es * 1.02) + (512 << 20)
 
 
 def main():

@@ -17,6 +17,8 @@
 // re-read through L1.  The FP32 form stores vectors in float, computes A v in
 // float and accumulates every dot product error-free (Dot2) before the double
 // block reduction.
+#include <type_traits>
+
 #include "kv_internal.h"
 #include "reduce.cuh"
 
@@ -141,7 +143,13 @@ __global__ void __launch_bounds__(SNT) k_stencil_alpha(const T* __restrict__ B, 
             const T r = hr ? B[idx + 1] : (T)0;
             const T d = hd ? B[idx - g.nx] : (T)0;
             const T u = hu ? B[idx + g.nx] : (T)0;
-            const T av = kx * (l + r) + ky * (d + u) + kz * (cm + cp) + kc * c;
+            T av;
+            if constexpr (std::is_same<T, float>::value) {
+                // difference form: neighbour - centre is exact for nearby values
+                av = kx * ((l - c) + (r - c)) + ky * ((d - c) + (u - c)) + kz * ((cm - c) + (cp - c));
+            } else {
+                av = kx * (l + r) + ky * (d + u) + kz * (cm + cp) + kc * c;
+            }
             acc.add_prod(c, av);
             cm = c;
             c = cp;
@@ -179,6 +187,11 @@ __global__ void __launch_bounds__(SNT) k_stencil_update(const T* __restrict__ B,
     if (x < g.nx && y < g.ny) {
         const T ax = (T)(c1 * g.kx), ay = (T)(c1 * g.ky), az = (T)(c1 * g.kz);
         const T bc = (T)c2, ba = (T)c3;
+        // float form: w = sum_a (s kappa_a) L_a + (-alpha s) c + (-beta s') a with
+        // L_a the difference-form second difference and every coefficient split
+        // into a float pair (hi + lo), accumulated as one FMA chain
+        const CoefPair fx = split_coef(c1 * g.kx), fy = split_coef(c1 * g.ky), fz = split_coef(c1 * g.kz);
+        const CoefPair fc = split_coef(-alpha * sj), fa = split_coef(c3);
         const int64_t P2 = g.nx * g.ny;
         int64_t idx = (z0 * g.ny + y) * g.nx + x;
         T cm = z0 > 0 ? B[idx - P2] : (T)0;
@@ -190,8 +203,24 @@ __global__ void __launch_bounds__(SNT) k_stencil_update(const T* __restrict__ B,
             const T r = hr ? B[idx + 1] : (T)0;
             const T d = hd ? B[idx - g.nx] : (T)0;
             const T u = hu ? B[idx + g.nx] : (T)0;
-            T w = ax * (l + r) + ay * (d + u) + az * (cm + cp) + bc * c;
-            if (!FIRST) w += ba * A[idx];
+            T w;
+            if constexpr (std::is_same<T, float>::value) {
+                const float Lx = (l - c) + (r - c), Ly = (d - c) + (u - c), Lz = (cm - c) + (cp - c);
+                float acc2 = fx.lo * Lx;
+                acc2 = fmaf(fy.lo, Ly, acc2);
+                acc2 = fmaf(fz.lo, Lz, acc2);
+                acc2 = fmaf(fc.lo, c, acc2);
+                if (!FIRST) acc2 = fmaf(fa.lo, A[idx], acc2);
+                acc2 = fmaf(fx.hi, Lx, acc2);
+                acc2 = fmaf(fy.hi, Ly, acc2);
+                acc2 = fmaf(fz.hi, Lz, acc2);
+                acc2 = fmaf(fc.hi, c, acc2);
+                if (!FIRST) acc2 = fmaf(fa.hi, A[idx], acc2);
+                w = acc2;
+            } else {
+                w = ax * (l + r) + ay * (d + u) + az * (cm + cp) + bc * c;
+                if (!FIRST) w += ba * A[idx];
+            }
             A[idx] = w;
             acc.add_prod(w, w);
             cm = c;

@@ -6,26 +6,37 @@
 //     w = A v_j - alpha_j v_j - beta_j v_{j-1}           (written to a third buffer)
 //     beta_{j+1}^2 = w . w,  alpha_{j+1} = (w . A w) / (w . w)
 //     P[:, j+1] = C w / beta_{j+1}
-// so alpha of the *next* iteration comes out of the same pass and every
-// iteration reads v_j and v_{j-1} once and writes w once (12 bytes per grid
-// point in FP32, the algorithmic minimum of a three-vector Lanczos step).
+// so alpha of the next iteration comes out of the same pass, and every
+// iteration reads v_j and v_{j-1} once and writes w once: 12 bytes per grid
+// point in FP32, the algorithmic minimum of a three-vector Lanczos step.
 //
-// Each CTA owns a 128 x 16 (x, y) tile and marches over a chunk of z planes.
-// Per plane, one elected thread issues TMA tile loads (cp.async.bulk.tensor,
-// completion counted on an mbarrier) of
-//     v_j     with a 2-point halo in y (and 4 in x, the 16-byte TMA granule),
-//     v_{j-1} with a 1-point halo in y,
-// into a shared-memory ring two planes ahead of the compute.  TMA fills
-// coordinates outside the grid with zeros, which is the Dirichlet-0 boundary.
-// w is evaluated on the tile plus a 1-point halo ring (so A w of the interior
-// needs no data from neighbouring CTAs) into a 3-plane ring; the interior of
-// plane q = p - 1 is then finished: A w, the two dot products (error-free
-// float accumulation, Dot2) and the store of w.  w is written to a buffer no
-// CTA reads in this pass, so tiles never race on halos.
+// w . A w without the neighbours of w on every side: for the Dirichlet-0
+// Laplacian, summation by parts gives
+//     w . A w = - sum_a kappa_a [ sum_p (w_p - w_{p - e_a})^2 + sum_{p on the
+//               high face of axis a} w_p^2 ]            (w = 0 outside the grid)
+// so each grid point only needs its backward neighbours, and every term has
+// the same sign (no cancellation).
+//
+// Tiling: a CTA owns 124 (x) x 15 (y) points and marches over a chunk of z
+// planes.  w is evaluated on the tile plus a one-point halo on the low x and
+// y sides (a 128 x 16 region: warp k owns rows 2k and 2k+1, lane l the four
+// consecutive x 4l..4l+3).  Per plane one elected thread issues TMA tile loads
+// (cp.async.bulk.tensor, completion counted on an mbarrier) of v_j (2 rows of
+// halo below, 1 above; x from x0-8) and v_{j-1} into a shared-memory ring
+// three planes ahead of the compute; TMA fills coordinates outside the grid
+// with zeros, which is the Dirichlet-0 boundary.  The x-1 neighbour of w comes
+// from the next lane (shuffle), y-1 from the warp's own other row or the
+// shared w plane, z-1 from registers kept from the previous plane.  w goes to
+// a buffer no CTA reads in this pass, so tiles never race on halos.
+//
+// The update is evaluated in float with the difference form of the Laplacian
+// ((l - c) + (r - c): exact subtraction for nearby values) and every double
+// coefficient split into a float pair (hi + lo), one FMA chain; both dot
+// products are summed per plane in float and accumulated in double.
 //
 // Every mbarrier wait is bounded; on expiry the CTA sets the column's status
-// word (reported as KV_ETIMEOUT), drains its own outstanding copies with a
-// bounded wait and leaves.
+// word (reported as KV_ETIMEOUT), drains its outstanding copies with bounded
+// waits and leaves.
 #include <cuda.h>
 
 #include "kv_internal.h"
@@ -33,20 +44,19 @@
 
 namespace kv {
 
-constexpr int FTX = 128, FTY = 16, FNT = 256;
-constexpr int HX = 4;                  // x halo: one 16-byte TMA granule of floats
-constexpr int BW = FTX + 2 * HX;       // 136: box width of both loads
-constexpr int BH = FTY + 4;            // 20: v_j box height (2-row halo)
-constexpr int AH = FTY + 2;            // 18: v_{j-1} box height (1-row halo)
-constexpr int WW = FTX + 2, WH = FTY + 2;  // w region: tile + 1 halo
-constexpr int DEPTH = 2;               // stages in flight
+constexpr int FNT = 256;
+constexpr int TXI = 124, TYI = 15;      // interior points of a tile
+constexpr int WC = 128, WR = 16;        // w region: x0-4 .. x0+123, y0-1 .. y0+14
+constexpr int BBW = 136, BBH = 18;      // v_j box: x0-8 .. x0+127, y0-2 .. y0+15
+constexpr int ABW = 128, ABH = 16;      // v_{j-1} box: x0-4 .. x0+123, y0-1 .. y0+14
+constexpr int DEPTH = 3;                // stages in flight
 constexpr int RB = DEPTH + 2, RA = DEPTH;
-constexpr int BBYTES = BW * BH * 4;    // 10880
-constexpr int ABYTES = BW * AH * 4;    // 9792
+constexpr int BBYTES = BBW * BBH * 4;   // 9792
+constexpr int ABYTES = ABW * ABH * 4;   // 8192
 constexpr int BSTRIDE = (BBYTES + 127) / 128 * 128;
-constexpr int ASTRIDE = (ABYTES + 127) / 128 * 128;
-constexpr int WSTRIDE = (WW * WH * 4 + 127) / 128 * 128;
-constexpr int SMEM_MAIN = RB * BSTRIDE + RA * ASTRIDE + 3 * WSTRIDE;
+constexpr int ASTRIDE = ABYTES;
+constexpr int WSTRIDE = WC * WR * 4;
+constexpr int SMEM_MAIN = RB * BSTRIDE + RA * ASTRIDE + 2 * WSTRIDE;
 constexpr int SMEM_TOTAL = SMEM_MAIN + 128 + 1024;  // + barriers + alignment slack
 constexpr long WAIT_LIMIT = 1L << 22;
 
@@ -106,32 +116,42 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     __shared__ double shred[FNT / 32];
     __shared__ int flag, abort_flag;
 
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const StencilGeom& g = a.g;
-    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
+    const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz;
+    const int x0 = blockIdx.x * TXI, y0 = blockIdx.y * TYI;
     const int z0 = blockIdx.z * a.zc;
-    const int z1 = (int)min((int64_t)z0 + a.zc, g.nz);
-    const int p0 = z0 - 1, pend = z1;  // w planes computed: p0 .. pend
+    const int z1 = min(z0 + a.zc, nz);
+    const int p0 = z0 - 1;  // w planes p0 .. z1-1; the interior work runs for z0 .. z1-1
 
-    // coefficients of w = ax (B_l + B_r) + ay (B_d + B_u) + az (B_b + B_f) + bc B_c + ba A
     const double sj = a.st->s[a.j];
     const double alpha = a.H[(int64_t)a.j * a.m + a.j];
-    const float ax = (float)(sj * g.kx), ay = (float)(sj * g.ky), az = (float)(sj * g.kz);
-    const float bc = (float)(sj * (g.kc - alpha));
-    const float ba = FIRST ? 0.f : (float)(-a.H[(int64_t)a.j * a.m + (a.j - 1)] * a.st->s[a.j - 1]);
-    const float kx = (float)g.kx, ky = (float)g.ky, kz = (float)g.kz, kc = (float)g.kc;
+    const CoefPair fx = split_coef(sj * g.kx), fy = split_coef(sj * g.ky), fz = split_coef(sj * g.kz);
+    const CoefPair fc = split_coef(-alpha * sj);
+    const CoefPair fa = split_coef(FIRST ? 0.0 : -a.H[(int64_t)a.j * a.m + (a.j - 1)] * a.st->s[a.j - 1]);
+    const float kx = (float)g.kx, ky = (float)g.ky, kz = (float)g.kz;
 
     auto bslot = [&](int plane) { return sB + (size_t)(((plane % RB) + RB) % RB) * (BSTRIDE / 4); };
     auto aslot = [&](int plane) { return sA + (size_t)(((plane % RA) + RA) % RA) * (ASTRIDE / 4); };
-    auto wslot = [&](int plane) { return sW + (size_t)(((plane % 3) + 3) % 3) * (WSTRIDE / 4); };
     const unsigned stage_bytes = BBYTES + (FIRST ? 0u : (unsigned)ABYTES);
-
     auto issue_stage = [&](int p) {  // B plane p+1, A plane p -> stage barrier of p
         uint64_t* bar = bars + ((p - p0) % DEPTH);
         mbar_expect_tx(bar, stage_bytes);
-        tma_load_3d(bslot(p + 1), &mapB, bar, x0 - HX, y0 - 2, p + 1);
-        if (!FIRST) tma_load_3d(aslot(p), &mapA, bar, x0 - HX, y0 - 1, p);
+        tma_load_3d(bslot(p + 1), &mapB, bar, x0 - 8, y0 - 2, p + 1);
+        if (!FIRST) tma_load_3d(aslot(p), &mapA, bar, x0 - 4, y0 - 1, p);
     };
+
+    // this thread's points: rows r0 = 2 warp, r0 + 1; columns c = 4 lane + u
+    const int r0 = 2 * warp;
+    const int xb = x0 - 4 + 4 * lane;                 // x of u = 0 (multiple of 4)
+    const bool xin = xb >= 0 && xb < nx;              // nx % 4 == 0: all four or none
+    const bool yin0 = (y0 - 1 + r0) >= 0 && (y0 - 1 + r0) < ny;
+    const bool yin1 = (y0 + r0) < ny;                 // y0 + r0 >= 0 always
+    const bool inner_x = lane >= 1 && xin;            // c >= 4: inside the tile
+    const bool inner0 = inner_x && r0 >= 1 && yin0;   // row r0 interior (r0 >= 1)
+    const bool inner1 = inner_x && yin1;              // row r0 + 1 >= 1 always
+    const bool xhi3 = xin && (xb + 3 == nx - 1);      // u = 3 on the high x face
+    const bool yhi0 = (y0 - 1 + r0) == ny - 1, yhi1 = (y0 + r0) == ny - 1;
 
     if (t == 0) {
         for (int q = 0; q <= DEPTH; ++q) mbar_init(bars + q, 1);
@@ -139,100 +159,156 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
         abort_flag = 0;
     }
     __syncthreads();
+    int issued_upto = p0 - 1;
     if (t == 0) {
         uint64_t* pro = bars + DEPTH;
         mbar_expect_tx(pro, 2 * BBYTES);
-        tma_load_3d(bslot(p0 - 1), &mapB, pro, x0 - HX, y0 - 2, p0 - 1);
-        tma_load_3d(bslot(p0), &mapB, pro, x0 - HX, y0 - 2, p0);
-        for (int q = 0; q < DEPTH && p0 + q <= pend; ++q) issue_stage(p0 + q);
+        tma_load_3d(bslot(p0 - 1), &mapB, pro, x0 - 8, y0 - 2, p0 - 1);
+        tma_load_3d(bslot(p0), &mapB, pro, x0 - 8, y0 - 2, p0);
+        for (int q = 0; q < DEPTH && p0 + q <= z1 - 1; ++q) {
+            issue_stage(p0 + q);
+            issued_upto = p0 + q;
+        }
     }
 
-    Dot2f dot, nrm;
-    int issued_upto = min(p0 + DEPTH - 1, pend);
-    for (int p = p0; p <= pend; ++p) {
+    float4 zp0 = make_float4(0.f, 0.f, 0.f, 0.f), zp1 = zp0;  // w of the previous plane
+    double acc_n = 0.0, acc_e = 0.0;
+    int pfail = -1;
+    for (int p = p0; p <= z1 - 1; ++p) {
         bool ok = true;
         if (p == p0) ok = mbar_wait(bars + DEPTH, 0);
         ok = ok && mbar_wait(bars + ((p - p0) % DEPTH), (unsigned)(((p - p0) / DEPTH) & 1));
         if (!ok) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) break;
-
-        // ---- w on plane p over the tile + 1 halo ring
+        __syncthreads();  // also: every read of the previous plane's shared w is done
+        if (abort_flag) {
+            pfail = p;
+            break;
+        }
         const float* Bm = bslot(p - 1);
         const float* Bc = bslot(p);
         const float* Bp = bslot(p + 1);
         const float* Ac = aslot(p);
-        float* Wp = wslot(p);
-        const bool pin = p >= 0 && p < g.nz;
-        for (int e = t; e < WW * WH; e += FNT) {
-            const int c = e % WW, r = e / WW;
-            const int x = x0 - 1 + c, y = y0 - 1 + r;
-            float w = 0.f;
-            if (pin && x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
-                const int bi = (r + 1) * BW + (c + HX - 1);
-                w = ax * (Bc[bi - 1] + Bc[bi + 1]) + ay * (Bc[bi - BW] + Bc[bi + BW]) + az * (Bm[bi] + Bp[bi]) +
-                    bc * Bc[bi];
-                if (!FIRST) w += ba * Ac[r * BW + (c + HX - 1)];
-            }
-            Wp[e] = w;
-        }
-        __syncthreads();
+        float* Wp = sW + (p & 1) * (WSTRIDE / 4);
+        const bool pin = p >= 0 && p < nz;
 
-        // ---- finish the interior of plane q = p - 1
-        const int q = p - 1;
-        if (q >= z0) {
-            const float* Wm = wslot(q - 1);
-            const float* Wc = wslot(q);
-            const float* Wn = wslot(q + 1);
-            const int i4 = (t & 31) * 4;
-            for (int k = t >> 5; k < FTY; k += FNT / 32) {
-                const int y = y0 + k;
-                const int x = x0 + i4;
-                if (y >= g.ny || x >= g.nx) continue;
-                float wv[4];
+        // ---- w on this thread's 2 x 4 points
+        float4 w2[2];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int wi = (k + 1) * WW + (i4 + u + 1);
-                    const float w = Wc[wi];
-                    const float aw = kx * (Wc[wi - 1] + Wc[wi + 1]) + ky * (Wc[wi - WW] + Wc[wi + WW]) +
-                                     kz * (Wm[wi] + Wn[wi]) + kc * w;
-                    dot.add_prod(w, aw);
-                    nrm.add_prod(w, w);
-                    wv[u] = w;
-                }
-                float* dst = a.W + ((int64_t)q * g.ny + y) * g.nx + x;
-                *reinterpret_cast<float4*>(dst) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+        for (int h = 0; h < 2; ++h) {
+            const int r = r0 + h;
+            const bool valid = pin && xin && (h == 0 ? yin0 : yin1);
+            const float* brow = Bc + (r + 1) * BBW + 4 * lane + 4;
+            const float4 c4 = *reinterpret_cast<const float4*>(brow);
+            const float lft = brow[-1], rgt = brow[4];
+            const float4 d4 = *reinterpret_cast<const float4*>(brow - BBW);
+            const float4 u4 = *reinterpret_cast<const float4*>(brow + BBW);
+            const float4 m4 = *reinterpret_cast<const float4*>(Bm + (r + 1) * BBW + 4 * lane + 4);
+            const float4 p4 = *reinterpret_cast<const float4*>(Bp + (r + 1) * BBW + 4 * lane + 4);
+            float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!FIRST) a4 = *reinterpret_cast<const float4*>(Ac + r * ABW + 4 * lane);
+            const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+            const float xl[4] = {lft, c4.x, c4.y, c4.z};
+            const float xr[4] = {c4.y, c4.z, c4.w, rgt};
+            const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
+            const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+            const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
+            const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
+            const float aa[4] = {a4.x, a4.y, a4.z, a4.w};
+            float wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float c = cc[u];
+                const float Lx = (xl[u] - c) + (xr[u] - c);
+                const float Ly = (dd[u] - c) + (uu[u] - c);
+                const float Lz = (mm[u] - c) + (pp[u] - c);
+                float acc = fx.lo * Lx;
+                acc = fmaf(fy.lo, Ly, acc);
+                acc = fmaf(fz.lo, Lz, acc);
+                acc = fmaf(fc.lo, c, acc);
+                if (!FIRST) acc = fmaf(fa.lo, aa[u], acc);
+                acc = fmaf(fx.hi, Lx, acc);
+                acc = fmaf(fy.hi, Ly, acc);
+                acc = fmaf(fz.hi, Lz, acc);
+                acc = fmaf(fc.hi, c, acc);
+                if (!FIRST) acc = fmaf(fa.hi, aa[u], acc);
+                wv[u] = valid ? acc : 0.f;
             }
+            w2[h] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+            *reinterpret_cast<float4*>(Wp + r * WC + 4 * lane) = w2[h];
         }
-        __syncthreads();
-        // ---- refill: B plane p-1's slot and A plane p's slot are free now
-        if (t == 0 && p + DEPTH <= pend) {
+        __syncthreads();  // w of this plane visible; B(p-1) and A(p) no longer read
+        if (t == 0 && p + DEPTH <= z1 - 1) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue_stage(p + DEPTH);
             issued_upto = p + DEPTH;
         }
+
+        // ---- interior of plane p: norm, edge terms of w . A w, store
+        if (p >= z0) {
+            const float left0 = __shfl_up_sync(0xffffffffu, w2[0].w, 1);
+            const float left1 = __shfl_up_sync(0xffffffffu, w2[1].w, 1);
+            float4 up0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r0 >= 1) up0 = *reinterpret_cast<const float4*>(Wp + (r0 - 1) * WC + 4 * lane);
+            float sn = 0.f, se = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool inn = h == 0 ? inner0 : inner1;
+                const float4 w4 = w2[h];
+                const float4 up = h == 0 ? up0 : w2[0];
+                const float4 zp = h == 0 ? zp0 : zp1;
+                const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                const float lf[4] = {h == 0 ? left0 : left1, w4.x, w4.y, w4.z};
+                const float uv[4] = {up.x, up.y, up.z, up.w};
+                const float zv[4] = {zp.x, zp.y, zp.z, zp.w};
+                const bool yhi = h == 0 ? yhi0 : yhi1;
+                float tn = 0.f, te = 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float w = wv[u];
+                    const float dx = w - lf[u], dy = w - uv[u], dz = w - zv[u];
+                    te = fmaf(kx * dx, dx, te);
+                    te = fmaf(ky * dy, dy, te);
+                    te = fmaf(kz * dz, dz, te);
+                    float ghost = (u == 3 && xhi3) ? kx : 0.f;  // edges to the zero ghost
+                    ghost += yhi ? ky : 0.f;
+                    ghost += (p == nz - 1) ? kz : 0.f;
+                    te = fmaf(ghost * w, w, te);
+                    tn = fmaf(w, w, tn);
+                }
+                if (inn) {
+                    sn += tn;
+                    se += te;
+                    float* dst = a.W + ((int64_t)p * ny + (y0 - 1 + r0 + h)) * nx + xb;
+                    *reinterpret_cast<float4*>(dst) = w4;
+                }
+            }
+            acc_n += (double)sn;
+            acc_e += (double)se;
+        }
+        zp0 = w2[0];
+        zp1 = w2[1];
     }
     if (abort_flag) {
-        // drain this CTA's copies (bounded) before leaving; report the timeout
+        // drain this CTA's outstanding copies (bounded), report the timeout
         if (t == 0) {
             atomicOr(&a.st->status, 1);
-            mbar_wait(bars + DEPTH, 0);
-            for (int q = 0; q < DEPTH; ++q) mbar_wait(bars + q, 0), mbar_wait(bars + q, 1);
+            if (pfail == p0) mbar_wait(bars + DEPTH, 0);
+            for (int q = pfail; q <= issued_upto; ++q)
+                mbar_wait(bars + ((q - p0) % DEPTH), (unsigned)(((q - p0) / DEPTH) & 1));
         }
         __syncthreads();
         return;
     }
-    (void)issued_upto;
 
-    // ---- deterministic grid reduction of (w.w, w.Aw)
-    const double d_nrm = block_sum<FNT>(nrm.value(), shred);
-    const double d_dot = block_sum<FNT>(dot.value(), shred);
+    // ---- deterministic grid reduction of (w.w, -w.Aw)
+    const double d_nrm = block_sum<FNT>(acc_n, shred);
+    const double d_edg = block_sum<FNT>(acc_e, shred);
     const int64_t nb = (int64_t)gridDim.x * gridDim.y * gridDim.z;
     const int64_t slot = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    if (t == 0) a.red.partials[nb + slot] = d_dot;
+    if (t == 0) a.red.partials[nb + slot] = d_edg;
     if (!grid_arrive(d_nrm, a.red.partials, a.red.counter, slot, nb, &flag)) return;
     const double nw2 = grid_finish<FNT>(a.red.partials, nb, a.red.counter, shred);
-    const double wAw = grid_finish<FNT>(a.red.partials + nb, nb, a.red.counter, shred);
+    const double edg = grid_finish<FNT>(a.red.partials + nb, nb, a.red.counter, shred);
     __shared__ double snext;
     __shared__ int cont;
     if (t == 0) {
@@ -250,7 +326,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
             snext = 1.0 / beta;
             if (j + 1 < m) {
                 a.H[(int64_t)j * m + (j + 1)] = beta;
-                a.H[(int64_t)(j + 1) * m + (j + 1)] = wAw / nw2;  // alpha_{j+1}
+                a.H[(int64_t)(j + 1) * m + (j + 1)] = -edg / nw2;  // alpha_{j+1}
             }
             cont = (j + 1 < m) ? 1 : 0;
         }
@@ -287,20 +363,21 @@ static PfnEncodeTiled encode_fn() {
 }
 
 // Whether the single-pass TMA iteration applies: FP32 grid, rows a multiple
-// of 16 bytes (TMA stride rule), extents within TMA limits.
+// of 16 bytes (TMA stride rule), extents that fit int coordinates.
 bool fused_tma_supported(const Prob* p) {
     const Sys* s = p->sys;
     if (s->kind != 0 || p->prec != KV_FP32) return false;
     const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
-    if (nx % 4 != 0 || nx > ((int64_t)1 << 31) || ny > ((int64_t)1 << 31) || nz > ((int64_t)1 << 31)) return false;
+    if (nx % 4 != 0 || nx >= ((int64_t)1 << 30) || ny >= ((int64_t)1 << 30) || nz >= ((int64_t)1 << 30))
+        return false;
     return encode_fn() != nullptr;
 }
 
-static int make_map(CUtensorMap* m, void* base, const Sys* s, int box_h) {
+static int make_map(CUtensorMap* m, void* base, const Sys* s, int box_w, int box_h) {
     const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)BW, (cuuint32_t)box_h, 1};
+    cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -315,7 +392,7 @@ static int make_map(CUtensorMap* m, void* base, const Sys* s, int box_h) {
 int fused_tma_blocks(const Prob* p, int* zc_out) {
     const Sys* s = p->sys;
     const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
-    const int64_t bx = (nx + FTX - 1) / FTX, by = (ny + FTY - 1) / FTY;
+    const int64_t bx = (nx + TXI - 1) / TXI, by = (ny + TYI - 1) / TYI;
     // z chunk: about 12 waves of 2 resident CTAs per SM, at least 16 planes
     const int64_t target = 152LL * 2 * 12;
     int64_t nzc = (target + bx * by - 1) / (bx * by);
@@ -338,12 +415,12 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     g.kz = s->ndim >= 3 ? s->coef / (s->h[2] * s->h[2]) : 0.0;
     g.kc = -2.0 * (g.kx + g.ky + g.kz);
     CUtensorMap mB, mA;
-    int rc = make_map(&mB, const_cast<void*>(B), s, BH);
-    if (!rc) rc = make_map(&mA, const_cast<void*>(A), s, AH);
+    int rc = make_map(&mB, const_cast<void*>(B), s, BBW, BBH);
+    if (!rc) rc = make_map(&mA, const_cast<void*>(A), s, ABW, ABH);
     if (rc) return rc;
     int zc;
     fused_tma_blocks(p, &zc);
-    dim3 grd((unsigned)((g.nx + FTX - 1) / FTX), (unsigned)((g.ny + FTY - 1) / FTY), (unsigned)((g.nz + zc - 1) / zc));
+    dim3 grd((unsigned)((g.nx + TXI - 1) / TXI), (unsigned)((g.ny + TYI - 1) / TYI), (unsigned)((g.nz + zc - 1) / zc));
     FusedArgs a;
     a.W = (float*)Wout;
     a.g = g;

@@ -86,6 +86,15 @@ struct Dot2d {  // plain double accumulation for the FP64 form
     __device__ __forceinline__ double value() const { return s; }
 };
 
+// A double coefficient as an unevaluated float pair hi + lo (about 48 bits).
+struct CoefPair {
+    float hi, lo;
+};
+__host__ __device__ __forceinline__ CoefPair split_coef(double c) {
+    const float h = (float)c;
+    return CoefPair{h, (float)(c - (double)h)};
+}
+
 template <typename T>
 struct AccOf;
 template <>
