@@ -67,7 +67,7 @@ template <typename T>
 __global__ void __launch_bounds__(SNT) k_stencil_init_box(T* __restrict__ B, StencilGeom g, int zc,
                                                           int64_t lx, int64_t ly, int64_t lz, int64_t hx,
                                                           int64_t hy, int64_t hz, double value,
-                                                          ColState* st, double* P, CDesc cd, int m,
+                                                          ColState* st, double* H0, double* P, CDesc cd, int m,
                                                           Reduce red) {
     __shared__ double sh[SNT / 32];
     __shared__ int flag;
@@ -109,6 +109,13 @@ __global__ void __launch_bounds__(SNT) k_stencil_init_box(T* __restrict__ B, Ste
             st->done = 0;
             st->s[0] = 1.0 / b0;
             s0 = 1.0 / b0;
+            // alpha_0 = v_0 . A v_0 for the box indicator in closed form: by
+            // summation by parts v . A v = -sum_a kappa_a sum_edges (difference)^2,
+            // and the indicator differs across exactly the two faces of the box
+            // on each axis (towards the zero ghost where the box meets the
+            // grid boundary), one edge per face cell.
+            const double ex = (double)(hx - lx), ey = (double)(hy - ly), ez = (double)(hz - lz);
+            H0[0] = -2.0 * (g.kx * ey * ez + g.ky * ex * ez + g.kz * ex * ey) / (ex * ey * ez);
         }
     }
     __syncthreads();
@@ -273,13 +280,14 @@ int launch_stencil_init_box(Prob* p, int j, void* B) {
     const int64_t hz = p->sys->ndim >= 3 ? c.box_hi[2] : 1, lz = p->sys->ndim >= 3 ? c.box_lo[2] : 0;
     const int64_t hy = p->sys->ndim >= 2 ? c.box_hi[1] : 1, ly = p->sys->ndim >= 2 ? c.box_lo[1] : 0;
     ColState* st = p->d_state + j;
+    double* H0 = p->d_H + (int64_t)j * (p->m + 1) * p->m;
     double* P = p->d_P + (int64_t)j * p->o * p->m;
     if (p->prec == KV_FP32)
         k_stencil_init_box<float><<<grd, blk, 0, p->ctx->stream>>>(
-            (float*)B, g, zc, c.box_lo[0], ly, lz, c.box_hi[0], hy, hz, c.value, st, P, cdesc(p), p->m, p->red);
+            (float*)B, g, zc, c.box_lo[0], ly, lz, c.box_hi[0], hy, hz, c.value, st, H0, P, cdesc(p), p->m, p->red);
     else
         k_stencil_init_box<double><<<grd, blk, 0, p->ctx->stream>>>(
-            (double*)B, g, zc, c.box_lo[0], ly, lz, c.box_hi[0], hy, hz, c.value, st, P, cdesc(p), p->m, p->red);
+            (double*)B, g, zc, c.box_lo[0], ly, lz, c.box_hi[0], hy, hz, c.value, st, H0, P, cdesc(p), p->m, p->red);
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;
 }

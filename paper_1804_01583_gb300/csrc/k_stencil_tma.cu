@@ -23,7 +23,8 @@
 // consecutive x 4l..4l+3).  Per plane one elected thread issues TMA tile loads
 // (cp.async.bulk.tensor, completion counted on an mbarrier) of v_j (2 rows of
 // halo below, 1 above; x from x0-8) and v_{j-1} into a shared-memory ring
-// three planes ahead of the compute; TMA fills coordinates outside the grid
+// three planes ahead of the compute (two CTAs per SM, so six stages in flight
+// per SM); TMA fills coordinates outside the grid
 // with zeros, which is the Dirichlet-0 boundary.  The x-1 neighbour of w comes
 // from the next lane (shuffle), y-1 from the warp's own other row or the
 // shared w plane, z-1 from registers kept from the previous plane.  w goes to
@@ -32,7 +33,8 @@
 // The update is evaluated in float with the difference form of the Laplacian
 // ((l - c) + (r - c): exact subtraction for nearby values) and every double
 // coefficient split into a float pair (hi + lo), one FMA chain; both dot
-// products are summed per plane in float and accumulated in double.
+// products are summed per plane in float (squared differences per axis,
+// weighted once per plane) and accumulated in double.
 //
 // Every mbarrier wait is bounded; on expiry the CTA sets the column's status
 // word (reported as KV_ETIMEOUT), drains its outstanding copies with bounded
@@ -49,7 +51,7 @@ constexpr int TXI = 124, TYI = 15;      // interior points of a tile
 constexpr int WC = 128, WR = 16;        // w region: x0-4 .. x0+123, y0-1 .. y0+14
 constexpr int BBW = 136, BBH = 18;      // v_j box: x0-8 .. x0+127, y0-2 .. y0+15
 constexpr int ABW = 128, ABH = 16;      // v_{j-1} box: x0-4 .. x0+123, y0-1 .. y0+14
-constexpr int DEPTH = 3;                // stages in flight
+constexpr int DEPTH = 3;                // stages in flight (x 2 CTAs per SM)
 constexpr int RB = DEPTH + 2, RA = DEPTH;
 constexpr int BBYTES = BBW * BBH * 4;   // 9792
 constexpr int ABYTES = ABW * ABH * 4;   // 8192
@@ -249,10 +251,13 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
             const float left1 = __shfl_up_sync(0xffffffffu, w2[1].w, 1);
             float4 up0 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (r0 >= 1) up0 = *reinterpret_cast<const float4*>(Wp + (r0 - 1) * WC + 4 * lane);
-            float sn = 0.f, se = 0.f;
+            // squared backward differences per axis, weighted once per plane
+            float tx = 0.f, ty = 0.f, tz = 0.f, tn = 0.f, tg = 0.f;
+            const bool zhi = p == nz - 1;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const bool inn = h == 0 ? inner0 : inner1;
+                if (!inn) continue;
                 const float4 w4 = w2[h];
                 const float4 up = h == 0 ? up0 : w2[0];
                 const float4 zp = h == 0 ? zp0 : zp1;
@@ -260,30 +265,29 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
                 const float lf[4] = {h == 0 ? left0 : left1, w4.x, w4.y, w4.z};
                 const float uv[4] = {up.x, up.y, up.z, up.w};
                 const float zv[4] = {zp.x, zp.y, zp.z, zp.w};
-                const bool yhi = h == 0 ? yhi0 : yhi1;
-                float tn = 0.f, te = 0.f;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const float w = wv[u];
                     const float dx = w - lf[u], dy = w - uv[u], dz = w - zv[u];
-                    te = fmaf(kx * dx, dx, te);
-                    te = fmaf(ky * dy, dy, te);
-                    te = fmaf(kz * dz, dz, te);
-                    float ghost = (u == 3 && xhi3) ? kx : 0.f;  // edges to the zero ghost
-                    ghost += yhi ? ky : 0.f;
-                    ghost += (p == nz - 1) ? kz : 0.f;
-                    te = fmaf(ghost * w, w, te);
+                    tx = fmaf(dx, dx, tx);
+                    ty = fmaf(dy, dy, ty);
+                    tz = fmaf(dz, dz, tz);
                     tn = fmaf(w, w, tn);
                 }
-                if (inn) {
-                    sn += tn;
-                    se += te;
-                    float* dst = a.W + ((int64_t)p * ny + (y0 - 1 + r0 + h)) * nx + xb;
-                    *reinterpret_cast<float4*>(dst) = w4;
+                float* dst = a.W + ((int64_t)p * ny + (y0 - 1 + r0 + h)) * nx + xb;
+                *reinterpret_cast<float4*>(dst) = w4;
+                // edges from the high faces to the zero ghost points
+                const float gy = ((h == 0 ? yhi0 : yhi1) ? ky : 0.f) + (zhi ? kz : 0.f);
+                if (gy != 0.f || xhi3) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float gc = gy + ((u == 3 && xhi3) ? kx : 0.f);
+                        tg = fmaf(gc * wv[u], wv[u], tg);
+                    }
                 }
             }
-            acc_n += (double)sn;
-            acc_e += (double)se;
+            acc_n += (double)tn;
+            acc_e += (double)(kx * tx + ky * ty + kz * tz + tg);
         }
         zp0 = w2[0];
         zp1 = w2[1];

@@ -647,10 +647,12 @@ static int run_column(Prob* p, int j) {
     }
     if (rc) return rc;
     if (p->method[j] == KV_LANCZOS && s->kind == 0 && p->fused) {
-        // alpha_0 by one read pass, then one fused pass per iteration over
-        // three rotating buffers (v_{j-1}, v_j, w)
-        rc = launch_stencil_alpha(p, j, 0, vec(0));
-        if (rc) return rc;
+        // alpha_0 (closed form for a box column, else one read pass), then
+        // one fused pass per iteration over three rotating buffers
+        if (c.kind != KV_COL_BOX) {
+            rc = launch_stencil_alpha(p, j, 0, vec(0));
+            if (rc) return rc;
+        }
         for (int it = 0; it < p->m; ++it) {
             rc = launch_lanczos_fused(p, j, it, vec(it % 3), vec((it + 2) % 3), vec((it + 1) % 3));
             if (rc) return rc;
