@@ -162,9 +162,15 @@ int64_t reduce_slots_needed(const Prob* p) {
         int zc;
         nb = std::max<int64_t>(nb, stencil_blocks(g, &zc));
         if (p->fused) nb = std::max<int64_t>(nb, 2 * (int64_t)fused_tma_blocks(p, &zc));
+        return nb * (int64_t)(p->m + 2);
     }
-    return nb * (int64_t)(p->m + 2);
+    // CSR: one region of partials per column (all columns run together)
+    return std::max<int64_t>(nb, (int64_t)p->i * csr_scratch_slots(p->N));
 }
+
+// Vector sets: grid problems run their columns one after another on one set;
+// CSR problems run all columns of a method together, one set per column.
+static int vector_sets(const Sys* s, int i) { return s->kind == 0 ? 1 : i; }
 
 }  // namespace kv
 
@@ -489,9 +495,11 @@ int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, s
     tmp.fused = !(d->flags & KV_FLAG_TWO_PASS) && fused_tma_supported(&tmp);
     const int64_t N = s->n + (std::count(tmp.aug.begin(), tmp.aug.end(), 1) ? 1 : 0);
     const int nv = vectors_needed(s, &tmp);
+    tmp.N = N;
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
     size_t t = 0;
-    t += r256((size_t)nv * N * elem_size(precision));
+    t += r256((size_t)nv * N * elem_size(precision) * vector_sets(s, d->i));
+    if (s->kind == 1) t += r256((size_t)d->i * 4) + r256((size_t)d->i * 4) + r256(d->i * csr_arnoldi_dev_bytes());
     t += r256((size_t)d->i * d->o * (d->steps + 1) * sizeof(double));  // basis (Eq. memory_basis)
     t += 2 * r256((size_t)d->o * (d->steps + 1) * sizeof(double));      // lo, hi
     t += r256((size_t)d->i * (d->krylov_m + 1) * d->krylov_m * sizeof(double));
@@ -543,7 +551,16 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
         if (rc) goto failed; \
     } while (0)
     {
-        TRY(dalloc(p, (char**)&p->d_vec, (size_t)p->nvec * p->N * elem_size(precision)));
+        p->nsets = vector_sets(s, p->i);
+        TRY(dalloc(p, (char**)&p->d_vec, (size_t)p->nvec * p->N * elem_size(precision) * p->nsets));
+        if (s->kind == 1) {
+            TRY(dalloc(p, &p->d_counters, (size_t)p->i));
+            TRY(dalloc(p, &p->d_aug, (size_t)p->i));
+            TRY(dalloc(p, (char**)&p->d_arnoldi, (size_t)p->i * csr_arnoldi_dev_bytes()));
+            KV_CHECK_CUDA(cudaMemsetAsync(p->d_counters, 0, (size_t)p->i * sizeof(unsigned), c->stream));
+            KV_CHECK_CUDA(cudaMemsetAsync(p->d_arnoldi, 0, (size_t)p->i * csr_arnoldi_dev_bytes(), c->stream));
+            TRY(upload(c, p->d_aug, p->aug.data(), (size_t)p->i * sizeof(int)));
+        }
         TRY(dalloc(p, &p->d_basis, (size_t)p->i * p->o * S));
         TRY(dalloc(p, &p->d_lo, (size_t)p->o * S));
         TRY(dalloc(p, &p->d_hi, (size_t)p->o * S));
@@ -669,16 +686,45 @@ static int run_column(Prob* p, int j) {
         }
         return KV_OK;
     }
-    return launch_arnoldi_column(p, j, p->d_vec);
+    return fail(KV_EINVAL, "grid systems run Lanczos only");
+}
+
+// CSR: initial vectors of every column into slot 0 of its own vector set,
+// then each run of consecutive same-method columns as one set of launches
+// (grid.y = column).
+static int run_csr(Prob* p) {
+    const size_t es = elem_size(p->prec);
+    const size_t set_bytes = (size_t)p->nvec * p->N * es;
+    auto set = [&](int j) { return (void*)((char*)p->d_vec + (size_t)j * set_bytes); };
+    int rc;
+    for (int j = 0; j < p->i; ++j) {
+        const kv_column& c = p->cols[j];
+        rc = c.kind == KV_COL_SPARSE ? launch_scatter(p, j, set(j)) : launch_dense_to(p, j, set(j));
+        if (!rc) rc = launch_init_norm(p, j, set(j));
+        if (rc) return rc;
+    }
+    for (int j0 = 0; j0 < p->i;) {
+        int j1 = j0;
+        while (j1 < p->i && p->method[j1] == p->method[j0]) ++j1;
+        rc = launch_csr_columns(p, j0, j1 - j0, set(j0), p->method[j0] == KV_LANCZOS);
+        if (rc) return rc;
+        j0 = j1;
+    }
+    return KV_OK;
 }
 
 int kv_enqueue(kv_prob* p) {
     if (!p) return fail(KV_EINVAL, "kv_enqueue: NULL problem");
     int rc = with_device(p->ctx->device);
     if (rc) return rc;
-    for (int j = 0; j < p->i; ++j) {
-        rc = run_column(p, j);
+    if (p->sys->kind == 1) {
+        rc = run_csr(p);
         if (rc) return rc;
+    } else {
+        for (int j = 0; j < p->i; ++j) {
+            rc = run_column(p, j);
+            if (rc) return rc;
+        }
     }
     rc = launch_expm_basis(p);
     if (rc) return rc;

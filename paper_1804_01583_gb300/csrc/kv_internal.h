@@ -151,7 +151,11 @@ struct Prob {
     int* d_viol = nullptr;
     void* d_vec = nullptr;  // Krylov vectors
     int64_t N = 0;          // vector length (n, or n+1 if any column is augmented)
-    int nvec = 0;           // vectors of length N reserved
+    int nvec = 0;           // vectors of length N per vector set
+    int nsets = 1;          // vector sets (grid: 1, columns run in turn; CSR: one per column)
+    unsigned* d_counters = nullptr;  // per-column reduction tickets (CSR)
+    int* d_aug = nullptr;            // per-column: runs on A' (CSR)
+    void* d_arnoldi = nullptr;       // per-column Gram matrix and coefficients (CSR)
     Reduce red{};
     int red_slots = 0;
     std::vector<void*> allocs;
@@ -175,8 +179,11 @@ int launch_init_norm(Prob* p, int j, void* B);
 int launch_scatter(Prob* p, int j, void* B);
 int launch_dense_to(Prob* p, int j, void* B);
 
-// CSR (k_csr.cu)
-int launch_arnoldi_column(Prob* p, int j, void* V);
+// CSR (k_csr.cu): Krylov iterations of columns j0 .. j0+ncols-1 (same method),
+// whose vector sets start at V (stride nvec * N elements per column)
+int launch_csr_columns(Prob* p, int j0, int ncols, void* V, bool lanczos);
+int64_t csr_scratch_slots(int64_t N);
+size_t csr_arnoldi_dev_bytes();
 
 // exponential + basis (k_expm.cu)
 int launch_expm_basis(Prob* p);

@@ -48,6 +48,23 @@ __device__ __forceinline__ bool grid_arrive(double partial, double* partials, un
     return last;
 }
 
+// Ticket for passes whose partials were written by several threads of the
+// block: every thread fences its own writes before the block takes a ticket.
+// Every thread must call it; returns true in the last block to arrive.
+__device__ __forceinline__ bool block_ticket(unsigned* counter, int64_t nblocks, int* sh_flag) {
+    __threadfence();
+    __syncthreads();
+    const int t = threadIdx.x + threadIdx.y * blockDim.x;
+    if (t == 0) {
+        const unsigned ticket = atomicAdd(counter, 1u);
+        *sh_flag = (ticket == (unsigned)(nblocks - 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool last = *sh_flag != 0;
+    if (last) __threadfence();
+    return last;
+}
+
 // Fixed-order sum of n partials by the (last) block; result in thread 0.
 // Resets the counter for the next reduction.
 template <int NT>

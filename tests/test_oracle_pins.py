@@ -366,3 +366,28 @@ def test_bounds_match_vertex_enumeration(seed):
         y = float(np.dot(r["zstar"], basis[:, rr, k]))
         assert abs(y - r["ystar"]) < 1e-12 and y >= theta[rr]
         assert np.all(r["zstar"] >= zlo - 1e-15) and np.all(r["zstar"] <= zhi + 1e-15)
+
+
+def test_arnoldi_output_matches_expm_multiply_on_random_csr():
+    """The random-CSR workload shape (n = 2e4, 16 unit generators + the fixed
+    column carrying the constant, m = 60): the oracle's projected Arnoldi output
+    C V e^{H t} e_1 beta0 equals C e^{A' t} E_j from scipy's expm_multiply
+    (Al-Mohy & Higham 2011) although modified Gram-Schmidt loses orthogonality
+    on this non-normal A -- the Arnoldi relation still holds."""
+    import scipy.sparse.linalg as spl
+    p = W.random_csr_problem(20000, seed=0, m=60, steps=40, dt=0.05)
+    s = p.system
+    n = s.n
+    A = sp.csr_matrix((s.val, s.col, s.row_ptr), shape=(n, n))
+    Aa = sp.bmat([[A, sp.csr_matrix(s.b.reshape(-1, 1))], [sp.csr_matrix((1, n)), sp.csr_matrix((1, 1))]]).tocsr()
+    Crows = np.zeros((p.o, n + 1))
+    for r in range(p.o):
+        Crows[r, p.C_col[p.C_row_ptr[r]:p.C_row_ptr[r + 1]]] = p.C_val[p.C_row_ptr[r]:p.C_row_ptr[r + 1]]
+    r = oracle.run(p, columns=[0, 16])
+    for j in (0, 16):
+        c = p.columns[j]
+        e = np.concatenate([W.column_dense(c, n), [1.0 if c.is_fixed else 0.0]])
+        X = spl.expm_multiply(Aa, e, start=0.0, stop=p.steps * p.dt, num=p.steps + 1, endpoint=True)
+        ref = (Crows @ X.T)
+        S = np.max(np.abs(ref))
+        assert np.max(np.abs(r["basis"][j] - ref)) <= 1e-10 * S
