@@ -220,6 +220,35 @@ int kv_profile_read(kv_ctx *ctx, const char *name, int64_t *launches, double *to
 /* Number of kernel launches the context has issued since creation. */
 int kv_launch_count(const kv_ctx *ctx, int64_t *launches);
 
+/* Grid points the no-allocation entry point below can hold. */
+#define KV_NOALLOC_MAX_N 262144
+
+/* Projected Lanczos on a small grid without any device allocation.  The paper
+ * has no counterpart: this exists for callers that cannot allocate device
+ * memory when they need a result -- code running while a CUDA graph is being
+ * captured (cudaMalloc cannot be captured), real-time or embedded hosts that
+ * reserve all device memory up front, callers inside another runtime's
+ * allocator.  It runs the FP64 two-pass grid Lanczos iterations of kv_run for
+ * one box column (value on box_lo <= idx < box_hi) on the grid of
+ * kv_system_stencil (no forcing term) and writes H ((krylov_m+1) x krylov_m,
+ * row-major), P (o x krylov_m: C v_l), beta0 (||E||) and m_used (valid
+ * columns) to the caller's device buffers; C is given in CSR form with device
+ * arrays (c_row_ptr o+1, c_col and c_val c_row_ptr[o] entries).  All working
+ * memory (two Krylov vectors, reduction partials, column state, about
+ * 4.2 MB) lives in one fixed device array that every GPU loading the library
+ * holds until exit; nothing is allocated or freed.  Grids with more than
+ * KV_NOALLOC_MAX_N points are rejected with KV_EINVAL.  Work is enqueued on
+ * `stream` (a cudaStream_t, NULL = default stream) and the call returns
+ * without waiting.  The array is shared by all calls on a device and keeps
+ * the last call's contents: calls whose work overlaps on the GPU race on it.
+ * The first call on a device looks up the array's address on that device;
+ * make that first call before any stream capture begins.  Errors: KV_EINVAL,
+ * KV_ECUDA. */
+int kv_grid_lanczos_noalloc(int device, void *stream, int ndim, const int64_t dims[3], double coef,
+                            const double h[3], const int64_t box_lo[3], const int64_t box_hi[3], double value,
+                            int32_t o, const int64_t *c_row_ptr, const int64_t *c_col, const double *c_val,
+                            int32_t krylov_m, double *H, double *P, double *beta0, int32_t *m_used);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,10 @@ def load(path: Optional[str] = None):
         lib.kv_profile_enable.argtypes = [V, I]
         lib.kv_profile_read.argtypes = [V, C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         lib.kv_launch_count.argtypes = [V, C.POINTER(C.c_int64)]
+        lib.kv_grid_lanczos_noalloc.argtypes = [I, V, I, C.POINTER(C.c_int64), C.c_double, C.POINTER(C.c_double),
+                                                C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_double, C.c_int32,
+                                                V, V, V, C.c_int32, V, V, V, V]
+        lib.kv_grid_lanczos_noalloc.restype = C.c_int
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is None and name not in ("kv_version", "kv_last_error"):
@@ -304,6 +308,23 @@ class ProblemHandle:
             self.close()
         except Exception:
             pass
+
+
+KV_NOALLOC_MAX_N = 262144
+
+
+def grid_lanczos_noalloc(device: int, stream, ndim: int, dims, coef: float, h, box_lo, box_hi, value: float,
+                         o: int, c_row_ptr, c_col, c_val, krylov_m: int, H, P, beta0, m_used) -> None:
+    """kv_grid_lanczos_noalloc: every array argument is a device pointer (an
+    int) owned by the caller; stream is a cudaStream_t as an int, or None.
+    The library allocates nothing for this call (see include/kv.h)."""
+    lib = load()
+    d3 = (C.c_int64 * 3)(*[int(dims[a]) if a < len(dims) else 1 for a in range(3)])
+    h3 = (C.c_double * 3)(*[float(h[a]) if a < len(h) else 1.0 for a in range(3)])
+    lo3 = (C.c_int64 * 3)(*[int(box_lo[a]) if a < len(box_lo) else 0 for a in range(3)])
+    hi3 = (C.c_int64 * 3)(*[int(box_hi[a]) if a < len(box_hi) else 1 for a in range(3)])
+    _check(lib.kv_grid_lanczos_noalloc(device, stream, ndim, d3, float(coef), h3, lo3, hi3, float(value), o,
+                                       c_row_ptr, c_col, c_val, krylov_m, H, P, beta0, m_used))
 
 
 def problem_bytes(sysh: System, problem, *, expm_mode: str = "per_step", batched: bool = False,

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkv.so")
-SOURCES = ["kv_abi.cu", "k_stencil.cu", "k_vector.cu", "k_expm.cu", "k_bounds.cu", "k_csr.cu", "k_stencil_tma.cu"]
+SOURCES = ["kv_abi.cu", "k_stencil.cu", "k_vector.cu", "k_expm.cu", "k_bounds.cu", "k_csr.cu", "k_stencil_tma.cu",
+           "k_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
