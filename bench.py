@@ -216,12 +216,30 @@ def run_gpu(args, rank: int, world: int):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     peak, peak_kind = peaks()
-    dom = "stencil_update"
-    nl, tms = kern.get(dom, (0, 0.0))
-    achieved = (bpi / (tms / nl * 1e-3) / 1e9) if nl else None
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-            "algorithmic_bytes_per_launch": bpi, "traffic": None}
+    # dominant kernel: largest share of the timed region
+    dom = max(kern, key=lambda k: kern[k][1])
+    nl, tms = kern[dom]
+    avg_s = tms / nl * 1e-3
+    if dom in ("lanczos_fused", "stencil_update"):
+        alg_bytes = bpi  # reads v_j and v_{j-1}, writes w: 3 vectors of n elements
+    elif dom == "stencil_alpha":
+        alg_bytes = bpi / 3.0
+    else:
+        alg_bytes = None
+    if p.precision == "fp64" and dom in ("stencil_update", "stencil_alpha"):
+        # the FP64 grid passes are bound by the FP64 pipe (9 and 8
+        # FP64 instructions per grid point; peak 2 per SM per clock)
+        dp = {"stencil_update": 9.0, "stencil_alpha": 8.0}[dom] * p.system.n
+        dp_peak = 2.0 * 152 * 2.07e9 / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": dp / avg_s / 1e12, "peak": dp_peak,
+                "unit": "T FP64-instr/s", "frac": dp / avg_s / 1e12 / dp_peak,
+                "peak_kind": "derived: 2 FP64 instructions per SM per clock x 152 SMs x 2.07 GHz",
+                "algorithmic_fp64_instr_per_launch": dp, "traffic": None}
+    else:
+        achieved = alg_bytes / avg_s / 1e9 if alg_bytes else None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind + " (copy, burst)",
+                "algorithmic_bytes_per_launch": alg_bytes, "traffic": profiled_traffic(dom, p)}
     kernels = {k: {"launches": v[0], "avg_ms": v[1] / v[0], "share": v[1] / ms_total} for k, v in kern.items()}
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -235,13 +253,61 @@ def run_gpu(args, rank: int, world: int):
         "roofline": roof, "kernels": kernels, "e2e": out_e2e, "gpu_launches": launches,
         "clocks": clk, "first_violation_step": res["viol_step"],
     }
+    if args.compare_fp64 and p.precision != "fp64":
+        line["fp64_plain"] = time_other_precision(kv, ctx, args, "fp64", torch, stream)
     ctx.close()
     return line, p
 
 
+def time_other_precision(kv, ctx, args, precision, torch, stream):
+    """The same query in another storage precision on the same context
+    (context only; the headline value is the main form)."""
+    q = workload(args.workload, precision)
+    sysh = kv.System(ctx, q.system, q.precision)
+    try:
+        ph = kv.ProblemHandle(ctx, sysh, q, expm_mode=args.expm)
+    except kv.KvError as e:
+        sysh.close()
+        return {"skipped": str(e)}
+    ph.enqueue()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = 2
+    e0.record(stream)
+    for _ in range(k):
+        ph.enqueue()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    ph.close()
+    sysh.close()
+    return {"precision": precision, "ms_per_step": ms, "value": q.m * bytes_per_iteration(q) / (ms * 1e-3) / 1e9,
+            "unit": "GB/s", "steps": k}
+
+
+def profiled_traffic(kernel: str, p):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, if
+    the kernel source has not changed since the capture (hash match), scaled
+    from the captured grid to this one by the number of points."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = os.path.join(ROOT, d["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if h != d["source_sha256"] or d.get("precision") != p.precision:
+            return None
+        return d["dram_bytes_per_launch"] * p.system.n / d["n"]
+    except Exception:
+        return None
+
+
 def kv_bytes_guess(p) -> int:
-    es = 8 if p.precision == "fp64" else 4
-    return int(3 * p.system.n * es * 1.02) + (512 << 20)
+    # the larger of the FP32 form (three float vectors) and the FP64 two-pass
+    # form (two double vectors), which may run on the same context
+    return int(max(3 * 4, 2 * 8) * p.system.n * 1.02) + (512 << 20)
 
 
 def main():
@@ -254,7 +320,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--expm", default="per_step", choices=["per_step", "propagate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=4)
+    ap.add_argument("--cpu-iters", type=int, default=24)
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -175,23 +175,27 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
     __shared__ double wsum[2 * (KV_MAX_M + 1)][CNT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * CCHUNK + threadIdx.x;
-    double wv[CR], vv[CR];
+    // FP64 form: double products; FP32 form: each thread's CR products summed
+    // in float (one rounding per product and add), then one double add per
+    // basis vector -- the FP64 pipe is 1/64 of the float pipe on this GPU
+    T wv[CR], vv[CR];
 #pragma unroll
     for (int k = 0; k < CR; ++k) {
         const int64_t r = r0 + (int64_t)k * CNT;
-        wv[k] = r < N ? (double)W[r] : 0.0;
-        vv[k] = r < N ? (double)Vj[r] : 0.0;
+        wv[k] = r < N ? W[r] : (T)0;
+        vv[k] = r < N ? Vj[r] : (T)0;
     }
     for (int l = 0; l <= j; ++l) {
         const T* Vl = Vc + (int64_t)l * N;
-        double a = 0.0, g = 0.0;
+        T at = 0, gt = 0;
 #pragma unroll
         for (int k = 0; k < CR; ++k) {
             const int64_t r = r0 + (int64_t)k * CNT;
-            const double x = r < N ? (double)Vl[r] : 0.0;
-            a = fma(x, wv[k], a);
-            g = fma(x, vv[k], g);
+            const T x = r < N ? Vl[r] : (T)0;
+            at = fma(x, wv[k], at);
+            gt = fma(x, vv[k], gt);
         }
+        double a = (double)at, g = (double)gt;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -256,19 +260,31 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_update(VecArgs<T> V, int64_t N,
     for (int l = threadIdx.x; l <= j; l += CNT) cf[l] = A->c[l];
     __syncthreads();
     const int64_t r0 = (int64_t)blockIdx.x * CCHUNK + threadIdx.x;
-    double wv[CR];
+    T wv[CR];
 #pragma unroll
     for (int k = 0; k < CR; ++k) {
         const int64_t r = r0 + (int64_t)k * CNT;
-        wv[k] = r < N ? (double)W[r] : 0.0;
+        wv[k] = r < N ? W[r] : (T)0;
     }
     for (int l = 0; l <= j; ++l) {
         const T* Vl = Vc + (int64_t)l * N;
-        const double c = cf[l];
+        if constexpr (std::is_same<T, float>::value) {
+            const CoefPair c = split_coef(-cf[l]);  // the coefficient to ~48 bits
 #pragma unroll
-        for (int k = 0; k < CR; ++k) {
-            const int64_t r = r0 + (int64_t)k * CNT;
-            if (r < N) wv[k] = fma(-c, (double)Vl[r], wv[k]);
+            for (int k = 0; k < CR; ++k) {
+                const int64_t r = r0 + (int64_t)k * CNT;
+                if (r < N) {
+                    const float v = Vl[r];
+                    wv[k] = fmaf(c.hi, v, fmaf(c.lo, v, wv[k]));
+                }
+            }
+        } else {
+            const double c = cf[l];
+#pragma unroll
+            for (int k = 0; k < CR; ++k) {
+                const int64_t r = r0 + (int64_t)k * CNT;
+                if (r < N) wv[k] = fma(-c, Vl[r], wv[k]);
+            }
         }
     }
     typename AccOf<T>::type acc;
