@@ -220,6 +220,68 @@ int kv_profile_read(kv_ctx *ctx, const char *name, int64_t *launches, double *to
 /* Number of kernel launches the context has issued since creation. */
 int kv_launch_count(const kv_ctx *ctx, int64_t *launches);
 
+/* ------------------------------------------------------------- serving --
+ * Continuous batching of verification queries on one context.  The paper
+ * verifies one problem at a time; the server keeps several on the device at
+ * once.  A worker thread owned by the server admits queued queries in
+ * arrival order whenever one of `slots` slots is free and the context pool
+ * can hold the query's system and problem (device memory is reserved as in
+ * kv_problem, the memory model of Sec. 5; a query that does not fit waits for
+ * running ones to finish, and one that cannot fit an idle pool fails with
+ * KV_ENOMEM).  Each admitted query's whole path is enqueued on its slot's own
+ * stream, so the work of different queries overlaps on the device; on
+ * completion its results are copied to host storage and its device memory
+ * and slot are released.  Results are identical to kv_run on the same query
+ * (deterministic reductions; no state is shared between queries). */
+typedef struct kv_server kv_server;
+
+/* One query: a system (as for kv_system_stencil / kv_system_csr, host
+ * arrays) and a problem description with its precision.  The kv_column array
+ * is copied by kv_submit; every other host array the query references (CSR
+ * arrays, b, column idx/val/dense arrays, C arrays, theta) must stay valid
+ * until kv_poll has returned something other than KV_ENOTREADY for it. */
+typedef struct {
+    int32_t kind;               /* 0: grid system, 1: CSR system */
+    int32_t ndim;               /* grid: 2 or 3 */
+    int64_t dims[3];            /* grid */
+    double coef;                /* grid */
+    double h[3];                /* grid */
+    int64_t n;                  /* CSR */
+    const int64_t *row_ptr;     /* CSR, host */
+    const int32_t *col;         /* CSR, host */
+    const double *val;          /* CSR, host */
+    int32_t symmetric;          /* CSR */
+    const double *b;            /* host, n entries, or NULL */
+    kv_problem_desc desc;       /* the problem */
+    int32_t precision;          /* KV_FP64 | KV_FP32 (CSR values stored likewise) */
+} kv_query;
+
+/* Start a server on ctx with `slots` concurrent queries (1..256).  While the
+ * server exists the context belongs to its worker thread: make no other call
+ * on ctx (or on objects created from it) until kv_server_destroy. */
+int kv_server_create(kv_ctx *ctx, kv_server **out, int32_t slots);
+
+/* Wait for every submitted query to finish, stop the worker, release the
+ * server's streams.  Results not yet polled are discarded. */
+int kv_server_destroy(kv_server *server);
+
+/* Queue one query; returns its ticket.  Thread-safe.  Errors: KV_EINVAL,
+ * KV_EBUSY (server shutting down). */
+int kv_submit(kv_server *server, const kv_query *query, uint64_t *ticket);
+
+/* KV_ENOTREADY while the query is queued or running.  Otherwise the query's
+ * status (KV_OK or the error it failed with): on KV_OK its results are copied
+ * into `res` (lo and hi required; beta0, m_used, z_star optional; basis, H, P
+ * are not kept by the server) and latency_ms (optional) receives the time
+ * from kv_submit to the results being on the host.  A ticket can be polled
+ * to completion once.  Thread-safe. */
+int kv_poll(kv_server *server, uint64_t ticket, kv_result *res, double *latency_ms);
+
+/* Counters: queries admitted, completed, still queued, the largest number
+ * running at once, and admissions deferred because the pool was full. */
+int kv_server_stats(kv_server *server, int64_t *admitted, int64_t *completed, int64_t *pending,
+                    int32_t *max_running, int64_t *memory_waits);
+
 /* Grid points the no-allocation entry point below can hold. */
 #define KV_NOALLOC_MAX_N 262144
 

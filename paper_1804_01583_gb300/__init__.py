@@ -310,6 +310,116 @@ class ProblemHandle:
             pass
 
 
+class kv_query(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("ndim", C.c_int32), ("dims", C.c_int64 * 3), ("coef", C.c_double),
+                ("h", C.c_double * 3), ("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("symmetric", C.c_int32), ("b", C.c_void_p), ("desc", kv_problem_desc),
+                ("precision", C.c_int32)]
+
+
+def _load_server(lib):
+    if getattr(lib, "_server_ready", False):
+        return
+    V = C.c_void_p
+    lib.kv_server_create.argtypes = [V, C.POINTER(V), C.c_int32]
+    lib.kv_server_destroy.argtypes = [V]
+    lib.kv_submit.argtypes = [V, C.POINTER(kv_query), C.POINTER(C.c_uint64)]
+    lib.kv_poll.argtypes = [V, C.c_uint64, C.POINTER(kv_result), C.POINTER(C.c_double)]
+    lib.kv_server_stats.argtypes = [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+    for f in (lib.kv_server_create, lib.kv_server_destroy, lib.kv_submit, lib.kv_poll, lib.kv_server_stats):
+        f.restype = C.c_int
+    lib._server_ready = True
+
+
+class Server:
+    """kv_server_create / kv_submit / kv_poll / kv_server_stats / kv_server_destroy.
+    The context belongs to the server's worker until close()."""
+
+    def __init__(self, ctx: Context, slots: int = 8):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        _load_server(self._lib)
+        h = C.c_void_p()
+        _check(self._lib.kv_server_create(ctx.h, C.byref(h), int(slots)))
+        self.h = h
+        self._keep: Dict[int, tuple] = {}
+
+    def submit(self, problem, *, expm_mode: str = "propagate", flags: int = 0) -> int:
+        keep: list = []
+        q = kv_query()
+        s = problem.system
+        b = getattr(s, "b", None)
+        if b is not None:
+            bb = np.ascontiguousarray(b, dtype=np.float64)
+            keep.append(bb)
+            q.b = _ptr(bb)
+        if hasattr(s, "dims"):
+            q.kind = 0
+            q.ndim = len(s.dims)
+            for a in range(3):
+                q.dims[a] = int(s.dims[a]) if a < q.ndim else 1
+                q.h[a] = float(s.h[a]) if a < q.ndim else 1.0
+            q.coef = float(s.coef)
+        else:
+            q.kind = 1
+            rp = np.ascontiguousarray(s.row_ptr, dtype=np.int64)
+            col = np.ascontiguousarray(s.col, dtype=np.int32)
+            val = np.ascontiguousarray(s.val, dtype=np.float64)
+            keep += [rp, col, val]
+            q.n = int(s.n)
+            q.row_ptr, q.col, q.val = _ptr(rp), _ptr(col), _ptr(val)
+            q.symmetric = 1 if s.symmetric else 0
+        q.desc = _desc(problem, expm_mode, False, keep, flags)
+        q.precision = _PREC[problem.precision]
+        t = C.c_uint64()
+        _check(self._lib.kv_submit(self.h, C.byref(q), C.byref(t)))
+        self._keep[t.value] = (q, keep, problem)
+        return t.value
+
+    def poll(self, ticket: int) -> Optional[Dict]:
+        """None while queued or running; the results once finished (raises
+        KvError if the query failed)."""
+        q, keep, p = self._keep[ticket]
+        S = p.steps + 1
+        out = dict(lo=np.zeros((p.o, S)), hi=np.zeros((p.o, S)), beta0=np.zeros(p.i),
+                   m_used=np.zeros(p.i, dtype=np.int32), zstar=np.zeros(p.i))
+        r = kv_result()
+        r.lo, r.hi, r.beta0, r.m_used, r.z_star = (_ptr(out["lo"]), _ptr(out["hi"]), _ptr(out["beta0"]),
+                                                   _ptr(out["m_used"]), _ptr(out["zstar"]))
+        lat = C.c_double()
+        rc = self._lib.kv_poll(self.h, ticket, C.byref(r), C.byref(lat))
+        if rc == KV_ENOTREADY:
+            return None
+        del self._keep[ticket]
+        _check(rc)
+        out["viol_step"] = int(r.first_violation_step)
+        out["viol_row"] = int(r.violation_row)
+        out["ystar"] = float(r.y_star) if out["viol_step"] >= 0 else None
+        if out["viol_step"] < 0:
+            out["zstar"] = None
+        out["latency_ms"] = float(lat.value)
+        return out
+
+    def stats(self) -> Dict:
+        a, c, pnd, mw = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        mr = C.c_int32()
+        _check(self._lib.kv_server_stats(self.h, C.byref(a), C.byref(c), C.byref(pnd), C.byref(mr), C.byref(mw)))
+        return dict(admitted=a.value, completed=c.value, pending=pnd.value, max_running=mr.value,
+                    memory_waits=mw.value)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._lib.kv_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 KV_NOALLOC_MAX_N = 262144
 
 

@@ -176,10 +176,6 @@ static int vector_sets(const Sys* s, int i) { return s->kind == 0 ? 1 : i; }
 
 using namespace kv;
 
-struct kv_ctx : public Ctx {};
-struct kv_sys : public Sys {};
-struct kv_prob : public Prob {};
-
 extern "C" {
 
 const char* kv_version(void) { return "kv 0.1 (sm_103a)"; }

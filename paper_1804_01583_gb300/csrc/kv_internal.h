@@ -197,3 +197,8 @@ int64_t reduce_slots_needed(const Prob* p);
 inline size_t elem_size(int prec) { return prec == KV_FP32 ? 4 : 8; }
 
 }  // namespace kv
+
+// the opaque handles of include/kv.h
+struct kv_ctx : public kv::Ctx {};
+struct kv_sys : public kv::Sys {};
+struct kv_prob : public kv::Prob {};

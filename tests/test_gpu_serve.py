@@ -1,0 +1,147 @@
+"""Continuous-batching server (kv_server_*, kv_submit, kv_poll).
+
+Each result must be the same alone and in the mix: queries run on their own
+streams with their own device memory and deterministic reductions, so the
+bounds are compared bit for bit -- against the same query served alone, and
+against kv_run.  FP32 results are also checked against the FP64 oracle
+(<= 1e-6 scale-normalised).
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from parity import bound_error
+
+pytestmark = pytest.mark.gpu
+
+kv = pytest.importorskip("paper_1804_01583_gb300")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1804_01583_gb300 import build as kvbuild
+    kvbuild.build()
+    return kv.load()
+
+
+def small_mix(n=16, seed=3):
+    return W.serving_mix(n, seed=seed, side2d=(40, 200), side3d=(20, 48), csr_n=(5000, 20000), steps=(50, 300),
+                         m=(10, 30))
+
+
+def wait_all(server, tickets, timeout=300.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = server.poll(t)
+                if r is not None:
+                    out[t] = r
+        if time.time() - t0 > timeout:
+            raise TimeoutError("server did not finish")
+        time.sleep(0.001)
+    return [out[t] for t in tickets]
+
+
+def test_results_identical_alone_and_in_mix(lib):
+    qs = small_mix()
+    # alone: one slot, each query waited for before the next is submitted
+    ctx1 = kv.Context(8 << 30)
+    s1 = kv.Server(ctx1, slots=1)
+    alone = []
+    for q in qs:
+        alone += wait_all(s1, [s1.submit(q)])
+    s1.close()
+    ctx1.close()
+    # in the mix: 8 slots, everything submitted at once
+    ctx2 = kv.Context(8 << 30)
+    s2 = kv.Server(ctx2, slots=8)
+    mixed = wait_all(s2, [s2.submit(q) for q in qs])
+    st = s2.stats()
+    s2.close()
+    ctx2.close()
+    assert st["completed"] == len(qs) and st["max_running"] > 1
+    # kv_run on the same queries
+    ctx3 = kv.Context(8 << 30)
+    for q, a, b in zip(qs, alone, mixed):
+        assert np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["hi"], b["hi"]), q.name
+        assert a["viol_step"] == b["viol_step"] and np.array_equal(a["m_used"], b["m_used"])
+        ref = kv.solve(q, ctx3, expm_mode="propagate")
+        assert np.array_equal(ref["hi"], b["hi"]) and np.array_equal(ref["lo"], b["lo"]), q.name
+    ctx3.close()
+
+
+def test_served_fp32_error_against_fp64_oracle(lib):
+    qs = small_mix(8, seed=11)
+    ctx = kv.Context(8 << 30)
+    s = kv.Server(ctx, slots=4)
+    res = wait_all(s, [s.submit(q) for q in qs])
+    s.close()
+    ctx.close()
+    for q, r in zip(qs, res):
+        q64 = W.Problem(**{**q.__dict__, "precision": "fp64"})
+        ref = oracle.run(q64)
+        assert bound_error(r, ref) <= 1e-6, q.name
+        assert r["latency_ms"] > 0
+
+
+def test_admission_waits_for_memory(lib):
+    """A pool that holds only a few of the queries at once: later queries wait
+    for running ones to release memory, and all complete."""
+    qs = [W.heat((64, 64, 64), block=(6, 6, 6), output="centre", dt=0.02, steps=100, m=20, precision="fp32")
+          for _ in range(10)]
+    ctx = kv.Context(10 << 20)  # ~3 MB per query (three 1 MB vectors + state)
+    s = kv.Server(ctx, slots=8)
+    res = wait_all(s, [s.submit(q) for q in qs])
+    st = s.stats()
+    s.close()
+    ctx.close()
+    assert st["completed"] == 10 and st["memory_waits"] > 0 and st["max_running"] < 8
+    for r in res[1:]:
+        assert np.array_equal(r["hi"], res[0]["hi"])
+
+
+def test_query_larger_than_the_pool_fails_and_server_continues(lib):
+    ctx = kv.Context(4 << 20)
+    s = kv.Server(ctx, slots=2)
+    big = W.heat((200, 200, 200), block=(4, 4, 4), output="centre", dt=0.02, steps=10, m=5, precision="fp32")
+    ok = W.heat((24, 24), block=(3, 3), output="centre", dt=0.1, steps=10, m=5, precision="fp32")
+    tb = s.submit(big)
+    to = s.submit(ok)
+    t0 = time.time()
+    err = None
+    while True:
+        try:
+            r = s.poll(tb)
+        except kv.KvError as e:
+            err = e
+            break
+        assert r is None and time.time() - t0 < 60
+        time.sleep(0.001)
+    assert err.code == kv.KV_ENOMEM
+    assert wait_all(s, [to])[0]["hi"].shape == (1, 11)
+    s.close()
+    ctx.close()
+
+
+def test_unknown_ticket(lib):
+    ctx = kv.Context(1 << 20)
+    s = kv.Server(ctx, slots=1)
+    q = W.heat((8, 8), block=(2, 2), output="centre", dt=0.1, steps=4, m=4)
+    t = s.submit(q)
+    wait_all(s, [t])
+    res = kv.kv_result()
+    out = np.zeros(5)
+    res.lo = out.ctypes.data
+    res.hi = out.ctypes.data
+    rc = lib.kv_poll(s.h, 987654321, res, None)
+    assert rc == kv.KV_EINVAL
+    s.close()
+    ctx.close()

@@ -248,6 +248,15 @@ def random_csr_problem(n: int = 2_000_000, *, seed: int = 0, n_gen: int = 16, o:
     generator per variable) plus the fixed centre column (zero state, constant
     variable 1); C = o random +-1 rows over c_width distinct variables."""
     sysm = random_csr(n, seed=seed, with_b=with_b)
+    return csr_problem_on(sysm, seed=seed, n_gen=n_gen, o=o, c_width=c_width, dt=dt, steps=steps, m=m,
+                          theta=theta, precision=precision, name=name)
+
+
+def csr_problem_on(sysm: CsrSystem, *, seed: int, n_gen: int = 16, o: int = 2, c_width: int = 1000,
+                   dt: float = 0.01, steps: int = 2000, m: int = 60, theta: Optional[Sequence[float]] = None,
+                   precision: str = "fp64", name: str = "") -> Problem:
+    """The initial set and outputs of random_csr_problem on a given system."""
+    n = sysm.n
     rng = np.random.default_rng(seed + 7919)
     gvars = rng.choice(n, size=n_gen, replace=False)
     cols = [Column(kind="sparse", zlo=-1.0, zhi=1.0, idx=np.array([v], dtype=np.int64),
@@ -355,3 +364,45 @@ def column_dense(col: Column, n: int, dims: Optional[Sequence[int]] = None) -> n
     else:
         raise ValueError(col.kind)
     return v
+
+
+# --------------------------------------------------------------------------
+# serving stream
+# --------------------------------------------------------------------------
+def serving_mix(n_queries: int = 512, seed: int = 0, *, side2d=(100, 2000), side3d=(100, 400),
+                csr_n=(100_000, 2_000_000), csr_sizes: int = 5, gens=(1, 32), steps=(100, 2000), m=(20, 60),
+                precision: str = "fp32") -> List[Problem]:
+    """A seeded mix of verification queries, one third each:
+      * 2D heat, side log-uniform in side2d (n = side^2), block side/4, centre output, dt 0.1;
+      * 3D heat, side log-uniform in side3d, block side/10, centre output, dt 0.02;
+      * random CSR systems of random_csr (sizes log-spaced in csr_n, `csr_sizes`
+        distinct systems shared by the queries), `gens` unit generators plus the
+        fixed column, two +-1 output rows, dt 0.01;
+    horizons uniform in `steps`, Krylov dimension uniform in `m`, thresholds +inf.
+    """
+    rng = np.random.default_rng(seed + 4242)
+    sizes = sorted(set(int(round(x)) for x in np.geomspace(csr_n[0], csr_n[1], csr_sizes)))
+    cache: dict = {}
+    out: List[Problem] = []
+    for q in range(n_queries):
+        kind = int(rng.integers(3))
+        st = int(rng.integers(steps[0], steps[1] + 1))
+        mm = int(rng.integers(m[0], m[1] + 1))
+        if kind == 0:
+            side = int(round(math.exp(rng.uniform(math.log(side2d[0]), math.log(side2d[1])))))
+            b = max(side // 4, 1)
+            out.append(heat((side, side), block=(b, b), output="centre", dt=0.1, steps=st, m=mm,
+                            precision=precision, name=f"q{q}-heat2d-{side}"))
+        elif kind == 1:
+            side = int(round(math.exp(rng.uniform(math.log(side3d[0]), math.log(side3d[1])))))
+            b = max(side // 10, 1)
+            out.append(heat((side, side, side), block=(b, b, b), output="centre", dt=0.02, steps=st, m=mm,
+                            precision=precision, name=f"q{q}-heat3d-{side}"))
+        else:
+            n = sizes[int(rng.integers(len(sizes)))]
+            if n not in cache:
+                cache[n] = random_csr(n, seed=1000 + len(cache))
+            g = int(rng.integers(gens[0], gens[1] + 1))
+            out.append(csr_problem_on(cache[n], seed=q, n_gen=g, o=2, c_width=min(1000, n // 4), dt=0.01,
+                                      steps=st, m=mm, precision=precision, name=f"q{q}-csr-{n}-g{g}"))
+    return out
