@@ -304,6 +304,91 @@ def profiled_traffic(kernel: str, p):
         return None
 
 
+def serve_bench(args, dev: int):
+    """The serving stream: a seeded mix of queries (2D heat n = 1e4..4e6, 3D heat
+    n = 1e6..6.4e7, random CSR n = 1e5..2e6 with 1..32 generators; horizons
+    100..2000 steps, m 20..60; FP32 storage) through the continuous-batching
+    server.  A burst of all queries measures capacity; then Poisson arrivals at
+    0.8 x capacity give queries/s and the p50 / p99 latency from kv_submit to
+    the results on the host.  The FP32 bounds are compared with the FP64 oracle
+    on the smallest queries and with the FP64 GPU path (parity-tested against the
+    oracle) on a random sample."""
+    import torch
+    import paper_1804_01583_gb300 as kv
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import bound_error
+
+    qs = W.serving_mix(args.serve_queries, seed=0)
+    ctx = kv.Context(args.serve_pool_gb << 30, device=dev)
+    srv = kv.Server(ctx, slots=args.serve_slots)
+
+    def drain(tickets, results, t_start):
+        done = 0
+        for t in list(tickets):
+            r = srv.poll(t)
+            if r is not None:
+                results[tickets.pop(t)] = r
+                done += 1
+        return done
+
+    # capacity: everything at once
+    t0 = time.perf_counter()
+    pend = {srv.submit(q): k for k, q in enumerate(qs)}
+    burst = {}
+    while pend:
+        drain(pend, burst, t0)
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    cap = len(qs) / makespan
+    # Poisson arrivals at 0.8 x capacity
+    rate = 0.8 * cap
+    rng = np.random.default_rng(12345)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(qs)))
+    pend, res = {}, {}
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(qs) or pend:
+        now = time.perf_counter() - t0
+        while k < len(qs) and arrivals[k] <= now:
+            pend[srv.submit(qs[k])] = k
+            k += 1
+        drain(pend, res, t0)
+        time.sleep(0.0002)
+    elapsed = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([res[i]["latency_ms"] for i in range(len(qs))])
+    # accuracy of the FP32 results
+    # oracle sample: the smallest queries whose bounds are not all zero (an
+    # output cell beyond stencil reach of the block gives exact zeros)
+    order = sorted(range(len(qs)), key=lambda i: qs[i].system.n * qs[i].i * qs[i].m)
+    picked = [i for i in order if np.any(res[i]["hi"] != 0.0)][:6]
+    err_oracle = 0.0
+    for i in picked:
+        q64 = W.Problem(**{**qs[i].__dict__, "precision": "fp64"})
+        err_oracle = max(err_oracle, bound_error(res[i], oracle.run(q64)))
+    sample = np.random.default_rng(7).choice(len(qs), size=min(24, len(qs)), replace=False)
+    err_gpu64 = 0.0
+    for i in sample:
+        q64 = W.Problem(**{**qs[int(i)].__dict__, "precision": "fp64"})
+        err_gpu64 = max(err_gpu64, bound_error(res[int(i)], kv.solve(q64, ctx, expm_mode="propagate")))
+    ctx.close()
+    kinds = {"heat2d": 0, "heat3d": 0, "csr": 0}
+    for q in qs:
+        for kk in kinds:
+            if f"-{kk}" in q.name:
+                kinds[kk] += 1
+    return {"queries": len(qs), "mix": kinds, "slots": args.serve_slots, "pool_gb": args.serve_pool_gb,
+            "capacity_qps": cap, "arrival_rate_qps": rate, "queries_per_s": len(qs) / elapsed,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_running": st["max_running"], "memory_waits": st["memory_waits"],
+            "max_rel_bound_err_vs_fp64_oracle": err_oracle,
+            "oracle_sample": [qs[i].name for i in picked],
+            "max_rel_bound_err_vs_fp64_gpu": err_gpu64, "fp64_gpu_sample": f"{len(sample)} random queries",
+            "precision": "fp32 storage, fp64 accumulation"}
+
+
 def kv_bytes_guess(p) -> int:
     # the larger of the FP32 form (three float vectors) and the FP64 two-pass
     # form (two double vectors), which may run on the same context
@@ -322,6 +407,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=24)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--no-serve", dest="serve", action="store_false")
+    ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--serve-queries", type=int, default=512)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-pool-gb", type=int, default=160)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -352,7 +442,17 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.serve_only:
+        import torch
+        from paper_1804_01583_gb300 import build as kvbuild
+        kvbuild.build()
+        dev = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(dev)
+        print(json.dumps({"metric": "serving queries/s", "serving": serve_bench(args, dev)}))
+        return
     line, p = run_gpu(args, rank, world)
+    if args.serve and world == 1:
+        line["serving"] = serve_bench(args, int(os.environ.get("LOCAL_RANK", "0")))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload(args.workload, "fp64"), iters=args.cpu_iters)
     if rank == 0:
