@@ -23,8 +23,8 @@
 // consecutive x 4l..4l+3).  Per plane one elected thread issues TMA tile loads
 // (cp.async.bulk.tensor, completion counted on an mbarrier) of v_j (2 rows of
 // halo below, 1 above; x from x0-8) and v_{j-1} into a shared-memory ring
-// three planes ahead of the compute (two CTAs per SM, so six stages in flight
-// per SM); TMA fills coordinates outside the grid
+// four planes ahead of the compute (two CTAs per SM, so eight stages, about
+// 144 KB, in flight per SM); TMA fills coordinates outside the grid
 // with zeros, which is the Dirichlet-0 boundary.  The x-1 neighbour of w comes
 // from the next lane (shuffle), y-1 from the warp's own other row or the
 // shared w plane, z-1 from registers kept from the previous plane.  w goes to
@@ -51,7 +51,7 @@ constexpr int TXI = 124, TYI = 15;      // interior points of a tile
 constexpr int WC = 128, WR = 16;        // w region: x0-4 .. x0+123, y0-1 .. y0+14
 constexpr int BBW = 136, BBH = 18;      // v_j box: x0-8 .. x0+127, y0-2 .. y0+15
 constexpr int ABW = 128, ABH = 16;      // v_{j-1} box: x0-4 .. x0+123, y0-1 .. y0+14
-constexpr int DEPTH = 3;                // stages in flight (x 2 CTAs per SM)
+constexpr int DEPTH = 4;                // stages in flight (x 2 CTAs per SM)
 constexpr int RB = DEPTH + 2, RA = DEPTH;
 constexpr int BBYTES = BBW * BBH * 4;   // 9792
 constexpr int ABYTES = ABW * ABH * 4;   // 8192
