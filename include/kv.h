@@ -220,6 +220,23 @@ int kv_profile_read(kv_ctx *ctx, const char *name, int64_t *launches, double *to
 /* Number of kernel launches the context has issued since creation. */
 int kv_launch_count(const kv_ctx *ctx, int64_t *launches);
 
+/* ------------------------------------------------------- packed queries --
+ * Many small problems under one CUDA graph.  A small query is dozens of tiny
+ * kernels whose cost is launch latency; kv_graph_create records the whole
+ * path of n problems (all created on ctx, any mix of systems) by stream
+ * capture, with the problems on up to KV_GRAPH_BRANCHES parallel branches, and
+ * kv_graph_launch replays everything with one graph launch on the context
+ * stream.  After a launch each problem's results are read with kv_fetch, as
+ * after kv_enqueue.  The graph holds the problems' device buffers: destroy it
+ * before any of its problems, and do not enqueue those problems elsewhere
+ * while a launch is in flight.  Per-kernel profiling must be off while
+ * capturing.  Errors: KV_EINVAL, KV_ECUDA. */
+#define KV_GRAPH_BRANCHES 8
+typedef struct kv_graph kv_graph;
+int kv_graph_create(kv_ctx *ctx, kv_prob *const *probs, int32_t n, kv_graph **out);
+int kv_graph_launch(kv_graph *graph);
+int kv_graph_destroy(kv_graph *graph);
+
 /* ------------------------------------------------------------- serving --
  * Continuous batching of verification queries on one context.  The paper
  * verifies one problem at a time; the server keeps several on the device at

@@ -310,6 +310,41 @@ class ProblemHandle:
             pass
 
 
+class Graph:
+    """kv_graph_create / kv_graph_launch / kv_graph_destroy over ProblemHandles
+    created on the same context."""
+
+    def __init__(self, ctx: Context, handles):
+        self.ctx = ctx
+        lib = ctx._lib
+        if not getattr(lib, "_graph_ready", False):
+            lib.kv_graph_create.argtypes = [C.c_void_p, C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]
+            lib.kv_graph_launch.argtypes = [C.c_void_p]
+            lib.kv_graph_destroy.argtypes = [C.c_void_p]
+            for f in (lib.kv_graph_create, lib.kv_graph_launch, lib.kv_graph_destroy):
+                f.restype = C.c_int
+            lib._graph_ready = True
+        self.handles = list(handles)
+        arr = (C.c_void_p * len(self.handles))(*[h.h.value for h in self.handles])
+        g = C.c_void_p()
+        _check(lib.kv_graph_create(ctx.h, arr, len(self.handles), C.byref(g)))
+        self.h = g
+
+    def launch(self):
+        _check(self.ctx._lib.kv_graph_launch(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.ctx._lib.kv_graph_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class kv_query(C.Structure):
     _fields_ = [("kind", C.c_int32), ("ndim", C.c_int32), ("dims", C.c_int64 * 3), ("coef", C.c_double),
                 ("h", C.c_double * 3), ("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),

@@ -263,17 +263,31 @@ static int upload_coeffs(int device) {
     return KV_OK;
 }
 
+// One-time set-up per process and device: the Pade coefficients in constant
+// memory and the shared-memory limit of both kernels (for the largest m).
+// Neither may run during stream capture, so graph capture calls this first.
+int expm_prepare(int device) {
+    int rc = upload_coeffs(device);
+    if (rc != KV_OK) return rc;
+    static bool attr_set = false;
+    if (!attr_set) {
+        const int smax = 6 * KV_MAX_M * KV_MAX_M * (int)sizeof(double);
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_per_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+        attr_set = true;
+    }
+    return KV_OK;
+}
+
 int launch_expm_basis(Prob* p) {
-    int rc = upload_coeffs(p->ctx->device);
+    int rc = expm_prepare(p->ctx->device);
     if (rc != KV_OK) return rc;
     ExpmArgs a{p->d_H, p->d_P, p->d_state, p->d_basis, p->m, p->o, p->steps, p->dt};
     const size_t smem = (size_t)6 * p->m * p->m * sizeof(double);
     if (p->expm_mode == KV_EXPM_PROPAGATE) {
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         LaunchScope ls(p->ctx, "expm_propagate");
         k_expm_propagate<<<p->i, ENT, smem, p->ctx->stream>>>(a);
     } else {
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_per_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int gx = p->steps + 1;
         if (gx > 65535 * 16) gx = 65535 * 16;
         dim3 grd((unsigned)gx, (unsigned)p->i);

@@ -393,6 +393,19 @@ static int make_map(CUtensorMap* m, void* base, const Sys* s, int box_w, int box
     return KV_OK;
 }
 
+// One-time shared-memory limit of the kernel (not allowed during capture).
+int fused_prepare() {
+    static bool attr_set = false;
+    if (!attr_set) {
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SMEM_TOTAL));
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SMEM_TOTAL));
+        attr_set = true;
+    }
+    return KV_OK;
+}
+
 int fused_tma_blocks(const Prob* p, int* zc_out) {
     const Sys* s = p->sys;
     const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
@@ -436,12 +449,8 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     a.m = p->m;
     a.j = it;
     a.red = p->red;
-    static bool attr_set = false;
-    if (!attr_set) {
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
-        attr_set = true;
-    }
+    rc = fused_prepare();
+    if (rc) return rc;
     LaunchScope ls(p->ctx, "lanczos_fused");
     if (it == 0)
         k_lanczos_fused_tma<true><<<grd, FNT, SMEM_TOTAL, p->ctx->stream>>>(mB, mA, a);

@@ -187,6 +187,10 @@ size_t csr_arnoldi_dev_bytes();
 
 // exponential + basis (k_expm.cu)
 int launch_expm_basis(Prob* p);
+int expm_prepare(int device);
+int fused_prepare();
+// one-time set-up that stream capture cannot contain (kv_graph.cu)
+int prepare_for_capture(int device);
 
 // bounds (k_bounds.cu)
 int launch_bounds(Prob* p);
