@@ -389,6 +389,97 @@ def serve_bench(args, dev: int):
             "precision": "fp32 storage, fp64 accumulation"}
 
 
+def batched_bench(dev: int, nq: int = 64, reps: int = 5):
+    """Small queries (the 20 x 20 heat configuration, FP64, m = 30, 500 steps):
+    nq of them enqueued one after another on the context stream, against the
+    same nq packed under one captured CUDA graph (kv_graph_*)."""
+    import torch
+    import paper_1804_01583_gb300 as kv
+    qs = [W.heat2d_20() for _ in range(nq)]
+    ctx = kv.Context(1 << 30, device=dev)
+    systems = [kv.System(ctx, q.system, q.precision) for q in qs]
+    handles = [kv.ProblemHandle(ctx, s, q) for s, q in zip(systems, qs)]
+    g = kv.Graph(ctx, handles)
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            for h in handles[-1:]:
+                h.fetch(full=False)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return statistics.median(ts[1:])
+
+    t_ind = timed(lambda: [h.enqueue() for h in handles])
+    t_graph = timed(g.launch)
+    same = all(np.array_equal(h.fetch(full=False)["hi"], handles[0].fetch(full=False)["hi"]) for h in handles)
+    g.close()
+    for h in handles:
+        h.close()
+    for s in systems:
+        s.close()
+    ctx.close()
+    return {"workload": "heat2d-20x20 fp64 m=30 500 steps", "queries": nq, "ms_enqueued_one_by_one": t_ind,
+            "ms_packed_graph": t_graph, "speedup": t_ind / t_graph, "queries_per_s_graph": nq / t_graph * 1e3,
+            "results_identical": bool(same)}
+
+
+def arnoldi_bytes(p) -> float:
+    """Algorithmic bytes of the random-CSR Arnoldi run: per column and
+    iteration j the SpMV (matrix values and column indices, one read of the
+    input vector, one write), the dots pass (j+2 vectors) and the update pass
+    (j+1 vectors read, w read and written)."""
+    es = 8 if p.precision == "fp64" else 4
+    s = p.system
+    nnz = int(s.row_ptr[-1])
+    N = s.n + (1 if s.b is not None else 0)
+    tot = 0.0
+    for _ in range(p.i):
+        for j in range(p.m):
+            tot += nnz * (4 + es) + 2 * N * es + (j + 2) * N * es + (j + 3) * N * es
+    return tot
+
+
+def csr_bench(args, dev: int):
+    """The random-CSR workload (n = 2e6, 16 generators + the fixed column,
+    m = 60, 2000 steps) in FP64 and FP32: time per query, Arnoldi GB/s."""
+    import torch
+    import paper_1804_01583_gb300 as kv
+    out = {}
+    for prec in ("fp64", "fp32"):
+        p = W.random_csr_problem(2_000_000, seed=0, precision=prec)
+        ctx = kv.Context(40 << 30, device=dev)
+        sysh = kv.System(ctx, p.system, p.precision)
+        ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
+        ph.enqueue()
+        ph.fetch(full=False)
+        ctx.profile_enable(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = 2
+        for _ in range(k):
+            ph.enqueue()
+        ph.fetch(full=False)
+        ms = (time.perf_counter() - t0) * 1e3 / k
+        kern = {}
+        for name in ["csr_spmm", "csr_spmv", "arnoldi_dots", "arnoldi_update", "expm_propagate", "init_norm",
+                     "scatter"]:
+            nl, tms = ctx.profile_read(name)
+            if nl:
+                kern[name] = {"launches": nl // k, "ms_per_query": tms / k}
+        ph.close()
+        sysh.close()
+        ctx.close()
+        out[prec] = {"ms_per_query": ms, "arnoldi_GBps": arnoldi_bytes(p) / (ms * 1e-3) / 1e9,
+                     "arnoldi_steps_per_s": p.i * p.m / (ms * 1e-3), "kernels": kern}
+    out["speedup_fp32_over_fp64"] = out["fp64"]["ms_per_query"] / out["fp32"]["ms_per_query"]
+    out["workload"] = "random CSR n=2e6, 10 off-diagonal nnz/row, i=17 (16 generators + fixed), o=2, m=60, 2000 steps"
+    return out
+
+
 def kv_bytes_guess(p) -> int:
     # the larger of the FP32 form (three float vectors) and the FP64 two-pass
     # form (two double vectors), which may run on the same context
@@ -408,6 +499,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=24)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-serve", dest="serve", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-csr", dest="csr", action="store_false")
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--serve-queries", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=16)
@@ -451,8 +544,13 @@ def main():
         print(json.dumps({"metric": "serving queries/s", "serving": serve_bench(args, dev)}))
         return
     line, p = run_gpu(args, rank, world)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.batched and world == 1:
+        line["batched"] = batched_bench(dev)
+    if args.csr and world == 1:
+        line["csr_workload"] = csr_bench(args, dev)
     if args.serve and world == 1:
-        line["serving"] = serve_bench(args, int(os.environ.get("LOCAL_RANK", "0")))
+        line["serving"] = serve_bench(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload(args.workload, "fp64"), iters=args.cpu_iters)
     if rank == 0:

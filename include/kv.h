@@ -123,6 +123,10 @@ typedef struct {
 /* kv_problem_desc.flags */
 #define KV_FLAG_TWO_PASS 1      /* grid Lanczos: use the two-pass kernels even where
                                    the single-pass TMA iteration applies */
+#define KV_FLAG_NO_SPMM 2       /* CSR Arnoldi: one SpMV per column instead of the
+                                   grouped SpMM (matrix read once per group) */
+#define KV_FLAG_NO_AUTOTUNE 4   /* CSR Arnoldi: fixed SpMM shape instead of timing the
+                                   candidates at kv_problem (and the on-disk cache) */
 
 #define KV_MAX_M 64
 

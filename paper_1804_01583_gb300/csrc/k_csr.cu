@@ -22,6 +22,10 @@
 //
 // All scalars stay on the device; the last block of each pass finishes the
 // deterministic reduction and writes them.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <string>
 #include <type_traits>
 
 #include "kv_internal.h"
@@ -30,8 +34,19 @@
 namespace kv {
 
 constexpr int CNT = 256;           // threads per block
-constexpr int CR = 8;              // rows per thread in the Gram-Schmidt passes
-constexpr int CCHUNK = CNT * CR;   // rows per block
+// rows per thread in the Gram-Schmidt passes: each basis vector's per-thread
+// partial is reduced across the warp in double, so the FP32 form takes more
+// rows per thread to keep those double adds rare (the FP64 pipe is 1/64 of
+// the float pipe); the FP64 form is bound by its FMAs either way
+template <typename T>
+struct RowsPer {
+    static constexpr int v = 8;
+};
+template <>
+struct RowsPer<float> {
+    static constexpr int v = 32;
+};
+constexpr int CCHUNK_MIN = CNT * 8;  // smallest rows per block (sizes the partials)
 
 struct ArnoldiDev {  // per-column device scratch of the Arnoldi passes
     double g[KV_MAX_M + 1][KV_MAX_M + 1];  // Gram matrix of the stored basis (normalised)
@@ -87,6 +102,103 @@ __global__ void __launch_bounds__(CNT) k_spmv(const int64_t* __restrict__ rp, co
     if (!grid_arrive(part, partials + cidx * nbx, counters + cidx, blockIdx.x, gridDim.x, &flag)) return;
     const double tot = grid_finish<CNT>(partials + cidx * nbx, gridDim.x, counters + cidx, sh);
     if (threadIdx.x == 0) H[(int64_t)cidx * (m + 1) * m + (int64_t)j * m + j] = tot;  // alpha_j
+}
+
+// ------------------------------------------------------------------ SpMM --
+// W_c = s_c A' X_c for a group of G columns of a run (blockIdx.y = group):
+// each row's values and column indices are read once for the G columns, and
+// LPR lanes share a row (consecutive entries, combined by shuffles).  The
+// group size and lanes per row are chosen per system by the autotuner.
+template <typename T, int G, int LPR>
+__global__ void __launch_bounds__(CNT) k_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                              const T* __restrict__ val, const double* __restrict__ b, VecArgs<T> V,
+                                              int xslot, int wslot, int64_t n, int64_t N, const int* aug,
+                                              const ColState* st, int j, int ncols) {
+    const int cg0 = blockIdx.y * G;
+    // the group's columns: X_k = xbase + k * cstride, W_k likewise
+    const T* xbase = V.base + (int64_t)cg0 * V.cstride + (int64_t)xslot * N;
+    T* wbase = V.base + (int64_t)cg0 * V.cstride + (int64_t)wslot * N;
+    double sc[G];
+    bool act[G], ag[G];
+    int64_t off[G];  // inactive slots (past the run, or broken down) read the group's first column
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        const int c = cg0 + k;
+        act[k] = c < ncols && !st[c].done;
+        sc[k] = act[k] ? st[c].s[j] : 0.0;
+        ag[k] = act[k] && aug[c] != 0;
+        off[k] = act[k] ? (int64_t)k * V.cstride : 0;
+    }
+    const int lane = threadIdx.x & 31, sub = lane % LPR;
+    constexpr int WR = 32 / LPR;  // rows per warp per step
+    const int64_t gw = ((int64_t)blockIdx.x * CNT + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t)gridDim.x * (CNT / 32);
+    // warp-uniform loop: every lane reaches every shuffle
+    for (int64_t rb = gw * WR; rb < N; rb += nw * WR) {
+        const int64_t r = rb + lane / LPR;
+        const bool inrow = r < n;
+        const int64_t e0 = inrow ? rp[r] : 0, e1 = inrow ? rp[r + 1] : 0;
+        if constexpr (std::is_same<T, float>::value) {
+            Dot2f d[G];
+            for (int64_t e = e0 + sub; e < e1; e += LPR) {
+                const float v = val[e];
+                const int c = col[e];
+#pragma unroll
+                for (int k = 0; k < G; ++k) d[k].add_prod(v, xbase[off[k] + c]);
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+#pragma unroll
+                for (int o = LPR / 2; o > 0; o >>= 1) {  // error-free combination of lane pairs
+                    const float s2 = __shfl_down_sync(0xffffffffu, d[k].s, o, LPR);
+                    const float c2 = __shfl_down_sync(0xffffffffu, d[k].c, o, LPR);
+                    const float t = __fadd_rn(d[k].s, s2);
+                    const float z = __fadd_rn(t, -d[k].s);
+                    const float err = __fadd_rn(__fadd_rn(d[k].s, -__fadd_rn(t, -z)), __fadd_rn(s2, -z));
+                    d[k].s = t;
+                    d[k].c = __fadd_rn(__fadd_rn(d[k].c, c2), err);
+                }
+            }
+            if (sub == 0 && r < N) {
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (!act[k]) continue;
+                    double y = 0.0;  // row n of A' (constant variable) is zero
+                    if (inrow) {
+                        y = d[k].value();
+                        if (ag[k] && b) y = fma(b[r], (double)xbase[off[k] + n], y);
+                    }
+                    wbase[k * V.cstride + r] = (T)(sc[k] * y);
+                }
+            }
+        } else {
+            double d[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) d[k] = 0.0;
+            for (int64_t e = e0 + sub; e < e1; e += LPR) {
+                const double v = val[e];
+                const int c = col[e];
+#pragma unroll
+                for (int k = 0; k < G; ++k) d[k] = fma(v, xbase[off[k] + c], d[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+#pragma unroll
+                for (int o = LPR / 2; o > 0; o >>= 1) d[k] += __shfl_down_sync(0xffffffffu, d[k], o, LPR);
+            if (sub == 0 && r < N) {
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (!act[k]) continue;
+                    double y = 0.0;
+                    if (inrow) {
+                        y = d[k];
+                        if (ag[k] && b) y = fma(b[r], (double)xbase[off[k] + n], y);
+                    }
+                    wbase[k * V.cstride + r] = (T)(sc[k] * y);
+                }
+            }
+        }
+    }
 }
 
 // gather of C x by a whole block; result in thread 0
@@ -174,7 +286,8 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
     const T* Vj = Vc + (int64_t)j * N;
     __shared__ double wsum[2 * (KV_MAX_M + 1)][CNT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * CCHUNK + threadIdx.x;
+    constexpr int CR = RowsPer<T>::v;
+    const int64_t r0 = (int64_t)blockIdx.x * (CNT * CR) + threadIdx.x;
     // FP64 form: double products; FP32 form: each thread's CR products summed
     // in float (one rounding per product and add), then one double add per
     // basis vector -- the FP64 pipe is 1/64 of the float pipe on this GPU
@@ -259,7 +372,8 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_update(VecArgs<T> V, int64_t N,
     __shared__ double cf[KV_MAX_M + 1];
     for (int l = threadIdx.x; l <= j; l += CNT) cf[l] = A->c[l];
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * CCHUNK + threadIdx.x;
+    constexpr int CR = 8;  // no per-vector reduction here: short rows keep occupancy
+    const int64_t r0 = (int64_t)blockIdx.x * (CNT * CR) + threadIdx.x;
     T wv[CR];
 #pragma unroll
     for (int k = 0; k < CR; ++k) {
@@ -307,7 +421,11 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_update(VecArgs<T> V, int64_t N,
 }
 
 // ------------------------------------------------------------ launchers --
-static int64_t row_blocks(int64_t N) { return (N + CCHUNK - 1) / CCHUNK; }
+static int64_t row_blocks(int64_t N) { return (N + CCHUNK_MIN - 1) / CCHUNK_MIN; }
+template <typename T>
+static int64_t row_blocks_t(int64_t N) {
+    return (N + CNT * RowsPer<T>::v - 1) / (CNT * RowsPer<T>::v);
+}
 static int64_t spmv_blocks(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
     return b > 152 * 16 ? 152 * 16 : b;
@@ -319,6 +437,143 @@ int64_t csr_scratch_slots(int64_t N) {  // reduction partials per column
 }
 
 size_t csr_arnoldi_dev_bytes() { return sizeof(ArnoldiDev); }
+
+// ------------------------------------------------------- SpMM dispatch --
+template <typename T, int G, int LPR>
+static void spmm_launch(const Prob* p, VecArgs<T> va, int xslot, int wslot, const int* aug, const ColState* st,
+                        int j, int ncols, cudaStream_t s) {
+    const Sys* sy = p->sys;
+    const int64_t rows_per_block = CNT / LPR;
+    int64_t gx = (p->N + rows_per_block - 1) / rows_per_block;
+    if (gx > 152 * 16) gx = 152 * 16;
+    dim3 grd((unsigned)gx, (unsigned)((ncols + G - 1) / G));
+    k_spmm<T, G, LPR><<<grd, CNT, 0, s>>>(sy->d_rp, sy->d_col, (const T*)sy->d_val, sy->d_b, va, xslot, wslot,
+                                          sy->n, p->N, aug, st, j, ncols);
+}
+
+template <typename T>
+static bool spmm_dispatch(const Prob* p, int G, int LPR, VecArgs<T> va, int xslot, int wslot, const int* aug,
+                          const ColState* st, int j, int ncols, cudaStream_t s) {
+#define KV_SPMM_CASE(g, l)                                                  \
+    if (G == g && LPR == l) {                                               \
+        spmm_launch<T, g, l>(p, va, xslot, wslot, aug, st, j, ncols, s);    \
+        return true;                                                        \
+    }
+    KV_SPMM_CASE(1, 1) KV_SPMM_CASE(1, 2) KV_SPMM_CASE(1, 4)
+    KV_SPMM_CASE(2, 1) KV_SPMM_CASE(2, 2) KV_SPMM_CASE(2, 4)
+    KV_SPMM_CASE(4, 1) KV_SPMM_CASE(4, 2) KV_SPMM_CASE(4, 4)
+    KV_SPMM_CASE(8, 1) KV_SPMM_CASE(8, 2) KV_SPMM_CASE(8, 4)
+#undef KV_SPMM_CASE
+    return false;
+}
+
+// ----------------------------------------------------------- autotuner --
+// Picks the SpMM group size G (columns per matrix read) and lanes per row
+// for a CSR problem by timing every candidate on the problem's own buffers
+// (CUDA events on the context stream) at problem creation.  Candidates keep
+// the G input vectors of a group within about 96 MB so the column gathers
+// stay in L2.  Results are cached in a text file (KV_AUTOTUNE_CACHE, default
+// $HOME/.cache/kv_autotune.txt) keyed by device, rows, nonzeros, element size
+// and column count.
+static std::string tune_cache_path() {
+    const char* e = getenv("KV_AUTOTUNE_CACHE");
+    if (e && *e) return e;
+    const char* h = getenv("HOME");
+    return std::string(h ? h : "/tmp") + "/.cache/kv_autotune.txt";
+}
+
+static std::string tune_key(const Prob* p, int ncols) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, p->ctx->device);
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s|%d.%d|n=%lld|N=%lld|nnz=%lld|es=%zu|cols=%d", prop.name, prop.major, prop.minor,
+             (long long)p->sys->n, (long long)p->N, (long long)p->sys->nnz, elem_size(p->prec), ncols);
+    for (char* c = buf; *c; ++c)
+        if (*c == ' ') *c = '_';
+    return buf;
+}
+
+template <typename T>
+static int autotune_t(Prob* p, int ncols, void* V) {
+    const std::string key = tune_key(p, ncols);
+    const std::string path = tune_cache_path();
+    if (FILE* f = fopen(path.c_str(), "r")) {
+        char k[512];
+        int g, l;
+        double us;
+        while (fscanf(f, "%511s %d %d %lf", k, &g, &l, &us) == 4) {
+            if (key == k) {
+                p->spmm_G = g;
+                p->spmm_LPR = l;
+            }
+        }
+        fclose(f);
+        if (p->spmm_G > 0) return KV_OK;
+    }
+    cudaStream_t s = p->ctx->stream;
+    VecArgs<T> va{(T*)V, (int64_t)p->nvec * p->N};
+    cudaEvent_t e0, e1;
+    KV_CHECK_CUDA(cudaEventCreate(&e0));
+    KV_CHECK_CUDA(cudaEventCreate(&e1));
+    const double l2_budget = 96.0 * 1024 * 1024;
+    double best = 1e30;
+    int bg = 1, bl = 1;
+    const int Gs[4] = {1, 2, 4, 8}, Ls[3] = {1, 2, 4};
+    for (int gi = 0; gi < 4; ++gi) {
+        const int G = Gs[gi];
+        if (G > 1 && (G > ncols || (double)G * p->N * sizeof(T) > l2_budget)) continue;
+        for (int li = 0; li < 3; ++li) {
+            const int L = Ls[li];
+            spmm_dispatch<T>(p, G, L, va, 0, 1, p->d_aug, p->d_state, 0, ncols, s);
+            KV_CHECK_CUDA(cudaEventRecord(e0, s));
+            for (int q = 0; q < 3; ++q) spmm_dispatch<T>(p, G, L, va, 0, 1, p->d_aug, p->d_state, 0, ncols, s);
+            KV_CHECK_CUDA(cudaEventRecord(e1, s));
+            KV_CHECK_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            KV_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bg = G;
+                bl = L;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    KV_CHECK_CUDA(cudaGetLastError());
+    p->spmm_G = bg;
+    p->spmm_LPR = bl;
+    const std::string dir = path.substr(0, path.find_last_of('/'));
+    (void)!system(("mkdir -p '" + dir + "' 2>/dev/null").c_str());
+    if (FILE* f = fopen(path.c_str(), "a")) {
+        fprintf(f, "%s %d %d %.3f\n", key.c_str(), bg, bl, best * 1000.0 / 3.0);
+        fclose(f);
+    }
+    return KV_OK;
+}
+
+// Called by kv_problem for CSR problems whose Arnoldi columns run as one group.
+int csr_autotune(Prob* p) {
+    int narn = 0;
+    for (int j = 0; j < p->i; ++j) narn += p->method[j] == KV_ARNOLDI;
+    p->spmm_G = 0;
+    p->spmm_LPR = 0;
+    if (narn == 0) return KV_OK;
+    if ((p->flags & KV_FLAG_NO_AUTOTUNE) || p->N < 65536) {  // small systems: a fixed choice
+        p->spmm_G = narn >= 4 ? 4 : (narn >= 2 ? 2 : 1);
+        p->spmm_LPR = 2;
+        return KV_OK;
+    }
+    // the first Arnoldi column's vector set starts the timed group
+    int j0 = 0;
+    while (p->method[j0] != KV_ARNOLDI) ++j0;
+    int run = 0;
+    while (j0 + run < p->i && p->method[j0 + run] == KV_ARNOLDI) ++run;
+    KV_CHECK_CUDA(cudaMemsetAsync(p->d_state, 0, sizeof(ColState) * (size_t)p->i, p->ctx->stream));
+    void* V = (char*)p->d_vec + (size_t)j0 * p->nvec * p->N * elem_size(p->prec);
+    const int rc = p->prec == KV_FP32 ? autotune_t<float>(p, run, V) : autotune_t<double>(p, run, V);
+    return rc;
+}
 
 template <typename T>
 static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad, bool lanczos) {
@@ -335,7 +590,7 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
     const int64_t nbx = row_blocks(N) > spmv_blocks(N) ? row_blocks(N) : spmv_blocks(N);
     double* partials = p->red.partials;
     unsigned* counters = p->d_counters;
-    dim3 gs((unsigned)spmv_blocks(N), (unsigned)ncols), gr((unsigned)row_blocks(N), (unsigned)ncols);
+    dim3 gs((unsigned)spmv_blocks(N), (unsigned)ncols), gr((unsigned)row_blocks_t<T>(N), (unsigned)ncols);
     for (int it = 0; it < m; ++it) {
         if (lanczos) {
             const int vs = it % 3, ws = (it + 1) % 3, ps = (it + 2) % 3;
@@ -354,7 +609,15 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
                                                                counters, nbx);
             KV_CHECK_CUDA(cudaGetLastError());
         } else {
-            {
+            if (p->spmm_G > 0 && !(p->flags & KV_FLAG_NO_SPMM)) {
+                // grouped SpMM: the matrix is read once per group of spmm_G columns
+                LaunchScope ls(p->ctx, "csr_spmm");
+                if (!spmm_dispatch<T>(p, p->spmm_G, p->spmm_LPR, va, it, it + 1, aug, stp, it, ncols, st)) {
+                    set_error("no SpMM kernel for G=%d LPR=%d", p->spmm_G, p->spmm_LPR);
+                    return KV_EINVAL;
+                }
+                KV_CHECK_CUDA(cudaGetLastError());
+            } else {
                 LaunchScope ls(p->ctx, "csr_spmv");
                 k_spmv<T, false><<<gs, CNT, 0, st>>>(s->d_rp, s->d_col, (const T*)s->d_val, s->d_b, va, it, it + 1, n,
                                                     N, aug, stp, H, m, it, partials, counters, nbx);
@@ -366,7 +629,8 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
                 KV_CHECK_CUDA(cudaGetLastError());
             }
             LaunchScope ls(p->ctx, "arnoldi_update");
-            k_arnoldi_update<T><<<gr, CNT, 0, st>>>(va, N, stp, H, P, ad, cd, m, it, partials, counters, nbx);
+            const dim3 gu((unsigned)row_blocks(N), (unsigned)ncols);  // 8 rows per thread
+            k_arnoldi_update<T><<<gu, CNT, 0, st>>>(va, N, stp, H, P, ad, cd, m, it, partials, counters, nbx);
             KV_CHECK_CUDA(cudaGetLastError());
         }
     }

@@ -620,6 +620,7 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
                 }
             }
         }
+        if (s->kind == 1) TRY(csr_autotune(p));
         if (cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) {
             rc = fail(KV_ECUDA, "event creation failed");
             goto failed;

@@ -178,6 +178,32 @@ def test_csr_breakdown_and_zero_column(ctx):
     assert ref["used"][0] == 3 and got["m_used"][0] == 3 and got["m_used"][1] == 0
 
 
+@pytest.mark.parametrize("flags", [0, 2, 6])  # default, KV_FLAG_NO_SPMM, NO_SPMM | NO_AUTOTUNE
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_spmm_and_spmv_paths(ctx, flags, precision):
+    """The grouped SpMM (matrix read once per group of columns) and the
+    per-column SpMV give the oracle's bounds (n = 1e5 > the autotuning floor)."""
+    mk = lambda prec: W.random_csr_problem(100_000, seed=12, n_gen=9, o=2, c_width=1000, dt=0.01, steps=300,
+                                           m=20, precision=prec)
+    ref = oracle.run(mk("fp64"))
+    got = run_gpu(ctx, mk(precision), flags=flags, expm_mode="propagate")
+    assert bound_error(got, ref) <= (1e-9 if precision == "fp64" else 1e-6)
+
+
+def test_autotuner_cache(ctx, tmp_path, monkeypatch):
+    """The SpMM shape is timed once per (device, n, N, nnz, element size,
+    columns) and cached in KV_AUTOTUNE_CACHE; the second problem reuses it."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("KV_AUTOTUNE_CACHE", str(path))
+    p = W.random_csr_problem(120_000, seed=13, n_gen=7, o=1, c_width=500, dt=0.01, steps=50, m=8, precision="fp32")
+    for _ in range(2):
+        run_gpu(ctx, p)
+    lines = path.read_text().strip().splitlines()
+    assert len(lines) == 1
+    key, g, l, us = lines[0].split()
+    assert int(g) in (1, 2, 4, 8) and int(l) in (1, 2, 4) and "n=120000" in key and "cols=8" in key
+
+
 def test_malformed_csr_rejected(ctx):
     rp = np.array([0, 2, 3], dtype=np.int64)
     for col in (np.array([1, 0, 0], dtype=np.int32), np.array([0, 5, 1], dtype=np.int32)):
