@@ -176,20 +176,28 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     float4 zp0 = make_float4(0.f, 0.f, 0.f, 0.f), zp1 = zp0;  // w of the previous plane
     double acc_n = 0.0, acc_e = 0.0;
     int pfail = -1;
+    // ring positions of B(p-1), B(p), B(p+1), A(p) and the stage barrier /
+    // parity of plane p, rotated by one per plane
+    int sbm = (((p0 - 1) % RB) + RB) % RB, sbc = ((p0 % RB) + RB) % RB, sbp = (((p0 + 1) % RB) + RB) % RB;
+    int sac = ((p0 % RA) + RA) % RA, sst = 0;
+    unsigned sph = 0;
+    // offset of this thread's row r0 in w at plane p (the row r0 + 1 is nx further)
+    int64_t woff = ((int64_t)p0 * ny + (y0 - 1 + r0)) * nx + xb;
+    const int64_t plane = (int64_t)nx * ny;
     for (int p = p0; p <= z1 - 1; ++p) {
         bool ok = true;
         if (p == p0) ok = mbar_wait(bars + DEPTH, 0);
-        ok = ok && mbar_wait(bars + ((p - p0) % DEPTH), (unsigned)(((p - p0) / DEPTH) & 1));
+        ok = ok && mbar_wait(bars + sst, sph);
         if (!ok) abort_flag = 1;
         __syncthreads();  // also: every read of the previous plane's shared w is done
         if (abort_flag) {
             pfail = p;
             break;
         }
-        const float* Bm = bslot(p - 1);
-        const float* Bc = bslot(p);
-        const float* Bp = bslot(p + 1);
-        const float* Ac = aslot(p);
+        const float* Bm = sB + (size_t)sbm * (BSTRIDE / 4);
+        const float* Bc = sB + (size_t)sbc * (BSTRIDE / 4);
+        const float* Bp = sB + (size_t)sbp * (BSTRIDE / 4);
+        const float* Ac = sA + (size_t)sac * (ASTRIDE / 4);
         float* Wp = sW + (p & 1) * (WSTRIDE / 4);
         const bool pin = p >= 0 && p < nz;
 
@@ -240,9 +248,15 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
         }
         __syncthreads();  // w of this plane visible; B(p-1) and A(p) no longer read
         if (t == 0 && p + DEPTH <= z1 - 1) {
+            // stage p + DEPTH reuses this stage's barrier, B(p-1)'s slot (it takes
+            // B(p + DEPTH + 1)) and A(p)'s slot
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_stage(p + DEPTH);
-            issued_upto = p + DEPTH;
+            const int q = p + DEPTH;
+            uint64_t* bar = bars + sst;
+            mbar_expect_tx(bar, stage_bytes);
+            tma_load_3d((void*)Bm, &mapB, bar, x0 - 8, y0 - 2, q + 1);
+            if (!FIRST) tma_load_3d((void*)Ac, &mapA, bar, x0 - 4, y0 - 1, q);
+            issued_upto = q;
         }
 
         // ---- interior of plane p: norm, edge terms of w . A w, store
@@ -274,7 +288,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
                     tz = fmaf(dz, dz, tz);
                     tn = fmaf(w, w, tn);
                 }
-                float* dst = a.W + ((int64_t)p * ny + (y0 - 1 + r0 + h)) * nx + xb;
+                float* dst = a.W + woff + (h == 0 ? 0 : nx);
                 *reinterpret_cast<float4*>(dst) = w4;
                 // edges from the high faces to the zero ghost points
                 const float gy = ((h == 0 ? yhi0 : yhi1) ? ky : 0.f) + (zhi ? kz : 0.f);
@@ -291,6 +305,15 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
         }
         zp0 = w2[0];
         zp1 = w2[1];
+        woff += plane;
+        sbm = sbc;
+        sbc = sbp;
+        sbp = sbp + 1 == RB ? 0 : sbp + 1;
+        sac = sac + 1 == RA ? 0 : sac + 1;
+        if (++sst == DEPTH) {
+            sst = 0;
+            sph ^= 1u;
+        }
     }
     if (abort_flag) {
         // drain this CTA's outstanding copies (bounded), report the timeout
@@ -397,10 +420,10 @@ static int make_map(CUtensorMap* m, void* base, const Sys* s, int box_w, int box
 int fused_prepare() {
     static bool attr_set = false;
     if (!attr_set) {
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SMEM_TOTAL));
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SMEM_TOTAL));
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
         attr_set = true;
     }
     return KV_OK;
@@ -452,10 +475,11 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     rc = fused_prepare();
     if (rc) return rc;
     LaunchScope ls(p->ctx, "lanczos_fused");
+    cudaStream_t st = p->ctx->stream;
     if (it == 0)
-        k_lanczos_fused_tma<true><<<grd, FNT, SMEM_TOTAL, p->ctx->stream>>>(mB, mA, a);
+        k_lanczos_fused_tma<true><<<grd, FNT, SMEM_TOTAL, st>>>(mB, mA, a);
     else
-        k_lanczos_fused_tma<false><<<grd, FNT, SMEM_TOTAL, p->ctx->stream>>>(mB, mA, a);
+        k_lanczos_fused_tma<false><<<grd, FNT, SMEM_TOTAL, st>>>(mB, mA, a);
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;
 }
