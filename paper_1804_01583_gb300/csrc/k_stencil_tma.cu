@@ -188,12 +188,11 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
         bool ok = true;
         if (p == p0) ok = mbar_wait(bars + DEPTH, 0);
         ok = ok && mbar_wait(bars + sst, sph);
+        // No barrier here: each thread's own wait makes the stage visible to
+        // it, and the w plane written below is the other half of a double
+        // buffer whose last readers passed the previous plane's barrier.
+        // A failed wait is acted on after the barrier below.
         if (!ok) abort_flag = 1;
-        __syncthreads();  // also: every read of the previous plane's shared w is done
-        if (abort_flag) {
-            pfail = p;
-            break;
-        }
         const float* Bm = sB + (size_t)sbm * (BSTRIDE / 4);
         const float* Bc = sB + (size_t)sbc * (BSTRIDE / 4);
         const float* Bp = sB + (size_t)sbp * (BSTRIDE / 4);
@@ -247,6 +246,10 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
             *reinterpret_cast<float4*>(Wp + r * WC + 4 * lane) = w2[h];
         }
         __syncthreads();  // w of this plane visible; B(p-1) and A(p) no longer read
+        if (abort_flag) {  // some thread's wait expired: the stage may be incomplete
+            pfail = p;
+            break;
+        }
         if (t == 0 && p + DEPTH <= z1 - 1) {
             // stage p + DEPTH reuses this stage's barrier, B(p-1)'s slot (it takes
             // B(p + DEPTH + 1)) and A(p)'s slot
