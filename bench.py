@@ -56,6 +56,11 @@ def workload(name: str, precision: str):
         return W.heat3d_100(precision=precision)
     if name == "heat2d-20":
         return W.heat2d_20(precision=precision)
+    if name == "heat3d-512":
+        # profiling case: 1.6 GB of FP32 vectors (above L2, a few GB on the
+        # device), few launches before the captured ones
+        return W.heat((512, 512, 512), block=(50, 50, 50), output="centre", dt=0.02, steps=10, m=4,
+                      precision=precision, name="heat3d-512^3-profile")
     raise ValueError(name)
 
 
@@ -65,7 +70,41 @@ def bytes_per_iteration(p) -> float:
 
 
 # ----------------------------------------------------------------- clocks
+CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def summarize_clocks(samples, t0=None, t1=None):
+    """Median SM clock, max clock and active throttle reasons of nvidia-smi
+    lines "index, sm, max_sm, power, hw, hw_thermal, sw_thermal, sw_power_cap"
+    taken at host times t; only samples inside [t0, t1] count when the window
+    holds any (a short timed region may fall between two samples, then the
+    nearest ones are used)."""
+    parsed = []
+    for t, ln in samples:
+        parts = [x.strip() for x in ln.split(",")]
+        if len(parts) < 8:
+            continue
+        try:
+            sm, mx = float(parts[1]), float(parts[2])
+        except ValueError:
+            continue
+        reasons = {nm for nm, v in zip(CLOCK_REASONS, parts[4:8]) if v.lower() == "active"}
+        parsed.append((t, sm, mx, reasons))
+    if not parsed:
+        return None
+    inside = [s for s in parsed if (t0 is None or s[0] >= t0) and (t1 is None or s[0] <= t1)]
+    if not inside and t0 is not None and t1 is not None:
+        mid = 0.5 * (t0 + t1)
+        inside = sorted(parsed, key=lambda s: abs(s[0] - mid))[:2]
+    if not inside:
+        inside = parsed
+    return {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": max(s[2] for s in inside),
+            "reasons": sorted(set().union(*(s[3] for s in inside))), "samples": len(inside)}
+
+
 class ClockSampler:
+    """nvidia-smi sampling (200 ms) around the timed region: start() waits for
+    the first sample, mark() brackets the timed region on the host clock."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -73,7 +112,8 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.lines: list[str] = []
+        self.samples: list[tuple[float, str]] = []
+        self.window = [None, None]
 
     def start(self):
         try:
@@ -84,36 +124,45 @@ class ClockSampler:
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        t_end = time.perf_counter() + 3.0
+        while not self.samples and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark(self, which: int):
+        self.window[which] = time.perf_counter()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.samples.append((time.perf_counter(), line.strip()))
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.25)  # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = max(mx, float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return summarize_clocks(self.samples, *self.window)
+
+
+def reduce_max(x: float, world: int, device: str = "cuda") -> float:
+    """Max of a per-rank value over all ranks (the slowest replica sets the
+    whole job's time); identity at world = 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job rate of `world` replicas that each process units_per_rank
+    units, timed by the slowest one."""
+    return world * units_per_rank / (ms_max * 1e-3)
 
 
 # ------------------------------------------------------------ CPU baseline
@@ -168,11 +217,13 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    clocks.mark(0)
     ev0.record(stream)
     for _ in range(args.steps):
         ph.enqueue()
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark(1)
     barrier()
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
@@ -187,13 +238,9 @@ def run_gpu(args, rank: int, world: int):
     res = ph.fetch(full=False)
     ph.close()
     sysh.close()
-    ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = reduce_max(ms_total / args.steps, world)
     bpi = bytes_per_iteration(p)
-    gbs = world * p.m * bpi / (ms_step * 1e-3) / 1e9
+    gbs = replica_throughput(p.m * bpi, ms_step, world) / 1e9
 
     # end to end through the public API with host inputs: system + problem
     # creation (host -> device), run, result fetch (device -> host)
@@ -209,10 +256,10 @@ def run_gpu(args, rank: int, world: int):
         s2.close()
         if q > 0:
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e = statistics.median(e2e_ms)
+    e2e = reduce_max(statistics.median(e2e_ms), world)
     h2d = 8 * (p.o + 1) + 8 * len(p.C_col) * 2 + 8 * p.o + 16 * p.i + 64 * p.i
     d2h = 8 * 2 * p.o * (p.steps + 1) + 8 * p.i + 16
-    out_e2e = {"value": world * p.m * bpi / (e2e * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e,
+    out_e2e = {"value": replica_throughput(p.m * bpi, e2e, world) / 1e9, "unit": "GB/s", "ms_per_step": e2e,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     peak, peak_kind = peaks()
@@ -492,7 +539,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kv", choices=["kv", "reference"])
-    ap.add_argument("--workload", default="heat3d-1000", choices=["heat3d-1000", "heat3d-100", "heat2d-20"])
+    ap.add_argument("--workload", default="heat3d-1000", choices=["heat3d-1000", "heat3d-100", "heat2d-20", "heat3d-512"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--expm", default="per_step", choices=["per_step", "propagate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
