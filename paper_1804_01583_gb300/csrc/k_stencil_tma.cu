@@ -21,20 +21,24 @@
 // planes.  w is evaluated on the tile plus a one-point halo on the low x and
 // y sides (a 128 x 16 region: warp k owns rows 2k and 2k+1, lane l the four
 // consecutive x 4l..4l+3).  Per plane one elected thread issues TMA tile loads
-// (cp.async.bulk.tensor, completion counted on an mbarrier) of v_j (2 rows of
-// halo below, 1 above; x from x0-8) and v_{j-1} into a shared-memory ring
-// four planes ahead of the compute (two CTAs per SM, so eight stages, about
-// 144 KB, in flight per SM); TMA fills coordinates outside the grid
-// with zeros, which is the Dirichlet-0 boundary.  The x-1 neighbour of w comes
-// from the next lane (shuffle), y-1 from the warp's own other row or the
-// shared w plane, z-1 from registers kept from the previous plane.  w goes to
-// a buffer no CTA reads in this pass, so tiles never race on halos.
+// (cp.async.bulk.tensor, completion counted on an mbarrier) of v_j (x0-4 ..
+// x0+123 with 2 rows of halo below and 1 above, plus a 4-column side box for
+// the x0+124 neighbour) and v_{j-1} into a shared-memory ring four planes
+// ahead of the compute (two CTAs per SM, so eight stages, about 140 KB, in
+// flight per SM); TMA fills coordinates outside the grid with zeros, which is
+// the Dirichlet-0 boundary.  Box rows are 512 bytes, so every float4 row load
+// is conflict-free; the x neighbours of a thread's four points come from the
+// adjacent lanes (shuffles).  The x-1 neighbour of w comes from the next lane
+// (shuffle), y-1 from the warp's own other row or the shared w plane, z-1
+// from registers kept from the previous plane.  w goes to a buffer no CTA
+// reads in this pass, so tiles never race on halos.
 //
 // The update is evaluated in float with the difference form of the Laplacian
 // ((l - c) + (r - c): exact subtraction for nearby values) and every double
 // coefficient split into a float pair (hi + lo), one FMA chain; both dot
 // products are summed per plane in float (squared differences per axis,
-// weighted once per plane) and accumulated in double.
+// weighted once per plane), accumulated over the planes as TwoSum float
+// pairs and reduced across threads and CTAs in double.
 //
 // Every mbarrier wait is bounded; on expiry the CTA sets the column's status
 // word (reported as KV_ETIMEOUT), drains its outstanding copies with bounded
@@ -49,16 +53,19 @@ namespace kv {
 constexpr int FNT = 256;
 constexpr int TXI = 124, TYI = 15;      // interior points of a tile
 constexpr int WC = 128, WR = 16;        // w region: x0-4 .. x0+123, y0-1 .. y0+14
-constexpr int BBW = 136, BBH = 18;      // v_j box: x0-8 .. x0+127, y0-2 .. y0+15
+constexpr int BBW = 128, BBH = 18;      // v_j box: x0-4 .. x0+123, y0-2 .. y0+15 (512-byte rows)
+constexpr int SBW = 4, SBH = 18;        // v_j side box: x0+124 .. x0+127, same rows
 constexpr int ABW = 128, ABH = 16;      // v_{j-1} box: x0-4 .. x0+123, y0-1 .. y0+14
 constexpr int DEPTH = 4;                // stages in flight (x 2 CTAs per SM)
 constexpr int RB = DEPTH + 2, RA = DEPTH;
-constexpr int BBYTES = BBW * BBH * 4;   // 9792
+constexpr int BBYTES = BBW * BBH * 4;   // 9216
+constexpr int SBYTES = SBW * SBH * 4;   // 288
 constexpr int ABYTES = ABW * ABH * 4;   // 8192
-constexpr int BSTRIDE = (BBYTES + 127) / 128 * 128;
+constexpr int BSTRIDE = BBYTES;
+constexpr int SSTRIDE = (SBYTES + 127) / 128 * 128;
 constexpr int ASTRIDE = ABYTES;
 constexpr int WSTRIDE = WC * WR * 4;
-constexpr int SMEM_MAIN = RB * BSTRIDE + RA * ASTRIDE + 2 * WSTRIDE;
+constexpr int SMEM_MAIN = RB * BSTRIDE + RB * SSTRIDE + RA * ASTRIDE + 2 * WSTRIDE;
 constexpr int SMEM_TOTAL = SMEM_MAIN + 128 + 1024;  // + barriers + alignment slack
 constexpr long WAIT_LIMIT = 1L << 22;
 
@@ -92,6 +99,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// hi + lo += x with the rounding error of the float add kept in lo (TwoSum,
+// Knuth; six float operations, valid for any ordering of |hi| and |x|):
+// the per-thread sums over a chunk of planes stay float pairs, without
+// conversions or adds on the FP64 pipe inside the plane loop.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += e;
+}
+
 struct FusedArgs {
     float* W;          // output buffer (w = unnormalised v_{j+1})
     StencilGeom g;
@@ -106,14 +125,16 @@ struct FusedArgs {
 
 template <bool FIRST>
 __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_constant__ CUtensorMap mapB,
+                                                             const __grid_constant__ CUtensorMap mapS,
                                                              const __grid_constant__ CUtensorMap mapA,
                                                              FusedArgs a) {
     if (a.st->done) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     float* sB = (float*)sm;
-    float* sA = (float*)(sm + RB * BSTRIDE);
-    float* sW = (float*)(sm + RB * BSTRIDE + RA * ASTRIDE);
+    float* sS = (float*)(sm + RB * BSTRIDE);
+    float* sA = (float*)(sm + RB * (BSTRIDE + SSTRIDE));
+    float* sW = (float*)(sm + RB * (BSTRIDE + SSTRIDE) + RA * ASTRIDE);
     uint64_t* bars = (uint64_t*)(sm + SMEM_MAIN);  // DEPTH stage barriers + 1 prologue barrier
     __shared__ double shred[FNT / 32];
     __shared__ int flag, abort_flag;
@@ -133,14 +154,18 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     const CoefPair fa = split_coef(FIRST ? 0.0 : -a.H[(int64_t)a.j * a.m + (a.j - 1)] * a.st->s[a.j - 1]);
     const float kx = (float)g.kx, ky = (float)g.ky, kz = (float)g.kz;
 
-    auto bslot = [&](int plane) { return sB + (size_t)(((plane % RB) + RB) % RB) * (BSTRIDE / 4); };
-    auto aslot = [&](int plane) { return sA + (size_t)(((plane % RA) + RA) % RA) * (ASTRIDE / 4); };
-    const unsigned stage_bytes = BBYTES + (FIRST ? 0u : (unsigned)ABYTES);
+    auto ring = [](int plane, int n) { return ((plane % n) + n) % n; };
+    auto load_b = [&](int plane, uint64_t* bar) {  // v_j plane: main box + side box, same ring slot
+        const int k = ring(plane, RB);
+        tma_load_3d(sB + (size_t)k * (BSTRIDE / 4), &mapB, bar, x0 - 4, y0 - 2, plane);
+        tma_load_3d(sS + (size_t)k * (SSTRIDE / 4), &mapS, bar, x0 + 124, y0 - 2, plane);
+    };
+    const unsigned stage_bytes = BBYTES + SBYTES + (FIRST ? 0u : (unsigned)ABYTES);
     auto issue_stage = [&](int p) {  // B plane p+1, A plane p -> stage barrier of p
         uint64_t* bar = bars + ((p - p0) % DEPTH);
         mbar_expect_tx(bar, stage_bytes);
-        tma_load_3d(bslot(p + 1), &mapB, bar, x0 - 8, y0 - 2, p + 1);
-        if (!FIRST) tma_load_3d(aslot(p), &mapA, bar, x0 - 4, y0 - 1, p);
+        load_b(p + 1, bar);
+        if (!FIRST) tma_load_3d(sA + (size_t)ring(p, RA) * (ASTRIDE / 4), &mapA, bar, x0 - 4, y0 - 1, p);
     };
 
     // this thread's points: rows r0 = 2 warp, r0 + 1; columns c = 4 lane + u
@@ -164,9 +189,9 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     int issued_upto = p0 - 1;
     if (t == 0) {
         uint64_t* pro = bars + DEPTH;
-        mbar_expect_tx(pro, 2 * BBYTES);
-        tma_load_3d(bslot(p0 - 1), &mapB, pro, x0 - 8, y0 - 2, p0 - 1);
-        tma_load_3d(bslot(p0), &mapB, pro, x0 - 8, y0 - 2, p0);
+        mbar_expect_tx(pro, 2 * (BBYTES + SBYTES));
+        load_b(p0 - 1, pro);
+        load_b(p0, pro);
         for (int q = 0; q < DEPTH && p0 + q <= z1 - 1; ++q) {
             issue_stage(p0 + q);
             issued_upto = p0 + q;
@@ -174,7 +199,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     }
 
     float4 zp0 = make_float4(0.f, 0.f, 0.f, 0.f), zp1 = zp0;  // w of the previous plane
-    double acc_n = 0.0, acc_e = 0.0;
+    float an_hi = 0.f, an_lo = 0.f, ae_hi = 0.f, ae_lo = 0.f;
     int pfail = -1;
     // ring positions of B(p-1), B(p), B(p+1), A(p) and the stage barrier /
     // parity of plane p, rotated by one per plane
@@ -196,6 +221,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
         const float* Bm = sB + (size_t)sbm * (BSTRIDE / 4);
         const float* Bc = sB + (size_t)sbc * (BSTRIDE / 4);
         const float* Bp = sB + (size_t)sbp * (BSTRIDE / 4);
+        const float* Sc = sS + (size_t)sbc * (SSTRIDE / 4);
         const float* Ac = sA + (size_t)sac * (ASTRIDE / 4);
         float* Wp = sW + (p & 1) * (WSTRIDE / 4);
         const bool pin = p >= 0 && p < nz;
@@ -206,13 +232,20 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
         for (int h = 0; h < 2; ++h) {
             const int r = r0 + h;
             const bool valid = pin && xin && (h == 0 ? yin0 : yin1);
-            const float* brow = Bc + (r + 1) * BBW + 4 * lane + 4;
+            // every row of a box is 512 bytes: each float4 load is four
+            // conflict-free wavefronts
+            const float* brow = Bc + (r + 1) * BBW + 4 * lane;
             const float4 c4 = *reinterpret_cast<const float4*>(brow);
-            const float lft = brow[-1], rgt = brow[4];
+            // x neighbours from the adjacent lanes; lane 0's left value feeds
+            // only w(x0-4), which nothing reads, and lane 31's right one is
+            // column x0+124 of the side box
+            const float lft = __shfl_up_sync(0xffffffffu, c4.w, 1);
+            float rgt = __shfl_down_sync(0xffffffffu, c4.x, 1);
+            if (lane == 31) rgt = Sc[(r + 1) * SBW];
             const float4 d4 = *reinterpret_cast<const float4*>(brow - BBW);
             const float4 u4 = *reinterpret_cast<const float4*>(brow + BBW);
-            const float4 m4 = *reinterpret_cast<const float4*>(Bm + (r + 1) * BBW + 4 * lane + 4);
-            const float4 p4 = *reinterpret_cast<const float4*>(Bp + (r + 1) * BBW + 4 * lane + 4);
+            const float4 m4 = *reinterpret_cast<const float4*>(Bm + (r + 1) * BBW + 4 * lane);
+            const float4 p4 = *reinterpret_cast<const float4*>(Bp + (r + 1) * BBW + 4 * lane);
             float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (!FIRST) a4 = *reinterpret_cast<const float4*>(Ac + r * ABW + 4 * lane);
             const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
@@ -257,7 +290,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
             const int q = p + DEPTH;
             uint64_t* bar = bars + sst;
             mbar_expect_tx(bar, stage_bytes);
-            tma_load_3d((void*)Bm, &mapB, bar, x0 - 8, y0 - 2, q + 1);
+            load_b(q + 1, bar);  // lands in B(p-1)'s slot: (q + 1) - (p - 1) = RB
             if (!FIRST) tma_load_3d((void*)Ac, &mapA, bar, x0 - 4, y0 - 1, q);
             issued_upto = q;
         }
@@ -303,8 +336,8 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
                     }
                 }
             }
-            acc_n += (double)tn;
-            acc_e += (double)(kx * tx + ky * ty + kz * tz + tg);
+            two_sum_acc(an_hi, an_lo, tn);
+            two_sum_acc(ae_hi, ae_lo, kx * tx + ky * ty + kz * tz + tg);
         }
         zp0 = w2[0];
         zp1 = w2[1];
@@ -331,8 +364,8 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     }
 
     // ---- deterministic grid reduction of (w.w, -w.Aw)
-    const double d_nrm = block_sum<FNT>(acc_n, shred);
-    const double d_edg = block_sum<FNT>(acc_e, shred);
+    const double d_nrm = block_sum<FNT>((double)an_hi + (double)an_lo, shred);
+    const double d_edg = block_sum<FNT>((double)ae_hi + (double)ae_lo, shred);
     const int64_t nb = (int64_t)gridDim.x * gridDim.y * gridDim.z;
     const int64_t slot = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     if (t == 0) a.red.partials[nb + slot] = d_edg;
@@ -457,8 +490,9 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     g.ky = s->ndim >= 2 ? s->coef / (s->h[1] * s->h[1]) : 0.0;
     g.kz = s->ndim >= 3 ? s->coef / (s->h[2] * s->h[2]) : 0.0;
     g.kc = -2.0 * (g.kx + g.ky + g.kz);
-    CUtensorMap mB, mA;
+    CUtensorMap mB, mS, mA;
     int rc = make_map(&mB, const_cast<void*>(B), s, BBW, BBH);
+    if (!rc) rc = make_map(&mS, const_cast<void*>(B), s, SBW, SBH);
     if (!rc) rc = make_map(&mA, const_cast<void*>(A), s, ABW, ABH);
     if (rc) return rc;
     int zc;
@@ -480,9 +514,9 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     LaunchScope ls(p->ctx, "lanczos_fused");
     cudaStream_t st = p->ctx->stream;
     if (it == 0)
-        k_lanczos_fused_tma<true><<<grd, FNT, SMEM_TOTAL, st>>>(mB, mA, a);
+        k_lanczos_fused_tma<true><<<grd, FNT, SMEM_TOTAL, st>>>(mB, mS, mA, a);
     else
-        k_lanczos_fused_tma<false><<<grd, FNT, SMEM_TOTAL, st>>>(mB, mA, a);
+        k_lanczos_fused_tma<false><<<grd, FNT, SMEM_TOTAL, st>>>(mB, mS, mA, a);
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;
 }
