@@ -45,6 +45,8 @@
 // waits and leaves.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "kv_internal.h"
 #include "reduce.cuh"
 
@@ -121,29 +123,40 @@ struct FusedArgs {
     CDesc cd;
     int m, j;
     Reduce red;
+    // 1-D grid: n_norm full-width tiles (x fastest, then y, then z chunk),
+    // then the narrow tiles of the last x columns (y, then z chunk)
+    int nbx, nby, n_norm;
+    int sg_log2, nby_s;  // narrow tiles: 2^sg_log2 lanes per row pair; 0 = none
 };
 
-template <bool FIRST>
-__global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_constant__ CUtensorMap mapB,
-                                                             const __grid_constant__ CUtensorMap mapS,
-                                                             const __grid_constant__ CUtensorMap mapA,
-                                                             FusedArgs a) {
-    if (a.st->done) return;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+// One CTA's tile and chunk of z planes.  LG = log2 of the lanes that share
+// a row pair: 5 for a full-width tile (32 lanes over 128 columns, one warp
+// per 2 rows); 2, 3 or 4 for a narrow tile of the last x columns (G = 4, 8 or
+// 16 lanes over 4G columns, one warp per 2 * 32/G rows).  Both shapes cover
+// a 2048-point w region and use the same shared-memory slots; the shape is a
+// compile-time constant, so the box offsets fold into the load instructions.
+// Returns false when a stage wait expired (the copies are drained and the
+// timeout reported); otherwise this thread's sums of w.w and -w.Aw.
+template <bool FIRST, int LG>
+__device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensorMap* mS, const CUtensorMap* mA,
+                                           const FusedArgs& a, int tx, int ty, int tz, unsigned char* sm,
+                                           int& abort_flag, double& sum_n, double& sum_e) {
+    constexpr bool NARROW = LG < 5;
+    constexpr int G = 1 << LG;         // lanes per row pair
+    constexpr int RGW = 32 >> LG;      // row pairs per warp
+    constexpr int WCM = 4 * G;         // columns of the w region and of both boxes
+    constexpr int WRM = 16 * RGW;      // rows of the w region
     float* sB = (float*)sm;
     float* sS = (float*)(sm + RB * BSTRIDE);
     float* sA = (float*)(sm + RB * (BSTRIDE + SSTRIDE));
     float* sW = (float*)(sm + RB * (BSTRIDE + SSTRIDE) + RA * ASTRIDE);
     uint64_t* bars = (uint64_t*)(sm + SMEM_MAIN);  // DEPTH stage barriers + 1 prologue barrier
-    __shared__ double shred[FNT / 32];
-    __shared__ int flag, abort_flag;
-
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const StencilGeom& g = a.g;
     const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz;
-    const int x0 = blockIdx.x * TXI, y0 = blockIdx.y * TYI;
-    const int z0 = blockIdx.z * a.zc;
+    const int x0 = tx * TXI, y0 = ty * (WRM - 1);
+    const int z0 = tz * a.zc;
+    constexpr unsigned bbytes = (unsigned)(WCM * (WRM + 2) * 4);
     const int z1 = min(z0 + a.zc, nz);
     const int p0 = z0 - 1;  // w planes p0 .. z1-1; the interior work runs for z0 .. z1-1
 
@@ -157,24 +170,26 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     auto ring = [](int plane, int n) { return ((plane % n) + n) % n; };
     auto load_b = [&](int plane, uint64_t* bar) {  // v_j plane: main box + side box, same ring slot
         const int k = ring(plane, RB);
-        tma_load_3d(sB + (size_t)k * (BSTRIDE / 4), &mapB, bar, x0 - 4, y0 - 2, plane);
-        tma_load_3d(sS + (size_t)k * (SSTRIDE / 4), &mapS, bar, x0 + 124, y0 - 2, plane);
+        tma_load_3d(sB + (size_t)k * (BSTRIDE / 4), mB, bar, x0 - 4, y0 - 2, plane);
+        if (!NARROW) tma_load_3d(sS + (size_t)k * (SSTRIDE / 4), mS, bar, x0 + 124, y0 - 2, plane);
     };
-    const unsigned stage_bytes = BBYTES + SBYTES + (FIRST ? 0u : (unsigned)ABYTES);
+    constexpr unsigned bplane_bytes = bbytes + (NARROW ? 0u : (unsigned)SBYTES);
+    constexpr unsigned stage_bytes = bplane_bytes + (FIRST ? 0u : (unsigned)ABYTES);
     auto issue_stage = [&](int p) {  // B plane p+1, A plane p -> stage barrier of p
         uint64_t* bar = bars + ((p - p0) % DEPTH);
         mbar_expect_tx(bar, stage_bytes);
         load_b(p + 1, bar);
-        if (!FIRST) tma_load_3d(sA + (size_t)ring(p, RA) * (ASTRIDE / 4), &mapA, bar, x0 - 4, y0 - 1, p);
+        if (!FIRST) tma_load_3d(sA + (size_t)ring(p, RA) * (ASTRIDE / 4), mA, bar, x0 - 4, y0 - 1, p);
     };
 
-    // this thread's points: rows r0 = 2 warp, r0 + 1; columns c = 4 lane + u
-    const int r0 = 2 * warp;
-    const int xb = x0 - 4 + 4 * lane;                 // x of u = 0 (multiple of 4)
+    // this thread's points: rows r0, r0 + 1; columns c = 4 cg + u
+    const int cg = lane & (G - 1);
+    const int r0 = 2 * (warp * RGW + (lane >> LG));
+    const int xb = x0 - 4 + 4 * cg;                   // x of u = 0 (multiple of 4)
     const bool xin = xb >= 0 && xb < nx;              // nx % 4 == 0: all four or none
     const bool yin0 = (y0 - 1 + r0) >= 0 && (y0 - 1 + r0) < ny;
     const bool yin1 = (y0 + r0) < ny;                 // y0 + r0 >= 0 always
-    const bool inner_x = lane >= 1 && xin;            // c >= 4: inside the tile
+    const bool inner_x = cg >= 1 && xin;              // c >= 4: inside the tile
     const bool inner0 = inner_x && r0 >= 1 && yin0;   // row r0 interior (r0 >= 1)
     const bool inner1 = inner_x && yin1;              // row r0 + 1 >= 1 always
     const bool xhi3 = xin && (xb + 3 == nx - 1);      // u = 3 on the high x face
@@ -189,7 +204,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     int issued_upto = p0 - 1;
     if (t == 0) {
         uint64_t* pro = bars + DEPTH;
-        mbar_expect_tx(pro, 2 * (BBYTES + SBYTES));
+        mbar_expect_tx(pro, 2 * bplane_bytes);
         load_b(p0 - 1, pro);
         load_b(p0, pro);
         for (int q = 0; q < DEPTH && p0 + q <= z1 - 1; ++q) {
@@ -232,22 +247,24 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
         for (int h = 0; h < 2; ++h) {
             const int r = r0 + h;
             const bool valid = pin && xin && (h == 0 ? yin0 : yin1);
-            // every row of a box is 512 bytes: each float4 load is four
-            // conflict-free wavefronts
-            const float* brow = Bc + (r + 1) * BBW + 4 * lane;
+            // full-width tiles: every box row is 512 bytes, so each float4
+            // row load is four conflict-free wavefronts
+            const int bo = (r + 1) * WCM + 4 * cg;
+            const float* brow = Bc + bo;
             const float4 c4 = *reinterpret_cast<const float4*>(brow);
-            // x neighbours from the adjacent lanes; lane 0's left value feeds
-            // only w(x0-4), which nothing reads, and lane 31's right one is
-            // column x0+124 of the side box
+            // x neighbours from the adjacent lanes.  cg = 0's left value feeds
+            // only w(x0-4), which nothing reads; the right one of cg = G-1 is
+            // column x0+124 of the side box (full width) or lies beyond the
+            // grid (a narrow tile covers the last columns): zero
             const float lft = __shfl_up_sync(0xffffffffu, c4.w, 1);
             float rgt = __shfl_down_sync(0xffffffffu, c4.x, 1);
-            if (lane == 31) rgt = Sc[(r + 1) * SBW];
-            const float4 d4 = *reinterpret_cast<const float4*>(brow - BBW);
-            const float4 u4 = *reinterpret_cast<const float4*>(brow + BBW);
-            const float4 m4 = *reinterpret_cast<const float4*>(Bm + (r + 1) * BBW + 4 * lane);
-            const float4 p4 = *reinterpret_cast<const float4*>(Bp + (r + 1) * BBW + 4 * lane);
+            if (cg == G - 1) rgt = NARROW ? 0.f : Sc[(r + 1) * SBW];
+            const float4 d4 = *reinterpret_cast<const float4*>(brow - WCM);
+            const float4 u4 = *reinterpret_cast<const float4*>(brow + WCM);
+            const float4 m4 = *reinterpret_cast<const float4*>(Bm + bo);
+            const float4 p4 = *reinterpret_cast<const float4*>(Bp + bo);
             float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (!FIRST) a4 = *reinterpret_cast<const float4*>(Ac + r * ABW + 4 * lane);
+            if (!FIRST) a4 = *reinterpret_cast<const float4*>(Ac + r * WCM + 4 * cg);
             const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
             const float xl[4] = {lft, c4.x, c4.y, c4.z};
             const float xr[4] = {c4.y, c4.z, c4.w, rgt};
@@ -276,7 +293,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
                 wv[u] = valid ? acc : 0.f;
             }
             w2[h] = make_float4(wv[0], wv[1], wv[2], wv[3]);
-            *reinterpret_cast<float4*>(Wp + r * WC + 4 * lane) = w2[h];
+            *reinterpret_cast<float4*>(Wp + r * WCM + 4 * cg) = w2[h];
         }
         __syncthreads();  // w of this plane visible; B(p-1) and A(p) no longer read
         if (abort_flag) {  // some thread's wait expired: the stage may be incomplete
@@ -291,7 +308,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
             uint64_t* bar = bars + sst;
             mbar_expect_tx(bar, stage_bytes);
             load_b(q + 1, bar);  // lands in B(p-1)'s slot: (q + 1) - (p - 1) = RB
-            if (!FIRST) tma_load_3d((void*)Ac, &mapA, bar, x0 - 4, y0 - 1, q);
+            if (!FIRST) tma_load_3d((void*)Ac, mA, bar, x0 - 4, y0 - 1, q);
             issued_upto = q;
         }
 
@@ -300,7 +317,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
             const float left0 = __shfl_up_sync(0xffffffffu, w2[0].w, 1);
             const float left1 = __shfl_up_sync(0xffffffffu, w2[1].w, 1);
             float4 up0 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r0 >= 1) up0 = *reinterpret_cast<const float4*>(Wp + (r0 - 1) * WC + 4 * lane);
+            if (r0 >= 1) up0 = *reinterpret_cast<const float4*>(Wp + (r0 - 1) * WCM + 4 * cg);
             // squared backward differences per axis, weighted once per plane
             float tx = 0.f, ty = 0.f, tz = 0.f, tn = 0.f, tg = 0.f;
             const bool zhi = p == nz - 1;
@@ -360,14 +377,48 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
                 mbar_wait(bars + ((q - p0) % DEPTH), (unsigned)(((q - p0) / DEPTH) & 1));
         }
         __syncthreads();
-        return;
+        return false;
     }
+    sum_n = (double)an_hi + (double)an_lo;
+    sum_e = (double)ae_hi + (double)ae_lo;
+    return true;
+}
+
+
+template <bool FIRST, int LGN>
+__global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_constant__ CUtensorMap mapB,
+                                                             const __grid_constant__ CUtensorMap mapS,
+                                                             const __grid_constant__ CUtensorMap mapA,
+                                                             const __grid_constant__ CUtensorMap mapBn,
+                                                             const __grid_constant__ CUtensorMap mapAn,
+                                                             FusedArgs a) {
+    if (a.st->done) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ double shred[FNT / 32];
+    __shared__ int flag, abort_flag;
+    const int t = threadIdx.x;
+    // 1-D grid: full-width tiles (x fastest, then y, then z chunk), then the
+    // narrow tiles of the last x columns (y, then z chunk)
+    const int bid = blockIdx.x;
+    double sum_n, sum_e;
+    bool ok;
+    if (bid < a.n_norm) {
+        ok = fused_tile<FIRST, 5>(&mapB, &mapS, &mapA, a, bid % a.nbx, (bid / a.nbx) % a.nby,
+                                  bid / (a.nbx * a.nby), sm, abort_flag, sum_n, sum_e);
+    } else {
+        const int q = bid - a.n_norm;
+        ok = fused_tile<FIRST, LGN>(&mapBn, &mapS, &mapAn, a, a.nbx, q % a.nby_s, q / a.nby_s, sm, abort_flag,
+                                    sum_n, sum_e);
+    }
+    if (!ok) return;
+    const double alpha = a.H[(int64_t)a.j * a.m + a.j];
 
     // ---- deterministic grid reduction of (w.w, -w.Aw)
-    const double d_nrm = block_sum<FNT>((double)an_hi + (double)an_lo, shred);
-    const double d_edg = block_sum<FNT>((double)ae_hi + (double)ae_lo, shred);
-    const int64_t nb = (int64_t)gridDim.x * gridDim.y * gridDim.z;
-    const int64_t slot = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const double d_nrm = block_sum<FNT>(sum_n, shred);
+    const double d_edg = block_sum<FNT>(sum_e, shred);
+    const int64_t nb = gridDim.x;
+    const int64_t slot = bid;
     if (t == 0) a.red.partials[nb + slot] = d_edg;
     if (!grid_arrive(d_nrm, a.red.partials, a.red.counter, slot, nb, &flag)) return;
     const double nw2 = grid_finish<FNT>(a.red.partials, nb, a.red.counter, shred);
@@ -456,28 +507,60 @@ static int make_map(CUtensorMap* m, void* base, const Sys* s, int box_w, int box
 int fused_prepare() {
     static bool attr_set = false;
     if (!attr_set) {
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_lanczos_fused_tma<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
+        const void* fns[] = {(const void*)k_lanczos_fused_tma<true, 2>,  (const void*)k_lanczos_fused_tma<true, 3>,
+                             (const void*)k_lanczos_fused_tma<true, 4>,  (const void*)k_lanczos_fused_tma<false, 2>,
+                             (const void*)k_lanczos_fused_tma<false, 3>, (const void*)k_lanczos_fused_tma<false, 4>};
+        for (const void* fn : fns)
+            KV_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
         attr_set = true;
     }
     return KV_OK;
 }
 
-int fused_tma_blocks(const Prob* p, int* zc_out) {
-    const Sys* s = p->sys;
+// Grid of one launch.  Full-width tiles cover 124 columns each; when 1 to 60
+// columns remain after them, narrow tiles of 4G - 4 >= remainder columns
+// (G = 4, 8 or 16) cover those instead of one more full-width tile that
+// would compute mostly outside the grid.
+struct FusedGrid {
+    int nbx, nby, sg_log2, nby_s, zc, nzch;
+    int64_t n_norm, n_narrow;
+};
+
+static FusedGrid fused_grid(const Sys* s) {
     const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
-    const int64_t bx = (nx + TXI - 1) / TXI, by = (ny + TYI - 1) / TYI;
+    FusedGrid f{};
+    const int64_t full = nx / TXI, rem = nx - full * TXI;
+    f.sg_log2 = 0;
+    if (rem == 0) {
+        f.nbx = (int)full;
+    } else if (rem <= 60) {
+        f.nbx = (int)full;
+        f.sg_log2 = rem <= 12 ? 2 : (rem <= 28 ? 3 : 4);
+    } else {
+        f.nbx = (int)full + 1;
+    }
+    f.nby = (int)((ny + TYI - 1) / TYI);
+    const int64_t ty_n = f.sg_log2 ? 16 * (32 >> f.sg_log2) - 1 : 1;
+    f.nby_s = f.sg_log2 ? (int)((ny + ty_n - 1) / ty_n) : 0;
     // z chunk: about 12 waves of 2 resident CTAs per SM, at least 16 planes
+    const int64_t per_z = (int64_t)f.nbx * f.nby + f.nby_s;
     const int64_t target = 152LL * 2 * 12;
-    int64_t nzc = (target + bx * by - 1) / (bx * by);
+    int64_t nzc = (target + per_z - 1) / per_z;
     if (nzc < 1) nzc = 1;
     int64_t zc = (nz + nzc - 1) / nzc;
     if (zc < 16) zc = 16;
     if (zc > nz) zc = nz;
-    *zc_out = (int)zc;
-    return (int)(bx * by * ((nz + zc - 1) / zc));
+    f.zc = (int)zc;
+    f.nzch = (int)((nz + zc - 1) / zc);
+    f.n_norm = (int64_t)f.nbx * f.nby * f.nzch;
+    f.n_narrow = (int64_t)f.nby_s * f.nzch;
+    return f;
+}
+
+int fused_tma_blocks(const Prob* p, int* zc_out) {
+    const FusedGrid f = fused_grid(p->sys);
+    *zc_out = f.zc;
+    return (int)(f.n_norm + f.n_narrow);
 }
 
 int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, void* Wout) {
@@ -490,18 +573,32 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     g.ky = s->ndim >= 2 ? s->coef / (s->h[1] * s->h[1]) : 0.0;
     g.kz = s->ndim >= 3 ? s->coef / (s->h[2] * s->h[2]) : 0.0;
     g.kc = -2.0 * (g.kx + g.ky + g.kz);
-    CUtensorMap mB, mS, mA;
+    const FusedGrid f = fused_grid(s);
+    // narrow tiles: 4G columns, 16 * 32/G rows of w (G = 4: 16 x 128)
+    const int lg = f.sg_log2 ? f.sg_log2 : 2;
+    const int wc_n = 4 << lg, wr_n = 16 * (32 >> lg);
+    CUtensorMap mB, mS, mA, mBn, mAn;
     int rc = make_map(&mB, const_cast<void*>(B), s, BBW, BBH);
     if (!rc) rc = make_map(&mS, const_cast<void*>(B), s, SBW, SBH);
     if (!rc) rc = make_map(&mA, const_cast<void*>(A), s, ABW, ABH);
+    if (!rc) rc = make_map(&mBn, const_cast<void*>(B), s, wc_n, wr_n + 2);
+    if (!rc) rc = make_map(&mAn, const_cast<void*>(A), s, wc_n, wr_n);
     if (rc) return rc;
-    int zc;
-    fused_tma_blocks(p, &zc);
-    dim3 grd((unsigned)((g.nx + TXI - 1) / TXI), (unsigned)((g.ny + TYI - 1) / TYI), (unsigned)((g.nz + zc - 1) / zc));
+    const int64_t nblk = f.n_norm + f.n_narrow;
+    if (nblk < 1 || nblk > INT32_MAX) {
+        set_error("fused grid of %lld blocks", (long long)nblk);
+        return KV_EINVAL;
+    }
+    dim3 grd((unsigned)nblk);
     FusedArgs a;
     a.W = (float*)Wout;
     a.g = g;
-    a.zc = zc;
+    a.zc = f.zc;
+    a.nbx = f.nbx;
+    a.nby = f.nby;
+    a.n_norm = (int)f.n_norm;
+    a.sg_log2 = f.sg_log2;
+    a.nby_s = f.nby_s;
     a.st = p->d_state + j;
     a.H = p->d_H + (int64_t)j * (p->m + 1) * p->m;
     a.P = p->d_P + (int64_t)j * p->o * p->m;
@@ -513,10 +610,26 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     if (rc) return rc;
     LaunchScope ls(p->ctx, "lanczos_fused");
     cudaStream_t st = p->ctx->stream;
-    if (it == 0)
-        k_lanczos_fused_tma<true><<<grd, FNT, SMEM_TOTAL, st>>>(mB, mS, mA, a);
-    else
-        k_lanczos_fused_tma<false><<<grd, FNT, SMEM_TOTAL, st>>>(mB, mS, mA, a);
+    // the narrow shape is a template argument (G = 4 when there are none:
+    // that branch is then never taken)
+    auto go = [&](auto first, auto lgn) {
+        k_lanczos_fused_tma<decltype(first)::value, decltype(lgn)::value>
+            <<<grd, FNT, SMEM_TOTAL, st>>>(mB, mS, mA, mBn, mAn, a);
+    };
+    using T = std::true_type;
+    using F = std::false_type;
+    using L2 = std::integral_constant<int, 2>;
+    using L3 = std::integral_constant<int, 3>;
+    using L4 = std::integral_constant<int, 4>;
+    if (it == 0) {
+        if (lg == 2) go(T{}, L2{});
+        else if (lg == 3) go(T{}, L3{});
+        else go(T{}, L4{});
+    } else {
+        if (lg == 2) go(F{}, L2{});
+        else if (lg == 3) go(F{}, L3{});
+        else go(F{}, L4{});
+    }
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;
 }

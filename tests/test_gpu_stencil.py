@@ -170,6 +170,28 @@ def test_fp32_storage_3d(ctx, dims, path):
         assert eh <= 1e-5, eh
 
 
+@pytest.mark.parametrize("dims", [(132, 19, 9),     # 1 full-width tile + narrow tiles of 4 lanes per row pair
+                                  (268, 70, 7),     # remainder 20: 8 lanes per row pair, two narrow y tiles
+                                  (172, 33, 6),     # remainder 48: 16 lanes per row pair
+                                  (224, 20, 5),     # remainder 100: one more full-width tile
+                                  (20, 300, 4),     # narrow tiles only, five of them in y
+                                  (1000, 40)])      # 2-D, 8 full-width tiles + a narrow one
+def test_fp32_fused_tile_shapes(ctx, dims):
+    """The single-pass iteration on every tile shape its grid plan uses (full
+    width, narrow of 4, 8 or 16 lanes per row pair, ragged full width), with
+    an initial block covering all but the last three cells of every axis, so
+    every tile sees non-zero data and the centre output is well inside it:
+    H within 1e-5 and bounds within 1e-6 of the FP64 oracle."""
+    block = tuple(max(1, d - 3) for d in dims)
+    kw = dict(block=block, output="centre8", dt=1e-4, steps=60, m=20)
+    got = run_gpu(ctx, W.heat(dims, precision="fp32", **kw))
+    ref = oracle.run(W.heat(dims, **kw))
+    eh, _ = krylov_error(got, ref, 0)
+    assert eh <= 1e-5, eh
+    e = bound_error(got, ref)
+    assert e <= 1e-6, e
+
+
 @pytest.mark.parametrize("path", ["fused", "two_pass"])
 def test_fp32_output_within_reach_100(ctx, path):
     """100^3 with a nearby output cell: non-zero bounds at full size in FP32."""
