@@ -123,9 +123,9 @@ struct FusedArgs {
     CDesc cd;
     int m, j;
     Reduce red;
-    // 1-D grid: n_norm full-width tiles (x fastest, then y, then z chunk),
-    // then the narrow tiles of the last x columns (y, then z chunk)
-    int nbx, nby, n_norm;
+    // 1-D grid of z chunks, each nbx * nby full-width tiles then nby_s
+    // narrow ones
+    int nbx, nby;
     int sg_log2, nby_s;  // narrow tiles: 2^sg_log2 lanes per row pair; 0 = none
 };
 
@@ -398,19 +398,19 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     __shared__ double shred[FNT / 32];
     __shared__ int flag, abort_flag;
     const int t = threadIdx.x;
-    // 1-D grid: full-width tiles (x fastest, then y, then z chunk), then the
-    // narrow tiles of the last x columns (y, then z chunk)
+    // 1-D grid, z chunk major: per chunk the full-width tiles (x fastest,
+    // then y) and then the narrow tiles of the last x columns, so the columns
+    // both read are still in L2
     const int bid = blockIdx.x;
+    const int per_z = a.nbx * a.nby + a.nby_s;
+    const int tz = bid / per_z, q = bid - tz * per_z;
     double sum_n, sum_e;
     bool ok;
-    if (bid < a.n_norm) {
-        ok = fused_tile<FIRST, 5>(&mapB, &mapS, &mapA, a, bid % a.nbx, (bid / a.nbx) % a.nby,
-                                  bid / (a.nbx * a.nby), sm, abort_flag, sum_n, sum_e);
-    } else {
-        const int q = bid - a.n_norm;
-        ok = fused_tile<FIRST, LGN>(&mapBn, &mapS, &mapAn, a, a.nbx, q % a.nby_s, q / a.nby_s, sm, abort_flag,
-                                    sum_n, sum_e);
-    }
+    if (q < a.nbx * a.nby)
+        ok = fused_tile<FIRST, 5>(&mapB, &mapS, &mapA, a, q % a.nbx, q / a.nbx, tz, sm, abort_flag, sum_n, sum_e);
+    else
+        ok = fused_tile<FIRST, LGN>(&mapBn, &mapS, &mapAn, a, a.nbx, q - a.nbx * a.nby, tz, sm, abort_flag, sum_n,
+                                    sum_e);
     if (!ok) return;
     const double alpha = a.H[(int64_t)a.j * a.m + a.j];
 
@@ -596,7 +596,6 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     a.zc = f.zc;
     a.nbx = f.nbx;
     a.nby = f.nby;
-    a.n_norm = (int)f.n_norm;
     a.sg_log2 = f.sg_log2;
     a.nby_s = f.nby_s;
     a.st = p->d_state + j;
