@@ -173,7 +173,7 @@ int kv_pool_stats(const kv_ctx *ctx, size_t *in_use, size_t *total);
 
 /* Matrix-free grid system: A = coef * discrete Laplacian with spacing h[a]
  * per axis and a Dirichlet-0 boundary (semi-finite-difference heat model,
- * Sec. 6.3).  ndim = 2 or 3; dims[ndim..2] are ignored; b: host, n entries,
+ * Sec. 5.3).  ndim = 2 or 3; dims[ndim..2] are ignored; b: host, n entries,
  * or NULL.  The Laplacian is symmetric, so KV_AUTO picks Lanczos for columns
  * without the constant variable. */
 int kv_system_stencil(kv_ctx *ctx, kv_sys **out, int ndim, const int64_t dims[3], double coef,
@@ -199,7 +199,7 @@ int kv_problem(kv_ctx *ctx, kv_prob **out, const kv_sys *sys, const kv_problem_d
                int precision);
 int kv_prob_destroy(kv_prob *prob);
 
-/* Device bytes kv_problem would reserve (the memory model of Sec. 5 for this
+/* Device bytes kv_problem would reserve (the memory model of Sec. 4.2-4.3 for this
  * implementation: two n-vectors for Lanczos, m+1 for Arnoldi, plus the
  * o x i x (steps+1) basis of Eq. memory_basis and small state). */
 int kv_problem_bytes(const kv_sys *sys, const kv_problem_desc *desc, int precision, size_t *bytes);
@@ -247,7 +247,7 @@ int kv_graph_destroy(kv_graph *graph);
  * once.  A worker thread owned by the server admits queued queries in
  * arrival order whenever one of `slots` slots is free and the context pool
  * can hold the query's system and problem (device memory is reserved as in
- * kv_problem, the memory model of Sec. 5; a query that does not fit waits for
+ * kv_problem, the memory model of Sec. 4.2-4.3; a query that does not fit waits for
  * running ones to finish, and one that cannot fit an idle pool fails with
  * KV_ENOMEM).  Each admitted query's whole path is enqueued on its slot's own
  * stream, so the work of different queries overlaps on the device; on

@@ -15,6 +15,11 @@ strings the steps together in the paper's order:
   3. basis[j][r][k] = beta0 * P[r,:] e^{H t_k} e_1 (Eq. approx-formula);
   4. box-initial-set output interval, first violation, counter-example vertex
      (the per-step LP of Sec. 2.1 in closed form).
+
+With an error target (Alg. 2 / Alg. 4) the Krylov dimension of a column is the
+first of 4, ceil(1.1 k), ... below krylov_m whose Lemma-1 bound (Sec. 4.2) is
+below the target, else krylov_m; the bound at the dimension used is reported
+either way.
 """
 from __future__ import annotations
 
@@ -70,6 +75,8 @@ def _load():
             lib.ora_expm.argtypes = [C.c_int, P, P]
             lib.ora_basis.argtypes = [C.c_int, C.c_int, P, C.c_int, P, C.c_double, C.c_double,
                                       C.c_int, P]
+            lib.ora_lemma1.restype = C.c_double
+            lib.ora_lemma1.argtypes = [C.c_int, C.c_int, P, C.c_double, C.c_double, C.c_double, C.c_int]
             lib.ora_bounds.restype = C.c_int
             lib.ora_bounds.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P,
                                        C.POINTER(C.c_int), C.POINTER(C.c_int), P,
@@ -191,6 +198,57 @@ def bounds(basis_all: np.ndarray, zlo, zhi, theta) -> Dict:
                 zstar=zstar if unsafe else None, ystar=ys.value if unsafe else None)
 
 
+def checkpoints(m: int) -> List[int]:
+    """Krylov dimensions at which Alg. 2 / Alg. 4 evaluate the error bound:
+    k = 4, then k <- ceil(1.1 k) in IEEE double, below m."""
+    import math
+    out, k = [], 4
+    while k < m:
+        out.append(k)
+        k = math.ceil(1.1 * k)
+    return out
+
+
+def mu_bound(system, carries_constant: bool) -> float:
+    """An upper bound of the largest eigenvalue of (A + A^T)/2, the matrix the
+    Krylov run of a column works on (A' = [[A, b], [0, 0]] for a column that
+    carries the constant variable, else A: a generator column stays in the
+    subspace where A' acts as A).
+
+    Grid Laplacian (symmetric): the largest eigenvalue itself, the Kronecker
+    sum of the 1-D Dirichlet second differences' largest eigenvalues
+    -(4/h^2) sin^2(pi / (2(N+1))).  CSR: the Gershgorin bound of the symmetric
+    part, max_i a_ii + (sum_{j != i} |a_ij| + |a_ji|) / 2 (+ |b_i|/2, and the
+    constant row sum |b_i|/2, for A')."""
+    import math
+    if hasattr(system, "dims"):
+        return float(sum(-system.coef * 4.0 / (h * h) * math.sin(math.pi / (2.0 * (N + 1))) ** 2
+                         for N, h in zip(system.dims, system.h)))
+    import scipy.sparse as sp
+    n = int(system.n)
+    A = sp.csr_matrix((np.asarray(system.val, dtype=np.float64), np.asarray(system.col),
+                       np.asarray(system.row_ptr)), shape=(n, n))
+    absA = abs(A)
+    d = A.diagonal()
+    off_r = np.asarray(absA.sum(axis=1)).ravel() - np.abs(d)
+    off_c = np.asarray(absA.sum(axis=0)).ravel() - np.abs(d)
+    g = d + 0.5 * (off_r + off_c)
+    if carries_constant and system.b is not None:
+        b = np.abs(np.asarray(system.b, dtype=np.float64))
+        g = g + 0.5 * b
+        return float(max(np.max(g), 0.5 * np.sum(b)))
+    return float(np.max(g))
+
+
+def lemma1(H: np.ndarray, k: int, mu: float, dt: float, steps: int) -> float:
+    """The Lemma-1 bound (Sec. 4.2) for dimension k of the Krylov matrix H
+    ((m+1) x m, rows beyond k unused except h_{k+1,k})."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    if k <= 0:
+        return 0.0
+    return float(_load().ora_lemma1(k, H.shape[1], _p(H), float(H[k, k - 1]), float(mu), float(dt), int(steps)))
+
+
 def column_method(problem, col) -> str:
     """Lanczos needs a symmetric operator: the system must be symmetric and the
     column must not carry the constant variable (A' = [[A, b], [0, 0]] is not
@@ -213,7 +271,8 @@ def run(problem, *, columns: Optional[List[int]] = None, want_basis: bool = True
     dims = getattr(sysm, "dims", None)
     aug = sysm.b is not None
     sel = list(range(problem.i)) if columns is None else list(columns)
-    Hs, Ps, used, beta0s, bases = {}, {}, {}, {}, {}
+    Hs, Ps, used, beta0s, bases, errs, checks = {}, {}, {}, {}, {}, {}, {}
+    eps = float(getattr(problem, "err_target", 0.0) or 0.0)
     for j in sel:
         col = problem.columns[j]
         e = column_dense(col, n, dims)
@@ -226,13 +285,28 @@ def run(problem, *, columns: Optional[List[int]] = None, want_basis: bool = True
             Ps[j] = np.zeros((problem.o, problem.m))
             used[j] = 0
             bases[j] = np.zeros((problem.o, problem.steps + 1))
+            errs[j], checks[j] = 0.0, []
             continue
         H, P, u = krylov(sysm, e / b0, problem.m, problem.C_row_ptr, problem.C_col, problem.C_val,
                          method=column_method(problem, col), aug=aug)
+        # Alg. 2 / Alg. 4: the first checkpoint below the dimension reached
+        # whose bound is under the target ends the iteration there
+        mu = mu_bound(sysm, aug and bool(col.is_fixed))
+        checks[j] = []
+        if eps > 0.0:
+            for k in checkpoints(problem.m):
+                if k >= u:
+                    break
+                ek = lemma1(H, k, mu, problem.dt, problem.steps)
+                checks[j].append((k, ek))
+                if ek < eps:
+                    u = k
+                    break
+        errs[j] = lemma1(H, u, mu, problem.dt, problem.steps)
         Hs[j], Ps[j], used[j] = H, P, u
         if want_basis:
             bases[j] = basis(H, P, u, b0, problem.dt, problem.steps)
-    out = dict(H=Hs, P=Ps, used=used, beta0=beta0s, basis=bases)
+    out = dict(H=Hs, P=Ps, used=used, beta0=beta0s, basis=bases, err=errs, checks=checks)
     if want_basis and len(sel) == problem.i:
         ball = np.stack([bases[j] for j in range(problem.i)])
         zlo = [c.zlo for c in problem.columns]

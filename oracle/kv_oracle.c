@@ -9,7 +9,7 @@
  * CUDA library.
  *
  * Everything is IEEE double precision (the paper sizes every buffer with
- * sizeof(double), Sec. 5), written in the order the paper states the steps:
+ * sizeof(double), Sec. 4.3), written in the order the paper states the steps:
  *
  *   ora_apply         y = A x, A a Dirichlet-0 grid Laplacian or a CSR matrix,
  *                     optionally augmented with the forcing column b and a zero
@@ -25,6 +25,9 @@
  *                     Appl. 26(4), 2005).
  *   ora_basis         one row block of the basis matrix C e^{At} E_j per step,
  *                     ||E_j|| * P * e^{H t_k} e_1 (Eq. "approx-formula", Sec. 4.2).
+ *   ora_lemma1        the a-posteriori error bound of Lemma 1 (Sec. 4.2) for a
+ *                     Krylov dimension k, which Alg. 2 / Alg. 4 compare with the
+ *                     error target at the dimensions 4, ceil(1.1 k), ...
  *   ora_bounds        per-step output interval over the box initial set, first
  *                     step whose upper bound reaches the unsafe half-space and the
  *                     counter-example vertex (the LP of Sec. 2.1 solved in closed
@@ -71,7 +74,7 @@ int64_t ora_dim(const ora_op *op) { return op->n + (op->aug ? 1 : 0); }
 /* ---------------------------------------------------------------- A x ---- */
 /* Second-order central differences: (A x)_p = coef * sum_axes
  * (x_{p-e} + x_{p+e} - 2 x_p) / h_axis^2, neighbours outside the grid are 0
- * (Dirichlet-0 boundary; semi-finite-difference model of Sec. 6.3). */
+ * (Dirichlet-0 boundary; semi-finite-difference model of Sec. 5.3). */
 static void grid_apply(const ora_op *op, const double *x, double *y) {
     const int64_t nx = op->dims[0];
     const int64_t ny = op->ndim >= 2 ? op->dims[1] : 1;
@@ -359,6 +362,42 @@ void ora_basis(int mu, int ldh, const double *H, int o, const double *P, double 
         }
         free(X); free(E);
     }
+}
+
+/* -------------------------------------------------------- error bound ---- */
+/* Lemma 1 (Sec. 4.2, after Wang and Ye) for the Krylov pair (V_k, H_k) of a
+ * unit start vector v, applied with B = -A as the paper prescribes:
+ *   || e^{tA} v - V_k e^{t H_k} e_1 || <= h_{k+1,k} e^{max(mu,0) T} int_0^T |h(t)| dt
+ * with h(t) = e_k^T e^{t H_k} e_1, T = steps * dt, and mu an upper bound of the
+ * largest eigenvalue of (A + A^T)/2 (the lemma's nu is the smallest eigenvalue
+ * of (B + B^T)/2 = -(A + A^T)/2, so -min(nu, 0) = max(mu, 0)).  Arnoldi on -A
+ * gives H_k(-A) = -D H_k(A) D, D = diag(1, -1, 1, ...), so |h| is the same for
+ * both matrices.  The integral is the composite trapezoid rule on the output
+ * grid t_j = j dt, j = 0..steps, with e^{t_j H_k} e_1 from the Pade exponential
+ * of t_j H_k.  H is row-major with leading dimension ldh (k <= ldh); hk1 is
+ * h_{k+1,k}.  Returns the bound (0 when hk1 = 0: the space is invariant). */
+double ora_lemma1(int k, int ldh, const double *H, double hk1, double mu, double dt, int steps) {
+    if (k <= 0 || hk1 == 0.0) return 0.0;
+    double *hv = (double *)malloc(sizeof(double) * (size_t)(steps + 1));
+#pragma omp parallel
+    {
+        double *X = (double *)malloc(sizeof(double) * (size_t)k * k);
+        double *E = (double *)malloc(sizeof(double) * (size_t)k * k);
+#pragma omp for schedule(dynamic, 4)
+        for (int j = 0; j <= steps; j++) {
+            const double t = (double)j * dt;
+            for (int r = 0; r < k; r++)
+                for (int c = 0; c < k; c++) X[r * k + c] = H[(int64_t)r * ldh + c] * t;
+            ora_expm(k, X, E);
+            hv[j] = fabs(E[(k - 1) * k + 0]);   /* row k, column 1 */
+        }
+        free(X); free(E);
+    }
+    double integral = 0.0;
+    for (int j = 1; j <= steps; j++) integral += 0.5 * dt * (hv[j - 1] + hv[j]);
+    free(hv);
+    const double T = (double)steps * dt;
+    return hk1 * exp((mu > 0.0 ? mu : 0.0) * T) * integral;
 }
 
 /* ------------------------------------------------------------- bounds ---- */

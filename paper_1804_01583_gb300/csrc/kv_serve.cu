@@ -3,7 +3,7 @@
 // Queries (a system plus a verification problem) are submitted from any host
 // thread.  One worker thread owns the context: it admits queued queries in
 // arrival order whenever a slot is free and the context pool can hold the
-// query's system and problem (the memory model of Sec. 5 via kv_problem's
+// query's system and problem (the memory model of Sec. 4.2-4.3 via kv_problem's
 // reservation; a query that does not fit waits for a running one to finish),
 // enqueues each admitted query's whole path on the slot's own stream -- so
 // the kernels of different queries overlap on the device -- and, when a

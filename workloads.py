@@ -9,10 +9,10 @@ computation they are compared on.
 Workload shapes follow the paper's benchmarks:
   * 2D / 3D heat diffusion on a uniform grid with a Dirichlet-0 boundary, a
     heated block as a one-generator initial set and the temperature at the
-    centre as output (Sec. 6.3, "Symmetric 3D Heat Diffusion");
+    centre as output (Sec. 5.3, "Symmetric 3D Heat Diffusion");
   * a random sparse nonsymmetric system with a forcing term b, a box initial
     set over a few variables and a couple of +-1 output rows, standing in for
-    the circuit benchmark of Sec. 6.1 (its matrix is not available);
+    the circuit benchmark of Sec. 5.1 (its matrix is not available);
   * the timed harmonic oscillator worked example of Sec. 2.2.
 """
 from __future__ import annotations
@@ -97,6 +97,7 @@ class Problem:
     method: str = "auto"       # auto | lanczos | arnoldi
     precision: str = "fp64"    # fp64 | fp32
     name: str = ""
+    err_target: float = 0.0    # > 0: a-posteriori error control with m as the maximum dimension
 
     @property
     def o(self) -> int:
@@ -127,7 +128,7 @@ def grid_index(dims: Sequence[int], cell: Sequence[int]) -> int:
 
 
 # --------------------------------------------------------------------------
-# heat diffusion (Sec. 6.3 shapes; Dirichlet-0 boundary)
+# heat diffusion (Sec. 5.3 shapes; Dirichlet-0 boundary)
 # --------------------------------------------------------------------------
 def heat(dims: Sequence[int], *, coef: float = 0.01, block: Sequence[int],
          output: str = "centre", theta: float = math.inf, dt: float,
@@ -206,7 +207,7 @@ def heat3d_truncated(full: Problem, side: int) -> Problem:
 
 
 # --------------------------------------------------------------------------
-# random sparse nonsymmetric system with forcing (stand-in for Sec. 6.1)
+# random sparse nonsymmetric system with forcing (stand-in for Sec. 5.1)
 # --------------------------------------------------------------------------
 def random_csr(n: int, nnz_per_row: int = 10, seed: int = 0, with_b: bool = True) -> CsrSystem:
     """n x n, nnz_per_row distinct off-diagonal columns per row drawn uniformly
