@@ -102,7 +102,21 @@ typedef struct {
  * box on z, outputs y = C x with C in CSR form over the n state variables
  * (Sec. 3.1), unsafe set y_r >= theta_r (theta_r = +inf: row not checked),
  * step dt and steps + 1 check points t_k = k dt (k = 0 included), Krylov
- * dimension krylov_m (the paper's k, 1 <= krylov_m <= KV_MAX_M). */
+ * dimension krylov_m (the paper's k, 1 <= krylov_m <= KV_MAX_M).
+ *
+ * err_target > 0 turns on the a-posteriori error control of Alg. 2 / Alg. 4:
+ * krylov_m is then the largest dimension, and each column stops at the first
+ * of the dimensions 4, ceil(1.1 k), ... (the growth rule evaluated in IEEE
+ * double) below krylov_m whose Lemma-1 bound (Sec. 4.2) is below err_target;
+ * a column whose bound never gets there runs to krylov_m.  The bound is
+ *   h_{k+1,k} e^{max(mu,0) T} sum_{j=1..steps} dt (|h(t_{j-1})| + |h(t_j)|) / 2,
+ *   h(t) = (e^{t H_k})_{k,1},  T = steps dt,
+ * the lemma applied with B = -A and its integral taken by the trapezoid rule
+ * on the output grid; mu is an upper bound of the largest eigenvalue of
+ * (A + A^T)/2 for the matrix the column works on (grid: the exact value;
+ * CSR: the Gershgorin bound of the symmetric part, of A' = [[A, b], [0, 0]]
+ * for a column that carries the constant).  err_target <= 0: fixed krylov_m.
+ * The bound at the dimension used is reported either way (kv_result.err_bound). */
 typedef struct {
     int32_t i;                  /* number of columns, >= 1 */
     const kv_column *cols;      /* host, i entries */
@@ -118,6 +132,7 @@ typedef struct {
     int32_t expm_mode;          /* KV_EXPM_PER_STEP | KV_EXPM_PROPAGATE */
     int32_t batched;            /* CSR: 1 = all Arnoldi columns share one SpMM */
     int32_t flags;              /* KV_FLAG_* bits, 0 = defaults */
+    double err_target;          /* > 0: error control with krylov_m as the largest dimension */
 } kv_problem_desc;
 
 /* kv_problem_desc.flags */
@@ -139,7 +154,9 @@ typedef struct {
  *   P        i x o x krylov_m              [j][r][l] = C v_l
  *   beta0    i                             ||E_j|| (with the constant entry)
  *   m_used   i                             valid columns of H and P
- *   z_star   i                             counter-example z (unsafe only) */
+ *   z_star   i                             counter-example z (unsafe only)
+ *   err_bound i                            Lemma-1 bound at m_used, for the
+ *                                          normalised start vector E_j/||E_j|| */
 typedef struct {
     double *lo;
     double *hi;
@@ -152,6 +169,7 @@ typedef struct {
     int32_t first_violation_step;   /* -1: safe */
     int32_t violation_row;          /* -1: safe */
     double y_star;                  /* hi_r(k) at the violation */
+    double *err_bound;
 } kv_result;
 
 /* Library version string (static storage). */

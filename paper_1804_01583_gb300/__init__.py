@@ -49,13 +49,14 @@ class kv_problem_desc(C.Structure):
                 ("c_row_ptr", C.c_void_p), ("c_col", C.c_void_p), ("c_val", C.c_void_p),
                 ("theta", C.c_void_p), ("dt", C.c_double), ("steps", C.c_int32),
                 ("krylov_m", C.c_int32), ("method", C.c_int32), ("expm_mode", C.c_int32),
-                ("batched", C.c_int32), ("flags", C.c_int32)]
+                ("batched", C.c_int32), ("flags", C.c_int32), ("err_target", C.c_double)]
 
 
 class kv_result(C.Structure):
     _fields_ = [("lo", C.c_void_p), ("hi", C.c_void_p), ("basis", C.c_void_p), ("H", C.c_void_p),
                 ("P", C.c_void_p), ("beta0", C.c_void_p), ("m_used", C.c_void_p), ("z_star", C.c_void_p),
-                ("first_violation_step", C.c_int32), ("violation_row", C.c_int32), ("y_star", C.c_double)]
+                ("first_violation_step", C.c_int32), ("violation_row", C.c_int32), ("y_star", C.c_double),
+                ("err_bound", C.c_void_p)]
 
 
 EXPORTED = ["kv_version", "kv_last_error", "kv_create", "kv_destroy", "kv_pool_stats", "kv_system_stencil",
@@ -250,6 +251,7 @@ def _desc(problem, expm_mode: str, batched: bool, keep: list, flags: int = 0) ->
     d.expm_mode = _EXPM[expm_mode]
     d.batched = 1 if batched else 0
     d.flags = int(flags)
+    d.err_target = float(getattr(problem, "err_target", 0.0) or 0.0)
     return d
 
 
@@ -278,8 +280,10 @@ class ProblemHandle:
             out.update(basis=np.zeros((p.i, p.o, S)), H=np.zeros((p.i, p.m + 1, p.m)),
                        P=np.zeros((p.i, p.o, p.m)), beta0=np.zeros(p.i), m_used=np.zeros(p.i, dtype=np.int32))
         out["zstar"] = np.zeros(p.i)
+        out["err_bound"] = np.zeros(p.i)
         r = kv_result()
         r.lo, r.hi = _ptr(out["lo"]), _ptr(out["hi"])
+        r.err_bound = _ptr(out["err_bound"])
         if full:
             r.basis, r.H, r.P = _ptr(out["basis"]), _ptr(out["H"]), _ptr(out["P"])
             r.beta0, r.m_used = _ptr(out["beta0"]), _ptr(out["m_used"])
@@ -418,10 +422,11 @@ class Server:
         q, keep, p = self._keep[ticket]
         S = p.steps + 1
         out = dict(lo=np.zeros((p.o, S)), hi=np.zeros((p.o, S)), beta0=np.zeros(p.i),
-                   m_used=np.zeros(p.i, dtype=np.int32), zstar=np.zeros(p.i))
+                   m_used=np.zeros(p.i, dtype=np.int32), zstar=np.zeros(p.i), err_bound=np.zeros(p.i))
         r = kv_result()
         r.lo, r.hi, r.beta0, r.m_used, r.z_star = (_ptr(out["lo"]), _ptr(out["hi"]), _ptr(out["beta0"]),
                                                    _ptr(out["m_used"]), _ptr(out["zstar"]))
+        r.err_bound = _ptr(out["err_bound"])
         lat = C.c_double()
         rc = self._lib.kv_poll(self.h, ticket, C.byref(r), C.byref(lat))
         if rc == KV_ENOTREADY:

@@ -633,6 +633,10 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
             k_arnoldi_update<T><<<gu, CNT, 0, st>>>(va, N, stp, H, P, ad, cd, m, it, partials, counters, nbx);
             KV_CHECK_CUDA(cudaGetLastError());
         }
+        if (is_checkpoint(p, it + 1)) {
+            const int rc = launch_error_check(p, j0, ncols, it + 1);
+            if (rc) return rc;
+        }
     }
     return KV_OK;
 }

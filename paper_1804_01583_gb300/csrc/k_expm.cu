@@ -13,6 +13,12 @@
 //   PROPAGATE  one CTA per column: M = e^{H dt}, u_0 = e_1, u_k = M u_{k-1};
 //              the same vectors in exact arithmetic, s matrix-vector products
 //              instead of s exponentials.
+//
+// Both also record |(u_k)_mu|, the last entry of u_k = e^{t_k H_mu} e_1: the
+// integrand of the a-posteriori bound of Lemma 1 (Sec. 4.2), which
+// k_error_bound integrates by the trapezoid rule over the output grid.  For
+// the error control of Alg. 2 / Alg. 4 the same kernels run on the leading
+// k x k block of H at the checkpoint dimensions (dim = k, no basis output).
 #include <math.h>
 
 #include "kv_internal.h"
@@ -166,7 +172,17 @@ struct ExpmArgs {
     double* basis;         // i x o x (steps+1)
     int m, o, steps;
     double dt;
+    double* hlast;         // i x (steps+1): |(e^{t_k H_mu} e_1)_mu|
+    int dim;               // 0: each column's m_used, basis written; k > 0: H_k, columns not done only
+    int j0;                // first column of the launch
 };
+
+// Dimension a column is evaluated at, or 0 to skip it (a checkpoint of a
+// column that has stopped already).
+__device__ __forceinline__ int eval_dim(const ExpmArgs& a, int j) {
+    if (a.dim > 0) return a.st[j].done ? -1 : a.dim;
+    return a.st[j].m_used;
+}
 
 __device__ void load_scaled_H(const ExpmArgs& a, int j, int mu, double t, double* X) {
     const double* H = a.H + (int64_t)j * (a.m + 1) * a.m;
@@ -195,18 +211,23 @@ __global__ void __launch_bounds__(ENT) k_expm_per_step(ExpmArgs a) {
     __shared__ double fac[KV_MAX_M];
     __shared__ int piv;
     __shared__ double red[ENT / 32];
-    const int j = blockIdx.y;
-    const int mu = a.st[j].m_used;
+    const int j = a.j0 + blockIdx.y;
+    const int mu = eval_dim(a, j);
+    if (mu < 0) return;
+    double* hl = a.hlast + (int64_t)j * (a.steps + 1);
     for (int k = blockIdx.x; k <= a.steps; k += gridDim.x) {
-        if (mu <= 0) {
-            for (int r = threadIdx.x; r < a.o; r += ENT) a.basis[((int64_t)j * a.o + r) * (a.steps + 1) + k] = 0.0;
+        if (mu == 0) {
+            if (a.dim == 0)
+                for (int r = threadIdx.x; r < a.o; r += ENT) a.basis[((int64_t)j * a.o + r) * (a.steps + 1) + k] = 0.0;
+            if (threadIdx.x == 0) hl[k] = 0.0;
             continue;
         }
         double* buf[6];
         for (int q = 0; q < 6; ++q) buf[q] = smem + q * mu * mu;
         load_scaled_H(a, j, mu, (double)k * a.dt, buf[0]);
         const int res = sexpm(mu, buf, fac, &piv, red);
-        project_rows(a, j, mu, buf[res], mu, k);  // first column: stride mu
+        if (threadIdx.x == 0) hl[k] = fabs(buf[res][(mu - 1) * mu]);  // row mu, column 1
+        if (a.dim == 0) project_rows(a, j, mu, buf[res], mu, k);  // first column: stride mu
         __syncthreads();
     }
 }
@@ -216,10 +237,15 @@ __global__ void __launch_bounds__(ENT) k_expm_propagate(ExpmArgs a) {
     __shared__ double fac[KV_MAX_M];
     __shared__ int piv;
     __shared__ double red[ENT / 32];
-    const int j = blockIdx.x;
-    const int mu = a.st[j].m_used;
-    if (mu <= 0) {
-        for (int e = threadIdx.x; e < a.o * (a.steps + 1); e += ENT) a.basis[(int64_t)j * a.o * (a.steps + 1) + e] = 0.0;
+    const int j = a.j0 + blockIdx.x;
+    const int mu = eval_dim(a, j);
+    if (mu < 0) return;
+    double* hl = a.hlast + (int64_t)j * (a.steps + 1);
+    if (mu == 0) {
+        if (a.dim == 0)
+            for (int e = threadIdx.x; e < a.o * (a.steps + 1); e += ENT)
+                a.basis[(int64_t)j * a.o * (a.steps + 1) + e] = 0.0;
+        for (int k = threadIdx.x; k <= a.steps; k += ENT) hl[k] = 0.0;
         return;
     }
     double* buf[6];
@@ -232,7 +258,8 @@ __global__ void __launch_bounds__(ENT) k_expm_propagate(ExpmArgs a) {
     for (int l = threadIdx.x; l < mu; l += ENT) u[l] = (l == 0) ? 1.0 : 0.0;
     __syncthreads();
     for (int k = 0; k <= a.steps; ++k) {
-        project_rows(a, j, mu, u, 1, k);
+        if (threadIdx.x == 0) hl[k] = fabs(u[mu - 1]);
+        if (a.dim == 0) project_rows(a, j, mu, u, 1, k);
         if (k == a.steps) break;
         for (int l = threadIdx.x; l < mu; l += ENT) {
             double s = 0.0;
@@ -243,6 +270,52 @@ __global__ void __launch_bounds__(ENT) k_expm_propagate(ExpmArgs a) {
         double* t = u;
         u = v;
         v = t;
+    }
+}
+
+struct ErrArgs {
+    const double* H;       // i x (m+1) x m
+    ColState* st;          // i
+    const double* hlast;   // i x (steps+1)
+    double* err;           // i
+    const int* aug;        // i, or null: column works on A' (carries the constant)
+    double mu, mu_aug;     // log-norm bounds of A and A'
+    int m, steps;
+    double dt, eps;
+    int dim, j0;
+};
+
+// Lemma 1 (Sec. 4.2) with B = -A: err = h_{k+1,k} e^{max(mu,0) T} times the
+// trapezoid sum of |h(t_j)| over the output grid.  One CTA per column; the
+// partial sums are combined in a fixed order.  At a checkpoint (dim = k) a
+// column whose bound is below eps stops: done = 1, m_used = k (Alg. 2 /
+// Alg. 4), and the Krylov launches that follow return at once.
+__global__ void __launch_bounds__(ENT) k_error_bound(ErrArgs a) {
+    __shared__ double red[ENT / 32];
+    const int j = a.j0 + blockIdx.x;
+    ColState* st = a.st + j;
+    if (a.dim > 0 && st->done) return;
+    const int mu = a.dim > 0 ? a.dim : st->m_used;
+    const double* hl = a.hlast + (int64_t)j * (a.steps + 1);
+    double s = 0.0;
+    if (mu > 0)
+        for (int k = 1 + threadIdx.x; k <= a.steps; k += ENT) s += 0.5 * a.dt * (hl[k - 1] + hl[k]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double integral = 0.0;
+    for (int w = 0; w < ENT / 32; ++w) integral += red[w];
+    double err = 0.0;
+    if (mu > 0) {
+        const double hk1 = a.H[((int64_t)j * (a.m + 1) + mu) * a.m + (mu - 1)];
+        const double mu_col = (a.aug && a.aug[j]) ? a.mu_aug : a.mu;
+        if (hk1 != 0.0) err = hk1 * exp(fmax(mu_col, 0.0) * a.steps * a.dt) * integral;
+    }
+    a.err[j] = err;
+    if (a.dim > 0 && err < a.eps) {
+        st->m_used = a.dim;
+        st->done = 1;
     }
 }
 
@@ -279,23 +352,44 @@ int expm_prepare(int device) {
     return KV_OK;
 }
 
-int launch_expm_basis(Prob* p) {
+// The exponentials of columns j0 .. j0+ncols-1 at dimension dim (0: each
+// column's m_used, with the basis rows).
+static int launch_expm(Prob* p, int j0, int ncols, int dim) {
     int rc = expm_prepare(p->ctx->device);
     if (rc != KV_OK) return rc;
-    ExpmArgs a{p->d_H, p->d_P, p->d_state, p->d_basis, p->m, p->o, p->steps, p->dt};
-    const size_t smem = (size_t)6 * p->m * p->m * sizeof(double);
+    ExpmArgs a{p->d_H, p->d_P, p->d_state, p->d_basis, p->m, p->o, p->steps, p->dt, p->d_hlast, dim, j0};
+    const int mm = dim > 0 ? dim : p->m;
+    const size_t smem = (size_t)6 * mm * mm * sizeof(double);
     if (p->expm_mode == KV_EXPM_PROPAGATE) {
-        LaunchScope ls(p->ctx, "expm_propagate");
-        k_expm_propagate<<<p->i, ENT, smem, p->ctx->stream>>>(a);
+        LaunchScope ls(p->ctx, dim > 0 ? "error_expm" : "expm_propagate");
+        k_expm_propagate<<<ncols, ENT, smem, p->ctx->stream>>>(a);
     } else {
         int gx = p->steps + 1;
         if (gx > 65535 * 16) gx = 65535 * 16;
-        dim3 grd((unsigned)gx, (unsigned)p->i);
-        LaunchScope ls(p->ctx, "expm_per_step");
+        dim3 grd((unsigned)gx, (unsigned)ncols);
+        LaunchScope ls(p->ctx, dim > 0 ? "error_expm" : "expm_per_step");
         k_expm_per_step<<<grd, ENT, smem, p->ctx->stream>>>(a);
     }
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;
 }
+
+static int launch_bound(Prob* p, int j0, int ncols, int dim) {
+    ErrArgs e{p->d_H, p->d_state, p->d_hlast, p->d_err, p->sys->kind == 1 ? p->d_aug : nullptr,
+              p->sys->mu, p->sys->mu_aug, p->m, p->steps, p->dt, p->err_target, dim, j0};
+    LaunchScope ls(p->ctx, "error_bound");
+    k_error_bound<<<ncols, ENT, 0, p->ctx->stream>>>(e);
+    KV_CHECK_CUDA(cudaGetLastError());
+    return KV_OK;
+}
+
+int launch_expm_basis(Prob* p) { return launch_expm(p, 0, p->i, 0); }
+
+int launch_error_check(Prob* p, int j0, int ncols, int dim) {
+    int rc = launch_expm(p, j0, ncols, dim);
+    return rc ? rc : launch_bound(p, j0, ncols, dim);
+}
+
+int launch_error_final(Prob* p) { return launch_bound(p, 0, p->i, 0); }
 
 }  // namespace kv

@@ -275,6 +275,14 @@ int kv_system_stencil(kv_ctx* c, kv_sys** out, int ndim, const int64_t dims[3], 
     s->coef = coef;
     s->n = n;
     s->symmetric = true;
+    // largest eigenvalue of the Dirichlet-0 Laplacian: the Kronecker sum of the
+    // 1-D second differences' largest eigenvalues -(4/h^2) sin^2(pi / (2(N+1)))
+    s->mu = 0.0;
+    for (int a = 0; a < ndim; ++a) {
+        const double sn = sin(M_PI / (2.0 * (double)(s->dims[a] + 1)));
+        s->mu -= coef * 4.0 / (s->h[a] * s->h[a]) * sn * sn;
+    }
+    s->mu_aug = s->mu;
     if (b) {
         s->d_b = (double*)c->arena.alloc((size_t)n * sizeof(double));
         if (!s->d_b) {
@@ -368,6 +376,15 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
         delete s;
         return fail(KV_ECUDA, "kv_system_csr: upload failed: %s", cudaGetErrorString(e));
     }
+    rc = csr_lognorm_bounds(s, b, &s->mu, &s->mu_aug);
+    if (rc) {
+        c->arena.free(s->d_rp);
+        c->arena.free(s->d_col);
+        c->arena.free(s->d_val);
+        c->arena.free(s->d_b);
+        delete s;
+        return rc;
+    }
     *out = s;
     return KV_OK;
 }
@@ -399,6 +416,7 @@ static int validate(const Sys* s, const kv_problem_desc* d, int precision) {
     if ((int64_t)(d->steps + 1) * d->o >= ((int64_t)1 << 31) - 1) return fail(KV_EINVAL, "o * (steps+1) too large");
     if (d->method < KV_AUTO || d->method > KV_ARNOLDI) return fail(KV_EINVAL, "method");
     if (d->expm_mode != KV_EXPM_PER_STEP && d->expm_mode != KV_EXPM_PROPAGATE) return fail(KV_EINVAL, "expm_mode");
+    if (isnan(d->err_target)) return fail(KV_EINVAL, "err_target is NaN");
     const int64_t n = s->n;
     if (d->c_row_ptr[0] != 0) return fail(KV_EINVAL, "c_row_ptr[0] != 0");
     for (int r = 0; r < d->o; ++r) {
@@ -504,6 +522,7 @@ int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, s
     t += r256((size_t)reduce_slots_needed(&tmp) * sizeof(double)) + 256;
     t += r256((size_t)(d->o + 1) * 8) + 2 * r256((size_t)d->c_row_ptr[d->o] * 8) + r256((size_t)d->o * 8);
     t += 3 * r256((size_t)d->i * 8) + 2 * 256;
+    t += r256((size_t)d->i * 8) + r256((size_t)d->i * (d->steps + 1) * 8);  // error bound, its integrand
     for (int j = 0; j < d->i; ++j) {
         const kv_column& c = d->cols[j];
         if (c.kind == KV_COL_SPARSE) t += r256((size_t)(c.nnz + 1) * 8) * 2;
@@ -534,6 +553,7 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
     p->expm_mode = d->expm_mode;
     p->batched = d->batched;
     p->flags = d->flags;
+    p->err_target = d->err_target > 0.0 ? d->err_target : 0.0;
     plan_methods(s, d, p);
     p->fused = !(d->flags & KV_FLAG_TWO_PASS) && fused_tma_supported(p);
     p->N = s->n + (std::count(p->aug.begin(), p->aug.end(), 1) ? 1 : 0);
@@ -575,6 +595,8 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
         TRY(dalloc(p, &p->d_zstar, (size_t)p->i));
         TRY(dalloc(p, &p->d_ystar, 1));
         TRY(dalloc(p, &p->d_viol, 1));
+        TRY(dalloc(p, &p->d_err, (size_t)p->i));
+        TRY(dalloc(p, &p->d_hlast, (size_t)p->i * S));
         TRY(upload(c, p->d_crp, d->c_row_ptr, (size_t)(p->o + 1) * 8));
         TRY(upload(c, p->d_ccol, d->c_col, (size_t)cnnz * 8));
         TRY(upload(c, p->d_cval, d->c_val, (size_t)cnnz * 8));
@@ -669,6 +691,7 @@ static int run_column(Prob* p, int j) {
         }
         for (int it = 0; it < p->m; ++it) {
             rc = launch_lanczos_fused(p, j, it, vec(it % 3), vec((it + 2) % 3), vec((it + 1) % 3));
+            if (!rc && is_checkpoint(p, it + 1)) rc = launch_error_check(p, j, 1, it + 1);
             if (rc) return rc;
         }
         return KV_OK;
@@ -679,6 +702,7 @@ static int run_column(Prob* p, int j) {
             void* A = vec((it + 1) & 1);
             rc = launch_stencil_alpha(p, j, it, B);
             if (!rc) rc = launch_stencil_update(p, j, it, B, A);
+            if (!rc && is_checkpoint(p, it + 1)) rc = launch_error_check(p, j, 1, it + 1);
             if (rc) return rc;
         }
         return KV_OK;
@@ -724,6 +748,7 @@ int kv_enqueue(kv_prob* p) {
         }
     }
     rc = launch_expm_basis(p);
+    if (!rc) rc = launch_error_final(p);
     if (rc) return rc;
     rc = launch_bounds(p);
     if (rc) return rc;
@@ -762,6 +787,7 @@ int kv_fetch(kv_prob* p, kv_result* r) {
         KV_CHECK_CUDA(cudaMemcpy(&r->y_star, p->d_ystar, sizeof(double), cudaMemcpyDeviceToHost));
         if (r->z_star) KV_CHECK_CUDA(cudaMemcpy(r->z_star, p->d_zstar, (size_t)p->i * 8, cudaMemcpyDeviceToHost));
     }
+    if (r->err_bound) KV_CHECK_CUDA(cudaMemcpy(r->err_bound, p->d_err, (size_t)p->i * 8, cudaMemcpyDeviceToHost));
     if (status) return fail(KV_ETIMEOUT, "a device-side wait gave up (status %d)", status);
     return KV_OK;
 }

@@ -3,8 +3,11 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -85,6 +88,9 @@ struct Sys {
     int val_prec = KV_FP64;
     double* d_b = nullptr;
     bool symmetric = false;
+    // upper bounds of the largest eigenvalue of (A + A^T)/2, for A and for
+    // A' = [[A, b], [0, 0]] (Lemma 1 of Sec. 4.2 takes e^{max(mu,0) T})
+    double mu = 0.0, mu_aug = 0.0;
 };
 
 // --------------------------------------------------------------- device state
@@ -126,6 +132,7 @@ struct Prob {
     int expm_mode = KV_EXPM_PER_STEP;
     int batched = 0;
     int flags = 0;
+    double err_target = 0.0;     // > 0: a-posteriori error control (Alg. 2 / Alg. 4)
     bool fused = false;          // single-pass TMA Lanczos iterations on the grid
     std::vector<int> method;     // per column: KV_LANCZOS | KV_ARNOLDI
     std::vector<int> aug;        // per column: runs on A' (carries the constant)
@@ -149,6 +156,8 @@ struct Prob {
     double* d_zstar = nullptr;
     double* d_ystar = nullptr;
     int* d_viol = nullptr;
+    double* d_err = nullptr;    // per column: Lemma-1 bound at the dimension used
+    double* d_hlast = nullptr;  // per column, steps+1: |(e^{t_k H} e_1)_mu|, the integrand of the bound
     void* d_vec = nullptr;  // Krylov vectors
     int64_t N = 0;          // vector length (n, or n+1 if any column is augmented)
     int nvec = 0;           // vectors of length N per vector set
@@ -174,6 +183,23 @@ int launch_stencil_update(Prob* p, int j, int it, const void* B, void* A);
 bool fused_tma_supported(const Prob* p);
 int fused_tma_blocks(const Prob* p, int* zc);
 int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, void* W);
+
+// a-posteriori error bound (k_expm.cu): the exponentials of H_k at every
+// step for columns j0 .. j0+ncols-1 (dim = k), then the bound and the stop
+// decision; dim = 0: the bound at each column's m_used after the final basis
+int launch_error_check(Prob* p, int j0, int ncols, int dim);
+// Alg. 2 / Alg. 4: whether the error bound is evaluated after the iteration
+// that completes Krylov dimension k (error control on, k in 4, ceil(1.1 k),
+// ... in IEEE double, k < m)
+inline bool is_checkpoint(const Prob* p, int k) {
+    if (!(p->err_target > 0.0)) return false;
+    for (int c = 4; c < p->m; c = (int)ceil(1.1 * (double)c))
+        if (c == k) return true;
+    return false;
+}
+int launch_error_final(Prob* p);
+// Gershgorin bound of the symmetric part of a CSR matrix (k_lognorm.cu)
+int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug);
 
 // generic vectors (k_vector.cu)
 int launch_init_norm(Prob* p, int j, void* B);

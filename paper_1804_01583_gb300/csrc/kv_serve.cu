@@ -33,7 +33,7 @@ struct Request {
     int status = KV_ENOTREADY;
     std::string error;
     // results (host)
-    std::vector<double> lo, hi, zstar, beta0;
+    std::vector<double> lo, hi, zstar, beta0, err_bound;
     std::vector<int32_t> m_used;
     int32_t viol_step = -1, viol_row = -1;
     double ystar = 0.0;
@@ -110,12 +110,14 @@ void finish(kv_server* s, Request* r) {
     r->zstar.assign((size_t)d.i, 0.0);
     r->beta0.assign((size_t)d.i, 0.0);
     r->m_used.assign((size_t)d.i, 0);
+    r->err_bound.assign((size_t)d.i, 0.0);
     kv_result res{};
     res.lo = r->lo.data();
     res.hi = r->hi.data();
     res.z_star = r->zstar.data();
     res.beta0 = r->beta0.data();
     res.m_used = r->m_used.data();
+    res.err_bound = r->err_bound.data();
     const int rc = kv_fetch(r->prob, &res);
     if (rc) r->error = kv_last_error();
     r->viol_step = res.first_violation_step;
@@ -305,6 +307,7 @@ int kv_poll(kv_server* s, uint64_t ticket, kv_result* out, double* latency_ms) {
         (void)no;
         if (out->beta0) std::copy(r->beta0.begin(), r->beta0.end(), out->beta0);
         if (out->m_used) std::copy(r->m_used.begin(), r->m_used.end(), out->m_used);
+        if (out->err_bound) std::copy(r->err_bound.begin(), r->err_bound.end(), out->err_bound);
         if (out->z_star && r->viol_step >= 0) std::copy(r->zstar.begin(), r->zstar.end(), out->z_star);
         out->first_violation_step = r->viol_step;
         out->violation_row = r->viol_row;

@@ -209,10 +209,12 @@ def heat3d_truncated(full: Problem, side: int) -> Problem:
 # --------------------------------------------------------------------------
 # random sparse nonsymmetric system with forcing (stand-in for Sec. 5.1)
 # --------------------------------------------------------------------------
-def random_csr(n: int, nnz_per_row: int = 10, seed: int = 0, with_b: bool = True) -> CsrSystem:
+def random_csr(n: int, nnz_per_row: int = 10, seed: int = 0, with_b: bool = True,
+               column_dominant: bool = False) -> CsrSystem:
     """n x n, nnz_per_row distinct off-diagonal columns per row drawn uniformly
     (never the row itself), values N(0,1)/sqrt(nnz_per_row), diagonal
-    -(row abs-sum + 0.1); b ~ U[-0.01, 0.01]."""
+    -(row abs-sum + 0.1), or with column_dominant -(max(row, column abs-sum)
+    + 0.1) (dominant in both directions); b ~ U[-0.01, 0.01]."""
     rng = np.random.default_rng(seed)
     k = nnz_per_row
     rows = np.arange(n, dtype=np.int64)
@@ -229,7 +231,11 @@ def random_csr(n: int, nnz_per_row: int = 10, seed: int = 0, with_b: bool = True
         redraw.sort(axis=1)
         off[bad] = redraw
     vals = rng.standard_normal((n, k)) / math.sqrt(k)
-    diag = -(np.abs(vals).sum(axis=1) + 0.1)
+    rsum = np.abs(vals).sum(axis=1)
+    if column_dominant:
+        csum = np.bincount(off.reshape(-1), weights=np.abs(vals).reshape(-1), minlength=n)
+        rsum = np.maximum(rsum, csum)
+    diag = -(rsum + 0.1)
     cols = np.concatenate([off, rows[:, None]], axis=1)
     allv = np.concatenate([vals, diag[:, None]], axis=1)
     order = np.argsort(cols, axis=1, kind="stable")
