@@ -299,6 +299,7 @@ def run_gpu(args, rank: int, world: int):
         "queries_per_s": world * 1e3 / ms_step,
         "roofline": roof, "kernels": kernels, "e2e": out_e2e, "gpu_launches": launches,
         "clocks": clk, "first_violation_step": res["viol_step"],
+        "lemma1_bound": float(res["err_bound"][0]),
     }
     if args.compare_fp64 and p.precision != "fp64":
         line["fp64_plain"] = time_other_precision(kv, ctx, args, "fp64", torch, stream)
@@ -434,6 +435,40 @@ def serve_bench(args, dev: int):
             "oracle_sample": [qs[i].name for i in picked],
             "max_rel_bound_err_vs_fp64_gpu": err_gpu64, "fp64_gpu_sample": f"{len(sample)} random queries",
             "precision": "fp32 storage, fp64 accumulation"}
+
+
+def error_control_bench(dev: int):
+    """Alg. 4 with the Lemma-1 error control on the 3D heat grid of 100^3
+    (m up to 64, target 1e-6): the Krylov dimension the control picks, the
+    bound, the time per query and the cost of the checkpoints."""
+    import torch
+    import paper_1804_01583_gb300 as kv
+    out = {}
+    ctx = kv.Context(4 << 30, device=dev)
+    try:
+        for label, prec in (("fp64", "fp64"), ("fp32", "fp32")):
+            p = W.heat3d_100(m=64, steps=1000, precision=prec)
+            cell = W.grid_index((100, 100, 100), (12, 12, 12))
+            p.C_row_ptr, p.C_col, p.C_val = np.array([0, 1]), np.array([cell]), np.array([1.0])
+            p.err_target = 1e-6
+            sysh = kv.System(ctx, p.system, p.precision)
+            ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
+            ph.run(full=False)
+            torch.cuda.synchronize()
+            ctx.profile_enable(True)
+            t0 = time.perf_counter()
+            r = ph.run(full=True)
+            ms = (time.perf_counter() - t0) * 1e3
+            chk = sum(ctx.profile_read(nm)[1] for nm in ("error_expm", "error_bound"))
+            ctx.profile_enable(False)
+            out[label] = {"m_used": int(r["m_used"][0]), "lemma1_bound": float(r["err_bound"][0]),
+                          "ms_per_query": ms, "checkpoint_ms": chk}
+            ph.close()
+            sysh.close()
+    finally:
+        ctx.close()
+    out["workload"] = "heat3d-100^3, output cell (12,12,12), dt 0.02, 1000 steps, m <= 64, target 1e-6"
+    return out
 
 
 def batched_bench(dev: int, nq: int = 64, reps: int = 5):
@@ -594,6 +629,7 @@ def main():
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     if args.batched and world == 1:
         line["batched"] = batched_bench(dev)
+        line["error_control"] = error_control_bench(dev)
     if args.csr and world == 1:
         line["csr_workload"] = csr_bench(args, dev)
     if args.serve and world == 1:

@@ -102,7 +102,8 @@ typedef struct {
  * box on z, outputs y = C x with C in CSR form over the n state variables
  * (Sec. 3.1), unsafe set y_r >= theta_r (theta_r = +inf: row not checked),
  * step dt and steps + 1 check points t_k = k dt (k = 0 included), Krylov
- * dimension krylov_m (the paper's k, 1 <= krylov_m <= KV_MAX_M).
+ * dimension krylov_m (the paper's k; 1 <= krylov_m <= KV_MAX_M, or
+ * <= KV_MAX_M_LANCZOS when every column runs Lanczos).
  *
  * err_target > 0 turns on the a-posteriori error control of Alg. 2 / Alg. 4:
  * krylov_m is then the largest dimension, and each column stops at the first
@@ -143,7 +144,9 @@ typedef struct {
 #define KV_FLAG_NO_AUTOTUNE 4   /* CSR Arnoldi: fixed SpMM shape instead of timing the
                                    candidates at kv_problem (and the on-disk cache) */
 
-#define KV_MAX_M 64
+#define KV_MAX_M 64            /* largest krylov_m when any column runs Arnoldi */
+#define KV_MAX_M_LANCZOS 4096  /* largest krylov_m when every column runs Lanczos
+                                  (above 64 the exponential runs in global memory) */
 
 /* Results copied to the host.  lo and hi are required; every other array is
  * optional (NULL = not copied).  Layouts are row-major:

@@ -383,10 +383,22 @@ static int launch_bound(Prob* p, int j0, int ncols, int dim) {
     return KV_OK;
 }
 
-int launch_expm_basis(Prob* p) { return launch_expm(p, 0, p->i, 0); }
+int launch_expm_basis(Prob* p) {
+    if (p->m <= KV_MAX_M) return launch_expm(p, 0, p->i, 0);
+    for (int j = 0; j < p->i; ++j) {  // dimensions above the shared-memory kernels' reach
+        const int rc = launch_expm_large_column(p, j, 0, true);
+        if (rc) return rc;
+    }
+    return KV_OK;
+}
 
 int launch_error_check(Prob* p, int j0, int ncols, int dim) {
-    int rc = launch_expm(p, j0, ncols, dim);
+    int rc = KV_OK;
+    if (dim <= KV_MAX_M) {
+        rc = launch_expm(p, j0, ncols, dim);
+    } else {
+        for (int j = j0; j < j0 + ncols && !rc; ++j) rc = launch_expm_large_column(p, j, dim, false);
+    }
     return rc ? rc : launch_bound(p, j0, ncols, dim);
 }
 

@@ -412,7 +412,15 @@ static int validate(const Sys* s, const kv_problem_desc* d, int precision) {
     if (d->o < 1 || !d->c_row_ptr || !d->theta) return fail(KV_EINVAL, "need at least one output row");
     if (!(d->dt > 0) || !isfinite(d->dt)) return fail(KV_EINVAL, "dt must be positive and finite");
     if (d->steps < 0) return fail(KV_EINVAL, "steps must be >= 0");
-    if (d->krylov_m < 1 || d->krylov_m > KV_MAX_M) return fail(KV_EINVAL, "krylov_m must be in [1, %d]", KV_MAX_M);
+    bool any_arnoldi = false;
+    for (int j = 0; d->cols && j < d->i; ++j) {
+        const bool carries = s->d_b != nullptr && d->cols[j].is_fixed;
+        any_arnoldi = any_arnoldi || d->method == KV_ARNOLDI ||
+                      (d->method == KV_AUTO && !(s->symmetric && !carries));
+    }
+    const int mmax = any_arnoldi ? KV_MAX_M : KV_MAX_M_LANCZOS;
+    if (d->krylov_m < 1 || d->krylov_m > mmax)
+        return fail(KV_EINVAL, "krylov_m must be in [1, %d]%s", mmax, any_arnoldi ? " (Arnoldi columns)" : "");
     if ((int64_t)(d->steps + 1) * d->o >= ((int64_t)1 << 31) - 1) return fail(KV_EINVAL, "o * (steps+1) too large");
     if (d->method < KV_AUTO || d->method > KV_ARNOLDI) return fail(KV_EINVAL, "method");
     if (d->expm_mode != KV_EXPM_PER_STEP && d->expm_mode != KV_EXPM_PROPAGATE) return fail(KV_EINVAL, "expm_mode");
@@ -523,6 +531,7 @@ int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, s
     t += r256((size_t)(d->o + 1) * 8) + 2 * r256((size_t)d->c_row_ptr[d->o] * 8) + r256((size_t)d->o * 8);
     t += 3 * r256((size_t)d->i * 8) + 2 * 256;
     t += r256((size_t)d->i * 8) + r256((size_t)d->i * (d->steps + 1) * 8);  // error bound, its integrand
+    if (d->krylov_m > KV_MAX_M) t += r256(large_expm_scratch_doubles(d->krylov_m, d->steps) * 8);
     for (int j = 0; j < d->i; ++j) {
         const kv_column& c = d->cols[j];
         if (c.kind == KV_COL_SPARSE) t += r256((size_t)(c.nnz + 1) * 8) * 2;
@@ -597,6 +606,7 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
         TRY(dalloc(p, &p->d_viol, 1));
         TRY(dalloc(p, &p->d_err, (size_t)p->i));
         TRY(dalloc(p, &p->d_hlast, (size_t)p->i * S));
+        if (p->m > KV_MAX_M) TRY(dalloc(p, &p->d_lx, large_expm_scratch_doubles(p->m, p->steps)));
         TRY(upload(c, p->d_crp, d->c_row_ptr, (size_t)(p->o + 1) * 8));
         TRY(upload(c, p->d_ccol, d->c_col, (size_t)cnnz * 8));
         TRY(upload(c, p->d_cval, d->c_val, (size_t)cnnz * 8));

@@ -103,7 +103,7 @@ struct ColState {
     int m_used;
     int status;
     int pad;
-    double s[KV_MAX_M + 2];
+    double s[KV_MAX_M_LANCZOS + 2];
 };
 
 struct CDesc {  // output matrix C in CSR form on the device
@@ -158,6 +158,7 @@ struct Prob {
     int* d_viol = nullptr;
     double* d_err = nullptr;    // per column: Lemma-1 bound at the dimension used
     double* d_hlast = nullptr;  // per column, steps+1: |(e^{t_k H} e_1)_mu|, the integrand of the bound
+    double* d_lx = nullptr;     // m > KV_MAX_M: scratch of the global-memory exponential (one column at a time)
     void* d_vec = nullptr;  // Krylov vectors
     int64_t N = 0;          // vector length (n, or n+1 if any column is augmented)
     int nvec = 0;           // vectors of length N per vector set
@@ -215,6 +216,9 @@ size_t csr_arnoldi_dev_bytes();
 
 // exponential + basis (k_expm.cu)
 int launch_expm_basis(Prob* p);
+// global-memory exponential for dimensions above KV_MAX_M (k_expm_large.cu)
+size_t large_expm_scratch_doubles(int m, int steps);
+int launch_expm_large_column(Prob* p, int j, int dim, bool write_basis);
 int expm_prepare(int device);
 int fused_prepare();
 // one-time set-up that stream capture cannot contain (kv_graph.cu)

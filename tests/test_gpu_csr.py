@@ -204,6 +204,23 @@ def test_autotuner_cache(ctx, tmp_path, monkeypatch):
     assert int(g) in (1, 2, 4, 8) and int(l) in (1, 2, 4) and "n=120000" in key and "cols=8" in key
 
 
+def test_krylov_limit_depends_on_the_method(ctx):
+    """Arnoldi columns (stored basis, shared-memory Gram scratch) allow
+    krylov_m <= KV_MAX_M; a problem whose columns all run Lanczos allows up
+    to KV_MAX_M_LANCZOS."""
+    p = W.random_csr_problem(2000, seed=1, n_gen=2, o=1, c_width=100, dt=0.01, steps=5, m=kv.KV_MAX_M + 1)
+    sysh = kv.System(ctx, p.system)
+    with pytest.raises(kv.KvError) as ei:
+        kv.ProblemHandle(ctx, sysh, p)
+    assert ei.value.code == kv.KV_EINVAL
+    sysh.close()
+    q = W.random_problem(W.random_symmetric_csr(300, seed=2), seed=3, n_cols=1, o=1, dt=0.05, steps=5,
+                         m=kv.KV_MAX_M + 1)
+    sysh = kv.System(ctx, q.system)
+    kv.ProblemHandle(ctx, sysh, q).close()
+    sysh.close()
+
+
 def test_malformed_csr_rejected(ctx):
     rp = np.array([0, 2, 3], dtype=np.int64)
     for col in (np.array([1, 0, 0], dtype=np.int32), np.array([0, 5, 1], dtype=np.int32)):

@@ -195,3 +195,75 @@ def test_serving_carries_the_bound(ctx):
         srv.close()
     assert np.array_equal(out["m_used"], solo["m_used"]) and np.array_equal(out["err_bound"], solo["err_bound"])
     assert np.array_equal(out["hi"], solo["hi"])
+
+
+# ---- Krylov dimensions above 64: the global-memory exponential (Taylor 18
+# with scaling and squaring, doubling over the output steps) against the
+# oracle's per-step Pade exponential
+
+def heat40(precision="fp64", m=120):
+    return W.heat((40, 40, 40), block=(6, 6, 6), output="centre", dt=0.05, steps=80, m=m, precision=precision)
+
+
+@pytest.mark.parametrize("expm_mode", ["per_step", "propagate"])
+def test_large_m_fixed(ctx, expm_mode):
+    """m = 120 > 64, fixed: H, the basis rows, the bounds and the Lemma-1
+    bound within 1e-9 of the oracle (the schedule setting does not apply
+    above 64: the doubling runs)."""
+    from parity import krylov_error
+    p = heat40()
+    got = run_gpu(ctx, p, expm_mode=expm_mode)
+    ref = oracle.run(p)
+    eh, ep = krylov_error(got, ref, 0)
+    assert eh <= 1e-9 and ep <= 1e-9, (eh, ep)
+    S = np.max(np.abs(ref["basis"][0]))
+    assert np.max(np.abs(got["basis"][0] - ref["basis"][0])) <= 1e-9 * S
+    check_control(got, ref, p, 1e-9, 1e-9)
+
+
+def test_large_m_error_control_fp64(ctx):
+    """Checkpoints below 64 (shared-memory exponential) and above (global
+    memory) in one run; the stop dimension is above 64."""
+    p = heat40(m=200)
+    p.err_target, (k,) = pick_target(p)
+    assert 64 < k < 200
+    ref = oracle.run(p)
+    got = run_gpu(ctx, p)
+    check_control(got, ref, p, 1e-9, 1e-9)
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_large_m_error_control_fp32(ctx, path):
+    p64 = W.heat((60, 50, 40), block=(8, 8, 8), output="centre", dt=0.05, steps=60, m=200)
+    eps, (k,) = pick_target(p64)
+    assert 64 < k < 200
+    p64.err_target = eps
+    ref = oracle.run(p64)
+    p32 = W.heat((60, 50, 40), block=(8, 8, 8), output="centre", dt=0.05, steps=60, m=200, precision="fp32")
+    p32.err_target = eps
+    got = run_gpu(ctx, p32, flags=path)
+    check_control(got, ref, p64, 1e-6, 1e-5)
+
+
+def laplacian2d_csr(N: int, coef: float = 0.01) -> "W.CsrSystem":
+    """The 2-D Dirichlet heat operator assembled as a symmetric CSR matrix
+    (a wide spectrum: the Krylov dimension the control needs is large)."""
+    import scipy.sparse as sp
+    h = 1.0 / (N + 1)
+    L1 = sp.diags([np.ones(N - 1), -2 * np.ones(N), np.ones(N - 1)], [-1, 0, 1])
+    A = (coef / h ** 2) * (sp.kron(sp.eye(N), L1) + sp.kron(L1, sp.eye(N))).tocsr()
+    A.sort_indices()
+    return W.CsrSystem(n=N * N, row_ptr=A.indptr.astype(np.int64), col=A.indices.astype(np.int32),
+                       val=A.data.astype(np.float64), b=None, symmetric=True)
+
+
+def test_large_m_csr_lanczos_columns(ctx):
+    """Symmetric CSR, three columns, m = 200 with error control: columns stop
+    on their own checkpoints (above 64, two different ones) and the final
+    exponential runs per column at each one's dimension."""
+    p = W.random_problem(laplacian2d_csr(60), seed=22, n_cols=3, o=2, dt=0.05, steps=60, m=200)
+    p.err_target, stops = pick_target(p, distinct=True, near=1e-7)
+    assert min(stops) > 64 and len(set(stops)) > 1
+    ref = oracle.run(p)
+    got = run_gpu(ctx, p)
+    check_control(got, ref, p, 1e-9, 1e-9)

@@ -239,7 +239,7 @@ def test_heat3d_1000_full_size(ctx, precision):
 def test_invalid_arguments(ctx):
     p = W.heat2d_20()
     sysh = kv.System(ctx, p.system)
-    for mutate in [lambda q: setattr(q, "m", 0), lambda q: setattr(q, "m", kv.KV_MAX_M + 1),
+    for mutate in [lambda q: setattr(q, "m", 0), lambda q: setattr(q, "m", kv.KV_MAX_M_LANCZOS + 1),
                    lambda q: setattr(q, "dt", -1.0), lambda q: setattr(q, "steps", -2),
                    lambda q: setattr(q.columns[0], "box_hi", (21, 5)),
                    lambda q: setattr(q, "C_col", np.array([400], dtype=np.int64)),
