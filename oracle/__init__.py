@@ -56,7 +56,7 @@ class _Op(C.Structure):
     _fields_ = [("kind", C.c_int), ("ndim", C.c_int), ("dims", C.c_int64 * 3),
                 ("coef", C.c_double), ("h", C.c_double * 3), ("n", C.c_int64),
                 ("rp", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
-                ("b", C.c_void_p), ("aug", C.c_int)]
+                ("b", C.c_void_p), ("aug", C.c_int), ("trans", C.c_int)]
 
 
 def _load():
@@ -96,7 +96,7 @@ def num_threads() -> int:
 class _OpHolder:
     """Keeps the numpy arrays referenced by an ora_op alive."""
 
-    def __init__(self, system, aug: bool):
+    def __init__(self, system, aug: bool, trans: bool = False):
         self.keep = []
         op = _Op()
         if hasattr(system, "dims"):
@@ -121,6 +121,7 @@ class _OpHolder:
             self.keep.append(b)
             op.b = _p(b)
         op.aug = 1 if aug else 0
+        op.trans = 1 if trans else 0
         self.op = op
 
     @property
@@ -128,9 +129,10 @@ class _OpHolder:
         return int(self.op.n) + int(self.op.aug)
 
 
-def apply(system, x: np.ndarray, aug: bool = False) -> np.ndarray:
-    """y = A x (or A' x with the constant variable appended when aug)."""
-    h = _OpHolder(system, aug)
+def apply(system, x: np.ndarray, aug: bool = False, trans: bool = False) -> np.ndarray:
+    """y = A x (or A' x with the constant variable appended when aug; the
+    transposes with trans)."""
+    h = _OpHolder(system, aug, trans)
     x = np.ascontiguousarray(x, dtype=np.float64)
     assert x.shape == (h.N,)
     y = np.empty(h.N)
@@ -145,10 +147,11 @@ def _c_arrays(C_row_ptr, C_col, C_val):
 
 
 def krylov(system, v1: np.ndarray, m: int, C_row_ptr, C_col, C_val, *, method: str,
-           aug: bool = False):
-    """Lanczos (Alg. 3/4) or Arnoldi (Alg. 1) from the normalised v1.
+           aug: bool = False, trans: bool = False):
+    """Lanczos (Alg. 3/4) or Arnoldi (Alg. 1) from the normalised v1, on A
+    (A' when aug; their transposes when trans).
     Returns (H (m+1) x m, P o x m, number of valid columns)."""
-    h = _OpHolder(system, aug)
+    h = _OpHolder(system, aug, trans)
     v1 = np.ascontiguousarray(v1, dtype=np.float64)
     assert v1.shape == (h.N,)
     crp, ccol, cval = _c_arrays(C_row_ptr, C_col, C_val)
@@ -260,11 +263,95 @@ def column_method(problem, col) -> str:
     return "lanczos" if (sym and not carries) else "arnoldi"
 
 
+def transposed(problem) -> bool:
+    """Whether the basis matrix is computed from the transpose dynamics
+    (Sec. 4.1: o simulations of x' = A^T x from the rows of C, projected by
+    E^T) rather than from the columns of E; "auto" takes the smaller of i
+    and o, as the paper proposes."""
+    mode = getattr(problem, "simulate", "forward")
+    if mode == "auto":
+        return problem.o < problem.i
+    return mode == "transpose"
+
+
+def _run_transposed(problem, sel, want_basis, eps):
+    """C e^{At} E = (E^T e^{A^T t} C^T)^T: one Krylov run per output row r on
+    A^T (A'^T = [[A^T, 0], [b^T, 0]] when a column carries the constant),
+    from C_r^T, with the rows of E^T (the constant entry of a fixed column
+    included) as the projection; basis[j][r][k] = ||C_r|| P_r[j, :] e^{H_r t_k} e_1."""
+    from workloads import column_dense
+
+    sysm = problem.system
+    n = int(sysm.n)
+    dims = getattr(sysm, "dims", None)
+    taug = sysm.b is not None and any(c.is_fixed for c in problem.columns)
+    N = n + (1 if taug else 0)
+    # E'^T as CSR rows (one per column of E)
+    erp, ecol, eval_ = [0], [], []
+    for c in problem.columns:
+        e = column_dense(c, n, dims)
+        if taug:
+            e = np.concatenate([e, [1.0 if c.is_fixed else 0.0]])
+        nz = np.nonzero(e)[0]
+        ecol.extend(nz.tolist())
+        eval_.extend(e[nz].tolist())
+        erp.append(len(ecol))
+    erp = np.array(erp, dtype=np.int64)
+    ecol = np.array(ecol, dtype=np.int64)
+    eval_ = np.array(eval_, dtype=np.float64)
+    sym = bool(getattr(sysm, "symmetric", False)) or dims is not None
+    method = problem.method if problem.method in ("lanczos", "arnoldi") else (
+        "lanczos" if (sym and not taug) else "arnoldi")
+    mu = mu_bound(sysm, taug)
+    crp = np.asarray(problem.C_row_ptr, dtype=np.int64)
+    ccol = np.asarray(problem.C_col, dtype=np.int64)
+    cval = np.asarray(problem.C_val, dtype=np.float64)
+    Hs, Ps, used, beta0s, errs, checks = {}, {}, {}, {}, {}, {}
+    bases = np.zeros((problem.i, problem.o, problem.steps + 1))
+    for r in sel:
+        c = np.zeros(N)
+        np.add.at(c, ccol[crp[r]:crp[r + 1]], cval[crp[r]:crp[r + 1]])
+        b0 = float(np.sqrt(np.dot(c, c)))
+        beta0s[r] = b0
+        if b0 == 0.0:
+            Hs[r], Ps[r], used[r] = np.zeros((problem.m + 1, problem.m)), np.zeros((problem.i, problem.m)), 0
+            errs[r], checks[r] = 0.0, []
+            continue
+        H, P, u = krylov(sysm, c / b0, problem.m, erp, ecol, eval_, method=method, aug=taug, trans=True)
+        checks[r] = []
+        if eps > 0.0:
+            for k in checkpoints(problem.m):
+                if k >= u:
+                    break
+                ek = lemma1(H, k, mu, problem.dt, problem.steps)
+                checks[r].append((k, ek))
+                if ek < eps:
+                    u = k
+                    break
+        errs[r] = lemma1(H, u, mu, problem.dt, problem.steps)
+        Hs[r], Ps[r], used[r] = H, P, u
+        if want_basis:
+            bases[:, r, :] = basis(H, P, u, b0, problem.dt, problem.steps)
+    out = dict(H=Hs, P=Ps, used=used, beta0=beta0s, err=errs, checks=checks, transposed=True,
+               basis={j: bases[j] for j in range(problem.i)})
+    if want_basis and len(sel) == problem.o:
+        zlo = [c.zlo for c in problem.columns]
+        zhi = [c.zhi for c in problem.columns]
+        out.update(bounds(bases, zlo, zhi, problem.theta))
+    return out
+
+
 def run(problem, *, columns: Optional[List[int]] = None, want_basis: bool = True) -> Dict:
     """The whole path for one problem.  `columns` restricts the Krylov runs to
-    a subset of the initial-space columns (for sampled checks on large cases);
-    bounds are then only computed when every column was run."""
+    a subset of the initial-space columns (for sampled checks on large cases;
+    of the output rows when the transpose dynamics run); bounds are then only
+    computed when every run was made."""
     from workloads import column_dense
+
+    if transposed(problem):
+        eps_t = float(getattr(problem, "err_target", 0.0) or 0.0)
+        sel_t = list(range(problem.o)) if columns is None else list(columns)
+        return _run_transposed(problem, sel_t, want_basis, eps_t)
 
     sysm = problem.system
     n = int(sysm.n)

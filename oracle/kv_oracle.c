@@ -59,6 +59,7 @@ typedef struct {
     const double *val;    /* CSR values */
     const double *b;      /* forcing term, n entries, or NULL */
     int aug;              /* 1: the state carries the constant variable at index n */
+    int trans;            /* 1: apply the transpose (A^T, or A'^T when aug) */
 } ora_op;
 
 int ora_num_threads(void) {
@@ -119,8 +120,28 @@ static void csr_apply(const ora_op *op, const double *x, double *y) {
     }
 }
 
-/* y = A' x with A' = [[A, b], [0, 0]] when aug (Sec. 2.1), else y = A x. */
+/* y = A^T x: every stored a_rc adds a_rc x_r to y_c (serial scatter). */
+static void csr_apply_transpose(const ora_op *op, const double *x, double *y) {
+    for (int64_t c = 0; c < op->n; c++) y[c] = 0.0;
+    for (int64_t r = 0; r < op->n; r++)
+        for (int64_t e = op->rp[r]; e < op->rp[r + 1]; e++) y[op->col[e]] += op->val[e] * x[r];
+}
+
+/* y = A' x with A' = [[A, b], [0, 0]] when aug (Sec. 2.1), else y = A x.
+ * trans: y = A'^T x = (A^T x_{0:n}, b . x_{0:n}), the transpose dynamics of
+ * Sec. 4.1 (the grid Laplacian is symmetric, A^T = A). */
 void ora_apply(const ora_op *op, const double *x, double *y) {
+    if (op->trans) {
+        if (op->kind == 0) grid_apply(op, x, y);
+        else csr_apply_transpose(op, x, y);
+        if (op->aug) {
+            double s = 0.0;
+            if (op->b)
+                for (int64_t r = 0; r < op->n; r++) s += op->b[r] * x[r];
+            y[op->n] = s;
+        }
+        return;
+    }
     if (op->kind == 0) grid_apply(op, x, y);
     else csr_apply(op, x, y);
     if (op->aug) {

@@ -98,6 +98,7 @@ class Problem:
     precision: str = "fp64"    # fp64 | fp32
     name: str = ""
     err_target: float = 0.0    # > 0: a-posteriori error control with m as the maximum dimension
+    simulate: str = "forward"  # forward | transpose | auto (the smaller of i and o runs)
 
     @property
     def o(self) -> int:
