@@ -134,7 +134,20 @@ typedef struct {
     int32_t batched;            /* CSR: 1 = all Arnoldi columns share one SpMM */
     int32_t flags;              /* KV_FLAG_* bits, 0 = defaults */
     double err_target;          /* > 0: error control with krylov_m as the largest dimension */
+    int32_t simulate;           /* KV_SIM_FORWARD | KV_SIM_TRANSPOSE | KV_SIM_AUTO */
 } kv_problem_desc;
+
+/* kv_problem_desc.simulate: how the basis matrix C e^{At} E is built (Sec. 4.1).
+ * FORWARD: one Krylov run per column of E (i runs), projected by C.
+ * TRANSPOSE: one run per row of C of the transpose dynamics x' = A^T x
+ *   (A'^T = [[A^T, 0], [b^T, 0]] when a column carries the constant), started
+ *   at C_r^T and projected by E^T: C e^{At} E = (E^T e^{A^T t} C^T)^T, o runs.
+ *   The per-run results of kv_result (H, P, beta0, m_used, err_bound) then
+ *   have o entries, and P is i x krylov_m per run (E^T V).
+ * AUTO: TRANSPOSE when o < i, else FORWARD (the smaller of i and o runs). */
+#define KV_SIM_FORWARD 0
+#define KV_SIM_TRANSPOSE 1
+#define KV_SIM_AUTO 2
 
 /* kv_problem_desc.flags */
 #define KV_FLAG_TWO_PASS 1      /* grid Lanczos: use the two-pass kernels even where
@@ -219,6 +232,11 @@ int kv_sys_destroy(kv_sys *sys);
 int kv_problem(kv_ctx *ctx, kv_prob **out, const kv_sys *sys, const kv_problem_desc *desc,
                int precision);
 int kv_prob_destroy(kv_prob *prob);
+
+/* Number of Krylov runs of a problem (i, or o with the transpose dynamics)
+ * and whether the transpose dynamics run: the length of the per-run arrays of
+ * kv_result. */
+int kv_problem_runs(const kv_prob *prob, int32_t *runs, int32_t *transposed);
 
 /* Device bytes kv_problem would reserve (the memory model of Sec. 4.2-4.3 for this
  * implementation: two n-vectors for Lanczos, m+1 for Arnoldi, plus the

@@ -31,6 +31,17 @@ KV_FLAG_TWO_PASS = 1
 _PREC = {"fp64": KV_FP64, "fp32": KV_FP32}
 _METH = {"auto": KV_AUTO, "lanczos": KV_LANCZOS, "arnoldi": KV_ARNOLDI}
 _EXPM = {"per_step": KV_EXPM_PER_STEP, "propagate": KV_EXPM_PROPAGATE}
+KV_SIM_FORWARD, KV_SIM_TRANSPOSE, KV_SIM_AUTO = 0, 1, 2
+_SIM = {"forward": KV_SIM_FORWARD, "transpose": KV_SIM_TRANSPOSE, "auto": KV_SIM_AUTO}
+
+
+def runs_of(problem):
+    """(runs, transposed): the Krylov runs a problem makes -- one per column
+    of E, or one per row of C with the transpose dynamics (the library's
+    rule: "auto" transposes when o < i)."""
+    mode = getattr(problem, "simulate", "forward")
+    tr = mode == "transpose" or (mode == "auto" and problem.o < problem.i)
+    return (problem.o if tr else problem.i), tr
 
 
 class KvError(RuntimeError):
@@ -50,7 +61,8 @@ class kv_problem_desc(C.Structure):
                 ("c_row_ptr", C.c_void_p), ("c_col", C.c_void_p), ("c_val", C.c_void_p),
                 ("theta", C.c_void_p), ("dt", C.c_double), ("steps", C.c_int32),
                 ("krylov_m", C.c_int32), ("method", C.c_int32), ("expm_mode", C.c_int32),
-                ("batched", C.c_int32), ("flags", C.c_int32), ("err_target", C.c_double)]
+                ("batched", C.c_int32), ("flags", C.c_int32), ("err_target", C.c_double),
+                ("simulate", C.c_int32)]
 
 
 class kv_result(C.Structure):
@@ -62,7 +74,8 @@ class kv_result(C.Structure):
 
 EXPORTED = ["kv_version", "kv_last_error", "kv_create", "kv_destroy", "kv_pool_stats", "kv_system_stencil",
             "kv_system_csr", "kv_sys_destroy", "kv_problem", "kv_prob_destroy", "kv_problem_bytes",
-            "kv_enqueue", "kv_fetch", "kv_run", "kv_profile_enable", "kv_profile_read", "kv_launch_count"]
+            "kv_enqueue", "kv_fetch", "kv_run", "kv_profile_enable", "kv_profile_read", "kv_launch_count",
+            "kv_problem_runs"]
 
 _lib = None
 _lock = threading.Lock()
@@ -99,6 +112,7 @@ def load(path: Optional[str] = None):
         lib.kv_profile_enable.argtypes = [V, I]
         lib.kv_profile_read.argtypes = [V, C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         lib.kv_launch_count.argtypes = [V, C.POINTER(C.c_int64)]
+        lib.kv_problem_runs.argtypes = [V, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         lib.kv_grid_lanczos_noalloc.argtypes = [I, V, I, C.POINTER(C.c_int64), C.c_double, C.POINTER(C.c_double),
                                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_double, C.c_int32,
                                                 V, V, V, C.c_int32, V, V, V, V]
@@ -253,6 +267,7 @@ def _desc(problem, expm_mode: str, batched: bool, keep: list, flags: int = 0) ->
     d.batched = 1 if batched else 0
     d.flags = int(flags)
     d.err_target = float(getattr(problem, "err_target", 0.0) or 0.0)
+    d.simulate = _SIM[getattr(problem, "simulate", "forward")]
     return d
 
 
@@ -269,6 +284,9 @@ class ProblemHandle:
         h = C.c_void_p()
         _check(ctx._lib.kv_problem(ctx.h, C.byref(h), sysh.h, C.byref(self.desc), _PREC[problem.precision]))
         self.h = h
+        runs, tr = C.c_int32(), C.c_int32()
+        _check(ctx._lib.kv_problem_runs(h, C.byref(runs), C.byref(tr)))
+        self.runs, self.transposed = int(runs.value), bool(tr.value)
 
     def enqueue(self):
         _check(self.ctx._lib.kv_enqueue(self.h))
@@ -277,11 +295,14 @@ class ProblemHandle:
         p = self.problem
         S = p.steps + 1
         out = dict(lo=np.zeros((p.o, S)), hi=np.zeros((p.o, S)))
+        R = self.runs                        # per-run arrays (o runs with the transpose dynamics)
+        prow = p.i if self.transposed else p.o  # rows of each run's P
         if full:
-            out.update(basis=np.zeros((p.i, p.o, S)), H=np.zeros((p.i, p.m + 1, p.m)),
-                       P=np.zeros((p.i, p.o, p.m)), beta0=np.zeros(p.i), m_used=np.zeros(p.i, dtype=np.int32))
+            out.update(basis=np.zeros((p.i, p.o, S)), H=np.zeros((R, p.m + 1, p.m)),
+                       P=np.zeros((R, prow, p.m)), beta0=np.zeros(R), m_used=np.zeros(R, dtype=np.int32))
         out["zstar"] = np.zeros(p.i)
-        out["err_bound"] = np.zeros(p.i)
+        out["err_bound"] = np.zeros(R)
+        out["transposed"] = self.transposed
         r = kv_result()
         r.lo, r.hi = _ptr(out["lo"]), _ptr(out["hi"])
         r.err_bound = _ptr(out["err_bound"])
@@ -422,8 +443,9 @@ class Server:
         KvError if the query failed)."""
         q, keep, p = self._keep[ticket]
         S = p.steps + 1
-        out = dict(lo=np.zeros((p.o, S)), hi=np.zeros((p.o, S)), beta0=np.zeros(p.i),
-                   m_used=np.zeros(p.i, dtype=np.int32), zstar=np.zeros(p.i), err_bound=np.zeros(p.i))
+        R, _ = runs_of(p)
+        out = dict(lo=np.zeros((p.o, S)), hi=np.zeros((p.o, S)), beta0=np.zeros(R),
+                   m_used=np.zeros(R, dtype=np.int32), zstar=np.zeros(p.i), err_bound=np.zeros(R))
         r = kv_result()
         r.lo, r.hi, r.beta0, r.m_used, r.z_star = (_ptr(out["lo"]), _ptr(out["hi"]), _ptr(out["beta0"]),
                                                    _ptr(out["m_used"]), _ptr(out["zstar"]))

@@ -623,6 +623,10 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
                                                     N, aug, stp, H, m, it, partials, counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }
+            if (p->d_brow) {  // A'^T of the transpose dynamics: its last row b . x
+                const int rc = launch_row_dot(p, j0, ncols, V, it, it + 1, it);
+                if (rc) return rc;
+            }
             {
                 LaunchScope ls(p->ctx, "arnoldi_dots");
                 k_arnoldi_dots<T><<<gr, CNT, 0, st>>>(va, N, stp, H, ad, m, it, partials, counters, nbx);

@@ -72,8 +72,7 @@ static int grid_for(int64_t n) {
 int launch_scatter(Prob* p, int j, void* B) {
     const size_t es = elem_size(p->prec);
     KV_CHECK_CUDA(cudaMemsetAsync(B, 0, (size_t)p->N * es, p->ctx->stream));
-    const kv_column& c = p->cols[j];
-    int64_t nnz = c.nnz + (p->aug[j] ? 1 : 0);
+    const int64_t nnz = p->sidx_n[j];  // exactly what kv_problem uploaded
     if (nnz == 0) return KV_OK;
     LaunchScope ls(p->ctx, "scatter");
     if (p->prec == KV_FP32)

@@ -398,6 +398,9 @@ int kv_sys_destroy(kv_sys* s) {
     c->arena.free(s->d_col);
     c->arena.free(s->d_val);
     c->arena.free(s->d_b);
+    c->arena.free(s->d_rpT);
+    c->arena.free(s->d_colT);
+    c->arena.free(s->d_valT);
     delete s;
     return KV_OK;
 }
@@ -425,6 +428,7 @@ static int validate(const Sys* s, const kv_problem_desc* d, int precision) {
     if (d->method < KV_AUTO || d->method > KV_ARNOLDI) return fail(KV_EINVAL, "method");
     if (d->expm_mode != KV_EXPM_PER_STEP && d->expm_mode != KV_EXPM_PROPAGATE) return fail(KV_EINVAL, "expm_mode");
     if (isnan(d->err_target)) return fail(KV_EINVAL, "err_target is NaN");
+    if (d->simulate < KV_SIM_FORWARD || d->simulate > KV_SIM_AUTO) return fail(KV_EINVAL, "simulate");
     const int64_t n = s->n;
     if (d->c_row_ptr[0] != 0) return fail(KV_EINVAL, "c_row_ptr[0] != 0");
     for (int r = 0; r < d->o; ++r) {
@@ -471,16 +475,116 @@ static int validate(const Sys* s, const kv_problem_desc* d, int precision) {
     return KV_OK;
 }
 
-static void plan_methods(const Sys* s, const kv_problem_desc* d, Prob* p) {
+// How a problem is built: the default, or the inner problem of the
+// transpose dynamics (its runs start at the rows of C with constant entry 0;
+// with trans_aug they run on A'^T, whose last row is b . x).
+struct BuildOpts {
+    bool trans_runs = false;
+    int trans_aug = 0;
+    const double* brow = nullptr;
+};
+
+static void plan_methods(const Sys* s, const kv_problem_desc* d, Prob* p, const BuildOpts& bo = BuildOpts{}) {
     p->method.resize(d->i);
     p->aug.resize(d->i);
     for (int j = 0; j < d->i; ++j) {
-        const bool carries = s->d_b != nullptr && d->cols[j].is_fixed != 0;
+        const bool carries = bo.trans_runs ? bo.trans_aug != 0 : (s->d_b != nullptr && d->cols[j].is_fixed != 0);
         p->aug[j] = carries ? 1 : 0;
         int m = d->method;
         if (m == KV_AUTO) m = (s->symmetric && !carries) ? KV_LANCZOS : KV_ARNOLDI;
         p->method[j] = m;
     }
+}
+
+static bool runs_transposed(const kv_problem_desc* d) {
+    return d->simulate == KV_SIM_TRANSPOSE || (d->simulate == KV_SIM_AUTO && d->o < d->i);
+}
+
+static bool carries_constant(const Sys* s, const kv_problem_desc* d) {
+    if (!s->d_b) return false;
+    for (int j = 0; j < d->i; ++j)
+        if (d->cols[j].is_fixed) return true;
+    return false;
+}
+
+// The inner problem of the transpose dynamics (Sec. 4.1): one run per row of
+// C (a sparse start vector, duplicate indices summed), the rows of
+// E'^T = [E; constant row]^T as its projection, thresholds unused.
+struct InnerDesc {
+    kv_problem_desc d{};
+    std::vector<kv_column> cols;
+    std::vector<std::vector<int64_t>> ridx;
+    std::vector<std::vector<double>> rval;
+    std::vector<int64_t> crp, ccol;
+    std::vector<double> cval, theta;
+};
+
+static void make_inner_desc(const Sys* s, const kv_problem_desc* d, bool taug, InnerDesc& in) {
+    in.d = *d;
+    in.cols.assign(d->o, kv_column{});
+    in.ridx.assign(d->o, {});
+    in.rval.assign(d->o, {});
+    for (int r = 0; r < d->o; ++r) {
+        std::vector<std::pair<int64_t, double>> e;
+        for (int64_t q = d->c_row_ptr[r]; q < d->c_row_ptr[r + 1]; ++q) e.emplace_back(d->c_col[q], d->c_val[q]);
+        std::sort(e.begin(), e.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (auto& pr : e) {
+            if (!in.ridx[r].empty() && in.ridx[r].back() == pr.first) in.rval[r].back() += pr.second;
+            else {
+                in.ridx[r].push_back(pr.first);
+                in.rval[r].push_back(pr.second);
+            }
+        }
+        kv_column& c = in.cols[r];
+        c.kind = KV_COL_SPARSE;
+        c.zlo = c.zhi = 1.0;
+        c.nnz = (int64_t)in.ridx[r].size();
+        c.idx = in.ridx[r].data();
+        c.val = in.rval[r].data();
+    }
+    in.crp.assign(1, 0);
+    const int64_t n = s->n;
+    for (int j = 0; j < d->i; ++j) {
+        const kv_column& c = d->cols[j];
+        if (c.kind == KV_COL_BOX) {
+            const int64_t nx = s->dims[0], ny = s->dims[1];
+            for (int64_t z = c.box_lo[2]; z < (s->ndim >= 3 ? c.box_hi[2] : 1); ++z)
+                for (int64_t y = c.box_lo[1]; y < (s->ndim >= 2 ? c.box_hi[1] : 1); ++y)
+                    for (int64_t x = c.box_lo[0]; x < c.box_hi[0]; ++x) {
+                        in.ccol.push_back((z * ny + y) * nx + x);
+                        in.cval.push_back(c.value);
+                    }
+        } else if (c.kind == KV_COL_SPARSE) {
+            std::vector<std::pair<int64_t, double>> e;
+            for (int64_t q = 0; q < c.nnz; ++q) e.emplace_back(c.idx[q], c.val[q]);
+            std::sort(e.begin(), e.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+            for (auto& pr : e) {
+                in.ccol.push_back(pr.first);
+                in.cval.push_back(pr.second);
+            }
+        } else {
+            for (int64_t q = 0; q < n; ++q)
+                if (c.dense[q] != 0.0) {
+                    in.ccol.push_back(q);
+                    in.cval.push_back(c.dense[q]);
+                }
+        }
+        if (taug && c.is_fixed) {
+            in.ccol.push_back(n);  // the constant variable's entry of E_j
+            in.cval.push_back(1.0);
+        }
+        in.crp.push_back((int64_t)in.ccol.size());
+    }
+    in.theta.assign(d->i, INFINITY);
+    in.d.i = d->o;
+    in.d.cols = in.cols.data();
+    in.d.o = d->i;
+    in.d.c_row_ptr = in.crp.data();
+    in.d.c_col = in.ccol.data();
+    in.d.c_val = in.cval.data();
+    in.d.theta = in.theta.data();
+    in.d.simulate = KV_SIM_FORWARD;
+    if (in.d.method == KV_AUTO) in.d.method = (s->symmetric && !taug) ? KV_LANCZOS : KV_ARNOLDI;
 }
 
 static int vectors_needed(const Sys* s, const Prob* p) {
@@ -501,10 +605,7 @@ static void free_prob(Prob* p) {
     p->done_ev = nullptr;
 }
 
-int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, size_t* bytes) {
-    if (!s || !d || !bytes) return fail(KV_EINVAL, "kv_problem_bytes: NULL argument");
-    int rc = validate(s, d, precision);
-    if (rc) return rc;
+static size_t bytes_core(const Sys* s, const kv_problem_desc* d, int precision, const BuildOpts& bo) {
     Prob tmp;
     tmp.sys = s;
     tmp.i = d->i;
@@ -513,7 +614,7 @@ int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, s
     tmp.steps = d->steps;
     tmp.prec = precision;
     tmp.flags = d->flags;
-    plan_methods(s, d, &tmp);
+    plan_methods(s, d, &tmp, bo);
     tmp.fused = !(d->flags & KV_FLAG_TWO_PASS) && fused_tma_supported(&tmp);
     const int64_t N = s->n + (std::count(tmp.aug.begin(), tmp.aug.end(), 1) ? 1 : 0);
     const int nv = vectors_needed(s, &tmp);
@@ -537,20 +638,40 @@ int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, s
         if (c.kind == KV_COL_SPARSE) t += r256((size_t)(c.nnz + 1) * 8) * 2;
         if (c.kind == KV_COL_DENSE) t += r256((size_t)N * 8);
     }
+    if (bo.brow) t += r256(((size_t)d->i * row_dot_blocks() + d->i) * 8);
+    return t;
+}
+
+int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, size_t* bytes) {
+    if (!s || !d || !bytes) return fail(KV_EINVAL, "kv_problem_bytes: NULL argument");
+    int rc = validate(s, d, precision);
+    if (rc) return rc;
+    if (!runs_transposed(d)) {
+        *bytes = bytes_core(s, d, precision, BuildOpts{});
+        return KV_OK;
+    }
+    const bool taug = carries_constant(s, d);
+    InnerDesc in;
+    make_inner_desc(s, d, taug, in);
+    BuildOpts bo;
+    bo.trans_runs = true;
+    bo.trans_aug = taug ? 1 : 0;
+    bo.brow = taug ? s->d_b : nullptr;
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t t = bytes_core(s, &in.d, precision, bo);
+    const size_t S = (size_t)d->steps + 1;
+    t += r256((size_t)d->i * d->o * S * 8) + 2 * r256((size_t)d->o * S * 8) + r256((size_t)d->o * 8) +
+         3 * r256((size_t)d->i * 8) + 2 * 256;
+    if (s->kind == 1 && !s->symmetric && !s->d_rpT)  // A^T, built on first use
+        t += r256((size_t)(s->n + 1) * 8) + r256((size_t)s->nnz * 4) + r256((size_t)s->nnz * elem_size(precision));
     *bytes = t;
     return KV_OK;
 }
 
-int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc* d, int precision) {
-    if (!c || !out || !s) return fail(KV_EINVAL, "kv_problem: NULL argument");
-    *out = nullptr;
-    if (s->ctx != c) return fail(KV_EINVAL, "kv_problem: system belongs to another context");
-    int rc = validate(s, d, precision);
-    if (rc) return rc;
-    rc = with_device(c->device);
-    if (rc) return rc;
-    kv_prob* p = new (std::nothrow) kv_prob();
-    if (!p) return fail(KV_ENOMEM, "host allocation");
+// Fills and allocates p (fresh) for problem d on system s; on failure p's
+// device memory is released (the caller deletes p).
+static int prob_build(Ctx* c, Prob* p, const Sys* s, const kv_problem_desc* d, int precision, const BuildOpts& bo) {
+    int rc = KV_OK;
     p->ctx = c;
     p->sys = s;
     p->prec = precision;
@@ -563,7 +684,9 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
     p->batched = d->batched;
     p->flags = d->flags;
     p->err_target = d->err_target > 0.0 ? d->err_target : 0.0;
-    plan_methods(s, d, p);
+    p->trans_runs = bo.trans_runs;
+    p->d_brow = bo.brow;
+    plan_methods(s, d, p, bo);
     p->fused = !(d->flags & KV_FLAG_TWO_PASS) && fused_tma_supported(p);
     p->N = s->n + (std::count(p->aug.begin(), p->aug.end(), 1) ? 1 : 0);
     p->nvec = vectors_needed(s, p);
@@ -607,6 +730,11 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
         TRY(dalloc(p, &p->d_err, (size_t)p->i));
         TRY(dalloc(p, &p->d_hlast, (size_t)p->i * S));
         if (p->m > KV_MAX_M) TRY(dalloc(p, &p->d_lx, large_expm_scratch_doubles(p->m, p->steps)));
+        if (p->d_brow) {
+            const size_t nrd = (size_t)p->i * row_dot_blocks() + p->i;  // partials, then tickets
+            TRY(dalloc(p, &p->d_rowdot, nrd));
+            KV_CHECK_CUDA(cudaMemsetAsync(p->d_rowdot, 0, nrd * 8, c->stream));
+        }
         TRY(upload(c, p->d_crp, d->c_row_ptr, (size_t)(p->o + 1) * 8));
         TRY(upload(c, p->d_ccol, d->c_col, (size_t)cnnz * 8));
         TRY(upload(c, p->d_cval, d->c_val, (size_t)cnnz * 8));
@@ -622,6 +750,7 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
         KV_CHECK_CUDA(cudaMemsetAsync(p->d_H, 0, (size_t)p->i * (p->m + 1) * p->m * 8, c->stream));
         KV_CHECK_CUDA(cudaMemsetAsync(p->d_P, 0, (size_t)p->i * p->o * p->m * 8, c->stream));
         p->d_sidx.assign(p->i, nullptr);
+        p->sidx_n.assign(p->i, 0);
         p->d_sval.assign(p->i, nullptr);
         p->d_dense.assign(p->i, nullptr);
         for (int j = 0; j < p->i; ++j) {
@@ -631,10 +760,11 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
             hc.val = nullptr;
             hc.dense = nullptr;
             if (col.kind == KV_COL_SPARSE) {
-                const int64_t nn = col.nnz + (p->aug[j] ? 1 : 0);
+                const bool cst = p->aug[j] && !p->trans_runs;  // the constant entry of E_j is 1
+                const int64_t nn = col.nnz + (cst ? 1 : 0);
                 std::vector<int64_t> ix(col.idx, col.idx + col.nnz);
                 std::vector<double> vv(col.val, col.val + col.nnz);
-                if (p->aug[j]) {
+                if (cst) {
                     ix.push_back(s->n);
                     vv.push_back(1.0);
                 }
@@ -642,13 +772,14 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
                 TRY(dalloc(p, &p->d_sval[j], (size_t)std::max<int64_t>(nn, 1)));
                 TRY(upload(c, p->d_sidx[j], ix.data(), (size_t)nn * 8));
                 TRY(upload(c, p->d_sval[j], vv.data(), (size_t)nn * 8));
+                p->sidx_n[j] = nn;
                 KV_CHECK_CUDA(cudaStreamSynchronize(c->stream));  // host vectors go out of scope
             } else if (col.kind == KV_COL_DENSE) {
                 TRY(dalloc(p, &p->d_dense[j], (size_t)p->N));
                 TRY(upload(c, p->d_dense[j], col.dense, (size_t)s->n * 8));
                 if (p->N > s->n) {
                     static const double one = 1.0, zero = 0.0;
-                    TRY(upload(c, p->d_dense[j] + s->n, p->aug[j] ? &one : &zero, 8));
+                    TRY(upload(c, p->d_dense[j] + s->n, (p->aug[j] && !p->trans_runs) ? &one : &zero, 8));
                 }
             }
         }
@@ -660,19 +791,146 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
         KV_CHECK_CUDA(cudaStreamSynchronize(c->stream));
     }
 #undef TRY
-    *out = p;
     return KV_OK;
 failed:
     cudaStreamSynchronize(c->stream);
     free_prob(p);
+    return rc;
+}
+
+// The transpose dynamics (Sec. 4.1): an inner problem with one run per row of
+// C on A^T (A'^T when a column carries the constant), projected by E'^T, and
+// this outer problem holding the external thresholds, box and outputs.
+static int build_transposed(kv_ctx* c, kv_prob** out, const Sys* s, const kv_problem_desc* d, int precision) {
+    const bool taug = carries_constant(s, d);
+    int rc = KV_OK;
+    if (s->kind == 1 && !s->symmetric) {
+        rc = csr_build_transpose(const_cast<Sys*>(s));
+        if (rc) return rc;
+    }
+    InnerDesc in;
+    make_inner_desc(s, d, taug, in);
+    Sys* view = new (std::nothrow) Sys(*s);
+    Prob* inner = new (std::nothrow) Prob();
+    kv_prob* p = new (std::nothrow) kv_prob();
+    if (!view || !inner || !p) {
+        delete view;
+        delete inner;
+        delete p;
+        return fail(KV_ENOMEM, "host allocation");
+    }
+    if (s->kind == 1 && !s->symmetric) {
+        view->d_rp = s->d_rpT;
+        view->d_col = s->d_colT;
+        view->d_val = s->d_valT;
+    }
+    view->d_rpT = nullptr;
+    view->d_colT = nullptr;
+    view->d_valT = nullptr;
+    view->d_b = nullptr;  // the rows of A'^T but the last carry no b; the last is k_row_dot's
+    BuildOpts bo;
+    bo.trans_runs = true;
+    bo.trans_aug = taug ? 1 : 0;
+    bo.brow = taug ? s->d_b : nullptr;
+    rc = prob_build(c, inner, view, &in.d, precision, bo);
+    if (rc) {
+        delete inner;
+        delete view;
+        delete p;
+        return rc;
+    }
+    p->ctx = c;
+    p->sys = s;
+    p->prec = precision;
+    p->i = d->i;
+    p->o = d->o;
+    p->m = d->krylov_m;
+    p->steps = d->steps;
+    p->dt = d->dt;
+    p->expm_mode = d->expm_mode;
+    p->flags = d->flags;
+    p->err_target = inner->err_target;
+    p->inner = inner;
+    p->view = view;
+    const int64_t S = d->steps + 1;
+#define TRY(x)               \
+    do {                     \
+        rc = (x);            \
+        if (rc) goto failed; \
+    } while (0)
+    {
+        TRY(dalloc(p, &p->d_basis, (size_t)p->i * p->o * S));
+        TRY(dalloc(p, &p->d_lo, (size_t)p->o * S));
+        TRY(dalloc(p, &p->d_hi, (size_t)p->o * S));
+        TRY(dalloc(p, &p->d_theta, (size_t)p->o));
+        TRY(dalloc(p, &p->d_zlo, (size_t)p->i));
+        TRY(dalloc(p, &p->d_zhi, (size_t)p->i));
+        TRY(dalloc(p, &p->d_zstar, (size_t)p->i));
+        TRY(dalloc(p, &p->d_ystar, 1));
+        TRY(dalloc(p, &p->d_viol, 1));
+        TRY(upload(c, p->d_theta, d->theta, (size_t)p->o * 8));
+        std::vector<double> zl(p->i), zh(p->i);
+        for (int j = 0; j < p->i; ++j) {
+            zl[j] = d->cols[j].zlo;
+            zh[j] = d->cols[j].zhi;
+        }
+        TRY(upload(c, p->d_zlo, zl.data(), (size_t)p->i * 8));
+        TRY(upload(c, p->d_zhi, zh.data(), (size_t)p->i * 8));
+        if (cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+            rc = fail(KV_ECUDA, "event creation failed");
+            goto failed;
+        }
+        KV_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+    }
+#undef TRY
+    *out = p;
+    return KV_OK;
+failed:
+    cudaStreamSynchronize(c->stream);
+    free_prob(inner);
+    delete inner;
+    delete view;
+    free_prob(p);
     delete p;
     return rc;
+}
+
+int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc* d, int precision) {
+    if (!c || !out || !s) return fail(KV_EINVAL, "kv_problem: NULL argument");
+    *out = nullptr;
+    if (s->ctx != c) return fail(KV_EINVAL, "kv_problem: system belongs to another context");
+    int rc = validate(s, d, precision);
+    if (rc) return rc;
+    rc = with_device(c->device);
+    if (rc) return rc;
+    if (runs_transposed(d)) return build_transposed(c, out, s, d, precision);
+    kv_prob* p = new (std::nothrow) kv_prob();
+    if (!p) return fail(KV_ENOMEM, "host allocation");
+    rc = prob_build(c, p, s, d, precision, BuildOpts{});
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return KV_OK;
+}
+
+int kv_problem_runs(const kv_prob* p, int32_t* runs, int32_t* transposed) {
+    if (!p || !runs || !transposed) return fail(KV_EINVAL, "kv_problem_runs: NULL argument");
+    *runs = p->inner ? p->inner->i : p->i;
+    *transposed = p->inner ? 1 : 0;
+    return KV_OK;
 }
 
 int kv_prob_destroy(kv_prob* p) {
     if (!p) return KV_OK;
     cudaSetDevice(p->ctx->device);
     cudaStreamSynchronize(p->ctx->stream);
+    if (p->inner) {
+        free_prob(p->inner);
+        delete p->inner;
+        delete p->view;
+    }
     free_prob(p);
     delete p;
     return KV_OK;
@@ -744,10 +1002,9 @@ static int run_csr(Prob* p) {
     return KV_OK;
 }
 
-int kv_enqueue(kv_prob* p) {
-    if (!p) return fail(KV_EINVAL, "kv_enqueue: NULL problem");
-    int rc = with_device(p->ctx->device);
-    if (rc) return rc;
+// The Krylov runs of p, the exponentials and basis rows, the error bounds.
+static int enqueue_runs(Prob* p) {
+    int rc = KV_OK;
     if (p->sys->kind == 1) {
         rc = run_csr(p);
         if (rc) return rc;
@@ -759,6 +1016,20 @@ int kv_enqueue(kv_prob* p) {
     }
     rc = launch_expm_basis(p);
     if (!rc) rc = launch_error_final(p);
+    return rc;
+}
+
+int kv_enqueue(kv_prob* p) {
+    if (!p) return fail(KV_EINVAL, "kv_enqueue: NULL problem");
+    int rc = with_device(p->ctx->device);
+    if (rc) return rc;
+    if (p->inner) {
+        // transpose dynamics: basis rows per output row, then transposed
+        rc = enqueue_runs(p->inner);
+        if (!rc) rc = launch_basis_transpose(p->inner, p->d_basis, p->ctx->stream);
+    } else {
+        rc = enqueue_runs(p);
+    }
     if (rc) return rc;
     rc = launch_bounds(p);
     if (rc) return rc;
@@ -775,12 +1046,13 @@ int kv_fetch(kv_prob* p, kv_result* r) {
     KV_CHECK_CUDA(cudaMemcpy(r->lo, p->d_lo, (size_t)p->o * S * 8, cudaMemcpyDeviceToHost));
     KV_CHECK_CUDA(cudaMemcpy(r->hi, p->d_hi, (size_t)p->o * S * 8, cudaMemcpyDeviceToHost));
     if (r->basis) KV_CHECK_CUDA(cudaMemcpy(r->basis, p->d_basis, (size_t)p->i * p->o * S * 8, cudaMemcpyDeviceToHost));
-    if (r->H) KV_CHECK_CUDA(cudaMemcpy(r->H, p->d_H, (size_t)p->i * (p->m + 1) * p->m * 8, cudaMemcpyDeviceToHost));
-    if (r->P) KV_CHECK_CUDA(cudaMemcpy(r->P, p->d_P, (size_t)p->i * p->o * p->m * 8, cudaMemcpyDeviceToHost));
-    std::vector<ColState> st(p->i);
-    KV_CHECK_CUDA(cudaMemcpy(st.data(), p->d_state, (size_t)p->i * sizeof(ColState), cudaMemcpyDeviceToHost));
+    const Prob* q = p->inner ? p->inner : p;  // the Krylov runs
+    if (r->H) KV_CHECK_CUDA(cudaMemcpy(r->H, q->d_H, (size_t)q->i * (q->m + 1) * q->m * 8, cudaMemcpyDeviceToHost));
+    if (r->P) KV_CHECK_CUDA(cudaMemcpy(r->P, q->d_P, (size_t)q->i * q->o * q->m * 8, cudaMemcpyDeviceToHost));
+    std::vector<ColState> st(q->i);
+    KV_CHECK_CUDA(cudaMemcpy(st.data(), q->d_state, (size_t)q->i * sizeof(ColState), cudaMemcpyDeviceToHost));
     int status = 0;
-    for (int j = 0; j < p->i; ++j) {
+    for (int j = 0; j < q->i; ++j) {
         if (r->beta0) r->beta0[j] = st[j].beta0;
         if (r->m_used) r->m_used[j] = st[j].m_used;
         status |= st[j].status;
@@ -797,7 +1069,7 @@ int kv_fetch(kv_prob* p, kv_result* r) {
         KV_CHECK_CUDA(cudaMemcpy(&r->y_star, p->d_ystar, sizeof(double), cudaMemcpyDeviceToHost));
         if (r->z_star) KV_CHECK_CUDA(cudaMemcpy(r->z_star, p->d_zstar, (size_t)p->i * 8, cudaMemcpyDeviceToHost));
     }
-    if (r->err_bound) KV_CHECK_CUDA(cudaMemcpy(r->err_bound, p->d_err, (size_t)p->i * 8, cudaMemcpyDeviceToHost));
+    if (r->err_bound) KV_CHECK_CUDA(cudaMemcpy(r->err_bound, q->d_err, (size_t)q->i * 8, cudaMemcpyDeviceToHost));
     if (status) return fail(KV_ETIMEOUT, "a device-side wait gave up (status %d)", status);
     return KV_OK;
 }

@@ -91,6 +91,11 @@ struct Sys {
     // upper bounds of the largest eigenvalue of (A + A^T)/2, for A and for
     // A' = [[A, b], [0, 0]] (Lemma 1 of Sec. 4.2 takes e^{max(mu,0) T})
     double mu = 0.0, mu_aug = 0.0;
+    // A^T in CSR form (non-symmetric CSR only), built on first use by a
+    // problem that runs the transpose dynamics (Sec. 4.1)
+    int64_t* d_rpT = nullptr;
+    int32_t* d_colT = nullptr;
+    void* d_valT = nullptr;
 };
 
 // --------------------------------------------------------------- device state
@@ -138,6 +143,7 @@ struct Prob {
     std::vector<int> aug;        // per column: runs on A' (carries the constant)
     std::vector<kv_column> cols; // host copy (pointers cleared)
     std::vector<int64_t*> d_sidx;
+    std::vector<int64_t> sidx_n;  // entries uploaded to d_sidx / d_sval (the scatter's count)
     std::vector<double*> d_sval;
     std::vector<double*> d_dense;
     // device arrays
@@ -159,6 +165,17 @@ struct Prob {
     double* d_err = nullptr;    // per column: Lemma-1 bound at the dimension used
     double* d_hlast = nullptr;  // per column, steps+1: |(e^{t_k H} e_1)_mu|, the integrand of the bound
     double* d_lx = nullptr;     // m > KV_MAX_M: scratch of the global-memory exponential (one column at a time)
+    // transpose dynamics (Sec. 4.1).  Outer problem: the basis matrix is built
+    // from the runs of `inner` (one per output row, on A^T or A'^T, projected
+    // by E'^T) and transposed; `view` is the operator the inner runs use.
+    Prob* inner = nullptr;
+    Sys* view = nullptr;
+    // inner problem: runs of the transpose dynamics (the constant entry of a
+    // start vector is 0, not 1); d_brow = b when the runs are on A'^T, whose
+    // last row b . x is computed after each SpMV (k_row_dot)
+    bool trans_runs = false;
+    const double* d_brow = nullptr;
+    double* d_rowdot = nullptr;  // i x row_dot_blocks() partials, then i tickets
     void* d_vec = nullptr;  // Krylov vectors
     int64_t N = 0;          // vector length (n, or n+1 if any column is augmented)
     int nvec = 0;           // vectors of length N per vector set
@@ -201,6 +218,12 @@ inline bool is_checkpoint(const Prob* p, int k) {
 int launch_error_final(Prob* p);
 // Gershgorin bound of the symmetric part of a CSR matrix (k_lognorm.cu)
 int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug);
+
+// transpose dynamics (k_csr_transpose.cu)
+int csr_build_transpose(Sys* s);
+int row_dot_blocks();
+int launch_row_dot(Prob* p, int j0, int ncols, void* V, int xslot, int wslot, int it);
+int launch_basis_transpose(const Prob* inner, double* out, cudaStream_t st);
 
 // generic vectors (k_vector.cu)
 int launch_init_norm(Prob* p, int j, void* B);

@@ -107,10 +107,12 @@ void finish(kv_server* s, Request* r) {
     const size_t S = (size_t)d.steps + 1;
     r->lo.assign((size_t)d.o * S, 0.0);
     r->hi.assign((size_t)d.o * S, 0.0);
+    int32_t runs = d.i, transposed = 0;  // per-run arrays: o entries with the transpose dynamics
+    kv_problem_runs(r->prob, &runs, &transposed);
     r->zstar.assign((size_t)d.i, 0.0);
-    r->beta0.assign((size_t)d.i, 0.0);
-    r->m_used.assign((size_t)d.i, 0);
-    r->err_bound.assign((size_t)d.i, 0.0);
+    r->beta0.assign((size_t)runs, 0.0);
+    r->m_used.assign((size_t)runs, 0);
+    r->err_bound.assign((size_t)runs, 0.0);
     kv_result res{};
     res.lo = r->lo.data();
     res.hi = r->hi.data();

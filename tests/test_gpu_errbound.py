@@ -41,12 +41,17 @@ def run_gpu(ctx, p, **kw):
 
 
 def checkpoint_bounds(p):
-    """Per column: the oracle's Lemma-1 bound at every checkpoint below the
-    dimension its Krylov run reaches."""
+    """Per Krylov run (a column of E, or a row of C with the transpose
+    dynamics): the oracle's Lemma-1 bound at every checkpoint below the
+    dimension the run reaches."""
     q = oracle.run(p)
     out = []
-    for j in range(p.i):
-        mu = oracle.mu_bound(p.system, bool(p.columns[j].is_fixed) and p.system.b is not None)
+    if q.get("transposed"):
+        taug = p.system.b is not None and any(c.is_fixed for c in p.columns)
+        mus = [oracle.mu_bound(p.system, taug)] * p.o
+    else:
+        mus = [oracle.mu_bound(p.system, bool(c.is_fixed) and p.system.b is not None) for c in p.columns]
+    for j, mu in enumerate(mus):
         ks = [k for k in oracle.checkpoints(p.m) if k < q["used"][j]]
         out.append([(k, oracle.lemma1(q["H"][j], k, mu, p.dt, p.steps)) for k in ks])
     return out
