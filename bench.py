@@ -529,12 +529,15 @@ def arnoldi_bytes(p) -> float:
 
 def csr_bench(args, dev: int):
     """The random-CSR workload (n = 2e6, 16 generators + the fixed column,
-    m = 60, 2000 steps) in FP64 and FP32: time per query, Arnoldi GB/s."""
+    m = 60, 2000 steps) in FP64 and FP32: time per query, Arnoldi GB/s; and
+    the same query by the transpose dynamics (Sec. 4.1: 2 runs on A'^T from
+    the output rows instead of 17 on A')."""
     import torch
     import paper_1804_01583_gb300 as kv
     out = {}
-    for prec in ("fp64", "fp32"):
+    for prec, sim in (("fp64", "forward"), ("fp32", "forward"), ("fp64", "transpose"), ("fp32", "transpose")):
         p = W.random_csr_problem(2_000_000, seed=0, precision=prec)
+        p.simulate = sim
         ctx = kv.Context(40 << 30, device=dev)
         sysh = kv.System(ctx, p.system, p.precision)
         ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
@@ -549,17 +552,22 @@ def csr_bench(args, dev: int):
         ph.fetch(full=False)
         ms = (time.perf_counter() - t0) * 1e3 / k
         kern = {}
-        for name in ["csr_spmm", "csr_spmv", "arnoldi_dots", "arnoldi_update", "expm_propagate", "init_norm",
-                     "scatter"]:
+        for name in ["csr_spmm", "csr_spmv", "row_dot", "arnoldi_dots", "arnoldi_update", "expm_propagate",
+                     "init_norm", "scatter"]:
             nl, tms = ctx.profile_read(name)
             if nl:
                 kern[name] = {"launches": nl // k, "ms_per_query": tms / k}
         ph.close()
         sysh.close()
         ctx.close()
-        out[prec] = {"ms_per_query": ms, "arnoldi_GBps": arnoldi_bytes(p) / (ms * 1e-3) / 1e9,
-                     "arnoldi_steps_per_s": p.i * p.m / (ms * 1e-3), "kernels": kern}
+        runs = p.o if sim == "transpose" else p.i
+        key = prec if sim == "forward" else prec + "_transposed"
+        out[key] = {"ms_per_query": ms, "runs": runs, "arnoldi_steps_per_s": runs * p.m / (ms * 1e-3),
+                    "kernels": kern}
+        if sim == "forward":
+            out[key]["arnoldi_GBps"] = arnoldi_bytes(p) / (ms * 1e-3) / 1e9
     out["speedup_fp32_over_fp64"] = out["fp64"]["ms_per_query"] / out["fp32"]["ms_per_query"]
+    out["speedup_transposed_fp32"] = out["fp32"]["ms_per_query"] / out["fp32_transposed"]["ms_per_query"]
     out["workload"] = "random CSR n=2e6, 10 off-diagonal nnz/row, i=17 (16 generators + fixed), o=2, m=60, 2000 steps"
     return out
 

@@ -92,3 +92,16 @@ def test_auto_takes_the_smaller_side():
     q = W.heat2d_20()
     q.simulate = "auto"
     assert not oracle.transposed(q)                # i = o = 1: forward
+
+
+def test_transpose_equals_forward_on_the_random_csr_workload():
+    """The random-CSR workload at n = 2e4 (16 generators + the fixed column
+    carrying the constant, o = 2, m = 60): 2 runs on A'^T and 17 on A' give
+    the same basis, both being converged at this m (the forward side is
+    itself pinned to scipy's expm_multiply)."""
+    f = oracle.run(W.random_csr_problem(20000, seed=0, m=60, steps=200))
+    p = W.random_csr_problem(20000, seed=0, m=60, steps=200)
+    p.simulate = "transpose"
+    t = oracle.run(p)
+    S = max(np.max(np.abs(f["basis"][j])) for j in range(p.i))
+    assert max(np.max(np.abs(t["basis"][j] - f["basis"][j])) for j in range(p.i)) <= 1e-11 * S
