@@ -9,10 +9,11 @@
 // matrix in shared memory; all arithmetic is double.
 //
 // Two schedules (kv_problem_desc.expm_mode):
-//   PER_STEP   one CTA per (column, step): e^{H t_k} for every k.
-//   PROPAGATE  one CTA per column: M = e^{H dt}, u_0 = e_1, u_k = M u_{k-1};
-//              the same vectors in exact arithmetic, s matrix-vector products
-//              instead of s exponentials.
+//   PER_STEP   one CTA per (column, step): e^{H t_k} for every k (this file,
+//              dimensions up to 64).
+//   PROPAGATE  M = e^{H dt}, u_k = M^k e_1: the same vectors in exact
+//              arithmetic, by GEMM doubling over the steps (k_expm_large.cu,
+//              which also takes every dimension above 64).
 //
 // Both also record |(u_k)_mu|, the last entry of u_k = e^{t_k H_mu} e_1: the
 // integrand of the a-posteriori bound of Lemma 1 (Sec. 4.2), which
@@ -232,47 +233,6 @@ __global__ void __launch_bounds__(ENT) k_expm_per_step(ExpmArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(ENT) k_expm_propagate(ExpmArgs a) {
-    extern __shared__ double smem[];
-    __shared__ double fac[KV_MAX_M];
-    __shared__ int piv;
-    __shared__ double red[ENT / 32];
-    const int j = a.j0 + blockIdx.x;
-    const int mu = eval_dim(a, j);
-    if (mu < 0) return;
-    double* hl = a.hlast + (int64_t)j * (a.steps + 1);
-    if (mu == 0) {
-        if (a.dim == 0)
-            for (int e = threadIdx.x; e < a.o * (a.steps + 1); e += ENT)
-                a.basis[(int64_t)j * a.o * (a.steps + 1) + e] = 0.0;
-        for (int k = threadIdx.x; k <= a.steps; k += ENT) hl[k] = 0.0;
-        return;
-    }
-    double* buf[6];
-    for (int q = 0; q < 6; ++q) buf[q] = smem + q * mu * mu;
-    load_scaled_H(a, j, mu, a.dt, buf[0]);
-    const int res = sexpm(mu, buf, fac, &piv, red);
-    const double* M = buf[res];
-    double* u = buf[(res + 1) % 6];
-    double* v = buf[(res + 2) % 6];
-    for (int l = threadIdx.x; l < mu; l += ENT) u[l] = (l == 0) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int k = 0; k <= a.steps; ++k) {
-        if (threadIdx.x == 0) hl[k] = fabs(u[mu - 1]);
-        if (a.dim == 0) project_rows(a, j, mu, u, 1, k);
-        if (k == a.steps) break;
-        for (int l = threadIdx.x; l < mu; l += ENT) {
-            double s = 0.0;
-            for (int q = 0; q < mu; ++q) s = fma(M[l * mu + q], u[q], s);
-            v[l] = s;
-        }
-        __syncthreads();
-        double* t = u;
-        u = v;
-        v = t;
-    }
-}
-
 struct ErrArgs {
     const double* H;       // i x (m+1) x m
     ColState* st;          // i
@@ -345,7 +305,6 @@ int expm_prepare(int device) {
     static bool attr_set = false;
     if (!attr_set) {
         const int smax = 6 * KV_MAX_M * KV_MAX_M * (int)sizeof(double);
-        KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
         KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_per_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
         attr_set = true;
     }
@@ -355,15 +314,13 @@ int expm_prepare(int device) {
 // The exponentials of columns j0 .. j0+ncols-1 at dimension dim (0: each
 // column's m_used, with the basis rows).
 static int launch_expm(Prob* p, int j0, int ncols, int dim) {
+    const int mm = dim > 0 ? dim : p->m;
+    if (p->expm_mode == KV_EXPM_PROPAGATE || mm > KV_MAX_M) return launch_expm_large(p, j0, ncols, dim, dim == 0);
     int rc = expm_prepare(p->ctx->device);
     if (rc != KV_OK) return rc;
     ExpmArgs a{p->d_H, p->d_P, p->d_state, p->d_basis, p->m, p->o, p->steps, p->dt, p->d_hlast, dim, j0};
-    const int mm = dim > 0 ? dim : p->m;
     const size_t smem = (size_t)6 * mm * mm * sizeof(double);
-    if (p->expm_mode == KV_EXPM_PROPAGATE) {
-        LaunchScope ls(p->ctx, dim > 0 ? "error_expm" : "expm_propagate");
-        k_expm_propagate<<<ncols, ENT, smem, p->ctx->stream>>>(a);
-    } else {
+    {
         int gx = p->steps + 1;
         if (gx > 65535 * 16) gx = 65535 * 16;
         dim3 grd((unsigned)gx, (unsigned)ncols);
@@ -383,22 +340,10 @@ static int launch_bound(Prob* p, int j0, int ncols, int dim) {
     return KV_OK;
 }
 
-int launch_expm_basis(Prob* p) {
-    if (p->m <= KV_MAX_M) return launch_expm(p, 0, p->i, 0);
-    for (int j = 0; j < p->i; ++j) {  // dimensions above the shared-memory kernels' reach
-        const int rc = launch_expm_large_column(p, j, 0, true);
-        if (rc) return rc;
-    }
-    return KV_OK;
-}
+int launch_expm_basis(Prob* p) { return launch_expm(p, 0, p->i, 0); }
 
 int launch_error_check(Prob* p, int j0, int ncols, int dim) {
-    int rc = KV_OK;
-    if (dim <= KV_MAX_M) {
-        rc = launch_expm(p, j0, ncols, dim);
-    } else {
-        for (int j = j0; j < j0 + ncols && !rc; ++j) rc = launch_expm_large_column(p, j, dim, false);
-    }
+    const int rc = launch_expm(p, j0, ncols, dim);
     return rc ? rc : launch_bound(p, j0, ncols, dim);
 }
 

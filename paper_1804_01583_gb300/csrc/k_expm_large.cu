@@ -1,9 +1,13 @@
-// k_expm_large.cu -- e^{t_k H} e_1 for Krylov dimensions above the
-// shared-memory exponential's 64 (Eq. approx-formula, Sec. 4.2), in global
-// memory with FP64 GEMMs.
+// k_expm_large.cu -- e^{t_k H} e_1 for all output steps in global memory
+// with FP64 GEMMs (Eq. approx-formula, Sec. 4.2): the exponential of Krylov
+// dimensions above the shared-memory kernels' 64, and the PROPAGATE schedule
+// (u_k = M^k e_1, M = e^{dt H}) at every dimension, where it replaces s
+// sequential matrix-vector products by ceil(log2(s+1)) rounds of GEMMs.
+// Runs are batched: blockIdx.z selects the run, every buffer has a per-run
+// stride.
 //
-// For one column with dimension k (known on the device only: the column's
-// m_used, or a checkpoint dimension of the error control):
+// For one run with dimension k (known on the device only: the run's m_used,
+// or a checkpoint dimension of the error control):
 //   1. X = dt H_k, s = the smallest scaling with ||X / 2^s||_1 = r where the
 //      Taylor remainder of degree 18, r^19 / 19! / (1 - r/20), is below 2^-53
 //      (derived from the Lagrange remainder with the geometric tail bound);
@@ -11,19 +15,17 @@
 //      in X^4 over blocks c_{4i} I + c_{4i+1} X + c_{4i+2} X^2 + c_{4i+3} X^3,
 //      c_j = 1/j!), then s squarings: E = e^{dt H_k};
 //   3. U[:, t] = e^{t dt H_k} e_1 for t = 0..steps by doubling: with
-//      P_i = E^(2^i), U[:, 2^i + c] = P_i U[:, c] for c < 2^i, P_{i+1} = P_i^2
-//      (ceil(log2(steps+1)) GEMM rounds instead of steps matrix-vector
-//      products in sequence);
+//      P_i = E^(2^i), U[:, 2^i + c] = P_i U[:, c] for c < 2^i, P_{i+1} = P_i^2;
 //   4. basis rows beta0 P U (o x (steps+1)) and the last row |U[k-1, :]|, the
 //      integrand of the Lemma-1 bound.
 // Every launch is sized for the largest dimension m and reads k from the
-// column state; tiles beyond k return at once, and a checkpoint of a column
-// that has stopped does nothing.  The number of squaring launches is fixed
-// (SQ_LAUNCHES); those beyond the column's s copy instead, so the launch
+// run's state; tiles beyond k return at once, and a checkpoint of a run that
+// has stopped does nothing.  The number of squaring launches is fixed
+// (SQ_LAUNCHES); those beyond the run's s copy instead, so the launch
 // sequence does not depend on device data (it can be captured in a graph).
 //
-// This replaces the paper's Pade exponential (Sec. 4.1) above dimension 64:
-// the same e^{t H} up to rounding, without a linear solve.
+// This is a different exponential from the paper's Pade (Sec. 4.1): the
+// same e^{t H} up to rounding, without a linear solve.
 #include <math.h>
 
 #include "kv_internal.h"
@@ -35,38 +37,44 @@ constexpr int GNT = 256;        // 16 x 16 threads, 2 x 2 outputs each
 constexpr int SQ_LAUNCHES = 32; // squarings enqueued (even); handles ||dt H||_1 up to 2^32
 
 struct KDim {
-    const ColState* st;
-    int dim;  // > 0: checkpoint dimension (columns that have stopped skip); 0: m_used
+    const ColState* st;  // the batch's first run; run z is st + z
+    int dim;             // > 0: checkpoint dimension (runs that have stopped skip); 0: m_used
 };
 
-__device__ __forceinline__ int kdim(const KDim& d) {
-    if (d.dim > 0) return d.st->done ? -1 : d.dim;
-    return d.st->m_used;
+__device__ __forceinline__ int kdim(const KDim& d, int z) {
+    const ColState* s = d.st + z;
+    if (d.dim > 0) return s->done ? -1 : d.dim;
+    return s->m_used;
 }
 
-struct Lin4 {  // c0 I + c1 X + c2 X2 + c3 X3 (leading dimension ld; X3 may be null)
+struct Lin4 {  // c0 I + c1 X + c2 X2 + c3 X3 (leading dimension ld, run stride sz; X3 may be null)
     double c0, c1, c2, c3;
     const double *X, *X2, *X3;
     int ld;
+    int64_t sz;
 };
 
 struct GemmArgs {
     const double* A;
     int lda;
+    int64_t sA;
     const double* B;
     int ldb;
+    int64_t sB;
     double* C;
     int ldc;
-    int M, N, K;      // fixed sizes; -1 = the column's k
+    int64_t sC;
+    int M, N, K;      // fixed sizes; -1 = the run's k
     KDim kd;
-    int epi;          // 0: C = AB; 1: C = AB + lin; 2: C = beta0 AB (beta0 of the column)
+    int epi;          // 0: C = AB; 1: C = AB + lin; 2: C = beta0 AB (beta0 of the run)
     Lin4 lin;
-    const int* gate;  // squaring gate: q >= *gate -> C = A (copy)
+    const double* gate;  // squaring gate (per run, stride sG): q >= gate -> C = A (copy)
+    int64_t sG;
     int q;
 };
 
-__device__ __forceinline__ double lin_at(const Lin4& l, int r, int c) {
-    const int64_t e = (int64_t)r * l.ld + c;
+__device__ __forceinline__ double lin_at(const Lin4& l, int z, int r, int c) {
+    const int64_t e = (int64_t)z * l.sz + (int64_t)r * l.ld + c;
     double v = (r == c) ? l.c0 : 0.0;
     v = fma(l.c1, l.X[e], v);
     v = fma(l.c2, l.X2[e], v);
@@ -75,22 +83,26 @@ __device__ __forceinline__ double lin_at(const Lin4& l, int r, int c) {
 }
 
 __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
-    const int k = kdim(g.kd);
+    const int z = blockIdx.z;
+    const int k = kdim(g.kd, z);
     if (k < 0) return;
     const int M = g.M < 0 ? k : g.M, N = g.N < 0 ? k : g.N, K = g.K < 0 ? k : g.K;
     const int r0 = blockIdx.y * GT, c0 = blockIdx.x * GT;
     if (r0 >= M || c0 >= N) return;
-    if (k == 0) {  // zero column: zero outputs (basis rows)
+    const double* A = g.A + z * g.sA;
+    const double* B = g.B + z * g.sB;
+    double* C = g.C + z * g.sC;
+    if (k == 0) {  // zero run: zero outputs (basis rows)
         for (int e = threadIdx.x; e < GT * GT; e += GNT) {
             const int r = r0 + e / GT, c = c0 + e % GT;
-            if (r < M && c < N) g.C[(int64_t)r * g.ldc + c] = 0.0;
+            if (r < M && c < N) C[(int64_t)r * g.ldc + c] = 0.0;
         }
         return;
     }
-    if (g.gate && g.q >= *g.gate) {
+    if (g.gate && g.q >= (int)g.gate[z * g.sG]) {
         for (int e = threadIdx.x; e < GT * GT; e += GNT) {
             const int r = r0 + e / GT, c = c0 + e % GT;
-            if (r < M && c < N) g.C[(int64_t)r * g.ldc + c] = g.A[(int64_t)r * g.lda + c];
+            if (r < M && c < N) C[(int64_t)r * g.ldc + c] = A[(int64_t)r * g.lda + c];
         }
         return;
     }
@@ -101,9 +113,9 @@ __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
         for (int e = threadIdx.x; e < GT * GT; e += GNT) {
             const int a = e / GT, b = e % GT;
             const int ar = r0 + a, ac = kk + b;
-            As[a][b] = (ar < M && ac < K) ? g.A[(int64_t)ar * g.lda + ac] : 0.0;
+            As[a][b] = (ar < M && ac < K) ? A[(int64_t)ar * g.lda + ac] : 0.0;
             const int br = kk + a, bc = c0 + b;
-            Bs[a][b] = (br < K && bc < N) ? g.B[(int64_t)br * g.ldb + bc] : 0.0;
+            Bs[a][b] = (br < K && bc < N) ? B[(int64_t)br * g.ldb + bc] : 0.0;
         }
         __syncthreads();
 #pragma unroll 8
@@ -118,7 +130,7 @@ __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
         __syncthreads();
     }
     const double accs[2][2] = {{acc00, acc01}, {acc10, acc11}};
-    const double beta0 = g.epi == 2 ? g.kd.st->beta0 : 1.0;
+    const double beta0 = g.epi == 2 ? (g.kd.st + z)->beta0 : 1.0;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -126,54 +138,62 @@ __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
             const int r = r0 + 2 * ty + i, c = c0 + 2 * tx + jj;
             if (r >= M || c >= N) continue;
             double v = accs[i][jj];
-            if (g.epi == 1) v += lin_at(g.lin, r, c);
+            if (g.epi == 1) v += lin_at(g.lin, z, r, c);
             if (g.epi == 2) v *= beta0;
-            g.C[(int64_t)r * g.ldc + c] = v;
+            C[(int64_t)r * g.ldc + c] = v;
         }
 }
 
-// C = lin on the leading k x k block
-__global__ void __launch_bounds__(GNT) k_lincomb(double* C, int ldc, Lin4 lin, KDim kd) {
-    const int k = kdim(kd);
+// C = lin on the leading k x k block of each run
+__global__ void __launch_bounds__(GNT) k_lincomb(double* C, int ldc, int64_t sC, Lin4 lin, KDim kd) {
+    const int z = blockIdx.z;
+    const int k = kdim(kd, z);
     if (k <= 0) return;
     const int64_t kk = (int64_t)k * k;
     for (int64_t e = (int64_t)blockIdx.x * GNT + threadIdx.x; e < kk; e += (int64_t)gridDim.x * GNT) {
         const int r = (int)(e / k), c = (int)(e - (int64_t)r * k);
-        C[(int64_t)r * ldc + c] = lin_at(lin, r, c);
+        C[z * sC + (int64_t)r * ldc + c] = lin_at(lin, z, r, c);
     }
 }
 
-// X = dt H_k (leading k x k block of the column's (m+1) x m H)
-__global__ void __launch_bounds__(GNT) k_lx_load(const double* H, int ldh, double* X, int ldx, double dt, KDim kd) {
-    const int k = kdim(kd);
+// X = dt H_k (leading k x k block of the run's (m+1) x m H)
+__global__ void __launch_bounds__(GNT) k_lx_load(const double* H, int ldh, int64_t sH, double* X, int ldx, int64_t sX,
+                                                 double dt, KDim kd) {
+    const int z = blockIdx.z;
+    const int k = kdim(kd, z);
     if (k <= 0) return;
     const int64_t kk = (int64_t)k * k;
     for (int64_t e = (int64_t)blockIdx.x * GNT + threadIdx.x; e < kk; e += (int64_t)gridDim.x * GNT) {
         const int r = (int)(e / k), c = (int)(e - (int64_t)r * k);
-        X[(int64_t)r * ldx + c] = dt * H[(int64_t)r * ldh + c];
+        X[z * sX + (int64_t)r * ldx + c] = dt * H[z * sH + (int64_t)r * ldh + c];
     }
 }
 
 // column sums of |X|, one warp per column
-__global__ void __launch_bounds__(GNT) k_lx_colsum(const double* X, int ldx, double* cs, KDim kd) {
-    const int k = kdim(kd);
+__global__ void __launch_bounds__(GNT) k_lx_colsum(const double* X, int ldx, int64_t sX, double* cs, int64_t sC,
+                                                   KDim kd) {
+    const int z = blockIdx.z;
+    const int k = kdim(kd, z);
     if (k <= 0) return;
     const int lane = threadIdx.x & 31;
     for (int c = blockIdx.x * (GNT / 32) + (threadIdx.x >> 5); c < k; c += gridDim.x * (GNT / 32)) {
         double s = 0.0;
-        for (int r = lane; r < k; r += 32) s += fabs(X[(int64_t)r * ldx + c]);
+        for (int r = lane; r < k; r += 32) s += fabs(X[z * sX + (int64_t)r * ldx + c]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) cs[c] = s;
+        if (lane == 0) cs[z * sC + c] = s;
     }
 }
 
-// one CTA: ||X||_1, the scaling s (device int, at most smax) and 2^-s
-__global__ void __launch_bounds__(GNT) k_lx_scaling(const double* cs, int* nsq, double* scale, int smax, KDim kd) {
+// one CTA per run: ||X||_1, the scaling s (stored as a double, at most smax)
+// and 2^-s, next to the column sums
+__global__ void __launch_bounds__(GNT) k_lx_scaling(const double* cs, int64_t sC, int m, int smax, KDim kd) {
     __shared__ double red[GNT / 32];
-    const int k = kdim(kd);
+    const int z = blockIdx.z;
+    const int k = kdim(kd, z);
     if (k <= 0) return;
+    const double* c = cs + z * sC;
     double mx = 0.0;
-    for (int c = threadIdx.x; c < k; c += GNT) mx = fmax(mx, cs[c]);
+    for (int q = threadIdx.x; q < k; q += GNT) mx = fmax(mx, c[q]);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -191,58 +211,78 @@ __global__ void __launch_bounds__(GNT) k_lx_scaling(const double* cs, int* nsq, 
         r *= 0.5;
         ++s;
     }
-    *nsq = s;
-    *scale = ldexp(1.0, -s);
+    double* out = const_cast<double*>(c) + m;
+    out[0] = (double)s;      // the squaring gate
+    out[1] = ldexp(1.0, -s);  // the scale
 }
 
-__global__ void __launch_bounds__(GNT) k_lx_scale(double* X, int ldx, const double* scale, KDim kd) {
-    const int k = kdim(kd);
+__global__ void __launch_bounds__(GNT) k_lx_scale(double* X, int ldx, int64_t sX, const double* scale, int64_t sS,
+                                                  KDim kd) {
+    const int z = blockIdx.z;
+    const int k = kdim(kd, z);
     if (k <= 0) return;
-    const double f = *scale;
+    const double f = scale[z * sS];
     const int64_t kk = (int64_t)k * k;
     for (int64_t e = (int64_t)blockIdx.x * GNT + threadIdx.x; e < kk; e += (int64_t)gridDim.x * GNT) {
         const int r = (int)(e / k), c = (int)(e - (int64_t)r * k);
-        X[(int64_t)r * ldx + c] *= f;
+        X[z * sX + (int64_t)r * ldx + c] *= f;
     }
 }
 
 // U[:, 0] = e_1
-__global__ void __launch_bounds__(GNT) k_lx_init_u(double* U, int ldu, KDim kd) {
-    const int k = kdim(kd);
+__global__ void __launch_bounds__(GNT) k_lx_init_u(double* U, int ldu, int64_t sU, KDim kd) {
+    const int z = blockIdx.z;
+    const int k = kdim(kd, z);
     if (k <= 0) return;
-    for (int r = blockIdx.x * GNT + threadIdx.x; r < k; r += gridDim.x * GNT) U[(int64_t)r * ldu] = (r == 0) ? 1.0 : 0.0;
+    for (int r = blockIdx.x * GNT + threadIdx.x; r < k; r += gridDim.x * GNT)
+        U[z * sU + (int64_t)r * ldu] = (r == 0) ? 1.0 : 0.0;
 }
 
-// hl[t] = |U[k-1, t]| (0 for a zero column)
-__global__ void __launch_bounds__(GNT) k_lx_hlast(const double* U, int ldu, int S, double* hl, KDim kd) {
-    const int k = kdim(kd);
+// hl[t] = |U[k-1, t]| (0 for a zero run)
+__global__ void __launch_bounds__(GNT) k_lx_hlast(const double* U, int ldu, int64_t sU, int S, double* hl, KDim kd) {
+    const int z = blockIdx.z;
+    const int k = kdim(kd, z);
     if (k < 0) return;
     for (int t = blockIdx.x * GNT + threadIdx.x; t < S; t += gridDim.x * GNT)
-        hl[t] = k == 0 ? 0.0 : fabs(U[(int64_t)(k - 1) * ldu + t]);
+        hl[(int64_t)z * S + t] = k == 0 ? 0.0 : fabs(U[z * sU + (int64_t)(k - 1) * ldu + t]);
 }
 
 // ---------------------------------------------------------------- host side
+// per-run scratch: X, X^2, X^3, X^4, two Horner / squaring buffers (m x m
+// each), U (m x (steps+1)), the column sums (m) and the gate and scale
 size_t large_expm_scratch_doubles(int m, int steps) {
     return (size_t)6 * m * m + (size_t)m * (steps + 1) + (size_t)m + 64;
 }
 
-static int gemm(Prob* p, const double* A, int lda, const double* B, int ldb, double* C, int ldc, int M, int N, int K,
-                KDim kd, int epi = 0, Lin4 lin = Lin4{}, const int* gate = nullptr, int q = 0) {
+// runs processed per batch: the scratch of one batch stays under 1 GB (at
+// least one run)
+int large_expm_batch(int m, int steps, int runs) {
+    const size_t per = large_expm_scratch_doubles(m, steps) * 8;
+    const size_t cap = (size_t)1 << 30;
+    int64_t b = (int64_t)(cap / per);
+    if (b < 1) b = 1;
+    return (int)std::min<int64_t>(b, runs);
+}
+
+static int gemm(Prob* p, int nb, const double* A, int lda, int64_t sA, const double* B, int ldb, int64_t sB, double* C,
+                int ldc, int64_t sC, int M, int N, int K, KDim kd, int epi = 0, Lin4 lin = Lin4{},
+                const double* gate = nullptr, int64_t sG = 0, int q = 0) {
     const int Mx = M < 0 ? p->m : M, Nx = N < 0 ? p->m : N;
-    dim3 grd((unsigned)((Nx + GT - 1) / GT), (unsigned)((Mx + GT - 1) / GT));
-    GemmArgs g{A, lda, B, ldb, C, ldc, M, N, K, kd, epi, lin, gate, q};
+    dim3 grd((unsigned)((Nx + GT - 1) / GT), (unsigned)((Mx + GT - 1) / GT), (unsigned)nb);
+    GemmArgs g{A, lda, sA, B, ldb, sB, C, ldc, sC, M, N, K, kd, epi, lin, gate, sG, q};
     k_dgemm<<<grd, GNT, 0, p->ctx->stream>>>(g);
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;
 }
 
-// e^{t dt H_k} e_1 for t = 0..steps of column j at dimension dim (0: m_used),
-// the integrand row into hlast, and (write_basis) the basis rows.
-int launch_expm_large_column(Prob* p, int j, int dim, bool write_basis) {
+// e^{t dt H_k} e_1 for t = 0..steps for runs j0 .. j0+nb-1 at dimension dim
+// (0: each run's m_used), the integrand rows into hlast, and (write_basis)
+// the basis rows.
+static int expm_large_batch(Prob* p, int j0, int nb, int dim, bool write_basis) {
     const int m = p->m, S = p->steps + 1;
     cudaStream_t st = p->ctx->stream;
-    LaunchScope ls(p->ctx, dim > 0 ? "error_expm" : "expm_large");
-    const KDim kd{p->d_state + j, dim};
+    const KDim kd{p->d_state + j0, dim};
+    const int64_t X_ = (int64_t)large_expm_scratch_doubles(m, p->steps);  // run stride of the scratch
     double* X = p->d_lx;
     double* X2 = X + (size_t)m * m;
     double* X3 = X2 + (size_t)m * m;
@@ -251,18 +291,19 @@ int launch_expm_large_column(Prob* p, int j, int dim, bool write_basis) {
     double* T1 = T0 + (size_t)m * m;
     double* U = T1 + (size_t)m * m;
     double* cs = U + (size_t)m * S;
-    double* scale = cs + m;
-    int* nsq = (int*)(scale + 8);
+    const double* gate = cs + m;
+    const double* scale = cs + m + 1;
+    const int64_t sH = (int64_t)(m + 1) * m;
     const unsigned eb = (unsigned)std::min<int64_t>(((int64_t)m * m + GNT - 1) / GNT, 152 * 8);
-    const double* H = p->d_H + (int64_t)j * (m + 1) * m;
-    k_lx_load<<<eb, GNT, 0, st>>>(H, m, X, m, p->dt, kd);
-    k_lx_colsum<<<(unsigned)((m + 7) / 8), GNT, 0, st>>>(X, m, cs, kd);
-    k_lx_scaling<<<1, GNT, 0, st>>>(cs, nsq, scale, SQ_LAUNCHES, kd);
-    k_lx_scale<<<eb, GNT, 0, st>>>(X, m, scale, kd);
+    const dim3 ge(eb, 1, (unsigned)nb);
+    k_lx_load<<<ge, GNT, 0, st>>>(p->d_H + (int64_t)j0 * sH, m, sH, X, m, X_, p->dt, kd);
+    k_lx_colsum<<<dim3((unsigned)((m + 7) / 8), 1, (unsigned)nb), GNT, 0, st>>>(X, m, X_, cs, X_, kd);
+    k_lx_scaling<<<dim3(1, 1, (unsigned)nb), GNT, 0, st>>>(cs, X_, m, SQ_LAUNCHES, kd);
+    k_lx_scale<<<ge, GNT, 0, st>>>(X, m, X_, scale, X_, kd);
     KV_CHECK_CUDA(cudaGetLastError());
-    int rc = gemm(p, X, m, X, m, X2, m, -1, -1, -1, kd);
-    if (!rc) rc = gemm(p, X2, m, X, m, X3, m, -1, -1, -1, kd);
-    if (!rc) rc = gemm(p, X2, m, X2, m, X4, m, -1, -1, -1, kd);
+    int rc = gemm(p, nb, X, m, X_, X, m, X_, X2, m, X_, -1, -1, -1, kd);
+    if (!rc) rc = gemm(p, nb, X2, m, X_, X, m, X_, X3, m, X_, -1, -1, -1, kd);
+    if (!rc) rc = gemm(p, nb, X2, m, X_, X2, m, X_, X4, m, X_, -1, -1, -1, kd);
     if (rc) return rc;
     // Paterson-Stockmeyer: blocks B_i = c_{4i} I + c_{4i+1} X + c_{4i+2} X^2 + c_{4i+3} X^3
     double c[19];
@@ -270,45 +311,57 @@ int launch_expm_large_column(Prob* p, int j, int dim, bool write_basis) {
     for (int i = 1; i <= 18; ++i) c[i] = c[i - 1] / (double)i;
     auto blk = [&](int i) {
         return Lin4{c[4 * i], c[4 * i + 1], c[4 * i + 2], 4 * i + 3 <= 18 ? c[4 * i + 3] : 0.0, X, X2,
-                    4 * i + 3 <= 18 ? X3 : nullptr, m};
+                    4 * i + 3 <= 18 ? X3 : nullptr, m, X_};
     };
-    k_lincomb<<<eb, GNT, 0, st>>>(T0, m, blk(4), kd);  // B_4 = c16 I + c17 X + c18 X^2
+    k_lincomb<<<ge, GNT, 0, st>>>(T0, m, X_, blk(4), kd);  // B_4 = c16 I + c17 X + c18 X^2
     KV_CHECK_CUDA(cudaGetLastError());
     double* cur = T0;
     double* nxt = T1;
     for (int i = 3; i >= 0; --i) {  // T = T X^4 + B_i
-        rc = gemm(p, cur, m, X4, m, nxt, m, -1, -1, -1, kd, 1, blk(i));
+        rc = gemm(p, nb, cur, m, X_, X4, m, X_, nxt, m, X_, -1, -1, -1, kd, 1, blk(i));
         if (rc) return rc;
         std::swap(cur, nxt);
     }
     // squarings (SQ_LAUNCHES is even: the result ends in `cur`)
     for (int q = 0; q < SQ_LAUNCHES; ++q) {
-        rc = gemm(p, cur, m, cur, m, nxt, m, -1, -1, -1, kd, 0, Lin4{}, nsq, q);
+        rc = gemm(p, nb, cur, m, X_, cur, m, X_, nxt, m, X_, -1, -1, -1, kd, 0, Lin4{}, gate, X_, q);
         if (rc) return rc;
         std::swap(cur, nxt);
     }
     // doubling over the output steps: P_0 = E (in cur), spare buffers X2 / X3
-    k_lx_init_u<<<(unsigned)((m + GNT - 1) / GNT), GNT, 0, st>>>(U, S, kd);
+    k_lx_init_u<<<dim3((unsigned)((m + GNT - 1) / GNT), 1, (unsigned)nb), GNT, 0, st>>>(U, S, X_, kd);
     KV_CHECK_CUDA(cudaGetLastError());
     const double* P = cur;
     double* spare[2] = {X2, X3};
     int sp = 0;
     for (int off = 1; off < S; off *= 2) {
         const int len = std::min(off, S - off);
-        rc = gemm(p, P, m, U, S, U + off, S, -1, len, -1, kd);
+        rc = gemm(p, nb, P, m, X_, U, S, X_, U + off, S, X_, -1, len, -1, kd);
         if (rc) return rc;
         if (2 * off < S) {
-            rc = gemm(p, P, m, P, m, spare[sp], m, -1, -1, -1, kd);
+            rc = gemm(p, nb, P, m, X_, P, m, X_, spare[sp], m, X_, -1, -1, -1, kd);
             if (rc) return rc;
             P = spare[sp];
             sp ^= 1;
         }
     }
-    k_lx_hlast<<<(unsigned)((S + GNT - 1) / GNT), GNT, 0, st>>>(U, S, S, p->d_hlast + (int64_t)j * S, kd);
+    k_lx_hlast<<<dim3((unsigned)((S + GNT - 1) / GNT), 1, (unsigned)nb), GNT, 0, st>>>(
+        U, S, X_, S, p->d_hlast + (int64_t)j0 * S, kd);
     KV_CHECK_CUDA(cudaGetLastError());
     if (write_basis) {
-        rc = gemm(p, p->d_P + (int64_t)j * p->o * m, m, U, S, p->d_basis + (int64_t)j * p->o * S, S, p->o, S, -1, kd,
-                  2);
+        rc = gemm(p, nb, p->d_P + (int64_t)j0 * p->o * m, m, (int64_t)p->o * m, U, S, X_,
+                  p->d_basis + (int64_t)j0 * p->o * S, S, (int64_t)p->o * S, p->o, S, -1, kd, 2);
+        if (rc) return rc;
+    }
+    return KV_OK;
+}
+
+int launch_expm_large(Prob* p, int j0, int ncols, int dim, bool write_basis) {
+    const char* name = dim > 0 ? "error_expm" : (p->expm_mode == KV_EXPM_PROPAGATE ? "expm_propagate" : "expm_large");
+    LaunchScope ls(p->ctx, name);
+    const int B = large_expm_batch(p->m, p->steps, p->i);
+    for (int j = j0; j < j0 + ncols; j += B) {
+        const int rc = expm_large_batch(p, j, std::min(B, j0 + ncols - j), dim, write_basis);
         if (rc) return rc;
     }
     return KV_OK;

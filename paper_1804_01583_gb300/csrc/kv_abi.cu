@@ -632,7 +632,9 @@ static size_t bytes_core(const Sys* s, const kv_problem_desc* d, int precision, 
     t += r256((size_t)(d->o + 1) * 8) + 2 * r256((size_t)d->c_row_ptr[d->o] * 8) + r256((size_t)d->o * 8);
     t += 3 * r256((size_t)d->i * 8) + 2 * 256;
     t += r256((size_t)d->i * 8) + r256((size_t)d->i * (d->steps + 1) * 8);  // error bound, its integrand
-    if (d->krylov_m > KV_MAX_M) t += r256(large_expm_scratch_doubles(d->krylov_m, d->steps) * 8);
+    if (needs_large_expm(d->krylov_m, d->expm_mode))
+        t += r256(large_expm_scratch_doubles(d->krylov_m, d->steps) * 8 *
+                  large_expm_batch(d->krylov_m, d->steps, d->i));
     for (int j = 0; j < d->i; ++j) {
         const kv_column& c = d->cols[j];
         if (c.kind == KV_COL_SPARSE) t += r256((size_t)(c.nnz + 1) * 8) * 2;
@@ -729,7 +731,8 @@ static int prob_build(Ctx* c, Prob* p, const Sys* s, const kv_problem_desc* d, i
         TRY(dalloc(p, &p->d_viol, 1));
         TRY(dalloc(p, &p->d_err, (size_t)p->i));
         TRY(dalloc(p, &p->d_hlast, (size_t)p->i * S));
-        if (p->m > KV_MAX_M) TRY(dalloc(p, &p->d_lx, large_expm_scratch_doubles(p->m, p->steps)));
+        if (needs_large_expm(p->m, p->expm_mode))
+            TRY(dalloc(p, &p->d_lx, large_expm_scratch_doubles(p->m, p->steps) * large_expm_batch(p->m, p->steps, p->i)));
         if (p->d_brow) {
             const size_t nrd = (size_t)p->i * row_dot_blocks() + p->i;  // partials, then tickets
             TRY(dalloc(p, &p->d_rowdot, nrd));

@@ -164,7 +164,7 @@ struct Prob {
     int* d_viol = nullptr;
     double* d_err = nullptr;    // per column: Lemma-1 bound at the dimension used
     double* d_hlast = nullptr;  // per column, steps+1: |(e^{t_k H} e_1)_mu|, the integrand of the bound
-    double* d_lx = nullptr;     // m > KV_MAX_M: scratch of the global-memory exponential (one column at a time)
+    double* d_lx = nullptr;     // scratch of the global-memory exponential (one batch of runs)
     // transpose dynamics (Sec. 4.1).  Outer problem: the basis matrix is built
     // from the runs of `inner` (one per output row, on A^T or A'^T, projected
     // by E'^T) and transposed; `view` is the operator the inner runs use.
@@ -239,9 +239,12 @@ size_t csr_arnoldi_dev_bytes();
 
 // exponential + basis (k_expm.cu)
 int launch_expm_basis(Prob* p);
-// global-memory exponential for dimensions above KV_MAX_M (k_expm_large.cu)
+// global-memory exponential (k_expm_large.cu): dimensions above KV_MAX_M and
+// the PROPAGATE schedule; runs in batches of large_expm_batch
 size_t large_expm_scratch_doubles(int m, int steps);
-int launch_expm_large_column(Prob* p, int j, int dim, bool write_basis);
+int large_expm_batch(int m, int steps, int runs);
+int launch_expm_large(Prob* p, int j0, int ncols, int dim, bool write_basis);
+inline bool needs_large_expm(int m, int expm_mode) { return m > KV_MAX_M || expm_mode == KV_EXPM_PROPAGATE; }
 int expm_prepare(int device);
 int fused_prepare();
 // one-time set-up that stream capture cannot contain (kv_graph.cu)
