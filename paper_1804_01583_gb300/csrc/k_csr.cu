@@ -34,18 +34,39 @@
 namespace kv {
 
 constexpr int CNT = 256;           // threads per block
-// rows per thread in the Gram-Schmidt passes: each basis vector's per-thread
-// partial is reduced across the warp in double, so the FP32 form takes more
-// rows per thread to keep those double adds rare (the FP64 pipe is 1/64 of
-// the float pipe); the FP64 form is bound by its FMAs either way
+// rows per thread in the dots pass (the FP32 form reduces each basis
+// vector's per-thread partials across the warp as float pairs, so it needs
+// no FP64 instruction per vector and can keep the rows per thread small)
 template <typename T>
 struct RowsPer {
     static constexpr int v = 8;
 };
 template <>
 struct RowsPer<float> {
-    static constexpr int v = 32;
+    static constexpr int v = 16;
 };
+
+// a + b = s + e exactly (TwoSum, Knuth), in float; the _rn intrinsics keep the
+// compiler from contracting or reassociating it
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+}
+
+// butterfly sum over the warp of x as a float pair (hi, lo): every lane ends
+// with the total, exact up to the float rounding of lo
+__device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        float sum, err;
+        two_sum_f(hi, oh, sum, err);
+        hi = sum;
+        lo = __fadd_rn(__fadd_rn(lo, ol), err);
+    }
+}
 constexpr int CCHUNK_MIN = CNT * 8;  // smallest rows per block (sizes the partials)
 
 struct ArnoldiDev {  // per-column device scratch of the Arnoldi passes
@@ -284,40 +305,66 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
     const T* Vc = V.base + cidx * V.cstride;
     const T* W = Vc + (int64_t)(j + 1) * N;
     const T* Vj = Vc + (int64_t)j * N;
+    // per (basis vector, warp): the warp's sums as a double (FP64 form) or a
+    // float pair (FP32 form), combined per block after the loop
     __shared__ double wsum[2 * (KV_MAX_M + 1)][CNT / 32];
+    __shared__ float2 wsumf[2 * (KV_MAX_M + 1)][CNT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int CR = RowsPer<T>::v;
     const int64_t r0 = (int64_t)blockIdx.x * (CNT * CR) + threadIdx.x;
-    // FP64 form: double products; FP32 form: each thread's CR products summed
-    // in float (one rounding per product and add), then one double add per
-    // basis vector -- the FP64 pipe is 1/64 of the float pipe on this GPU
-    T wv[CR], vv[CR];
+    T wv[CR], vv[CR], xa[CR], xb[CR];
 #pragma unroll
     for (int k = 0; k < CR; ++k) {
         const int64_t r = r0 + (int64_t)k * CNT;
         wv[k] = r < N ? W[r] : (T)0;
         vv[k] = r < N ? Vj[r] : (T)0;
     }
-    for (int l = 0; l <= j; ++l) {
+    auto load = [&](T (&x)[CR], int l) {
         const T* Vl = Vc + (int64_t)l * N;
-        T at = 0, gt = 0;
 #pragma unroll
         for (int k = 0; k < CR; ++k) {
             const int64_t r = r0 + (int64_t)k * CNT;
-            const T x = r < N ? Vl[r] : (T)0;
-            at = fma(x, wv[k], at);
-            gt = fma(x, vv[k], gt);
+            x[k] = r < N ? Vl[r] : (T)0;
         }
-        double a = (double)at, g = (double)gt;
+    };
+    // this thread's products with basis vector l, reduced over the warp
+    auto dots = [&](const T (&x)[CR], int l) {
+        T at = 0, gt = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            g += __shfl_xor_sync(0xffffffffu, g, o);
+        for (int k = 0; k < CR; ++k) {
+            at = fma(x[k], wv[k], at);
+            gt = fma(x[k], vv[k], gt);
         }
-        if (lane == 0) {
-            wsum[l][warp] = a;
-            wsum[KV_MAX_M + 1 + l][warp] = g;
+        if constexpr (std::is_same<T, float>::value) {
+            float ah = at, al = 0.f, gh = gt, gl = 0.f;
+            warp_sum_pair(ah, al);
+            warp_sum_pair(gh, gl);
+            if (lane == 0) {
+                wsumf[l][warp] = make_float2(ah, al);
+                wsumf[KV_MAX_M + 1 + l][warp] = make_float2(gh, gl);
+            }
+        } else {
+            double a = at, g = gt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                g += __shfl_xor_sync(0xffffffffu, g, o);
+            }
+            if (lane == 0) {
+                wsum[l][warp] = a;
+                wsum[KV_MAX_M + 1 + l][warp] = g;
+            }
         }
+    };
+    // two register buffers: the loads of vector l+1 are in flight while the
+    // products of vector l are formed and reduced
+    load(xa, 0);
+    for (int l = 0; l <= j; l += 2) {
+        if (l + 1 <= j) load(xb, l + 1);
+        dots(xa, l);
+        if (l + 1 > j) break;
+        if (l + 2 <= j) load(xa, l + 2);
+        dots(xb, l + 1);
     }
     __syncthreads();
     const int K = j + 1;
@@ -325,7 +372,10 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
     for (int q = threadIdx.x; q < 2 * K; q += CNT) {
         const int row = q < K ? q : (KV_MAX_M + 1 + q - K);
         double v = 0.0;
-        for (int w = 0; w < CNT / 32; ++w) v += wsum[row][w];
+        for (int w = 0; w < CNT / 32; ++w) {
+            if constexpr (std::is_same<T, float>::value) v += (double)wsumf[row][w].x + (double)wsumf[row][w].y;
+            else v += wsum[row][w];
+        }
         part[(int64_t)q * nbx + blockIdx.x] = v;
     }
     __shared__ int flag;
@@ -369,37 +419,53 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_update(VecArgs<T> V, int64_t N,
     T* Vc = V.base + cidx * V.cstride;
     T* W = Vc + (int64_t)(j + 1) * N;
     const ArnoldiDev* A = ad + cidx;
+    // coefficients: double (FP64 form), or split once per block into float
+    // pairs hi + lo carrying ~48 bits (FP32 form)
     __shared__ double cf[KV_MAX_M + 1];
-    for (int l = threadIdx.x; l <= j; l += CNT) cf[l] = A->c[l];
+    __shared__ float cfh[KV_MAX_M + 1], cfl[KV_MAX_M + 1];
+    for (int l = threadIdx.x; l <= j; l += CNT) {
+        cf[l] = A->c[l];
+        const CoefPair c = split_coef(-A->c[l]);
+        cfh[l] = c.hi;
+        cfl[l] = c.lo;
+    }
     __syncthreads();
     constexpr int CR = 8;  // no per-vector reduction here: short rows keep occupancy
     const int64_t r0 = (int64_t)blockIdx.x * (CNT * CR) + threadIdx.x;
-    T wv[CR];
+    T wv[CR], xa[CR], xb[CR];
 #pragma unroll
     for (int k = 0; k < CR; ++k) {
         const int64_t r = r0 + (int64_t)k * CNT;
         wv[k] = r < N ? W[r] : (T)0;
     }
-    for (int l = 0; l <= j; ++l) {
+    auto load = [&](T (&x)[CR], int l) {
         const T* Vl = Vc + (int64_t)l * N;
-        if constexpr (std::is_same<T, float>::value) {
-            const CoefPair c = split_coef(-cf[l]);  // the coefficient to ~48 bits
 #pragma unroll
-            for (int k = 0; k < CR; ++k) {
-                const int64_t r = r0 + (int64_t)k * CNT;
-                if (r < N) {
-                    const float v = Vl[r];
-                    wv[k] = fmaf(c.hi, v, fmaf(c.lo, v, wv[k]));
-                }
-            }
+        for (int k = 0; k < CR; ++k) {
+            const int64_t r = r0 + (int64_t)k * CNT;
+            x[k] = r < N ? Vl[r] : (T)0;
+        }
+    };
+    auto apply = [&](const T (&x)[CR], int l) {
+        if constexpr (std::is_same<T, float>::value) {
+            const float ch = cfh[l], cl = cfl[l];
+#pragma unroll
+            for (int k = 0; k < CR; ++k) wv[k] = fmaf(ch, x[k], fmaf(cl, x[k], wv[k]));
         } else {
             const double c = cf[l];
 #pragma unroll
-            for (int k = 0; k < CR; ++k) {
-                const int64_t r = r0 + (int64_t)k * CNT;
-                if (r < N) wv[k] = fma(-c, Vl[r], wv[k]);
-            }
+            for (int k = 0; k < CR; ++k) wv[k] = fma(-c, x[k], wv[k]);
         }
+    };
+    // the loads of vector l+1 are in flight while vector l is applied (rows
+    // past N load 0 and are never stored)
+    load(xa, 0);
+    for (int l = 0; l <= j; l += 2) {
+        if (l + 1 <= j) load(xb, l + 1);
+        apply(xa, l);
+        if (l + 1 > j) break;
+        if (l + 2 <= j) load(xa, l + 2);
+        apply(xb, l + 1);
     }
     typename AccOf<T>::type acc;
 #pragma unroll
