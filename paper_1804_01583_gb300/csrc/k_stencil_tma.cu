@@ -34,8 +34,8 @@
 // reads in this pass, so tiles never race on halos.
 //
 // The update is evaluated in float with the difference form of the Laplacian
-// ((l - c) + (r - c): exact subtraction for nearby values) and every double
-// coefficient split into a float pair (hi + lo), one FMA chain; both dot
+// ((l - c) + (r - c): exact subtraction for nearby values) and one FMA chain
+// with the double coefficients rounded to float; both dot
 // products are summed per plane in float (squared differences per axis,
 // weighted once per plane), accumulated over the planes as TwoSum float
 // pairs and reduced across threads and CTAs in double.
@@ -162,9 +162,13 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
 
     const double sj = a.st->s[a.j];
     const double alpha = a.H[(int64_t)a.j * a.m + a.j];
-    const CoefPair fx = split_coef(sj * g.kx), fy = split_coef(sj * g.ky), fz = split_coef(sj * g.kz);
-    const CoefPair fc = split_coef(-alpha * sj);
-    const CoefPair fa = split_coef(FIRST ? 0.0 : -a.H[(int64_t)a.j * a.m + (a.j - 1)] * a.st->s[a.j - 1]);
+    // the coefficients of w = s_j A v_j - alpha s_j v_j - beta s_{j-1} v_{j-1},
+    // rounded to float once (with the difference form of the Laplacian this
+    // is as accurate as carrying them as float pairs: the error is that of
+    // the FP32 storage)
+    const float fx = (float)(sj * g.kx), fy = (float)(sj * g.ky), fz = (float)(sj * g.kz);
+    const float fc = (float)(-alpha * sj);
+    const float fa = (float)(FIRST ? 0.0 : -a.H[(int64_t)a.j * a.m + (a.j - 1)] * a.st->s[a.j - 1]);
     const float kx = (float)g.kx, ky = (float)g.ky, kz = (float)g.kz;
 
     auto ring = [](int plane, int n) { return ((plane % n) + n) % n; };
@@ -280,16 +284,11 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
                 const float Lx = (xl[u] - c) + (xr[u] - c);
                 const float Ly = (dd[u] - c) + (uu[u] - c);
                 const float Lz = (mm[u] - c) + (pp[u] - c);
-                float acc = fx.lo * Lx;
-                acc = fmaf(fy.lo, Ly, acc);
-                acc = fmaf(fz.lo, Lz, acc);
-                acc = fmaf(fc.lo, c, acc);
-                if (!FIRST) acc = fmaf(fa.lo, aa[u], acc);
-                acc = fmaf(fx.hi, Lx, acc);
-                acc = fmaf(fy.hi, Ly, acc);
-                acc = fmaf(fz.hi, Lz, acc);
-                acc = fmaf(fc.hi, c, acc);
-                if (!FIRST) acc = fmaf(fa.hi, aa[u], acc);
+                float acc = fx * Lx;
+                acc = fmaf(fy, Ly, acc);
+                acc = fmaf(fz, Lz, acc);
+                acc = fmaf(fc, c, acc);
+                if (!FIRST) acc = fmaf(fa, aa[u], acc);
                 wv[u] = valid ? acc : 0.f;
             }
             w2[h] = make_float4(wv[0], wv[1], wv[2], wv[3]);
