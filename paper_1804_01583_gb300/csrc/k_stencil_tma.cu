@@ -247,15 +247,19 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
 
         // ---- w on this thread's 2 x 4 points
         float4 w2[2];
+        // v_j box rows r0 .. r0+3 (w rows r0-1 .. r0+2): the y neighbours and
+        // centres of both of this thread's rows, each loaded once.  In
+        // full-width tiles every box row is 512 bytes, so each float4 row
+        // load is four conflict-free wavefronts.
+        float4 brows[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) brows[q] = *reinterpret_cast<const float4*>(Bc + (r0 + q) * WCM + 4 * cg);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int r = r0 + h;
             const bool valid = pin && xin && (h == 0 ? yin0 : yin1);
-            // full-width tiles: every box row is 512 bytes, so each float4
-            // row load is four conflict-free wavefronts
             const int bo = (r + 1) * WCM + 4 * cg;
-            const float* brow = Bc + bo;
-            const float4 c4 = *reinterpret_cast<const float4*>(brow);
+            const float4 c4 = brows[h + 1];
             // x neighbours from the adjacent lanes.  cg = 0's left value feeds
             // only w(x0-4), which nothing reads; the right one of cg = G-1 is
             // column x0+124 of the side box (full width) or lies beyond the
@@ -263,8 +267,8 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
             const float lft = __shfl_up_sync(0xffffffffu, c4.w, 1);
             float rgt = __shfl_down_sync(0xffffffffu, c4.x, 1);
             if (cg == G - 1) rgt = NARROW ? 0.f : Sc[(r + 1) * SBW];
-            const float4 d4 = *reinterpret_cast<const float4*>(brow - WCM);
-            const float4 u4 = *reinterpret_cast<const float4*>(brow + WCM);
+            const float4 d4 = brows[h];
+            const float4 u4 = brows[h + 2];
             const float4 m4 = *reinterpret_cast<const float4*>(Bm + bo);
             const float4 p4 = *reinterpret_cast<const float4*>(Bp + bo);
             float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
