@@ -371,6 +371,18 @@ int kv_grid_lanczos_noalloc(int device, void *stream, int ndim, const int64_t di
                             int32_t o, const int64_t *c_row_ptr, const int64_t *c_col, const double *c_val,
                             int32_t krylov_m, double *H, double *P, double *beta0, int32_t *m_used);
 
+/* Check of the failure path of the device waits.  Not in the paper: the
+ * single-pass grid kernel waits for its TMA stages on mbarriers with a limit
+ * on the number of polls and reports an expired wait through the column's
+ * status word (kv_fetch then returns KV_ETIMEOUT) instead of hanging the GPU.
+ * This launches one block that waits, with the same bounded-wait routine and
+ * `polls` polls (1 .. 4194304), on an mbarrier that nothing completes, so the
+ * wait must expire; the block records the expiry in a status word and exits.
+ * The call waits for the block and returns KV_ETIMEOUT when the wait expired
+ * (the expected outcome), KV_OK if it did not, KV_EINVAL for a bad argument,
+ * KV_ECUDA on a CUDA error.  The device and any context on it stay usable. */
+int kv_diag_bounded_wait(int device, int64_t polls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,7 +75,7 @@ class kv_result(C.Structure):
 EXPORTED = ["kv_version", "kv_last_error", "kv_create", "kv_destroy", "kv_pool_stats", "kv_system_stencil",
             "kv_system_csr", "kv_sys_destroy", "kv_problem", "kv_prob_destroy", "kv_problem_bytes",
             "kv_enqueue", "kv_fetch", "kv_run", "kv_profile_enable", "kv_profile_read", "kv_launch_count",
-            "kv_problem_runs"]
+            "kv_problem_runs", "kv_diag_bounded_wait"]
 
 _lib = None
 _lock = threading.Lock()
@@ -113,6 +113,7 @@ def load(path: Optional[str] = None):
         lib.kv_profile_read.argtypes = [V, C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         lib.kv_launch_count.argtypes = [V, C.POINTER(C.c_int64)]
         lib.kv_problem_runs.argtypes = [V, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        lib.kv_diag_bounded_wait.argtypes = [I, C.c_int64]
         lib.kv_grid_lanczos_noalloc.argtypes = [I, V, I, C.POINTER(C.c_int64), C.c_double, C.POINTER(C.c_double),
                                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_double, C.c_int32,
                                                 V, V, V, C.c_int32, V, V, V, V]
@@ -524,3 +525,9 @@ def solve(problem, ctx: Optional[Context] = None, *, pool_bytes: int = 1 << 30, 
         sysh.close()
         if own:
             ctx.close()
+
+
+def diag_bounded_wait(polls: int, device: int = 0) -> int:
+    """kv_diag_bounded_wait: the status code (KV_ETIMEOUT when the bounded
+    wait expired, as it must)."""
+    return int(load().kv_diag_bounded_wait(int(device), int(polls)))

@@ -88,8 +88,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
-    for (long it = 0; it < WAIT_LIMIT; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, long limit = WAIT_LIMIT) {
+    for (long it = 0; it < limit; ++it)
         if (mbar_try_wait(b, parity)) return true;
     return false;
 }
@@ -636,4 +636,52 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     return KV_OK;
 }
 
+// One block waits on an mbarrier nothing arrives on, with the kernel's own
+// bounded-wait routine: the wait must expire and is recorded in *status.
+__global__ void k_diag_wait(unsigned* status, long polls) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, polls);
+    if (!ok) atomicOr(status, 1u);
+}
+
 }  // namespace kv
+
+extern "C" int kv_diag_bounded_wait(int device, int64_t polls) {
+    using namespace kv;
+    if (polls < 1 || polls > WAIT_LIMIT) {
+        set_error("kv_diag_bounded_wait: polls must be in [1, %ld]", WAIT_LIMIT);
+        return KV_EINVAL;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        set_error("kv_diag_bounded_wait: device %d", device);
+        return KV_EINVAL;
+    }
+    unsigned* d_status = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        k_diag_wait<<<1, 32, 0, st>>>(d_status, (long)polls);
+        e = cudaGetLastError();
+    }
+    unsigned h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d_status) cudaFree(d_status);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) {
+        set_error("kv_diag_bounded_wait: %s", cudaGetErrorString(e));
+        return KV_ECUDA;
+    }
+    if (h) {
+        set_error("kv_diag_bounded_wait: the wait expired after %lld polls", (long long)polls);
+        return KV_ETIMEOUT;
+    }
+    return KV_OK;
+}
