@@ -632,6 +632,7 @@ static size_t bytes_core(const Sys* s, const kv_problem_desc* d, int precision, 
     t += r256((size_t)(d->o + 1) * 8) + 2 * r256((size_t)d->c_row_ptr[d->o] * 8) + r256((size_t)d->o * 8);
     t += 3 * r256((size_t)d->i * 8) + 2 * 256;
     t += r256((size_t)d->i * 8) + r256((size_t)d->i * (d->steps + 1) * 8);  // error bound, its integrand
+    t += r256(bounds_scratch_doubles(d->i, d->o, d->steps) * 8);
     if (needs_large_expm(d->krylov_m, d->expm_mode))
         t += r256(large_expm_scratch_doubles(d->krylov_m, d->steps) * 8 *
                   large_expm_batch(d->krylov_m, d->steps, d->i));
@@ -663,7 +664,7 @@ int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, s
     size_t t = bytes_core(s, &in.d, precision, bo);
     const size_t S = (size_t)d->steps + 1;
     t += r256((size_t)d->i * d->o * S * 8) + 2 * r256((size_t)d->o * S * 8) + r256((size_t)d->o * 8) +
-         3 * r256((size_t)d->i * 8) + 2 * 256;
+         3 * r256((size_t)d->i * 8) + 2 * 256 + r256(bounds_scratch_doubles(d->i, d->o, d->steps) * 8);
     if (s->kind == 1 && !s->symmetric && !s->d_rpT)  // A^T, built on first use
         t += r256((size_t)(s->n + 1) * 8) + r256((size_t)s->nnz * 4) + r256((size_t)s->nnz * elem_size(precision));
     *bytes = t;
@@ -730,6 +731,8 @@ static int prob_build(Ctx* c, Prob* p, const Sys* s, const kv_problem_desc* d, i
         TRY(dalloc(p, &p->d_ystar, 1));
         TRY(dalloc(p, &p->d_viol, 1));
         TRY(dalloc(p, &p->d_err, (size_t)p->i));
+        if (bounds_scratch_doubles(p->i, p->o, p->steps))
+            TRY(dalloc(p, &p->d_bpart, bounds_scratch_doubles(p->i, p->o, p->steps)));
         TRY(dalloc(p, &p->d_hlast, (size_t)p->i * S));
         if (needs_large_expm(p->m, p->expm_mode))
             TRY(dalloc(p, &p->d_lx, large_expm_scratch_doubles(p->m, p->steps) * large_expm_batch(p->m, p->steps, p->i)));
@@ -871,6 +874,8 @@ static int build_transposed(kv_ctx* c, kv_prob** out, const Sys* s, const kv_pro
         TRY(dalloc(p, &p->d_zstar, (size_t)p->i));
         TRY(dalloc(p, &p->d_ystar, 1));
         TRY(dalloc(p, &p->d_viol, 1));
+        if (bounds_scratch_doubles(p->i, p->o, p->steps))
+            TRY(dalloc(p, &p->d_bpart, bounds_scratch_doubles(p->i, p->o, p->steps)));
         TRY(upload(c, p->d_theta, d->theta, (size_t)p->o * 8));
         std::vector<double> zl(p->i), zh(p->i);
         for (int j = 0; j < p->i; ++j) {

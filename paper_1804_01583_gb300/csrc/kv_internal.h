@@ -163,6 +163,7 @@ struct Prob {
     double* d_ystar = nullptr;
     int* d_viol = nullptr;
     double* d_err = nullptr;    // per column: Lemma-1 bound at the dimension used
+    double* d_bpart = nullptr;  // column-chunk partial bounds (many columns only)
     double* d_hlast = nullptr;  // per column, steps+1: |(e^{t_k H} e_1)_mu|, the integrand of the bound
     double* d_lx = nullptr;     // scratch of the global-memory exponential (one batch of runs)
     // transpose dynamics (Sec. 4.1).  Outer problem: the basis matrix is built
@@ -252,6 +253,7 @@ int prepare_for_capture(int device);
 
 // bounds (k_bounds.cu)
 int launch_bounds(Prob* p);
+size_t bounds_scratch_doubles(int ncol, int o, int steps);
 
 // number of reduction partial slots a problem needs
 int64_t reduce_slots_needed(const Prob* p);

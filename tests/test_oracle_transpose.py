@@ -105,3 +105,14 @@ def test_transpose_equals_forward_on_the_random_csr_workload():
     t = oracle.run(p)
     S = max(np.max(np.abs(f["basis"][j])) for j in range(p.i))
     assert max(np.max(np.abs(t["basis"][j] - f["basis"][j])) for j in range(p.i)) <= 1e-11 * S
+
+
+def test_transpose_equals_forward_on_replicated_blocks():
+    """The replicated-block shape (Sec. 5.2, h = 20: n = 560, i = 160, o = 1):
+    one transposed run gives the basis of the 160 forward runs (both exact:
+    the Krylov spaces are invariant within 28 dimensions)."""
+    t = oracle.run(W.replicated_blocks(20, simulate="transpose"))
+    f = oracle.run(W.replicated_blocks(20, simulate="forward"))
+    assert list(t["used"].values()) == [28] and set(f["used"].values()) == {28}
+    S = max(np.max(np.abs(f["basis"][j])) for j in range(160))
+    assert max(np.max(np.abs(t["basis"][j] - f["basis"][j])) for j in range(160)) <= 1e-12 * S

@@ -304,6 +304,44 @@ def oscillator(theta: float = 4.0) -> Problem:
                    name="oscillator")
 
 
+def replicated_blocks(h: int, *, seed: int = 0, dt: float = 0.1, steps: int = 300, m: int = 28,
+                      theta: float = 0.45, precision: str = "fp64", simulate: str = "auto") -> Problem:
+    """The replicated-helicopter shape of Sec. 5.2 with a stand-in block: the
+    28-dimensional helicopter model is not available, so one seeded random
+    stable 28 x 28 block B (entries N(0,1)/sqrt(28), shifted so that its
+    rightmost eigenvalue has real part -0.05) is copied h times on the
+    diagonal, n = 28 h.  Eight variables of every copy (its first eight) are
+    intervals [0.9, 1.1] * (their seeded base value in [0.1, 0.3]), so i = 8 h unit
+    generators; the output is the mean of the eighth variable over the copies
+    (o = 1), unsafe above theta; horizon 30 at step 0.1 (300 steps)."""
+    rng = np.random.default_rng(seed + 2828)
+    B = rng.standard_normal((28, 28)) / math.sqrt(28)
+    B -= (np.max(np.linalg.eigvals(B).real) + 0.05) * np.eye(28)
+    base = rng.uniform(0.1, 0.3, 8)
+    nzr, nzc = np.nonzero(B)
+    vals_b = B[nzr, nzc]
+    per = len(vals_b)
+    n = 28 * h
+    offs = (np.arange(h, dtype=np.int64) * 28)[:, None]
+    rows = (offs + nzr[None, :]).reshape(-1)
+    cols = (offs + nzc[None, :]).reshape(-1)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    sysm = CsrSystem(n=n, row_ptr=row_ptr, col=cols.astype(np.int32), val=np.tile(vals_b, h).astype(np.float64),
+                     b=None, symmetric=False)
+    cols_e = []
+    for k in range(h):
+        for v in range(8):
+            cols_e.append(Column(kind="sparse", zlo=0.9 * base[v], zhi=1.1 * base[v],
+                                 idx=np.array([28 * k + v], dtype=np.int64), val=np.array([1.0])))
+    rp, cc, cv = _c_rows([(np.arange(h, dtype=np.int64) * 28 + 7, np.full(h, 1.0 / h))])
+    assert per * h == len(sysm.val)
+    return Problem(system=sysm, columns=cols_e, C_row_ptr=rp, C_col=cc, C_val=cv, theta=np.array([theta]),
+                   dt=dt, steps=steps, m=m, precision=precision, simulate=simulate,
+                   name=f"replicated-blocks-h{h}")
+
+
 # --------------------------------------------------------------------------
 # small random cases
 # --------------------------------------------------------------------------
