@@ -473,6 +473,44 @@ def error_control_bench(dev: int):
     return out
 
 
+def replicated_bench(dev: int, h: int = 20_000):
+    """The replicated-block shape of Sec. 5.2 (n = 28 h, i = 8 h, o = 1, 300
+    steps) at h = 20 000: one Krylov run of the transpose dynamics instead of
+    8 h forward runs; time per query and where it goes."""
+    import torch
+    import paper_1804_01583_gb300 as kv
+    out = {"workload": f"replicated 28x28 blocks h={h}: n={28 * h}, i={8 * h}, o=1, 300 steps, transposed"}
+    t0 = time.perf_counter()
+    p = W.replicated_blocks(h, simulate="transpose")
+    out["host_build_s"] = time.perf_counter() - t0
+    ctx = kv.Context(8 << 30, device=dev)
+    try:
+        t0 = time.perf_counter()
+        sysh = kv.System(ctx, p.system, p.precision)
+        ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
+        out["problem_setup_s"] = time.perf_counter() - t0
+        ph.run(full=False)
+        torch.cuda.synchronize()
+        ctx.profile_enable(True)
+        k = 3
+        t0 = time.perf_counter()
+        for _ in range(k):
+            r = ph.run(full=False)
+        out["ms_per_query"] = (time.perf_counter() - t0) * 1e3 / k
+        out["kernels_ms_per_query"] = {nm: ctx.profile_read(nm)[1] / k for nm in
+                                       ("csr_spmv", "csr_spmm", "arnoldi_dots", "arnoldi_update", "project",
+                                        "expm_propagate", "bounds") if ctx.profile_read(nm)[0]}
+        ctx.profile_enable(False)
+        out["krylov_runs"] = 1
+        out["m_used"] = int(ph.fetch(full=True)["m_used"][0])
+        out["first_violation_step"] = r["viol_step"]
+        ph.close()
+        sysh.close()
+    finally:
+        ctx.close()
+    return out
+
+
 def batched_bench(dev: int, nq: int = 64, reps: int = 5):
     """Small queries (the 20 x 20 heat configuration, FP64, m = 30, 500 steps):
     nq of them enqueued one after another on the context stream, against the
@@ -640,6 +678,7 @@ def main():
     if args.batched and world == 1:
         line["batched"] = batched_bench(dev)
         line["error_control"] = error_control_bench(dev)
+        line["replicated"] = replicated_bench(dev)
     if args.csr and world == 1:
         line["csr_workload"] = csr_bench(args, dev)
     if args.serve and world == 1:

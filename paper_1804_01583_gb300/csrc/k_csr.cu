@@ -255,7 +255,7 @@ __device__ void finish_vector(double nw2, const T* W, ColState* s, double* H, do
         }
     }
     __syncthreads();
-    if (!cont) return;
+    if (!cont || cd.o > PROJ_INLINE_MAX) return;  // launch_project takes many rows
     for (int r = 0; r < cd.o; ++r) {
         const double v = cgather<T>(cd, r, W, sh);
         if (threadIdx.x == 0) P[(int64_t)r * m + (j + 1)] = snext * v;
@@ -666,14 +666,18 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
                                                    aug, stp, H, m, it, partials, counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }
-            LaunchScope ls(p->ctx, "csr_lanczos_update");
-            if (it == 0)
-                k_lanczos3_update<T, true><<<gs, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
-                                                              counters, nbx);
-            else
-                k_lanczos3_update<T, false><<<gs, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
-                                                               counters, nbx);
-            KV_CHECK_CUDA(cudaGetLastError());
+            {
+                LaunchScope ls(p->ctx, "csr_lanczos_update");
+                if (it == 0)
+                    k_lanczos3_update<T, true><<<gs, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
+                                                                  counters, nbx);
+                else
+                    k_lanczos3_update<T, false><<<gs, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
+                                                                   counters, nbx);
+                KV_CHECK_CUDA(cudaGetLastError());
+            }
+            const int rc = launch_project(p, j0, ncols, (T*)V + (int64_t)ws * N, va.cstride, it + 1);
+            if (rc) return rc;
         } else {
             if (p->spmm_G > 0 && !(p->flags & KV_FLAG_NO_SPMM)) {
                 // grouped SpMM: the matrix is read once per group of spmm_G columns
@@ -698,10 +702,14 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
                 k_arnoldi_dots<T><<<gr, CNT, 0, st>>>(va, N, stp, H, ad, m, it, partials, counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }
-            LaunchScope ls(p->ctx, "arnoldi_update");
-            const dim3 gu((unsigned)row_blocks(N), (unsigned)ncols);  // 8 rows per thread
-            k_arnoldi_update<T><<<gu, CNT, 0, st>>>(va, N, stp, H, P, ad, cd, m, it, partials, counters, nbx);
-            KV_CHECK_CUDA(cudaGetLastError());
+            {
+                LaunchScope ls(p->ctx, "arnoldi_update");
+                const dim3 gu((unsigned)row_blocks(N), (unsigned)ncols);  // 8 rows per thread
+                k_arnoldi_update<T><<<gu, CNT, 0, st>>>(va, N, stp, H, P, ad, cd, m, it, partials, counters, nbx);
+                KV_CHECK_CUDA(cudaGetLastError());
+            }
+            const int rc = launch_project(p, j0, ncols, (T*)V + (int64_t)(it + 1) * N, va.cstride, it + 1);
+            if (rc) return rc;
         }
         if (is_checkpoint(p, it + 1)) {
             const int rc = launch_error_check(p, j0, ncols, it + 1);

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(SNT) k_stencil_init_box(T* __restrict__ B, Ste
         }
     }
     __syncthreads();
+    if (cd.o > PROJ_INLINE_MAX) return;  // launch_project takes the rows
     for (int r = 0; r < cd.o; ++r) {
         const double v = c_gather_row<T>(cd, r, B, sh);
         if (t == 0) P[(int64_t)r * m + 0] = s0 * v;
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(SNT) k_stencil_update(const T* __restrict__ B,
         }
     }
     __syncthreads();
-    if (!cont) return;
+    if (!cont || cd.o > PROJ_INLINE_MAX) return;
     for (int r = 0; r < cd.o; ++r) {
         const double v = c_gather_row<T>(cd, r, A, sh);
         if (t == 0) P[(int64_t)r * m + (j + 1)] = snext * v;
@@ -276,6 +277,7 @@ int launch_stencil_init_box(Prob* p, int j, void* B) {
     dim3 blk(SBX, SBY), grd((unsigned)((g.nx + SBX - 1) / SBX), (unsigned)((g.ny + SBY - 1) / SBY),
                            (unsigned)((g.nz + zc - 1) / zc));
     const kv_column& c = p->cols[j];
+    {
     LaunchScope ls(p->ctx, "stencil_init");
     const int64_t hz = p->sys->ndim >= 3 ? c.box_hi[2] : 1, lz = p->sys->ndim >= 3 ? c.box_lo[2] : 0;
     const int64_t hy = p->sys->ndim >= 2 ? c.box_hi[1] : 1, ly = p->sys->ndim >= 2 ? c.box_lo[1] : 0;
@@ -289,7 +291,8 @@ int launch_stencil_init_box(Prob* p, int j, void* B) {
         k_stencil_init_box<double><<<grd, blk, 0, p->ctx->stream>>>(
             (double*)B, g, zc, c.box_lo[0], ly, lz, c.box_hi[0], hy, hz, c.value, st, H0, P, cdesc(p), p->m, p->red);
     KV_CHECK_CUDA(cudaGetLastError());
-    return KV_OK;
+    }
+    return launch_project(p, j, 1, B, 0, 0);
 }
 
 int launch_stencil_alpha(Prob* p, int j, int it, const void* B) {

@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
         }
     }
     __syncthreads();
-    if (!cont) return;
+    if (!cont || a.cd.o > PROJ_INLINE_MAX) return;  // launch_project takes many rows
     for (int r = 0; r < a.cd.o; ++r) {
         double v = 0.0;
         for (int64_t e = a.cd.rp[r] + t; e < a.cd.rp[r + 1]; e += FNT)

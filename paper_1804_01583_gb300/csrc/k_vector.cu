@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(VNT) k_init_norm(const T* __restrict__ B, int6
         }
     }
     __syncthreads();
+    if (cd.o > PROJ_INLINE_MAX) return;  // launch_project takes the rows
     for (int r = 0; r < cd.o; ++r) {
         double v = 0.0;
         for (int64_t e = cd.rp[r] + threadIdx.x; e < cd.rp[r + 1]; e += VNT)
@@ -61,6 +62,47 @@ __global__ void __launch_bounds__(VNT) k_init_norm(const T* __restrict__ B, int6
         v = block_sum<VNT>(v, sh);
         if (threadIdx.x == 0) P[(int64_t)r * m] = s0 * v;
     }
+}
+
+// P[r][jcol] = s_jcol (C_r . w) for every row of C, one warp per row, for the
+// columns of a launch group (blockIdx.y); a column that stopped before jcol
+// is skipped (its P columns past m_used are not used)
+template <typename T>
+__global__ void __launch_bounds__(VNT) k_project(const T* w0, int64_t cstride, const ColState* st, CDesc cd,
+                                                 double* P0, int64_t pstride, int m, int jcol) {
+    const int c = blockIdx.y;
+    const ColState* s = st + c;
+    if (s->done && s->m_used <= jcol) return;
+    const T* W = w0 + c * cstride;
+    double* P = P0 + c * pstride;
+    const double sc = s->s[jcol];
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (VNT / 32);
+    for (int64_t r = (int64_t)blockIdx.x * (VNT / 32) + (threadIdx.x >> 5); r < cd.o; r += nw) {
+        double v = 0.0;
+        for (int64_t e = cd.rp[r] + lane; e < cd.rp[r + 1]; e += 32) v += cd.val[e] * (double)__ldcg(W + cd.col[e]);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) P[r * m + jcol] = sc * v;
+    }
+}
+
+int launch_project(Prob* p, int j0, int ncols, const void* w0, int64_t cstride, int jcol) {
+    if (p->o <= PROJ_INLINE_MAX || jcol >= p->m) return KV_OK;
+    LaunchScope ls(p->ctx, "project");
+    CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval};
+    int64_t g = ((int64_t)p->o + (VNT / 32) - 1) / (VNT / 32);
+    if (g > 152 * 16) g = 152 * 16;
+    const dim3 grd((unsigned)g, (unsigned)ncols);
+    double* P0 = p->d_P + (int64_t)j0 * p->o * p->m;
+    const int64_t ps = (int64_t)p->o * p->m;
+    if (p->prec == KV_FP32)
+        k_project<float><<<grd, VNT, 0, p->ctx->stream>>>((const float*)w0, cstride, p->d_state + j0, cd, P0, ps,
+                                                          p->m, jcol);
+    else
+        k_project<double><<<grd, VNT, 0, p->ctx->stream>>>((const double*)w0, cstride, p->d_state + j0, cd, P0, ps,
+                                                           p->m, jcol);
+    KV_CHECK_CUDA(cudaGetLastError());
+    return KV_OK;
 }
 
 static int grid_for(int64_t n) {
@@ -94,17 +136,19 @@ int launch_dense_to(Prob* p, int j, void* B) {
 }
 
 int launch_init_norm(Prob* p, int j, void* B) {
-    LaunchScope ls(p->ctx, "init_norm");
-    const int g = grid_for(p->N);
-    CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval};
-    ColState* st = p->d_state + j;
-    double* P = p->d_P + (int64_t)j * p->o * p->m;
-    if (p->prec == KV_FP32)
-        k_init_norm<float><<<g, VNT, 0, p->ctx->stream>>>((const float*)B, p->N, st, P, cd, p->m, p->red);
-    else
-        k_init_norm<double><<<g, VNT, 0, p->ctx->stream>>>((const double*)B, p->N, st, P, cd, p->m, p->red);
-    KV_CHECK_CUDA(cudaGetLastError());
-    return KV_OK;
+    {
+        LaunchScope ls(p->ctx, "init_norm");
+        const int g = grid_for(p->N);
+        CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval};
+        ColState* st = p->d_state + j;
+        double* P = p->d_P + (int64_t)j * p->o * p->m;
+        if (p->prec == KV_FP32)
+            k_init_norm<float><<<g, VNT, 0, p->ctx->stream>>>((const float*)B, p->N, st, P, cd, p->m, p->red);
+        else
+            k_init_norm<double><<<g, VNT, 0, p->ctx->stream>>>((const double*)B, p->N, st, P, cd, p->m, p->red);
+        KV_CHECK_CUDA(cudaGetLastError());
+    }
+    return launch_project(p, j, 1, B, 0, 0);
 }
 
 }  // namespace kv

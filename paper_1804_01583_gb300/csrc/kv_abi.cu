@@ -967,6 +967,7 @@ static int run_column(Prob* p, int j) {
         }
         for (int it = 0; it < p->m; ++it) {
             rc = launch_lanczos_fused(p, j, it, vec(it % 3), vec((it + 2) % 3), vec((it + 1) % 3));
+            if (!rc) rc = launch_project(p, j, 1, vec((it + 1) % 3), 0, it + 1);
             if (!rc && is_checkpoint(p, it + 1)) rc = launch_error_check(p, j, 1, it + 1);
             if (rc) return rc;
         }
@@ -978,6 +979,7 @@ static int run_column(Prob* p, int j) {
             void* A = vec((it + 1) & 1);
             rc = launch_stencil_alpha(p, j, it, B);
             if (!rc) rc = launch_stencil_update(p, j, it, B, A);
+            if (!rc) rc = launch_project(p, j, 1, A, 0, it + 1);
             if (!rc && is_checkpoint(p, it + 1)) rc = launch_error_check(p, j, 1, it + 1);
             if (rc) return rc;
         }

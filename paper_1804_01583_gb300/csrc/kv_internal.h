@@ -226,6 +226,13 @@ int row_dot_blocks();
 int launch_row_dot(Prob* p, int j0, int ncols, void* V, int xslot, int wslot, int it);
 int launch_basis_transpose(const Prob* inner, double* out, cudaStream_t st);
 
+// The projection P[:, jcol] = s_jcol C v of a new Krylov vector: done inline
+// by the block that finishes the vector for up to PROJ_INLINE_MAX rows of C,
+// else by launch_project over the whole grid (one warp per row; the
+// transpose dynamics project by E'^T, one row per column of E).
+constexpr int PROJ_INLINE_MAX = 16;
+int launch_project(Prob* p, int j0, int ncols, const void* w0, int64_t cstride, int jcol);
+
 // generic vectors (k_vector.cu)
 int launch_init_norm(Prob* p, int j, void* B);
 int launch_scatter(Prob* p, int j, void* B);

@@ -228,3 +228,14 @@ def test_malformed_csr_rejected(ctx):
         with pytest.raises(kv.KvError) as ei:
             kv.System(ctx, bad)
         assert ei.value.code == kv.KV_EINVAL
+
+
+@pytest.mark.parametrize("method", ["lanczos", "arnoldi"])
+def test_many_output_rows_csr(ctx, method):
+    """24 dense output rows: the projection runs as a separate grid kernel for
+    CSR Lanczos and Arnoldi columns."""
+    sysm = W.random_symmetric_csr(700, seed=31) if method == "lanczos" else W.random_csr(700, seed=31, with_b=False)
+    p = W.random_problem(sysm, seed=32, n_cols=3, o=24, dt=0.05, steps=60, m=20)
+    got = run_gpu(ctx, p)
+    ref = oracle.run(p)
+    assert bound_error(got, ref) <= 1e-9

@@ -264,3 +264,27 @@ def test_pool_exhaustion_is_reported(ctx):
     assert small.pool_stats()[0] == 0
     sysh.close()
     small.close()
+
+
+@pytest.mark.parametrize("precision,flags", [("fp64", 0), ("fp32", 0), ("fp32", 1)])
+def test_many_output_rows(ctx, precision, flags):
+    """40 output rows (more than the rows a finishing block projects itself):
+    the projection of every new Krylov vector runs as its own grid kernel."""
+    dims = (40, 36, 20)
+    rng = np.random.default_rng(17)
+    p = W.heat(dims, block=(10, 9, 5), output="centre8", dt=0.02, steps=60, m=30, precision=precision)
+    rows = []
+    for _ in range(40):
+        cells = rng.choice(int(np.prod(dims)), size=5, replace=False)
+        rows.append((np.sort(cells), rng.standard_normal(5)))
+    p.C_row_ptr, p.C_col, p.C_val = W._c_rows(rows)
+    p.theta = np.full(40, math.inf)
+    got = run_gpu(ctx, p, flags=flags)
+    p64 = W.heat(dims, block=(10, 9, 5), output="centre8", dt=0.02, steps=60, m=30)
+    p64.C_row_ptr, p64.C_col, p64.C_val, p64.theta = p.C_row_ptr, p.C_col, p.C_val, p.theta
+    ref = oracle.run(p64)
+    tol = 1e-9 if precision == "fp64" else 1e-6
+    assert bound_error(got, ref) <= tol
+    if precision == "fp64":
+        eh, ep = krylov_error(got, ref, 0)
+        assert eh <= 1e-9 and ep <= 1e-9
