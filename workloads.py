@@ -417,14 +417,15 @@ def column_dense(col: Column, n: int, dims: Optional[Sequence[int]] = None) -> n
 # --------------------------------------------------------------------------
 def serving_mix(n_queries: int = 512, seed: int = 0, *, side2d=(100, 2000), side3d=(100, 400),
                 csr_n=(100_000, 2_000_000), csr_sizes: int = 5, gens=(1, 32), steps=(100, 2000), m=(20, 60),
-                precision: str = "fp32") -> List[Problem]:
+                precision: str = "fp32", simulate: str = "auto") -> List[Problem]:
     """A seeded mix of verification queries, one third each:
       * 2D heat, side log-uniform in side2d (n = side^2), block side/4, centre output, dt 0.1;
       * 3D heat, side log-uniform in side3d, block side/10, centre output, dt 0.02;
       * random CSR systems of random_csr (sizes log-spaced in csr_n, `csr_sizes`
         distinct systems shared by the queries), `gens` unit generators plus the
         fixed column, two +-1 output rows, dt 0.01;
-    horizons uniform in `steps`, Krylov dimension uniform in `m`, thresholds +inf.
+    horizons uniform in `steps`, Krylov dimension uniform in `m`, thresholds +inf;
+    `simulate` for every query ("auto": the transpose dynamics where o < i).
     """
     rng = np.random.default_rng(seed + 4242)
     sizes = sorted(set(int(round(x)) for x in np.geomspace(csr_n[0], csr_n[1], csr_sizes)))
@@ -451,4 +452,5 @@ def serving_mix(n_queries: int = 512, seed: int = 0, *, side2d=(100, 2000), side
             g = int(rng.integers(gens[0], gens[1] + 1))
             out.append(csr_problem_on(cache[n], seed=q, n_gen=g, o=2, c_width=min(1000, n // 4), dt=0.01,
                                       steps=st, m=mm, precision=precision, name=f"q{q}-csr-{n}-g{g}"))
+        out[-1].simulate = simulate
     return out
