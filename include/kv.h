@@ -157,7 +157,7 @@ typedef struct {
 #define KV_FLAG_NO_AUTOTUNE 4   /* CSR Arnoldi: fixed SpMM shape instead of timing the
                                    candidates at kv_problem (and the on-disk cache) */
 
-#define KV_MAX_M 64            /* largest krylov_m when any column runs Arnoldi */
+#define KV_MAX_M 256           /* largest krylov_m when any column runs Arnoldi */
 #define KV_MAX_M_LANCZOS 4096  /* largest krylov_m when every column runs Lanczos
                                   (above 64 the exponential runs in global memory) */
 

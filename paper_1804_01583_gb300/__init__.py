@@ -24,7 +24,7 @@ KV_FP64, KV_FP32 = 0, 1
 KV_AUTO, KV_LANCZOS, KV_ARNOLDI = 0, 1, 2
 KV_COL_BOX, KV_COL_SPARSE, KV_COL_DENSE = 0, 1, 2
 KV_EXPM_PER_STEP, KV_EXPM_PROPAGATE = 0, 1
-KV_MAX_M = 64
+KV_MAX_M = 256
 KV_MAX_M_LANCZOS = 4096
 KV_FLAG_TWO_PASS = 1
 

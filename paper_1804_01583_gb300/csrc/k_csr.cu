@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
     }
     __syncthreads();
     const int K = j + 1;
-    double* part = partials + (int64_t)cidx * nbx * 2 * (KV_MAX_M + 1);
+    double* part = partials + (int64_t)cidx * nbx * 2 * (m + 1);
     for (int q = threadIdx.x; q < 2 * K; q += CNT) {
         const int row = q < K ? q : (KV_MAX_M + 1 + q - K);
         double v = 0.0;
@@ -497,9 +497,9 @@ static int64_t spmv_blocks(int64_t N) {
     return b > 152 * 16 ? 152 * 16 : b;
 }
 
-int64_t csr_scratch_slots(int64_t N) {  // reduction partials per column
+int64_t csr_scratch_slots(int64_t N, int m) {  // reduction partials per column
     const int64_t nb = row_blocks(N) > spmv_blocks(N) ? row_blocks(N) : spmv_blocks(N);
-    return nb * 2 * (KV_MAX_M + 1);
+    return nb * 2 * (m + 1);
 }
 
 size_t csr_arnoldi_dev_bytes() { return sizeof(ArnoldiDev); }

@@ -209,7 +209,7 @@ __device__ void project_rows(const ExpmArgs& a, int j, int mu, const double* u, 
 
 __global__ void __launch_bounds__(ENT) k_expm_per_step(ExpmArgs a) {
     extern __shared__ double smem[];
-    __shared__ double fac[KV_MAX_M];
+    __shared__ double fac[EXPM_SMEM_M];
     __shared__ int piv;
     __shared__ double red[ENT / 32];
     const int j = a.j0 + blockIdx.y;
@@ -304,7 +304,7 @@ int expm_prepare(int device) {
     if (rc != KV_OK) return rc;
     static bool attr_set = false;
     if (!attr_set) {
-        const int smax = 6 * KV_MAX_M * KV_MAX_M * (int)sizeof(double);
+        const int smax = 6 * EXPM_SMEM_M * EXPM_SMEM_M * (int)sizeof(double);
         KV_CHECK_CUDA(cudaFuncSetAttribute(k_expm_per_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
         attr_set = true;
     }
@@ -315,7 +315,7 @@ int expm_prepare(int device) {
 // column's m_used, with the basis rows).
 static int launch_expm(Prob* p, int j0, int ncols, int dim) {
     const int mm = dim > 0 ? dim : p->m;
-    if (p->expm_mode == KV_EXPM_PROPAGATE || mm > KV_MAX_M) return launch_expm_large(p, j0, ncols, dim, dim == 0);
+    if (p->expm_mode == KV_EXPM_PROPAGATE || mm > EXPM_SMEM_M) return launch_expm_large(p, j0, ncols, dim, dim == 0);
     int rc = expm_prepare(p->ctx->device);
     if (rc != KV_OK) return rc;
     ExpmArgs a{p->d_H, p->d_P, p->d_state, p->d_basis, p->m, p->o, p->steps, p->dt, p->d_hlast, dim, j0};

@@ -165,7 +165,7 @@ int64_t reduce_slots_needed(const Prob* p) {
         return nb * (int64_t)(p->m + 2);
     }
     // CSR: one region of partials per column (all columns run together)
-    return std::max<int64_t>(nb, (int64_t)p->i * csr_scratch_slots(p->N));
+    return std::max<int64_t>(nb, (int64_t)p->i * csr_scratch_slots(p->N, p->m));
 }
 
 // Vector sets: grid problems run their columns one after another on one set;

@@ -241,18 +241,21 @@ int launch_dense_to(Prob* p, int j, void* B);
 // CSR (k_csr.cu): Krylov iterations of columns j0 .. j0+ncols-1 (same method),
 // whose vector sets start at V (stride nvec * N elements per column)
 int launch_csr_columns(Prob* p, int j0, int ncols, void* V, bool lanczos);
-int64_t csr_scratch_slots(int64_t N);
+int64_t csr_scratch_slots(int64_t N, int m);
 int csr_autotune(Prob* p);
 size_t csr_arnoldi_dev_bytes();
 
 // exponential + basis (k_expm.cu)
 int launch_expm_basis(Prob* p);
-// global-memory exponential (k_expm_large.cu): dimensions above KV_MAX_M and
-// the PROPAGATE schedule; runs in batches of large_expm_batch
+// Largest dimension of the shared-memory exponential (k_expm.cu: six m x m
+// double matrices per block); above it, and for the PROPAGATE schedule, the
+// global-memory exponential (k_expm_large.cu) runs, in batches of
+// large_expm_batch runs
+constexpr int EXPM_SMEM_M = 64;
 size_t large_expm_scratch_doubles(int m, int steps);
 int large_expm_batch(int m, int steps, int runs);
 int launch_expm_large(Prob* p, int j0, int ncols, int dim, bool write_basis);
-inline bool needs_large_expm(int m, int expm_mode) { return m > KV_MAX_M || expm_mode == KV_EXPM_PROPAGATE; }
+inline bool needs_large_expm(int m, int expm_mode) { return m > EXPM_SMEM_M || expm_mode == KV_EXPM_PROPAGATE; }
 int expm_prepare(int device);
 int fused_prepare();
 // one-time set-up that stream capture cannot contain (kv_graph.cu)
