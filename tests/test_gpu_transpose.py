@@ -158,3 +158,22 @@ def test_transposed_through_the_server(ctx):
         srv.close()
     assert out["m_used"].shape == (2,) and np.array_equal(out["m_used"], solo["m_used"])
     assert np.array_equal(out["hi"], solo["hi"]) and np.array_equal(out["lo"], solo["lo"])
+
+
+_FULL_REF = {}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_random_csr_full_size_transposed(ctx, precision):
+    """The benchmark's random-CSR query at full size (n = 2e6, i = 17 with the
+    fixed column, o = 2, m = 60, 2000 steps, PROPAGATE as the benchmark runs
+    it) by the transpose dynamics: both runs against the oracle's."""
+    p64 = W.random_csr_problem(2_000_000, seed=0)
+    p64.simulate = "transpose"
+    if "ref" not in _FULL_REF:
+        _FULL_REF["ref"] = oracle.run(p64)
+    ref = _FULL_REF["ref"]
+    p = W.random_csr_problem(2_000_000, seed=0, precision=precision)
+    p.simulate = "transpose"
+    got = run_gpu(ctx, p, expm_mode="propagate")
+    check(got, ref, p64, 1e-9 if precision == "fp64" else 1e-6, False)
