@@ -179,9 +179,24 @@ def cpu_baseline(p, iters: int = 4):
     t = time.perf_counter() - t0
     del e
     gbs = iters * 3.0 * 8 * n / t / 1e9
-    return {"value": gbs, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same on one thread, a shorter sample
+    one = max(1, iters // 12)
+    oracle.set_threads(1)
+    try:
+        e = W.column_dense(p.columns[0], n, p.system.dims)
+        e /= b0
+        t0 = time.perf_counter()
+        oracle.krylov(p.system, e, one, p.C_row_ptr, p.C_col, p.C_val, method="lanczos")
+        t1 = time.perf_counter() - t0
+        del e
+    finally:
+        oracle.set_threads(cores)
+    return {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": f"{iters} Lanczos iterations of the FP64 oracle on the full {p.name} grid "
-                      f"(n={n}), {t:.1f} s"}
+                      f"(n={n}), {t:.1f} s",
+            "single_thread": {"value": one * 3.0 * 8 * n / t1 / 1e9, "unit": "GB/s", "cores": 1,
+                              "sample": f"{one} iterations, {t1:.1f} s"}}
 
 
 # ------------------------------------------------------------------ GPU arm

@@ -75,6 +75,7 @@ def _load():
             lib.ora_expm.argtypes = [C.c_int, P, P]
             lib.ora_basis.argtypes = [C.c_int, C.c_int, P, C.c_int, P, C.c_double, C.c_double,
                                       C.c_int, P]
+            lib.ora_set_threads.argtypes = [C.c_int]
             lib.ora_lemma1.restype = C.c_double
             lib.ora_lemma1.argtypes = [C.c_int, C.c_int, P, C.c_double, C.c_double, C.c_double, C.c_int]
             lib.ora_bounds.restype = C.c_int
@@ -87,6 +88,11 @@ def _load():
 
 def _p(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's loops from now on."""
+    _load().ora_set_threads(int(n))
 
 
 def num_threads() -> int:

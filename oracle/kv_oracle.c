@@ -70,6 +70,16 @@ int ora_num_threads(void) {
 #endif
 }
 
+/* Threads of the OpenMP loops from now on (the benchmark's single-thread
+ * figure); 0 or less leaves the count unchanged. */
+void ora_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int64_t ora_dim(const ora_op *op) { return op->n + (op->aug ? 1 : 0); }
 
 /* ---------------------------------------------------------------- A x ---- */
