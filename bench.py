@@ -580,7 +580,7 @@ def arnoldi_bytes(p) -> float:
     return tot
 
 
-def csr_bench(args, dev: int):
+def csr_bench(args, dev: int, n: int = 2_000_000, legs=None):
     """The random-CSR workload (n = 2e6, 16 generators + the fixed column,
     m = 60, 2000 steps) in FP64 and FP32: time per query, Arnoldi GB/s; and
     the same query by the transpose dynamics (Sec. 4.1: 2 runs on A'^T from
@@ -588,8 +588,8 @@ def csr_bench(args, dev: int):
     import torch
     import paper_1804_01583_gb300 as kv
     out = {}
-    for prec, sim in (("fp64", "forward"), ("fp32", "forward"), ("fp64", "transpose"), ("fp32", "transpose")):
-        p = W.random_csr_problem(2_000_000, seed=0, precision=prec)
+    for prec, sim in legs or (("fp64", "forward"), ("fp32", "forward"), ("fp64", "transpose"), ("fp32", "transpose")):
+        p = W.random_csr_problem(n, seed=0, precision=prec)
         p.simulate = sim
         ctx = kv.Context(40 << 30, device=dev)
         sysh = kv.System(ctx, p.system, p.precision)
@@ -619,9 +619,12 @@ def csr_bench(args, dev: int):
                     "kernels": kern}
         if sim == "forward":
             out[key]["arnoldi_GBps"] = arnoldi_bytes(p) / (ms * 1e-3) / 1e9
-    out["speedup_fp32_over_fp64"] = out["fp64"]["ms_per_query"] / out["fp32"]["ms_per_query"]
-    out["speedup_transposed_fp32"] = out["fp32"]["ms_per_query"] / out["fp32_transposed"]["ms_per_query"]
-    out["workload"] = "random CSR n=2e6, 10 off-diagonal nnz/row, i=17 (16 generators + fixed), o=2, m=60, 2000 steps"
+    if "fp64" in out and "fp32" in out:
+        out["speedup_fp32_over_fp64"] = out["fp64"]["ms_per_query"] / out["fp32"]["ms_per_query"]
+    if "fp32" in out and "fp32_transposed" in out:
+        out["speedup_transposed_fp32"] = out["fp32"]["ms_per_query"] / out["fp32_transposed"]["ms_per_query"]
+    out["workload"] = (f"random CSR n={n}, 10 off-diagonal nnz/row, i=17 (16 generators + fixed), o=2, m=60, "
+                       f"2000 steps")
     return out
 
 
@@ -647,6 +650,8 @@ def main():
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-csr", dest="csr", action="store_false")
     ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--csr-only", type=int, default=0, metavar="N",
+                    help="only the random-CSR query (FP32, forward) at n = N (profiling case)")
     ap.add_argument("--serve-queries", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-pool-gb", type=int, default=160)
@@ -680,6 +685,15 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.csr_only:
+        import torch
+        from paper_1804_01583_gb300 import build as kvbuild
+        kvbuild.build()
+        dev = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(dev)
+        print(json.dumps({"metric": "random-CSR query ms", "csr_workload":
+                          csr_bench(args, dev, n=args.csr_only, legs=(("fp32", "forward"),))}))
+        return
     if args.serve_only:
         import torch
         from paper_1804_01583_gb300 import build as kvbuild
