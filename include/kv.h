@@ -156,6 +156,19 @@ typedef struct {
                                    grouped SpMM (matrix read once per group) */
 #define KV_FLAG_NO_AUTOTUNE 4   /* CSR Arnoldi: fixed SpMM shape instead of timing the
                                    candidates at kv_problem (and the on-disk cache) */
+/* CSR Arnoldi SpMM shapes.  Column-major: G in {1, 2, 4, 8} columns share one
+   read of the matrix and gather x_k[col] from each column's own vector.
+   Interleaved: before each SpMM the group's current vectors are copied
+   row-interleaved (row r holds x_0[r] .. x_{G-1}[r]), so one gather serves the
+   G columns; G * element size in {16, 32, 64} bytes.  The autotuner times both
+   forms (problems from 65536 rows) and keeps the fastest.  LPR lanes share a
+   row: 1, 2 or 4 (column-major form), 0 (one lane per row, the warp's entries
+   staged in shared memory by coalesced loads), 1 or 2 (interleaved form).
+   The environment variable KV_SPMM_SHAPE="G,LPR" (G < 0 for the interleaved
+   form of -G columns) fixes the shape of problems created while it is set;
+   an unknown shape is ignored.  The interleaved form adds
+   ceil(run / G) * G * N * element size bytes to kv_problem_bytes (run = the
+   longest run of Arnoldi columns). */
 
 #define KV_MAX_M 256           /* largest krylov_m when any column runs Arnoldi */
 #define KV_MAX_M_LANCZOS 4096  /* largest krylov_m when every column runs Lanczos

@@ -130,94 +130,176 @@ __global__ void __launch_bounds__(CNT) k_spmv(const int64_t* __restrict__ rp, co
 // each row's values and column indices are read once for the G columns, and
 // LPR lanes share a row (consecutive entries, combined by shuffles).  The
 // group size and lanes per row are chosen per system by the autotuner.
-template <typename T, int G, int LPR>
+//
+// IL (interleaved input): the group's inputs come from xi, which holds row r
+// of the group's G vectors side by side (xi[r * G + k] = X_k[r], G * size
+// of T a multiple of 16 bytes), so the gather of row c for all G columns is
+// one contiguous G-wide load (one 32-byte sector for 32 bytes) instead of G
+// scattered ones.  k_interleave builds xi for every group from the
+// column-major vectors just before the SpMM.
+template <typename T, int G>
+__device__ __forceinline__ void load_row(const T* __restrict__ src, T (&x)[G]) {
+    static_assert((G * sizeof(T)) % 16 == 0, "interleaved rows are whole 16-byte words");
+    constexpr int W = (int)(G * sizeof(T) / 16);
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4 w[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) w[q] = __ldg(s4 + q);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        T t[16 / sizeof(T)];
+        memcpy(t, &w[q], 16);
+#pragma unroll
+        for (int u = 0; u < (int)(16 / sizeof(T)); ++u) x[q * (16 / sizeof(T)) + u] = t[u];
+    }
+}
+
+// error-free (float pairs) or plain (double) sum of the partial dot products
+// of the LPR lanes that share a row, into the first of them
+template <int LPR>
+__device__ __forceinline__ void combine_lanes(Dot2f& d) {
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, d.s, o, LPR);
+        const float c2 = __shfl_down_sync(0xffffffffu, d.c, o, LPR);
+        float t, err;
+        two_sum_f(d.s, s2, t, err);
+        d.s = t;
+        d.c = __fadd_rn(__fadd_rn(d.c, c2), err);
+    }
+}
+template <int LPR>
+__device__ __forceinline__ void combine_lanes(Dot2d& d) {
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) d.s += __shfl_down_sync(0xffffffffu, d.s, o, LPR);
+}
+
+constexpr int STAGE = 384;  // matrix entries per warp staged in shared memory (LPR = 0)
+
+// LPR = 0 (staged): one lane per row; the warp's 32 rows have their entries
+// contiguous in the CSR arrays, so the warp copies them to shared memory with
+// coalesced loads (STAGE at a time) and each lane walks its own row there.
+// With LPR >= 1 the lanes read their rows' entries directly.
+template <typename T, int G, int LPR, bool IL>
 __global__ void __launch_bounds__(CNT) k_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                               const T* __restrict__ val, const double* __restrict__ b, VecArgs<T> V,
-                                              int xslot, int wslot, int64_t n, int64_t N, const int* aug,
-                                              const ColState* st, int j, int ncols) {
+                                              const T* __restrict__ xi, int xslot, int wslot, int64_t n, int64_t N,
+                                              const int* aug, const ColState* st, int j, int ncols) {
+    static_assert(G <= 32, "column flags are bit masks");
+    using Acc = typename std::conditional<std::is_same<T, float>::value, Dot2f, Dot2d>::type;
+    constexpr bool STAGED = LPR == 0;
+    constexpr int LP = STAGED ? 1 : LPR;  // lanes per row
     const int cg0 = blockIdx.y * G;
-    // the group's columns: X_k = xbase + k * cstride, W_k likewise
+    // the group's columns: X_k = xbase + k * cstride (or xg[. * G + k]), W_k = wbase + k * cstride
     const T* xbase = V.base + (int64_t)cg0 * V.cstride + (int64_t)xslot * N;
+    const T* xg = IL ? xi + (int64_t)blockIdx.y * N * G : nullptr;
     T* wbase = V.base + (int64_t)cg0 * V.cstride + (int64_t)wslot * N;
-    double sc[G];
-    bool act[G], ag[G];
-    int64_t off[G];  // inactive slots (past the run, or broken down) read the group's first column
+    // live columns (inside the run, not broken down) and those that carry the
+    // constant; the scales s_j and x[n] are read again in the epilogue, so the
+    // loop keeps only accumulators and gathered values in registers
+    unsigned act = 0, ag = 0;
 #pragma unroll
     for (int k = 0; k < G; ++k) {
         const int c = cg0 + k;
-        act[k] = c < ncols && !st[c].done;
-        sc[k] = act[k] ? st[c].s[j] : 0.0;
-        ag[k] = act[k] && aug[c] != 0;
-        off[k] = act[k] ? (int64_t)k * V.cstride : 0;
+        if (c < ncols && !st[c].done) {
+            act |= 1u << k;
+            if (aug[c] != 0 && b) ag |= 1u << k;
+        }
     }
-    const int lane = threadIdx.x & 31, sub = lane % LPR;
-    constexpr int WR = 32 / LPR;  // rows per warp per step
+    // x_k[c] for the G columns: one G-wide load (interleaved) or G loads
+    // (column-major; dead slots read the group's first column)
+    auto gather = [&](int c, T(&x)[G]) {
+        if constexpr (IL) {
+            load_row<T, G>(xg + (int64_t)c * G, x);
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k) x[k] = xbase[(((act >> k) & 1u) ? (int64_t)k * V.cstride : 0) + c];
+        }
+    };
+    auto epilogue = [&](int k, int64_t r, bool inrow, double dot) {
+        double y = 0.0;  // row n of A' (constant variable) is zero
+        if (inrow) {
+            y = dot;
+            if ((ag >> k) & 1u) y = fma(b[r], (double)(IL ? xg[n * G + k] : xbase[(int64_t)k * V.cstride + n]), y);
+        }
+        wbase[k * V.cstride + r] = (T)(st[cg0 + k].s[j] * y);
+    };
+    const int lane = threadIdx.x & 31, sub = lane % LP;
+    constexpr int WR = 32 / LP;  // rows per warp per step
     const int64_t gw = ((int64_t)blockIdx.x * CNT + threadIdx.x) >> 5;
     const int64_t nw = (int64_t)gridDim.x * (CNT / 32);
-    // warp-uniform loop: every lane reaches every shuffle
+    // warp-uniform loop: every lane reaches every shuffle and warp barrier
     for (int64_t rb = gw * WR; rb < N; rb += nw * WR) {
-        const int64_t r = rb + lane / LPR;
+        const int64_t r = rb + lane / LP;
         const bool inrow = r < n;
-        const int64_t e0 = inrow ? rp[r] : 0, e1 = inrow ? rp[r + 1] : 0;
-        if constexpr (std::is_same<T, float>::value) {
-            Dot2f d[G];
-            for (int64_t e = e0 + sub; e < e1; e += LPR) {
-                const float v = val[e];
-                const int c = col[e];
-#pragma unroll
-                for (int k = 0; k < G; ++k) d[k].add_prod(v, xbase[off[k] + c]);
-            }
-#pragma unroll
-            for (int k = 0; k < G; ++k) {
-#pragma unroll
-                for (int o = LPR / 2; o > 0; o >>= 1) {  // error-free combination of lane pairs
-                    const float s2 = __shfl_down_sync(0xffffffffu, d[k].s, o, LPR);
-                    const float c2 = __shfl_down_sync(0xffffffffu, d[k].c, o, LPR);
-                    const float t = __fadd_rn(d[k].s, s2);
-                    const float z = __fadd_rn(t, -d[k].s);
-                    const float err = __fadd_rn(__fadd_rn(d[k].s, -__fadd_rn(t, -z)), __fadd_rn(s2, -z));
-                    d[k].s = t;
-                    d[k].c = __fadd_rn(__fadd_rn(d[k].c, c2), err);
+        Acc d[G];
+        if constexpr (STAGED) {
+            __shared__ T sv[CNT / 32][STAGE];
+            __shared__ int32_t scol[CNT / 32][STAGE];
+            const int w = threadIdx.x >> 5;
+            // rows past n have the empty range at rp[n]
+            const int64_t e0 = rp[inrow ? r : n], e1 = inrow ? rp[r + 1] : e0;
+            const int64_t E0 = __shfl_sync(0xffffffffu, e0, 0), E1 = __shfl_sync(0xffffffffu, e1, 31);
+            for (int64_t base = E0; base < E1; base += STAGE) {
+                const int cnt = (int)(E1 - base < STAGE ? E1 - base : STAGE);
+                for (int q = lane; q < cnt; q += 32) {
+                    sv[w][q] = val[base + q];
+                    scol[w][q] = col[base + q];
                 }
-            }
-            if (sub == 0 && r < N) {
+                __syncwarp();
+                const int lo = (int)((e0 > base ? e0 : base) - base);
+                const int hi = (int)((e1 < base + cnt ? e1 : base + cnt) - base);
+#pragma unroll 4
+                for (int q = lo; q < hi; ++q) {
+                    T x[G];
+                    gather(scol[w][q], x);
+                    const T v = sv[w][q];
 #pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    if (!act[k]) continue;
-                    double y = 0.0;  // row n of A' (constant variable) is zero
-                    if (inrow) {
-                        y = d[k].value();
-                        if (ag[k] && b) y = fma(b[r], (double)xbase[off[k] + n], y);
-                    }
-                    wbase[k * V.cstride + r] = (T)(sc[k] * y);
+                    for (int k = 0; k < G; ++k) d[k].add_prod(v, x[k]);
                 }
+                __syncwarp();
             }
         } else {
-            double d[G];
+            const int64_t e0 = inrow ? rp[r] : 0, e1 = inrow ? rp[r + 1] : 0;
+#pragma unroll 4
+            for (int64_t e = e0 + sub; e < e1; e += LP) {
+                T x[G];
+                gather(col[e], x);
+                const T v = val[e];
 #pragma unroll
-            for (int k = 0; k < G; ++k) d[k] = 0.0;
-            for (int64_t e = e0 + sub; e < e1; e += LPR) {
-                const double v = val[e];
-                const int c = col[e];
-#pragma unroll
-                for (int k = 0; k < G; ++k) d[k] = fma(v, xbase[off[k] + c], d[k]);
+                for (int k = 0; k < G; ++k) d[k].add_prod(v, x[k]);
             }
+#pragma unroll
+            for (int k = 0; k < G; ++k) combine_lanes<LP>(d[k]);
+        }
+        if (sub == 0 && r < N) {
 #pragma unroll
             for (int k = 0; k < G; ++k)
+                if ((act >> k) & 1u) epilogue(k, r, inrow, d[k].value());
+        }
+    }
+}
+
+// xi[g][r][k] = X_{g G + k}[r] (slot xslot of column g G + k; zero past the
+// run): one thread per row, G column reads coalesced across the warp, one
+// contiguous G-wide store.  blockIdx.y = group.
+template <typename T, int G>
+__global__ void __launch_bounds__(CNT) k_interleave(VecArgs<T> V, int xslot, int64_t N, int ncols, T* __restrict__ xi) {
+    static_assert((G * sizeof(T)) % 16 == 0, "interleaved rows are whole 16-byte words");
+    const int cg0 = blockIdx.y * G;
+    const T* x0 = V.base + (int64_t)cg0 * V.cstride + (int64_t)xslot * N;
+    T* out = xi + (int64_t)blockIdx.y * N * G;
+    const int nk = ncols - cg0 < G ? ncols - cg0 : G;
+    for (int64_t r = (int64_t)blockIdx.x * CNT + threadIdx.x; r < N; r += (int64_t)gridDim.x * CNT) {
+        T v[G];
 #pragma unroll
-                for (int o = LPR / 2; o > 0; o >>= 1) d[k] += __shfl_down_sync(0xffffffffu, d[k], o, LPR);
-            if (sub == 0 && r < N) {
+        for (int k = 0; k < G; ++k) v[k] = k < nk ? x0[k * V.cstride + r] : T(0);
+        uint4* o4 = reinterpret_cast<uint4*>(out + r * G);
 #pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    if (!act[k]) continue;
-                    double y = 0.0;
-                    if (inrow) {
-                        y = d[k];
-                        if (ag[k] && b) y = fma(b[r], (double)xbase[off[k] + n], y);
-                    }
-                    wbase[k * V.cstride + r] = (T)(sc[k] * y);
-                }
-            }
+        for (int q = 0; q < (int)(G * sizeof(T) / 16); ++q) {
+            uint4 w;
+            memcpy(&w, v + q * (16 / sizeof(T)), 16);
+            o4[q] = w;
         }
     }
 }
@@ -505,42 +587,79 @@ int64_t csr_scratch_slots(int64_t N, int m) {  // reduction partials per column
 size_t csr_arnoldi_dev_bytes() { return sizeof(ArnoldiDev); }
 
 // ------------------------------------------------------- SpMM dispatch --
-template <typename T, int G, int LPR>
-static void spmm_launch(const Prob* p, VecArgs<T> va, int xslot, int wslot, const int* aug, const ColState* st,
-                        int j, int ncols, cudaStream_t s) {
-    const Sys* sy = p->sys;
-    const int64_t rows_per_block = CNT / LPR;
-    int64_t gx = (p->N + rows_per_block - 1) / rows_per_block;
-    if (gx > 152 * 16) gx = 152 * 16;
-    dim3 grd((unsigned)gx, (unsigned)((ncols + G - 1) / G));
-    k_spmm<T, G, LPR><<<grd, CNT, 0, s>>>(sy->d_rp, sy->d_col, (const T*)sy->d_val, sy->d_b, va, xslot, wslot,
-                                          sy->n, p->N, aug, st, j, ncols);
+// Grid-stride kernels get one full wave: the SMs times the blocks of CNT
+// threads that fit on one SM at the kernel's register count.
+template <typename K>
+static int64_t one_wave(K kernel, int device) {
+    int nb = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, CNT, 0) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || nsm < 1) nsm = 152;
+    return (int64_t)nb * nsm;
 }
 
+// warm_only: size the grids (occupancy queries, once per kernel) and launch
+// nothing; done when the problem is created, so that no query runs inside a
+// stream capture.
+template <typename T, int G, int LPR, bool IL>
+static void spmm_launch(const Prob* p, VecArgs<T> va, int xslot, int wslot, const int* aug, const ColState* st,
+                        int j, int ncols, cudaStream_t s, bool warm_only) {
+    static const int64_t wave = one_wave(k_spmm<T, G, LPR, IL>, p->ctx->device);
+    static const int64_t iwave = IL ? one_wave(k_interleave<T, IL ? G : 16 / sizeof(T)>, p->ctx->device) : 0;
+    if (warm_only) return;
+    const Sys* sy = p->sys;
+    const int64_t rows_per_block = CNT / (LPR > 0 ? LPR : 1);
+    int64_t gx = (p->N + rows_per_block - 1) / rows_per_block;
+    if (gx > wave) gx = wave;
+    const unsigned ng = (unsigned)((ncols + G - 1) / G);
+    if constexpr (IL) {  // the groups' inputs, row-interleaved, first
+        int64_t gi = (p->N + CNT - 1) / CNT;
+        if (gi > iwave) gi = iwave;
+        k_interleave<T, G><<<dim3((unsigned)gi, ng), CNT, 0, s>>>(va, xslot, p->N, ncols, (T*)p->d_xi);
+    }
+    k_spmm<T, G, LPR, IL><<<dim3((unsigned)gx, ng), CNT, 0, s>>>(sy->d_rp, sy->d_col, (const T*)sy->d_val, sy->d_b,
+                                                                  va, (const T*)p->d_xi, xslot, wslot, sy->n, p->N,
+                                                                  aug, st, j, ncols);
+}
+
+// Interleaved group widths: 16, 32 and 64 bytes per row.
+template <typename T>
+struct IlWidths {
+    static constexpr int g[3] = {16 / (int)sizeof(T), 32 / (int)sizeof(T), 64 / (int)sizeof(T)};
+};
+
+// G > 0: column-major gathers; G < 0: groups of -G columns from the
+// interleaved copy (built in the same call)
 template <typename T>
 static bool spmm_dispatch(const Prob* p, int G, int LPR, VecArgs<T> va, int xslot, int wslot, const int* aug,
-                          const ColState* st, int j, int ncols, cudaStream_t s) {
-#define KV_SPMM_CASE(g, l)                                                  \
-    if (G == g && LPR == l) {                                               \
-        spmm_launch<T, g, l>(p, va, xslot, wslot, aug, st, j, ncols, s);    \
-        return true;                                                        \
+                          const ColState* st, int j, int ncols, cudaStream_t s, bool warm_only = false) {
+#define KV_SPMM_CASE(g, l, il)                                                          \
+    if (G == (il ? -(g) : (g)) && LPR == l) {                                           \
+        spmm_launch<T, g, l, il>(p, va, xslot, wslot, aug, st, j, ncols, s, warm_only); \
+        return true;                                                                    \
     }
-    KV_SPMM_CASE(1, 1) KV_SPMM_CASE(1, 2) KV_SPMM_CASE(1, 4)
-    KV_SPMM_CASE(2, 1) KV_SPMM_CASE(2, 2) KV_SPMM_CASE(2, 4)
-    KV_SPMM_CASE(4, 1) KV_SPMM_CASE(4, 2) KV_SPMM_CASE(4, 4)
-    KV_SPMM_CASE(8, 1) KV_SPMM_CASE(8, 2) KV_SPMM_CASE(8, 4)
+    KV_SPMM_CASE(1, 1, false) KV_SPMM_CASE(1, 2, false) KV_SPMM_CASE(1, 4, false)
+    KV_SPMM_CASE(2, 1, false) KV_SPMM_CASE(2, 2, false) KV_SPMM_CASE(2, 4, false)
+    KV_SPMM_CASE(4, 1, false) KV_SPMM_CASE(4, 2, false) KV_SPMM_CASE(4, 4, false)
+    KV_SPMM_CASE(8, 1, false) KV_SPMM_CASE(8, 2, false) KV_SPMM_CASE(8, 4, false)
+    constexpr int g0 = IlWidths<T>::g[0], g1 = IlWidths<T>::g[1], g2 = IlWidths<T>::g[2];
+    if (p->d_xi) {
+        KV_SPMM_CASE(g0, 0, true) KV_SPMM_CASE(g0, 1, true) KV_SPMM_CASE(g0, 2, true)
+        KV_SPMM_CASE(g1, 0, true) KV_SPMM_CASE(g1, 1, true) KV_SPMM_CASE(g1, 2, true)
+        KV_SPMM_CASE(g2, 0, true) KV_SPMM_CASE(g2, 1, true) KV_SPMM_CASE(g2, 2, true)
+    }
 #undef KV_SPMM_CASE
     return false;
 }
 
 // ----------------------------------------------------------- autotuner --
-// Picks the SpMM group size G (columns per matrix read) and lanes per row
-// for a CSR problem by timing every candidate on the problem's own buffers
-// (CUDA events on the context stream) at problem creation.  Candidates keep
-// the G input vectors of a group within about 96 MB so the column gathers
-// stay in L2.  Results are cached in a text file (KV_AUTOTUNE_CACHE, default
-// $HOME/.cache/kv_autotune.txt) keyed by device, rows, nonzeros, element size
-// and column count.
+// Picks the SpMM form (column-major gathers, or gathers from the interleaved
+// copy with the interleave pass counted), the group size G (columns per
+// matrix read) and lanes per row for a CSR problem by timing every candidate
+// on the problem's own buffers (CUDA events on the context stream) at problem
+// creation.  Results are cached in a text file (KV_AUTOTUNE_CACHE, default
+// $HOME/.cache/kv_autotune.txt; one line "key G LPR microseconds", G < 0 for
+// the interleaved form) keyed by device, rows, nonzeros, element size and
+// column count.
 static std::string tune_cache_path() {
     const char* e = getenv("KV_AUTOTUNE_CACHE");
     if (e && *e) return e;
@@ -552,11 +671,67 @@ static std::string tune_key(const Prob* p, int ncols) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, p->ctx->device);
     char buf[512];
-    snprintf(buf, sizeof(buf), "%s|%d.%d|n=%lld|N=%lld|nnz=%lld|es=%zu|cols=%d", prop.name, prop.major, prop.minor,
+    snprintf(buf, sizeof(buf), "%s|%d.%d|n=%lld|N=%lld|nnz=%lld|es=%zu|cols=%d|il", prop.name, prop.major, prop.minor,
              (long long)p->sys->n, (long long)p->N, (long long)p->sys->nnz, elem_size(p->prec), ncols);
     for (char* c = buf; *c; ++c)
         if (*c == ' ') *c = '_';
     return buf;
+}
+
+// The autotuner's candidates keep a group's inputs within about 96 MB so its
+// gathers stay in L2.  Interleaved widths larger than the smallest one are
+// tried only when the smallest would need more than one group.
+constexpr double L2_BUDGET = 96.0 * 1024 * 1024;
+static bool plain_candidate(int G, int64_t N, size_t es, int ncols) {
+    return G == 1 || (G <= ncols && (double)G * N * es <= L2_BUDGET);
+}
+static bool il_candidate(int G, int g0, int64_t N, size_t es, int ncols) {
+    return (double)G * N * es <= L2_BUDGET && (G == g0 || G / 2 < ncols);
+}
+static int il_width(size_t es, int q) { return (16 << q) / (int)es; }  // q = 0, 1, 2
+
+static bool autotuned(const Prob* p) {
+    return !(p->flags & (KV_FLAG_NO_AUTOTUNE | KV_FLAG_NO_SPMM)) && p->N >= 65536;
+}
+
+// KV_SPMM_SHAPE="G,LPR" fixes the SpMM shape of every CSR Arnoldi problem
+// created afterwards (G < 0: interleaved groups of -G columns); for tests and
+// measurements.  Returns false when unset or not a shape that exists.
+static bool forced_shape(size_t es, int* G, int* L) {
+    const char* e = getenv("KV_SPMM_SHAPE");
+    if (!e || sscanf(e, "%d,%d", G, L) != 2) return false;
+    if (*G > 0) return (*G == 1 || *G == 2 || *G == 4 || *G == 8) && (*L == 1 || *L == 2 || *L == 4);
+    if (*L != 0 && *L != 1 && *L != 2) return false;
+    for (int q = 0; q < 3; ++q)
+        if (-*G == il_width(es, q)) return true;
+    return false;
+}
+
+static int longest_arnoldi_run(const Prob* p) {  // one SpMM group set per run
+    int run = 0;
+    for (int j = 0, r = 0; j < p->i; ++j) {
+        r = p->method[j] == KV_ARNOLDI ? r + 1 : 0;
+        run = r > run ? r : run;
+    }
+    return run;
+}
+
+size_t csr_xi_bytes(const Prob* p) {
+    if (p->sys->kind != 1 || (p->flags & KV_FLAG_NO_SPMM)) return 0;
+    const int run = longest_arnoldi_run(p);
+    if (run == 0) return 0;
+    const size_t es = elem_size(p->prec);
+    int fg, fl;
+    if (forced_shape(es, &fg, &fl)) return fg < 0 ? (size_t)((run - fg - 1) / -fg) * -fg * p->N * es : 0;
+    if (!autotuned(p)) return 0;
+    size_t best = 0;
+    for (int q = 0; q < 3; ++q) {
+        const int G = il_width(es, q);
+        if (!il_candidate(G, il_width(es, 0), p->N, es, run)) continue;
+        const size_t b = (size_t)((run + G - 1) / G) * G * p->N * es;
+        best = b > best ? b : best;
+    }
+    return best;
 }
 
 template <typename T>
@@ -568,29 +743,34 @@ static int autotune_t(Prob* p, int ncols, void* V) {
         int g, l;
         double us;
         while (fscanf(f, "%511s %d %d %lf", k, &g, &l, &us) == 4) {
-            if (key == k) {
+            if (key == k && (g > 0 || p->d_xi)) {
                 p->spmm_G = g;
                 p->spmm_LPR = l;
             }
         }
         fclose(f);
-        if (p->spmm_G > 0) return KV_OK;
+        if (p->spmm_G != 0) return KV_OK;
     }
     cudaStream_t s = p->ctx->stream;
     VecArgs<T> va{(T*)V, (int64_t)p->nvec * p->N};
     cudaEvent_t e0, e1;
     KV_CHECK_CUDA(cudaEventCreate(&e0));
     KV_CHECK_CUDA(cudaEventCreate(&e1));
-    const double l2_budget = 96.0 * 1024 * 1024;
     double best = 1e30;
     int bg = 1, bl = 1;
-    const int Gs[4] = {1, 2, 4, 8}, Ls[3] = {1, 2, 4};
-    for (int gi = 0; gi < 4; ++gi) {
-        const int G = Gs[gi];
-        if (G > 1 && (G > ncols || (double)G * p->N * sizeof(T) > l2_budget)) continue;
-        for (int li = 0; li < 3; ++li) {
+    const int Ls[4] = {0, 1, 2, 4};  // 0: staged rows (interleaved form only)
+    std::vector<int> cand;  // signed group sizes: > 0 column-major, < 0 interleaved
+    for (int G : {1, 2, 4, 8})
+        if (plain_candidate(G, p->N, sizeof(T), ncols)) cand.push_back(G);
+    if (p->d_xi)
+        for (int q = 0; q < 3; ++q) {
+            const int G = il_width(sizeof(T), q);
+            if (il_candidate(G, il_width(sizeof(T), 0), p->N, sizeof(T), ncols)) cand.push_back(-G);
+        }
+    for (int G : cand) {
+        for (int li = 0; li < 4; ++li) {
             const int L = Ls[li];
-            spmm_dispatch<T>(p, G, L, va, 0, 1, p->d_aug, p->d_state, 0, ncols, s);
+            if (!spmm_dispatch<T>(p, G, L, va, 0, 1, p->d_aug, p->d_state, 0, ncols, s)) continue;
             KV_CHECK_CUDA(cudaEventRecord(e0, s));
             for (int q = 0; q < 3; ++q) spmm_dispatch<T>(p, G, L, va, 0, 1, p->d_aug, p->d_state, 0, ncols, s);
             KV_CHECK_CUDA(cudaEventRecord(e1, s));
@@ -618,14 +798,19 @@ static int autotune_t(Prob* p, int ncols, void* V) {
     return KV_OK;
 }
 
-// Called by kv_problem for CSR problems whose Arnoldi columns run as one group.
-int csr_autotune(Prob* p) {
+static int choose_shape(Prob* p) {
     int narn = 0;
     for (int j = 0; j < p->i; ++j) narn += p->method[j] == KV_ARNOLDI;
     p->spmm_G = 0;
     p->spmm_LPR = 0;
     if (narn == 0) return KV_OK;
-    if ((p->flags & KV_FLAG_NO_AUTOTUNE) || p->N < 65536) {  // small systems: a fixed choice
+    int fg, fl;
+    if (!(p->flags & KV_FLAG_NO_SPMM) && forced_shape(elem_size(p->prec), &fg, &fl)) {
+        p->spmm_G = fg;
+        p->spmm_LPR = fl;
+        return KV_OK;
+    }
+    if (!autotuned(p)) {  // small systems, or asked for: a fixed choice
         p->spmm_G = narn >= 4 ? 4 : (narn >= 2 ? 2 : 1);
         p->spmm_LPR = 2;
         return KV_OK;
@@ -637,8 +822,22 @@ int csr_autotune(Prob* p) {
     while (j0 + run < p->i && p->method[j0 + run] == KV_ARNOLDI) ++run;
     KV_CHECK_CUDA(cudaMemsetAsync(p->d_state, 0, sizeof(ColState) * (size_t)p->i, p->ctx->stream));
     void* V = (char*)p->d_vec + (size_t)j0 * p->nvec * p->N * elem_size(p->prec);
-    const int rc = p->prec == KV_FP32 ? autotune_t<float>(p, run, V) : autotune_t<double>(p, run, V);
-    return rc;
+    return p->prec == KV_FP32 ? autotune_t<float>(p, run, V) : autotune_t<double>(p, run, V);
+}
+
+// Called by kv_problem for CSR problems: picks the SpMM shape of the Arnoldi
+// columns and sizes its grids.
+int csr_autotune(Prob* p) {
+    const int rc = choose_shape(p);
+    if (rc || p->spmm_G == 0) return rc;
+    const bool ok = p->prec == KV_FP32
+                        ? spmm_dispatch<float>(p, p->spmm_G, p->spmm_LPR, {}, 0, 0, nullptr, nullptr, 0, 0, 0, true)
+                        : spmm_dispatch<double>(p, p->spmm_G, p->spmm_LPR, {}, 0, 0, nullptr, nullptr, 0, 0, 0, true);
+    if (!ok) {
+        set_error("no SpMM kernel for G=%d LPR=%d", p->spmm_G, p->spmm_LPR);
+        return KV_EINVAL;
+    }
+    return KV_OK;
 }
 
 template <typename T>
@@ -679,8 +878,8 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
             const int rc = launch_project(p, j0, ncols, (T*)V + (int64_t)ws * N, va.cstride, it + 1);
             if (rc) return rc;
         } else {
-            if (p->spmm_G > 0 && !(p->flags & KV_FLAG_NO_SPMM)) {
-                // grouped SpMM: the matrix is read once per group of spmm_G columns
+            if (p->spmm_G != 0 && !(p->flags & KV_FLAG_NO_SPMM)) {
+                // grouped SpMM: the matrix is read once per group of |spmm_G| columns
                 LaunchScope ls(p->ctx, "csr_spmm");
                 if (!spmm_dispatch<T>(p, p->spmm_G, p->spmm_LPR, va, it, it + 1, aug, stp, it, ncols, st)) {
                     set_error("no SpMM kernel for G=%d LPR=%d", p->spmm_G, p->spmm_LPR);

@@ -642,6 +642,7 @@ static size_t bytes_core(const Sys* s, const kv_problem_desc* d, int precision, 
         if (c.kind == KV_COL_DENSE) t += r256((size_t)N * 8);
     }
     if (bo.brow) t += r256(((size_t)d->i * row_dot_blocks() + d->i) * 8);
+    if (s->kind == 1) t += r256(csr_xi_bytes(&tmp));
     return t;
 }
 
@@ -789,7 +790,10 @@ static int prob_build(Ctx* c, Prob* p, const Sys* s, const kv_problem_desc* d, i
                 }
             }
         }
-        if (s->kind == 1) TRY(csr_autotune(p));
+        if (s->kind == 1) {
+            if (const size_t xb = csr_xi_bytes(p)) TRY(dalloc(p, (char**)&p->d_xi, xb));
+            TRY(csr_autotune(p));
+        }
         if (cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) {
             rc = fail(KV_ECUDA, "event creation failed");
             goto failed;

@@ -184,7 +184,9 @@ struct Prob {
     unsigned* d_counters = nullptr;  // per-column reduction tickets (CSR)
     int* d_aug = nullptr;            // per-column: runs on A' (CSR)
     void* d_arnoldi = nullptr;       // per-column Gram matrix and coefficients (CSR)
-    int spmm_G = 0, spmm_LPR = 0;    // CSR Arnoldi SpMM shape (autotuned; 0 = per-column SpMV)
+    int spmm_G = 0, spmm_LPR = 0;    // CSR Arnoldi SpMM shape (autotuned; 0 = per-column SpMV;
+                                     // G < 0: groups of -G columns read from d_xi)
+    void* d_xi = nullptr;  // row-interleaved copy of the Arnoldi columns' current vectors
     Reduce red{};
     int red_slots = 0;
     std::vector<void*> allocs;
@@ -243,6 +245,7 @@ int launch_dense_to(Prob* p, int j, void* B);
 int launch_csr_columns(Prob* p, int j0, int ncols, void* V, bool lanczos);
 int64_t csr_scratch_slots(int64_t N, int m);
 int csr_autotune(Prob* p);
+size_t csr_xi_bytes(const Prob* p);  // interleaved SpMM input (0 if no candidate uses it)
 size_t csr_arnoldi_dev_bytes();
 
 // exponential + basis (k_expm.cu)

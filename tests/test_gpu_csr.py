@@ -201,7 +201,58 @@ def test_autotuner_cache(ctx, tmp_path, monkeypatch):
     lines = path.read_text().strip().splitlines()
     assert len(lines) == 1
     key, g, l, us = lines[0].split()
-    assert int(g) in (1, 2, 4, 8) and int(l) in (1, 2, 4) and "n=120000" in key and "cols=8" in key
+    assert int(g) in (1, 2, 4, 8, -4, -8, -16) and int(l) in (1, 2, 4) and "n=120000" in key and "cols=8" in key
+
+
+# (G, LPR) per precision: G < 0 gathers from the row-interleaved copy of -G columns
+# (LPR = 0: one lane per row, the warp's entries staged in shared memory)
+_SHAPES = {"fp32": [(1, 1), (8, 4), (-4, 0), (-4, 1), (-8, 2), (-16, 0)],
+           "fp64": [(2, 2), (-2, 0), (-4, 2), (-8, 0)]}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_forced_spmm_shapes(ctx, monkeypatch, precision):
+    """Every SpMM form against the oracle on a system with the forcing term
+    (the fixed column carries the constant): 10 columns in ragged groups
+    (4+4+2, 8+2, one padded group of 16), n = 3001 rows."""
+    mk = lambda prec: W.random_csr_problem(3001, seed=21, n_gen=9, o=2, c_width=300, dt=0.01, steps=150, m=24,
+                                           precision=prec)
+    p64 = mk("fp64")
+    ref = oracle.run(p64)
+    tol = 1e-9 if precision == "fp64" else 1e-6
+    for G, L in _SHAPES[precision]:
+        monkeypatch.setenv("KV_SPMM_SHAPE", f"{G},{L}")
+        got = run_gpu(ctx, mk(precision))
+        assert np.array_equal(got["m_used"], np.array([ref["used"][j] for j in range(p64.i)])), (G, L)
+        assert max(basis_error(got, ref, j) for j in range(p64.i)) <= tol, (G, L)
+        assert bound_error(got, ref) <= tol, (G, L)
+
+
+def test_forced_interleaved_spmm_with_breakdown(ctx, monkeypatch):
+    """Interleaved groups with a column that breaks down after 3 steps and an
+    all-zero column (done before the first SpMM) next to live ones."""
+    rng = np.random.default_rng(22)
+    n = 300
+    A = np.zeros((n, n))
+    for b0 in range(0, n, 3):
+        A[b0:b0 + 3, b0:b0 + 3] = rng.standard_normal((3, 3)) - 2 * np.eye(3)
+    A[np.arange(n - 1), np.arange(1, n)] += 0.1 * (np.arange(n - 1) % 3 == 2)  # couple all but block 0
+    A[0:3, 3:] = 0.0
+    sysm = W.dense_to_csr(A)
+    e0 = np.zeros(n)
+    e0[0:3] = rng.standard_normal(3)  # block 0 is invariant: breakdown at 3
+    cols = [W.Column(kind="dense", zlo=-1, zhi=1, dense=e0),
+            W.Column(kind="sparse", zlo=-1, zhi=1, idx=np.zeros(0, dtype=np.int64), val=np.zeros(0)),
+            W.Column(kind="dense", zlo=-1, zhi=1, dense=rng.standard_normal(n)),
+            W.Column(kind="sparse", zlo=0, zhi=2, idx=np.array([5, 150, 299]), val=np.array([1.0, -1.0, 0.5]))]
+    rp, cc, cv = W._c_rows([(np.arange(n), rng.standard_normal(n))])
+    p = W.Problem(system=sysm, columns=cols, C_row_ptr=rp, C_col=cc, C_val=cv, theta=np.array([np.inf]),
+                  dt=0.05, steps=40, m=12)
+    ref = oracle.run(p)
+    assert ref["used"][0] == 3 and ref["used"][1] == 0 and ref["used"][2] == 12
+    for shape in ("-4,2", "-2,0", "-8,1"):
+        monkeypatch.setenv("KV_SPMM_SHAPE", shape)
+        got, _ = check(ctx, p, ref=ref)
 
 
 def test_krylov_limit_depends_on_the_method(ctx):
