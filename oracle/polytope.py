@@ -24,12 +24,20 @@ half-space.  Each step's LP is solved by scipy's HiGHS (a library routine).
 """
 from __future__ import annotations
 
+import warnings
 from typing import Dict, Optional
 
 import numpy as np
-from scipy.optimize import linprog
+from scipy.optimize import OptimizeWarning, linprog
 
 OPTIMAL, UNBOUNDED, EMPTY = 0, 1, 2  # UNBOUNDED: t*_k = -inf; EMPTY: no initial state
+
+# HiGHS by default drops matrix entries below 1e-9 and stops at 1e-7
+# feasibility, which moves t* by ~1e-9 when B_k is small (seen against
+# brute-force vertex enumeration); the oracle keeps every entry above 1e-12,
+# solves without presolve and to 1e-10 feasibility.
+HIGHS_OPTIONS = {"presolve": False, "small_matrix_value": 1e-12, "primal_feasibility_tolerance": 1e-10,
+                 "dual_feasibility_tolerance": 1e-10}
 
 
 def normalise(U: np.ndarray, v: np.ndarray):
@@ -56,7 +64,10 @@ def step_lp(B: np.ndarray, zlo, zhi, U, v, Iz=None, iota=None):
     c = np.zeros(i + 1)
     c[i] = 1.0
     bounds = [(float(zlo[j]), float(zhi[j])) for j in range(i)] + [(None, None)]
-    res = linprog(c, A_ub=np.vstack(rows), b_ub=np.concatenate(rhs), bounds=bounds, method="highs")
+    with warnings.catch_warnings():  # small_matrix_value reaches HiGHS as a raw option
+        warnings.simplefilter("ignore", OptimizeWarning)
+        res = linprog(c, A_ub=np.vstack(rows), b_ub=np.concatenate(rhs), bounds=bounds, method="highs",
+                      options=HIGHS_OPTIONS)
     if res.status == 2:
         return EMPTY, np.nan, np.full(i, np.nan)
     if res.status == 3:

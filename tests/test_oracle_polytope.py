@@ -124,6 +124,23 @@ def test_brute_force_vertices():
                                Iz, iota, res["z"][k], 1e-9)
 
 
+def test_brute_force_small_basis():
+    """A basis of size ~1e-9 (early steps of a heat problem): the unsafe
+    rows' z coefficients are tiny next to the t coefficient, and the margin
+    still matches the vertices to 1e-12."""
+    rng = np.random.default_rng(3)
+    for trial in range(40):
+        i, o = 1 + trial % 4, 1 + trial % 3
+        B = rng.standard_normal((o, i)) * 1e-9
+        zlo = rng.uniform(-1, 0, i)
+        zhi = zlo + rng.uniform(0.2, 2, i)
+        U = rng.standard_normal((1 + trial % 3, o))
+        v = rng.standard_normal(len(U))
+        want = brute_force(B, zlo, zhi, U, v, np.zeros((0, i)), np.zeros(0))
+        st, t, z = LP.step_lp(B, zlo, zhi, U, v)
+        assert st == LP.OPTIMAL and abs(t - want) < 1e-12 * max(1.0, abs(want)), (trial, t, want)
+
+
 def test_empty_initial_set():
     rng = np.random.default_rng(2)
     B = random_basis(rng, 3, 2, 5)
