@@ -355,6 +355,53 @@ int kv_poll(kv_server *server, uint64_t ticket, kv_result *res, double *latency_
 int kv_server_stats(kv_server *server, int64_t *admitted, int64_t *completed, int64_t *pending,
                     int32_t *max_running, int64_t *memory_waits);
 
+/* Polyhedral initial and unsafe sets (Sec. 2.1, over the projected basis of
+ * Sec. 3.1-3.2).  The closed-form bounds of kv_run treat each output row as
+ * its own half-space over a box of z; kv_check_polytope instead solves, at
+ * every step k, the LP of Sec. 2.1 for an unsafe set given as a conjunction
+ * U y <= upsilon of rows over the o outputs and an initial set given by the
+ * columns' boxes and optional extra rows I z <= iota over the i columns:
+ *     t*_k = min over the initial set of max_u (U_u B_k z - upsilon_u) / ||U_u||
+ * with B_k = C e^{A t_k} E the o x i basis matrix.  t*_k <= 0 iff a state of
+ * the initial set reaches the unsafe set at step k; for one unsafe row t*_k is
+ * the signed distance (in output units) from the reachable output interval
+ * to the half-space.  The LP's optimal value is unique; the minimiser z* (a
+ * counter-example where t*_k <= tol) need not be. */
+typedef struct {
+    int32_t rows;        /* number of inequalities */
+    const double *a;     /* host, rows x dim, row-major (dim = o for the unsafe set, i for the initial set) */
+    const double *rhs;   /* host, rows */
+} kv_polytope;
+
+/* kv_lp_result.status per step */
+#define KV_LP_OPTIMAL 0
+#define KV_LP_FAILED 1     /* the dual's phase 1 found no feasible point (numerical failure) */
+#define KV_LP_EMPTY 2      /* the initial set is empty */
+#define KV_LP_ITER 3       /* iteration limit of a simplex phase reached */
+
+typedef struct {
+    double *margin;                /* caller, steps+1: t*_k (NaN unless KV_LP_OPTIMAL) */
+    int32_t *status;               /* caller, steps+1: KV_LP_* */
+    double *z;                     /* caller or NULL, (steps+1) x i: the minimiser per step */
+    int32_t first_violation_step;  /* first k with KV_LP_OPTIMAL and margin <= tol, -1: none */
+    double *z_star;                /* caller or NULL, i: the minimiser at that step */
+    double *y_star;                /* caller or NULL, o: B_k z* at that step */
+} kv_lp_result;
+
+/* The per-step LPs for a problem whose results are complete (after kv_run, or
+ * kv_enqueue + kv_fetch): one CTA per step on the device (dense two-phase
+ * simplex on the LP's dual in shared memory, Bland's rule) over the basis
+ * kept on the device, on the context's stream; the call waits for them.
+ * unsafe: rows over the o outputs (rows >= 1, no zero row); init: rows over
+ * the i columns or NULL; every column's box must be finite.  The LP must fit
+ * one CTA's shared memory: 8 ((i+2)(m+i+2) + m + i + 2) + 4 (i+1) bytes with
+ * m = unsafe rows + init rows + 2 i, at most the device's opt-in limit
+ * (232448 bytes on GB300).  Temporary device memory (about 8 (steps+1)(i+o+2)
+ * bytes) comes from the context's pool.  Errors: KV_EINVAL (bad argument, the
+ * problem has not run, a set or LP too large), KV_ENOMEM, KV_ECUDA. */
+int kv_check_polytope(kv_prob *prob, const kv_polytope *unsafe, const kv_polytope *init, double tol,
+                      kv_lp_result *res);
+
 /* Grid points the no-allocation entry point below can hold. */
 #define KV_NOALLOC_MAX_N 262144
 

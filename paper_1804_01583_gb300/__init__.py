@@ -72,10 +72,21 @@ class kv_result(C.Structure):
                 ("err_bound", C.c_void_p)]
 
 
+class kv_polytope(C.Structure):
+    _fields_ = [("rows", C.c_int32), ("a", C.c_void_p), ("rhs", C.c_void_p)]
+
+
+class kv_lp_result(C.Structure):
+    _fields_ = [("margin", C.c_void_p), ("status", C.c_void_p), ("z", C.c_void_p),
+                ("first_violation_step", C.c_int32), ("z_star", C.c_void_p), ("y_star", C.c_void_p)]
+
+
+KV_LP_OPTIMAL, KV_LP_FAILED, KV_LP_EMPTY, KV_LP_ITER = 0, 1, 2, 3
+
 EXPORTED = ["kv_version", "kv_last_error", "kv_create", "kv_destroy", "kv_pool_stats", "kv_system_stencil",
             "kv_system_csr", "kv_sys_destroy", "kv_problem", "kv_prob_destroy", "kv_problem_bytes",
             "kv_enqueue", "kv_fetch", "kv_run", "kv_profile_enable", "kv_profile_read", "kv_launch_count",
-            "kv_problem_runs", "kv_diag_bounded_wait"]
+            "kv_problem_runs", "kv_diag_bounded_wait", "kv_check_polytope"]
 
 _lib = None
 _lock = threading.Lock()
@@ -114,6 +125,8 @@ def load(path: Optional[str] = None):
         lib.kv_launch_count.argtypes = [V, C.POINTER(C.c_int64)]
         lib.kv_problem_runs.argtypes = [V, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         lib.kv_diag_bounded_wait.argtypes = [I, C.c_int64]
+        lib.kv_check_polytope.argtypes = [V, C.POINTER(kv_polytope), C.POINTER(kv_polytope), C.c_double,
+                                          C.POINTER(kv_lp_result)]
         lib.kv_grid_lanczos_noalloc.argtypes = [I, V, I, C.POINTER(C.c_int64), C.c_double, C.POINTER(C.c_double),
                                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_double, C.c_int32,
                                                 V, V, V, C.c_int32, V, V, V, V]
@@ -324,6 +337,36 @@ class ProblemHandle:
     def run(self, full: bool = True) -> Dict:
         self.enqueue()
         return self.fetch(full)
+
+    def check_polytope(self, U, v, Iz=None, iota=None, tol: float = 0.0) -> Dict:
+        """kv_check_polytope: the per-step LP margins t*_k for the unsafe set
+        U y <= v (rows over the o outputs) and the initial set of the columns'
+        boxes with I_z z <= iota; the first step with t*_k <= tol, its z*, y*."""
+        p = self.problem
+        S = p.steps + 1
+        U = np.ascontiguousarray(np.atleast_2d(np.asarray(U, dtype=np.float64)))
+        v = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1))
+        if U.shape != (len(v), p.o):
+            raise ValueError(f"unsafe rows must be {len(v)} x {p.o}")
+        un = kv_polytope(len(v), _ptr(U), _ptr(v))
+        ini = None
+        if Iz is not None and len(Iz):
+            Iz = np.ascontiguousarray(np.atleast_2d(np.asarray(Iz, dtype=np.float64)))
+            iota = np.ascontiguousarray(np.asarray(iota, dtype=np.float64).reshape(-1))
+            if Iz.shape != (len(iota), p.i):
+                raise ValueError(f"initial rows must be {len(iota)} x {p.i}")
+            ini = kv_polytope(len(iota), _ptr(Iz), _ptr(iota))
+        out = dict(margin=np.zeros(S), status=np.zeros(S, dtype=np.int32), z=np.zeros((S, p.i)),
+                   z_star=np.zeros(p.i), y_star=np.zeros(p.o))
+        r = kv_lp_result()
+        r.margin, r.status, r.z = _ptr(out["margin"]), _ptr(out["status"]), _ptr(out["z"])
+        r.z_star, r.y_star = _ptr(out["z_star"]), _ptr(out["y_star"])
+        _check(self.ctx._lib.kv_check_polytope(self.h, C.byref(un), C.byref(ini) if ini is not None else None,
+                                               float(tol), C.byref(r)))
+        out["viol_step"] = int(r.first_violation_step)
+        if out["viol_step"] < 0:
+            out["z_star"] = out["y_star"] = None
+        return out
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -1,0 +1,272 @@
+// k_lp.cu -- the per-step LP of Sec. 2.1 for polyhedral initial and unsafe
+// sets, over the projected basis B_k = C e^{A t_k} E (Sec. 3.1-3.2).
+//
+// Step k asks for
+//     t*_k = min t   over (z, t)
+//            s.t.    U_u B_k z - t <= upsilon_u   (unsafe rows, unit norm)
+//                    I_q z         <= iota_q      (extra initial-set rows)
+//                    lo <= z <= hi                (the columns' boxes)
+// the largest normalised violation of the unsafe constraints that the
+// initial set can bring down to; the unsafe set is reachable at step k iff
+// t*_k <= tol, and the minimiser z* is a counter-example.
+//
+// One CTA per step solves the dual of that LP,
+//     min b^T y   s.t.   A^T y = -c,  y >= 0      (c = e_t),
+// by the two-phase dense simplex method with Bland's rule (smallest entering
+// index, smallest basic index among tied ratios; no cycling) on a tableau in
+// shared memory: d = i + 1 equality rows (one per primal variable), one
+// column per primal constraint scaled to unit norm (the same half-space),
+// d artificial columns and the right-hand side.  The primal optimum is
+// t* = -(min b^T y) and the minimiser (z*, t*) is the simplex multiplier
+// vector, read from the reduced costs of the artificial columns.
+#include <limits.h>
+#include <math.h>
+
+#include <vector>
+
+#include "kv_internal.h"
+
+namespace kv {
+
+constexpr int LNT = 256;
+constexpr double LP_EPS_PIV = 1e-11;   // smallest usable pivot (columns have unit norm)
+constexpr double LP_EPS_FEAS = 1e-9;   // phase-1 optimum above this: the dual is infeasible
+constexpr double LP_EPS_RC = 1e-10;    // entering threshold on reduced costs (x the largest cost in phase 2)
+
+struct LpArgs {
+    const double* basis;  // [j][r][k], i x o x S
+    int i, o, S;
+    const double* U;      // qu x o, rows of unit norm
+    const double* v;      // qu
+    int qu;
+    const double* Iz;     // qi x i
+    const double* iota;   // qi
+    int qi;
+    const double* zlo;    // i (device, from the problem)
+    const double* zhi;
+    int m;                // primal constraints = dual columns
+    int W;                // tableau row stride: m + d + 1
+    int max_iter;         // per phase
+    double* margin;       // S
+    int* status;          // S
+    double* zx;           // S x i
+    double* yx;           // S x o
+};
+
+struct LpShared {
+    int enter, leave, iters;
+    double piv, wmin;
+};
+
+// Pivot on row kp, column e: row kp /= T[kp][e], then every other row
+// (the objective row d included) loses its multiple of row kp.
+__device__ void lp_pivot(double* T, int* bas, double* fcol, int d, int W, int kp, int e, LpShared& sh) {
+    if (threadIdx.x == 0) sh.piv = T[(size_t)kp * W + e];
+    __syncthreads();
+    for (int c = threadIdx.x; c < W; c += LNT) T[(size_t)kp * W + c] = c == e ? 1.0 : T[(size_t)kp * W + c] / sh.piv;
+    for (int r = threadIdx.x; r <= d; r += LNT) fcol[r] = r == kp ? 0.0 : T[(size_t)r * W + e];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (d + 1) * W; idx += LNT) {
+        const int r = idx / W, c = idx - r * W;
+        if (r == kp || fcol[r] == 0.0) continue;
+        T[idx] = c == e ? 0.0 : T[idx] - fcol[r] * T[(size_t)kp * W + c];
+    }
+    if (threadIdx.x == 0) bas[kp] = e;
+    __syncthreads();
+}
+
+// One simplex phase over the entering columns [0, m) (artificial columns
+// never enter).  Returns 0 optimal, 1 unbounded, 2 iteration limit.
+__device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, double eps_rc, int max_iter,
+                        LpShared& sh) {
+    const int rhs = m + d;
+    for (int it = 0;; ++it) {
+        if (threadIdx.x == 0) sh.enter = INT_MAX;
+        __syncthreads();
+        for (int c = threadIdx.x; c < m; c += LNT)
+            if (T[(size_t)d * W + c] < -eps_rc) {  // a thread's first hit is its smallest index
+                atomicMin(&sh.enter, c);
+                break;
+            }
+        __syncthreads();
+        const int e = sh.enter;
+        if (e == INT_MAX) return 0;
+        if (it >= max_iter) return 2;
+        if (threadIdx.x < 32) {  // ratio test, warp 0
+            const int lane = threadIdx.x;
+            double q = INFINITY;
+            for (int r = lane; r < d; r += 32) {
+                const double a = T[(size_t)r * W + e];
+                if (a > LP_EPS_PIV) q = fmin(q, fmax(T[(size_t)r * W + rhs], 0.0) / a);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q = fmin(q, __shfl_xor_sync(0xffffffffu, q, o));
+            // among the rows within rounding of the smallest ratio, the smallest basic index
+            int best = INT_MAX, brow = -1;
+            for (int r = lane; r < d; r += 32) {
+                const double a = T[(size_t)r * W + e];
+                if (!(a > LP_EPS_PIV)) continue;
+                const double qr = fmax(T[(size_t)r * W + rhs], 0.0) / a;
+                if (qr <= q + 1e-12 * (1.0 + q) && bas[r] < best) {
+                    best = bas[r];
+                    brow = r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+                if (ob < best) {
+                    best = ob;
+                    brow = orow;
+                }
+            }
+            if (lane == 0) sh.leave = q == INFINITY ? -1 : brow;
+        }
+        __syncthreads();
+        if (sh.leave < 0) return 1;
+        lp_pivot(T, bas, fcol, d, W, sh.leave, e, sh);
+    }
+}
+
+__global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
+    extern __shared__ double smem[];
+    __shared__ LpShared sh;
+    const int d = a.i + 1, m = a.m, W = a.W, rhs = m + d, k = blockIdx.x;
+    double* T = smem;                        // (d + 1) x W; row d is the objective
+    double* cost = T + (size_t)(d + 1) * W;  // m: b of the dual (scaled)
+    double* fcol = cost + m;                 // d + 1
+    int* bas = (int*)(fcol + d + 1);         // d
+    // primal constraint columns, unscaled: A[col][row] with row = z_0..z_{i-1}, t
+    const int nbox0 = a.qu + a.qi;
+    for (int idx = threadIdx.x; idx < (d + 1) * W; idx += LNT) T[idx] = 0.0;
+    for (int c = threadIdx.x; c < m; c += LNT) cost[c] = 0.0;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < a.qu * a.i; idx += LNT) {  // U_u B_k e_j
+        const int u = idx / a.i, j = idx - u * a.i;
+        double s = 0.0;
+        for (int r = 0; r < a.o; ++r) s = fma(a.U[(size_t)u * a.o + r], a.basis[((size_t)j * a.o + r) * a.S + k], s);
+        T[(size_t)j * W + u] = s;
+    }
+    for (int u = threadIdx.x; u < a.qu; u += LNT) {
+        T[(size_t)a.i * W + u] = -1.0;  // the t coefficient
+        cost[u] = a.v[u];
+    }
+    for (int idx = threadIdx.x; idx < a.qi * a.i; idx += LNT) {
+        const int q = idx / a.i, j = idx - q * a.i;
+        T[(size_t)j * W + a.qu + q] = a.Iz[(size_t)q * a.i + j];
+    }
+    for (int q = threadIdx.x; q < a.qi; q += LNT) cost[a.qu + q] = a.iota[q];
+    if (threadIdx.x == 0) {  // finite box sides, in column order
+        int c = nbox0;
+        for (int j = 0; j < a.i; ++j) {
+            if (isfinite(a.zhi[j])) {
+                T[(size_t)j * W + c] = 1.0;
+                cost[c++] = a.zhi[j];
+            }
+            if (isfinite(a.zlo[j])) {
+                T[(size_t)j * W + c] = -1.0;
+                cost[c++] = -a.zlo[j];
+            }
+        }
+    }
+    __syncthreads();
+    // unit-norm columns; the t row is negated so that the right-hand side
+    // -c = -e_t becomes +1 (all right-hand sides >= 0); artificial identity;
+    // phase-1 objective: minimise the sum of the artificials
+    for (int c = threadIdx.x; c < m; c += LNT) {
+        double nrm = 0.0;
+        for (int r = 0; r < d; ++r) nrm = fma(T[(size_t)r * W + c], T[(size_t)r * W + c], nrm);
+        nrm = sqrt(nrm);
+        const double sc = nrm > 0.0 ? 1.0 / nrm : 1.0;
+        double colsum = 0.0;
+        for (int r = 0; r < d; ++r) {
+            const double x = T[(size_t)r * W + c] * sc * (r == a.i ? -1.0 : 1.0);
+            T[(size_t)r * W + c] = x;
+            colsum += x;
+        }
+        cost[c] *= sc;
+        T[(size_t)d * W + c] = -colsum;
+    }
+    for (int r = threadIdx.x; r < d; r += LNT) {
+        T[(size_t)r * W + m + r] = 1.0;
+        T[(size_t)r * W + rhs] = r == a.i ? 1.0 : 0.0;
+        bas[r] = m + r;
+    }
+    if (threadIdx.x == 0) T[(size_t)d * W + rhs] = -1.0;
+    __syncthreads();
+
+    int st = 0;  // KV_LP_OPTIMAL
+    // phase 1 is bounded below by 0: a column without a pivot there is rounding
+    // noise in its reduced cost, and the sum of artificials decides
+    int rc = lp_phase(T, bas, fcol, d, m, W, LP_EPS_RC, a.max_iter, sh);
+    if (rc == 2) st = 3;                                      // KV_LP_ITER
+    else if (-T[(size_t)d * W + rhs] > LP_EPS_FEAS) st = 1;  // KV_LP_FAILED
+    if (st == 0) {
+        // basic artificials at level zero leave the basis where a structural
+        // column can replace them (else their row is redundant)
+        for (int r = 0; r < d; ++r) {
+            if (bas[r] < m) continue;  // uniform: bas is shared
+            if (threadIdx.x == 0) sh.enter = INT_MAX;
+            __syncthreads();
+            for (int c = threadIdx.x; c < m; c += LNT)
+                if (fabs(T[(size_t)r * W + c]) > 1e-9) {
+                    atomicMin(&sh.enter, c);
+                    break;
+                }
+            __syncthreads();
+            if (sh.enter != INT_MAX) lp_pivot(T, bas, fcol, d, W, r, sh.enter, sh);
+        }
+        // phase 2: the dual's costs, reduced against the current basis
+        double cmax = 0.0;
+        for (int c = 0; c < m; ++c) cmax = fmax(cmax, fabs(cost[c]));
+        for (int c = threadIdx.x; c < W; c += LNT) {
+            double x = c < m ? cost[c] : 0.0;
+            for (int r = 0; r < d; ++r) {
+                const int bc = bas[r];
+                if (bc < m) x = fma(-cost[bc], T[(size_t)r * W + c], x);
+            }
+            T[(size_t)d * W + c] = x;
+        }
+        __syncthreads();
+        rc = lp_phase(T, bas, fcol, d, m, W, LP_EPS_RC * fmax(1.0, cmax), a.max_iter, sh);
+        if (rc == 1) st = 2;       // dual unbounded: the initial set is empty
+        else if (rc == 2) st = 3;
+    }
+    if (threadIdx.x == 0) {
+        a.status[k] = st;
+        a.margin[k] = st == 0 ? T[(size_t)d * W + rhs] : (st == 1 ? -INFINITY : NAN);
+    }
+    // z*_j: the multiplier of row z_j (sign +1), clamped into the box -- where
+    // B_k is tiny next to the t coefficient two nearly parallel unsafe
+    // columns can share the optimal basis and leave z* off the box by the
+    // rounding of that ill-conditioned solve (the margin is unaffected)
+    for (int j = threadIdx.x; j < a.i; j += LNT)
+        fcol[j] = st == 0 ? fmin(fmax(-T[(size_t)d * W + m + j], a.zlo[j]), a.zhi[j]) : NAN;
+    __syncthreads();
+    for (int j = threadIdx.x; j < a.i; j += LNT) a.zx[(size_t)k * a.i + j] = fcol[j];
+    for (int r = threadIdx.x; r < a.o; r += LNT) {
+        double y = 0.0;
+        for (int j = 0; j < a.i; ++j) y = fma(a.basis[((size_t)j * a.o + r) * a.S + k], fcol[j], y);
+        a.yx[(size_t)k * a.o + r] = y;
+    }
+}
+
+size_t lp_smem_bytes(int i, int m) {
+    const size_t d = (size_t)i + 1, W = (size_t)m + d + 1;
+    return ((d + 1) * W + (size_t)m + d + 1) * sizeof(double) + d * sizeof(int);
+}
+
+int launch_step_lp(const Prob* p, const double* dU, const double* dv, int qu, const double* dIz,
+                   const double* diota, int qi, int m, double* dmargin, int* dstatus, double* dzx, double* dyx) {
+    LpArgs a{p->d_basis, p->i, p->o, p->steps + 1, dU, dv, qu, dIz, diota, qi, p->d_zlo, p->d_zhi, m,
+             m + p->i + 2, 50 * (m + p->i + 1) + 100, dmargin, dstatus, dzx, dyx};
+    const size_t sm = lp_smem_bytes(p->i, m);
+    if (sm > 48 * 1024)
+        KV_CHECK_CUDA(cudaFuncSetAttribute(k_step_lp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_step_lp<<<(unsigned)(p->steps + 1), LNT, sm, p->ctx->stream>>>(a);
+    KV_CHECK_CUDA(cudaGetLastError());
+    return KV_OK;
+}
+
+}  // namespace kv

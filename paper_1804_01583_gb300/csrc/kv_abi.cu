@@ -862,6 +862,12 @@ static int build_transposed(kv_ctx* c, kv_prob** out, const Sys* s, const kv_pro
     p->err_target = inner->err_target;
     p->inner = inner;
     p->view = view;
+    p->cols.assign(d->cols, d->cols + d->i);  // boxes only: the caller's arrays are not kept
+    for (kv_column& hc : p->cols) {
+        hc.idx = nullptr;
+        hc.val = nullptr;
+        hc.dense = nullptr;
+    }
     const int64_t S = d->steps + 1;
 #define TRY(x)               \
     do {                     \
@@ -1048,6 +1054,7 @@ int kv_enqueue(kv_prob* p) {
     rc = launch_bounds(p);
     if (rc) return rc;
     KV_CHECK_CUDA(cudaEventRecord(p->done_ev, p->ctx->stream));
+    p->ran = true;
     return KV_OK;
 }
 
@@ -1086,6 +1093,87 @@ int kv_fetch(kv_prob* p, kv_result* r) {
     if (r->err_bound) KV_CHECK_CUDA(cudaMemcpy(r->err_bound, q->d_err, (size_t)q->i * 8, cudaMemcpyDeviceToHost));
     if (status) return fail(KV_ETIMEOUT, "a device-side wait gave up (status %d)", status);
     return KV_OK;
+}
+
+int kv_check_polytope(kv_prob* p, const kv_polytope* unsafe, const kv_polytope* init, double tol, kv_lp_result* r) {
+    if (!p || !unsafe || !r || !r->margin || !r->status) return fail(KV_EINVAL, "kv_check_polytope: NULL argument");
+    if (!p->ran) return fail(KV_EINVAL, "kv_check_polytope: the problem has not run");
+    const int qu = unsafe->rows, qi = init ? init->rows : 0;
+    if (qu < 1 || !unsafe->a || !unsafe->rhs) return fail(KV_EINVAL, "kv_check_polytope: the unsafe set needs rows");
+    if (qi < 0 || (qi > 0 && (!init->a || !init->rhs))) return fail(KV_EINVAL, "kv_check_polytope: bad initial rows");
+    if (std::isnan(tol)) return fail(KV_EINVAL, "kv_check_polytope: tol is NaN");
+    const int i = p->i, o = p->o;
+    const int64_t S = (int64_t)p->steps + 1;
+    for (int j = 0; j < i; ++j)
+        if (!std::isfinite(p->cols[j].zlo) || !std::isfinite(p->cols[j].zhi))
+            return fail(KV_EINVAL, "kv_check_polytope: column %d has an infinite box", j);
+    // unsafe rows scaled to unit norm (the same half-spaces)
+    std::vector<double> U((size_t)qu * o), v(qu);
+    for (int u = 0; u < qu; ++u) {
+        double nr = 0.0;
+        for (int c = 0; c < o; ++c) nr += unsafe->a[(size_t)u * o + c] * unsafe->a[(size_t)u * o + c];
+        nr = std::sqrt(nr);
+        if (!(nr > 0.0) || !std::isfinite(nr) || !std::isfinite(unsafe->rhs[u]))
+            return fail(KV_EINVAL, "kv_check_polytope: unsafe row %d is zero or not finite", u);
+        for (int c = 0; c < o; ++c) U[(size_t)u * o + c] = unsafe->a[(size_t)u * o + c] / nr;
+        v[u] = unsafe->rhs[u] / nr;
+    }
+    for (int64_t q = 0; q < (int64_t)qi * (i + 1); ++q) {
+        const double x = q < (int64_t)qi * i ? init->a[q] : init->rhs[q - (int64_t)qi * i];
+        if (!std::isfinite(x)) return fail(KV_EINVAL, "kv_check_polytope: initial rows not finite");
+    }
+    const int m = qu + qi + 2 * i;
+    int dev_max = 0;
+    KV_CHECK_CUDA(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->ctx->device));
+    if (lp_smem_bytes(i, m) > (size_t)dev_max)
+        return fail(KV_EINVAL, "kv_check_polytope: the LP (i = %d, %d constraints) needs %zu bytes of shared memory, "
+                    "the device allows %d", i, m, lp_smem_bytes(i, m), dev_max);
+    int rc = with_device(p->ctx->device);
+    if (rc) return rc;
+    Ctx* c = p->ctx;
+    // one arena block: U, v, Iz, iota, margin, zx, yx (doubles), status (ints)
+    const size_t nd = (size_t)qu * o + qu + (size_t)qi * i + qi + S + (size_t)S * i + (size_t)S * o;
+    char* buf = (char*)c->arena.alloc(nd * 8 + (size_t)S * 4);
+    if (!buf) return fail(KV_ENOMEM, "kv_check_polytope: device pool exhausted (%zu bytes)", nd * 8 + (size_t)S * 4);
+    double* dU = (double*)buf;
+    double* dv = dU + (size_t)qu * o;
+    double* dIz = dv + qu;
+    double* diota = dIz + (size_t)qi * i;
+    double* dmargin = diota + qi;
+    double* dzx = dmargin + S;
+    double* dyx = dzx + (size_t)S * i;
+    int* dstatus = (int*)(dyx + (size_t)S * o);
+    std::vector<double> zx((size_t)S * i), yrow(o);
+    auto run = [&]() -> int {
+        int e = upload(c, dU, U.data(), U.size() * 8);
+        if (!e) e = upload(c, dv, v.data(), v.size() * 8);
+        if (!e && qi) e = upload(c, dIz, init->a, (size_t)qi * i * 8);
+        if (!e && qi) e = upload(c, diota, init->rhs, (size_t)qi * 8);
+        if (!e) KV_CHECK_CUDA(cudaStreamWaitEvent(c->stream, p->done_ev, 0));
+        if (!e) e = launch_step_lp(p, dU, dv, qu, dIz, diota, qi, m, dmargin, dstatus, dzx, dyx);
+        if (e) return e;
+        KV_CHECK_CUDA(cudaMemcpyAsync(r->margin, dmargin, (size_t)S * 8, cudaMemcpyDeviceToHost, c->stream));
+        KV_CHECK_CUDA(cudaMemcpyAsync(r->status, dstatus, (size_t)S * 4, cudaMemcpyDeviceToHost, c->stream));
+        KV_CHECK_CUDA(cudaMemcpyAsync(zx.data(), dzx, zx.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        KV_CHECK_CUDA(cudaStreamSynchronize(c->stream));
+        r->first_violation_step = -1;
+        for (int64_t k = 0; k < S; ++k)
+            if (r->status[k] == KV_LP_OPTIMAL && r->margin[k] <= tol) {
+                r->first_violation_step = (int32_t)k;
+                break;
+            }
+        if (r->z) std::copy(zx.begin(), zx.end(), r->z);
+        const int64_t kv = r->first_violation_step;
+        if (kv >= 0) {
+            if (r->z_star) std::copy(zx.begin() + kv * i, zx.begin() + (kv + 1) * i, r->z_star);
+            if (r->y_star) KV_CHECK_CUDA(cudaMemcpy(r->y_star, dyx + kv * o, (size_t)o * 8, cudaMemcpyDeviceToHost));
+        }
+        return KV_OK;
+    };
+    rc = run();
+    cudaStreamSynchronize(c->stream);  // nothing in flight reads the block when it is freed
+    c->arena.free(buf);
+    return rc;
 }
 
 int kv_run(kv_prob* p, kv_result* r) {

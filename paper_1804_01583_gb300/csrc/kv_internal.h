@@ -139,6 +139,7 @@ struct Prob {
     int flags = 0;
     double err_target = 0.0;     // > 0: a-posteriori error control (Alg. 2 / Alg. 4)
     bool fused = false;          // single-pass TMA Lanczos iterations on the grid
+    bool ran = false;            // enqueued at least once (the basis on the device is a result)
     std::vector<int> method;     // per column: KV_LANCZOS | KV_ARNOLDI
     std::vector<int> aug;        // per column: runs on A' (carries the constant)
     std::vector<kv_column> cols; // host copy (pointers cleared)
@@ -246,6 +247,10 @@ int launch_csr_columns(Prob* p, int j0, int ncols, void* V, bool lanczos);
 int64_t csr_scratch_slots(int64_t N, int m);
 int csr_autotune(Prob* p);
 size_t csr_xi_bytes(const Prob* p);  // interleaved SpMM input (0 if no candidate uses it)
+// per-step LP for polyhedral sets (k_lp.cu)
+size_t lp_smem_bytes(int i, int m);
+int launch_step_lp(const Prob* p, const double* dU, const double* dv, int qu, const double* dIz,
+                   const double* diota, int qi, int m, double* dmargin, int* dstatus, double* dzx, double* dyx);
 size_t csr_arnoldi_dev_bytes();
 
 // exponential + basis (k_expm.cu)
