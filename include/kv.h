@@ -381,7 +381,9 @@ typedef struct {
 
 typedef struct {
     double *margin;                /* caller, steps+1: t*_k (NaN unless KV_LP_OPTIMAL) */
-    int32_t *status;               /* caller, steps+1: KV_LP_* */
+    int32_t *status;               /* caller, steps+1: KV_LP_*; every step checks its own answer (no
+                                      primal-dual gap, z* in the initial set) and reports KV_LP_FAILED
+                                      where rounding has spoilt it */
     double *z;                     /* caller or NULL, (steps+1) x i: the minimiser per step */
     int32_t first_violation_step;  /* first k with KV_LP_OPTIMAL and margin <= tol, -1: none */
     double *z_star;                /* caller or NULL, i: the minimiser at that step */
@@ -390,7 +392,7 @@ typedef struct {
 
 /* The per-step LPs for a problem whose results are complete (after kv_run, or
  * kv_enqueue + kv_fetch): one CTA per step on the device (dense two-phase
- * simplex on the LP's dual in shared memory, Bland's rule) over the basis
+ * simplex on the LP's dual in shared memory) over the basis
  * kept on the device, on the context's stream; the call waits for them.
  * unsafe: rows over the o outputs (rows >= 1, no zero row); init: rows over
  * the i columns or NULL; every column's box must be finite.  The LP must fit

@@ -12,10 +12,10 @@
 //
 // One CTA per step solves the dual of that LP,
 //     min b^T y   s.t.   A^T y = -c,  y >= 0      (c = e_t),
-// by the two-phase dense simplex method with Bland's rule (smallest entering
-// index, smallest basic index among tied ratios; no cycling) on a tableau in
-// shared memory: d = i + 1 equality rows (one per primal variable), one
-// column per primal constraint scaled to unit norm (the same half-space),
+// by the two-phase dense simplex method (Dantzig pricing, Harris ratio test,
+// Bland's rule against cycling) on a tableau in shared memory: d = i + 1
+// equality rows (one per primal variable), one column per primal constraint
+// scaled to unit norm (the same half-space),
 // d artificial columns and the right-hand side.  The primal optimum is
 // t* = -(min b^T y) and the minimiser (z*, t*) is the simplex multiplier
 // vector, read from the reduced costs of the artificial columns.
@@ -32,6 +32,9 @@ constexpr int LNT = 256;
 constexpr double LP_EPS_PIV = 1e-11;   // smallest usable pivot (columns have unit norm)
 constexpr double LP_EPS_FEAS = 1e-9;   // phase-1 optimum above this: the dual is infeasible
 constexpr double LP_EPS_RC = 1e-10;    // entering threshold on reduced costs (x the largest cost in phase 2)
+constexpr double LP_HARRIS = 1e-11;    // right-hand-side relaxation of the Harris ratio test
+constexpr double LP_GAP_REL = 1e-8;    // largest primal-dual gap of an accepted step (relative)
+constexpr double LP_ROW_TOL = 1e-7;    // largest violation of an extra initial row by z* (x the box size)
 
 struct LpArgs {
     const double* basis;  // [j][r][k], i x o x S
@@ -51,11 +54,13 @@ struct LpArgs {
     int* status;          // S
     double* zx;           // S x i
     double* yx;           // S x o
+    int zonly;            // 1: the initial-set emptiness check (one CTA; the unsafe row is t >= 0)
+    int* zflag;           // written by the check: 0 non-empty, 1 empty, 2 undecided; read by the steps
 };
 
 struct LpShared {
-    int enter, leave, iters;
-    double piv, wmin;
+    int enter, leave, degen;
+    double piv;
 };
 
 // Pivot on row kp, column e: row kp /= T[kp][e], then every other row
@@ -77,17 +82,55 @@ __device__ void lp_pivot(double* T, int* bas, double* fcol, int d, int W, int kp
 
 // One simplex phase over the entering columns [0, m) (artificial columns
 // never enter).  Returns 0 optimal, 1 unbounded, 2 iteration limit.
+//
+// Pricing: the most negative reduced cost (Dantzig), ratio test: Harris's
+// two passes (the smallest ratio with the right-hand sides relaxed by
+// LP_HARRIS, then the largest pivot among the rows within it) -- few pivots
+// and no tiny pivots, so little rounding accumulates in the tableau.  After
+// more than d degenerate pivots in a row the phase switches to Bland's rule
+// (smallest entering index, smallest basic index among the tied rows whose
+// pivot is not tiny) until a pivot makes progress, which rules out cycling.
 __device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, double eps_rc, int max_iter,
                         LpShared& sh) {
     const int rhs = m + d;
+    __shared__ double wval[LNT / 32];
+    __shared__ int widx[LNT / 32];
+    if (threadIdx.x == 0) sh.degen = 0;
+    __syncthreads();
     for (int it = 0;; ++it) {
-        if (threadIdx.x == 0) sh.enter = INT_MAX;
-        __syncthreads();
-        for (int c = threadIdx.x; c < m; c += LNT)
-            if (T[(size_t)d * W + c] < -eps_rc) {  // a thread's first hit is its smallest index
-                atomicMin(&sh.enter, c);
-                break;
+        const bool bland = sh.degen > d;  // uniform: read after a barrier
+        // entering column: (reduced cost, index) minimum, or the first negative one
+        double bv = -eps_rc;
+        int bi = INT_MAX;
+        for (int c = threadIdx.x; c < m; c += LNT) {
+            const double x = T[(size_t)d * W + c];
+            if (x < -eps_rc && (bland ? c < bi : (x < bv || (x == bv && c < bi)))) {
+                bv = x;
+                bi = c;
             }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (bland ? oi < bi : (ov < bv || (ov == bv && oi < bi))) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            wval[threadIdx.x >> 5] = bv;
+            widx[threadIdx.x >> 5] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < LNT / 32; ++w)
+                if (bland ? widx[w] < bi : (wval[w] < bv || (wval[w] == bv && widx[w] < bi))) {
+                    bv = wval[w];
+                    bi = widx[w];
+                }
+            sh.enter = bi;
+        }
         __syncthreads();
         const int e = sh.enter;
         if (e == INT_MAX) return 0;
@@ -97,18 +140,28 @@ __device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, 
             double q = INFINITY;
             for (int r = lane; r < d; r += 32) {
                 const double a = T[(size_t)r * W + e];
-                if (a > LP_EPS_PIV) q = fmin(q, fmax(T[(size_t)r * W + rhs], 0.0) / a);
+                if (a > LP_EPS_PIV)
+                    q = fmin(q, (fmax(T[(size_t)r * W + rhs], 0.0) + (bland ? 0.0 : LP_HARRIS)) / a);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) q = fmin(q, __shfl_xor_sync(0xffffffffu, q, o));
-            // among the rows within rounding of the smallest ratio, the smallest basic index
+            const double qtie = bland ? q + 1e-12 * (1.0 + q) : q;
+            double amax = 0.0;
+            for (int r = lane; r < d; r += 32) {
+                const double a = T[(size_t)r * W + e];
+                if (a > LP_EPS_PIV && fmax(T[(size_t)r * W + rhs], 0.0) / a <= qtie) amax = fmax(amax, a);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            // Harris: the largest pivot (smallest row on ties); Bland: the
+            // smallest basic index among pivots not tiny next to the largest
             int best = INT_MAX, brow = -1;
             for (int r = lane; r < d; r += 32) {
                 const double a = T[(size_t)r * W + e];
-                if (!(a > LP_EPS_PIV)) continue;
-                const double qr = fmax(T[(size_t)r * W + rhs], 0.0) / a;
-                if (qr <= q + 1e-12 * (1.0 + q) && bas[r] < best) {
-                    best = bas[r];
+                if (!(a > LP_EPS_PIV) || fmax(T[(size_t)r * W + rhs], 0.0) / a > qtie) continue;
+                const int key = bland ? (a >= 1e-3 * amax ? bas[r] : INT_MAX) : (a == amax ? r : INT_MAX);
+                if (key < best) {
+                    best = key;
                     brow = r;
                 }
             }
@@ -121,7 +174,13 @@ __device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, 
                     brow = orow;
                 }
             }
-            if (lane == 0) sh.leave = q == INFINITY ? -1 : brow;
+            if (lane == 0) {
+                sh.leave = q == INFINITY ? -1 : brow;
+                if (brow >= 0) {
+                    const double step = fmax(T[(size_t)brow * W + rhs], 0.0) / T[(size_t)brow * W + e];
+                    sh.degen = step <= 1e-12 ? sh.degen + 1 : 0;
+                }
+            }
         }
         __syncthreads();
         if (sh.leave < 0) return 1;
@@ -133,6 +192,16 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
     extern __shared__ double smem[];
     __shared__ LpShared sh;
     const int d = a.i + 1, m = a.m, W = a.W, rhs = m + d, k = blockIdx.x;
+    if (!a.zonly && *a.zflag != 0) {  // empty (or undecided) initial set: no step LP
+        const int st = *a.zflag == 1 ? 2 : 1;
+        if (threadIdx.x == 0) {
+            a.status[k] = st;
+            a.margin[k] = NAN;
+        }
+        for (int j = threadIdx.x; j < a.i; j += LNT) a.zx[(size_t)k * a.i + j] = NAN;
+        for (int r = threadIdx.x; r < a.o; r += LNT) a.yx[(size_t)k * a.o + r] = NAN;
+        return;
+    }
     double* T = smem;                        // (d + 1) x W; row d is the objective
     double* cost = T + (size_t)(d + 1) * W;  // m: b of the dual (scaled)
     double* fcol = cost + m;                 // d + 1
@@ -142,7 +211,7 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
     for (int idx = threadIdx.x; idx < (d + 1) * W; idx += LNT) T[idx] = 0.0;
     for (int c = threadIdx.x; c < m; c += LNT) cost[c] = 0.0;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < a.qu * a.i; idx += LNT) {  // U_u B_k e_j
+    for (int idx = threadIdx.x; idx < (a.zonly ? 0 : a.qu * a.i); idx += LNT) {  // U_u B_k e_j
         const int u = idx / a.i, j = idx - u * a.i;
         double s = 0.0;
         for (int r = 0; r < a.o; ++r) s = fma(a.U[(size_t)u * a.o + r], a.basis[((size_t)j * a.o + r) * a.S + k], s);
@@ -150,7 +219,7 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
     }
     for (int u = threadIdx.x; u < a.qu; u += LNT) {
         T[(size_t)a.i * W + u] = -1.0;  // the t coefficient
-        cost[u] = a.v[u];
+        cost[u] = a.zonly ? 0.0 : a.v[u];
     }
     for (int idx = threadIdx.x; idx < a.qi * a.i; idx += LNT) {
         const int q = idx / a.i, j = idx - q * a.i;
@@ -233,9 +302,10 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
         if (rc == 1) st = 2;       // dual unbounded: the initial set is empty
         else if (rc == 2) st = 3;
     }
-    if (threadIdx.x == 0) {
-        a.status[k] = st;
-        a.margin[k] = st == 0 ? T[(size_t)d * W + rhs] : (st == 1 ? -INFINITY : NAN);
+    if (threadIdx.x == 0) a.status[k] = st;
+    if (a.zonly) {  // the check LP is bounded (t >= 0): unbounded dual = empty set
+        if (threadIdx.x == 0) *a.zflag = st == 0 ? 0 : (st == 2 ? 1 : 2);
+        return;
     }
     // z*_j: the multiplier of row z_j (sign +1), clamped into the box -- where
     // B_k is tiny next to the t coefficient two nearly parallel unsafe
@@ -244,11 +314,45 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
     for (int j = threadIdx.x; j < a.i; j += LNT)
         fcol[j] = st == 0 ? fmin(fmax(-T[(size_t)d * W + m + j], a.zlo[j]), a.zhi[j]) : NAN;
     __syncthreads();
-    for (int j = threadIdx.x; j < a.i; j += LNT) a.zx[(size_t)k * a.i + j] = fcol[j];
+    // y* = B_k z*; the tableau's constraint rows are free now: y* in row 0
+    double* ys = T;
     for (int r = threadIdx.x; r < a.o; r += LNT) {
         double y = 0.0;
         for (int j = 0; j < a.i; ++j) y = fma(a.basis[((size_t)j * a.o + r) * a.S + k], fcol[j], y);
         a.yx[(size_t)k * a.o + r] = y;
+        if (r < W) ys[r] = y;
+    }
+    for (int j = threadIdx.x; j < a.i; j += LNT) a.zx[(size_t)k * a.i + j] = fcol[j];
+    __syncthreads();
+    // The margin is the primal objective at z*, max_u (U_u y* - upsilon_u):
+    // the value the reported counter-example attains.  The step checks
+    // itself: that value must equal the dual objective (no duality gap) and
+    // z* must meet the extra initial rows; otherwise the tableau has lost
+    // too much to rounding and the step reports KV_LP_FAILED.
+    if (threadIdx.x == 0) {
+        double t = -INFINITY;
+        for (int u = 0; u < a.qu; ++u) {
+            double s = -a.v[u];
+            for (int r = 0; r < a.o; ++r) s = fma(a.U[(size_t)u * a.o + r], r < W ? ys[r] : a.yx[(size_t)k * a.o + r], s);
+            t = fmax(t, s);
+        }
+        if (st == 0) {
+            const double gap = fabs(t - T[(size_t)d * W + rhs]);
+            double zmax = 1.0;
+            for (int j = 0; j < a.i; ++j) zmax = fmax(zmax, fmax(fabs(a.zlo[j]), fabs(a.zhi[j])));
+            double viol = 0.0;
+            for (int q = 0; q < a.qi; ++q) {
+                double s = -a.iota[q], nq = 0.0;
+                for (int j = 0; j < a.i; ++j) {
+                    s = fma(a.Iz[(size_t)q * a.i + j], fcol[j], s);
+                    nq = fma(a.Iz[(size_t)q * a.i + j], a.Iz[(size_t)q * a.i + j], nq);
+                }
+                if (nq > 0.0) viol = fmax(viol, s / sqrt(nq));
+            }
+            if (gap > LP_GAP_REL * fmax(1.0, fabs(t)) || viol > LP_ROW_TOL * zmax) st = 1;
+        }
+        a.status[k] = st;
+        a.margin[k] = st == 0 ? t : NAN;
     }
 }
 
@@ -257,13 +361,26 @@ size_t lp_smem_bytes(int i, int m) {
     return ((d + 1) * W + (size_t)m + d + 1) * sizeof(double) + d * sizeof(int);
 }
 
+// Two launches: the emptiness check of the initial set (one CTA; the unsafe
+// part replaced by the single row t >= 0, so that its LP is bounded exactly
+// when the set is non-empty), then one CTA per step.  With a non-empty
+// initial set every step's LP is feasible and bounded (finite boxes).
 int launch_step_lp(const Prob* p, const double* dU, const double* dv, int qu, const double* dIz,
-                   const double* diota, int qi, int m, double* dmargin, int* dstatus, double* dzx, double* dyx) {
+                   const double* diota, int qi, int m, double* dmargin, int* dstatus, double* dzx, double* dyx,
+                   int* dzflag) {
     LpArgs a{p->d_basis, p->i, p->o, p->steps + 1, dU, dv, qu, dIz, diota, qi, p->d_zlo, p->d_zhi, m,
-             m + p->i + 2, 50 * (m + p->i + 1) + 100, dmargin, dstatus, dzx, dyx};
+             m + p->i + 2, 50 * (m + p->i + 1) + 100, dmargin, dstatus, dzx, dyx, 1, dzflag};
     const size_t sm = lp_smem_bytes(p->i, m);
     if (sm > 48 * 1024)
         KV_CHECK_CUDA(cudaFuncSetAttribute(k_step_lp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    LpArgs z = a;  // the check: one unsafe row (0 . z - t <= 0)
+    z.qu = 1;
+    z.m = 1 + qi + 2 * p->i;
+    z.W = z.m + p->i + 2;
+    z.max_iter = 50 * (z.m + p->i + 1) + 100;
+    k_step_lp<<<1, LNT, lp_smem_bytes(p->i, z.m), p->ctx->stream>>>(z);
+    KV_CHECK_CUDA(cudaGetLastError());
+    a.zonly = 0;
     k_step_lp<<<(unsigned)(p->steps + 1), LNT, sm, p->ctx->stream>>>(a);
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;

@@ -1133,8 +1133,8 @@ int kv_check_polytope(kv_prob* p, const kv_polytope* unsafe, const kv_polytope* 
     Ctx* c = p->ctx;
     // one arena block: U, v, Iz, iota, margin, zx, yx (doubles), status (ints)
     const size_t nd = (size_t)qu * o + qu + (size_t)qi * i + qi + S + (size_t)S * i + (size_t)S * o;
-    char* buf = (char*)c->arena.alloc(nd * 8 + (size_t)S * 4);
-    if (!buf) return fail(KV_ENOMEM, "kv_check_polytope: device pool exhausted (%zu bytes)", nd * 8 + (size_t)S * 4);
+    char* buf = (char*)c->arena.alloc(nd * 8 + (size_t)S * 4 + 4);
+    if (!buf) return fail(KV_ENOMEM, "kv_check_polytope: device pool exhausted (%zu bytes)", nd * 8 + (size_t)S * 4 + 4);
     double* dU = (double*)buf;
     double* dv = dU + (size_t)qu * o;
     double* dIz = dv + qu;
@@ -1143,6 +1143,7 @@ int kv_check_polytope(kv_prob* p, const kv_polytope* unsafe, const kv_polytope* 
     double* dzx = dmargin + S;
     double* dyx = dzx + (size_t)S * i;
     int* dstatus = (int*)(dyx + (size_t)S * o);
+    int* dzflag = dstatus + S;  // the initial set's emptiness, from the first launch
     std::vector<double> zx((size_t)S * i), yrow(o);
     auto run = [&]() -> int {
         int e = upload(c, dU, U.data(), U.size() * 8);
@@ -1150,7 +1151,7 @@ int kv_check_polytope(kv_prob* p, const kv_polytope* unsafe, const kv_polytope* 
         if (!e && qi) e = upload(c, dIz, init->a, (size_t)qi * i * 8);
         if (!e && qi) e = upload(c, diota, init->rhs, (size_t)qi * 8);
         if (!e) KV_CHECK_CUDA(cudaStreamWaitEvent(c->stream, p->done_ev, 0));
-        if (!e) e = launch_step_lp(p, dU, dv, qu, dIz, diota, qi, m, dmargin, dstatus, dzx, dyx);
+        if (!e) e = launch_step_lp(p, dU, dv, qu, dIz, diota, qi, m, dmargin, dstatus, dzx, dyx, dzflag);
         if (e) return e;
         KV_CHECK_CUDA(cudaMemcpyAsync(r->margin, dmargin, (size_t)S * 8, cudaMemcpyDeviceToHost, c->stream));
         KV_CHECK_CUDA(cudaMemcpyAsync(r->status, dstatus, (size_t)S * 4, cudaMemcpyDeviceToHost, c->stream));

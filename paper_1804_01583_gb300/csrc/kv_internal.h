@@ -250,7 +250,8 @@ size_t csr_xi_bytes(const Prob* p);  // interleaved SpMM input (0 if no candidat
 // per-step LP for polyhedral sets (k_lp.cu)
 size_t lp_smem_bytes(int i, int m);
 int launch_step_lp(const Prob* p, const double* dU, const double* dv, int qu, const double* dIz,
-                   const double* diota, int qi, int m, double* dmargin, int* dstatus, double* dzx, double* dyx);
+                   const double* diota, int qi, int m, double* dmargin, int* dstatus, double* dzx, double* dyx,
+                   int* dzflag);
 size_t csr_arnoldi_dev_bytes();
 
 // exponential + basis (k_expm.cu)

@@ -201,7 +201,7 @@ def test_autotuner_cache(ctx, tmp_path, monkeypatch):
     lines = path.read_text().strip().splitlines()
     assert len(lines) == 1
     key, g, l, us = lines[0].split()
-    assert int(g) in (1, 2, 4, 8, -4, -8, -16) and int(l) in (1, 2, 4) and "n=120000" in key and "cols=8" in key
+    assert int(g) in (1, 2, 4, 8, -4, -8, -16) and int(l) in (0, 1, 2, 4) and "n=120000" in key and "cols=8" in key
 
 
 # (G, LPR) per precision: G < 0 gathers from the row-interleaved copy of -G columns
