@@ -74,7 +74,48 @@ def step_lp(B: np.ndarray, zlo, zhi, U, v, Iz=None, iota=None):
         return UNBOUNDED, -np.inf, np.full(i, np.nan)
     if res.status != 0:
         raise RuntimeError(f"linprog: {res.message}")
-    return OPTIMAL, float(res.fun), np.asarray(res.x[:i])
+    x = _vertex(np.vstack(rows), np.concatenate(rhs), bounds, np.asarray(res.x))
+    return OPTIMAL, float(x[i]), x[:i]
+
+
+def _vertex(A, b, bounds, x):
+    """HiGHS stops at 1e-10 feasibility; an optimum of an LP is attained at a
+    vertex, the solution of its active constraints, so the oracle solves the
+    constraints active at HiGHS's point (rows within 1e-8 of equality and
+    bounds within 1e-9) as a linear system.  The vertex replaces HiGHS's
+    point when it is feasible to 1e-12 and no worse; t is then recomputed
+    from z as max_u (U_u B z - upsilon_u), i.e. the last column of A."""
+    n = len(x)
+    rows, rhs = [], []
+    for r in range(len(b)):
+        if abs(b[r] - A[r] @ x) <= 1e-8 * (1.0 + abs(b[r])):
+            rows.append(A[r])
+            rhs.append(b[r])
+    for j, (lo, hi) in enumerate(bounds):
+        for bd in (lo, hi):
+            if bd is not None and abs(x[j] - bd) <= 1e-9 * (1.0 + abs(bd)):
+                e = np.zeros(n)
+                e[j] = 1.0
+                rows.append(e)
+                rhs.append(bd)
+    if len(rows) < n:
+        return x
+    M, r = np.array(rows), np.array(rhs)
+    if np.linalg.matrix_rank(M) < n:
+        return x
+    y = np.linalg.lstsq(M, r, rcond=None)[0]
+    z = y[:-1].copy()
+    for j, (lo, hi) in enumerate(bounds[:-1]):
+        if lo is not None:
+            z[j] = max(z[j], lo)
+        if hi is not None:
+            z[j] = min(z[j], hi)
+    unsafe = A[:, -1] != 0.0   # rows with the t coefficient
+    t = float(np.max(A[unsafe, :-1] @ z - b[unsafe]))
+    y = np.append(z, t)
+    if np.all(A @ y <= b + 1e-12 * (1.0 + np.abs(b))) and t <= x[-1] + 1e-9:
+        return y
+    return x
 
 
 def check(basis_all, zlo, zhi, U, v, Iz=None, iota=None, tol: float = 0.0) -> Dict:
