@@ -580,6 +580,35 @@ def arnoldi_bytes(p) -> float:
     return tot
 
 
+def polytope_leg(ph, p) -> dict:
+    """The per-step LP of Sec. 2.1 on a finished query (kv_check_polytope):
+    an unsafe triangle in the 2-D output plane (y1 >= a, y2 >= b,
+    y1 + y2 <= c with a, b at 40% of the outputs' peak upper bounds) and a
+    budget row on the 16 generators (sum z_j <= 4): one LP per step, i + 1 =
+    18 rows, 38 constraints.  Host wall time of the call (uploads, the two
+    launches, result copies)."""
+    import torch
+    r = ph.fetch(full=False)
+    a, b = 0.4 * float(np.max(r["hi"][0])), 0.4 * float(np.max(r["hi"][1]))
+    U = np.array([[-1.0, 0.0], [0.0, -1.0], [1.0, 1.0]])
+    v = np.array([-a, -b, 3.0 * (abs(a) + abs(b))])
+    Iz = np.zeros((1, p.i))
+    Iz[0, :min(16, p.i)] = 1.0
+    iota = np.array([4.0])
+    ph.check_polytope(U, v, Iz, iota)  # warm-up
+    reps, t = 3, []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        res = ph.check_polytope(U, v, Iz, iota)
+        t.append((time.perf_counter() - t0) * 1e3)
+    ms = statistics.median(t)
+    S = p.steps + 1
+    return {"ms_per_check": ms, "lps_per_s": S / (ms * 1e-3), "steps": S, "lp_rows": p.i + 1,
+            "constraints": 3 + 1 + 2 * p.i, "first_violation_step": int(res["viol_step"]),
+            "failed_steps": int(np.sum(res["status"] != 0)),
+            "note": "host wall time of kv_check_polytope (uploads, 2 launches, result copies)"}
+
+
 def csr_bench(args, dev: int, n: int = 2_000_000, legs=None):
     """The random-CSR workload (n = 2e6, 16 generators + the fixed column,
     m = 60, 2000 steps) in FP64 and FP32: time per query, Arnoldi GB/s; and
@@ -610,6 +639,9 @@ def csr_bench(args, dev: int, n: int = 2_000_000, legs=None):
             nl, tms = ctx.profile_read(name)
             if nl:
                 kern[name] = {"launches": nl // k, "ms_per_query": tms / k}
+        lp = None
+        if prec == "fp32" and sim == "forward":
+            lp = polytope_leg(ph, p)
         ph.close()
         sysh.close()
         ctx.close()
@@ -617,6 +649,8 @@ def csr_bench(args, dev: int, n: int = 2_000_000, legs=None):
         key = prec if sim == "forward" else prec + "_transposed"
         out[key] = {"ms_per_query": ms, "runs": runs, "arnoldi_steps_per_s": runs * p.m / (ms * 1e-3),
                     "kernels": kern}
+        if lp:
+            out[key]["polytope"] = lp
         if sim == "forward":
             out[key]["arnoldi_GBps"] = arnoldi_bytes(p) / (ms * 1e-3) / 1e9
     if "fp64" in out and "fp32" in out:

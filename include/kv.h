@@ -392,11 +392,11 @@ typedef struct {
 
 /* The per-step LPs for a problem whose results are complete (after kv_run, or
  * kv_enqueue + kv_fetch): one CTA per step on the device (dense two-phase
- * simplex on the LP's dual in shared memory) over the basis
+ * simplex on the LP's dual in shared memory, double-double tableau) over the basis
  * kept on the device, on the context's stream; the call waits for them.
  * unsafe: rows over the o outputs (rows >= 1, no zero row); init: rows over
  * the i columns or NULL; every column's box must be finite.  The LP must fit
- * one CTA's shared memory: 8 ((i+2)(m+i+2) + m + i + 2) + 4 (i+1) bytes with
+ * one CTA's shared memory: 16 ((i+2)(m+i+2) + m + i + 2) + 4 (i+1) bytes with
  * m = unsafe rows + init rows + 2 i, at most the device's opt-in limit
  * (232448 bytes on GB300).  Temporary device memory (about 8 (steps+1)(i+o+2)
  * bytes) comes from the context's pool.  Errors: KV_EINVAL (bad argument, the

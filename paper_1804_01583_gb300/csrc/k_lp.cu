@@ -15,26 +15,94 @@
 // by the two-phase dense simplex method (Dantzig pricing, Harris ratio test,
 // Bland's rule against cycling) on a tableau in shared memory: d = i + 1
 // equality rows (one per primal variable), one column per primal constraint
-// scaled to unit norm (the same half-space),
-// d artificial columns and the right-hand side.  The primal optimum is
-// t* = -(min b^T y) and the minimiser (z*, t*) is the simplex multiplier
-// vector, read from the reduced costs of the artificial columns.
+// scaled to unit norm (the same half-space), d artificial columns and the
+// right-hand side.  The minimiser (z*, t*) is the simplex multiplier vector,
+// read from the reduced costs of the artificial columns.
+//
+// The tableau is kept in double-double arithmetic (each entry an unevaluated
+// sum hi + lo of two doubles, about 106 bits).  Outputs that depend only
+// weakly on some columns of E (a basis entry of 1e-7 next to the unit t
+// coefficient) force small but genuine pivots, whose element growth turns
+// exact zeros into double-precision noise of 1e-11 that a later pivot can
+// take for a real entry; at 106 bits that noise is ~1e-27, far below the
+// pivot threshold, while genuine entries of 1e-12 stay usable.
 #include <limits.h>
 #include <math.h>
-
-#include <vector>
 
 #include "kv_internal.h"
 
 namespace kv {
 
 constexpr int LNT = 256;
-constexpr double LP_EPS_PIV = 1e-11;   // smallest usable pivot (columns have unit norm)
+constexpr double LP_EPS_PIV = 1e-13;   // smallest usable pivot (columns start with unit norm)
 constexpr double LP_EPS_FEAS = 1e-9;   // phase-1 optimum above this: the dual is infeasible
-constexpr double LP_EPS_RC = 1e-10;    // entering threshold on reduced costs (x the largest cost in phase 2)
-constexpr double LP_HARRIS = 1e-11;    // right-hand-side relaxation of the Harris ratio test
+// Reduced costs and right-hand sides are double-double accurate, so the
+// entering threshold can resolve improvements of the margin far below the
+// size of the basis entries (a generator that moves the outputs by 1e-7
+// changes the margin by ~1e-10).
+constexpr double LP_EPS_RC = 1e-14;    // entering threshold on reduced costs (x the largest cost in phase 2)
+constexpr double LP_HARRIS = 1e-14;    // right-hand-side relaxation of the Harris ratio test
 constexpr double LP_GAP_REL = 1e-8;    // largest primal-dual gap of an accepted step (relative)
 constexpr double LP_ROW_TOL = 1e-7;    // largest violation of an extra initial row by z* (x the box size)
+
+// ---------------------------------------------------------------- double-double
+// Error-free transformations (Knuth's TwoSum, Dekker's fast two-sum for
+// |a| >= |b|, the FMA form of the exact product) and the double-double sum,
+// product and quotient built from them.  The _rn intrinsics keep the
+// compiler from contracting or reassociating the error terms.
+struct dd {
+    double h, l;
+};
+__device__ __forceinline__ dd two_sum(double a, double b) {
+    const double s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    return {s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
+}
+__device__ __forceinline__ dd fast_two_sum(double a, double b) {
+    const double s = __dadd_rn(a, b);
+    return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ __forceinline__ dd two_prod(double a, double b) {
+    const double p = __dmul_rn(a, b);
+    return {p, __fma_rn(a, b, -p)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+    dd s = two_sum(a.h, b.h);
+    const dd t = two_sum(a.l, b.l);
+    s.l = __dadd_rn(s.l, t.h);
+    s = fast_two_sum(s.h, s.l);
+    s.l = __dadd_rn(s.l, t.l);
+    return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+    dd p = two_prod(a.h, b.h);
+    p.l = __fma_rn(a.h, b.l, p.l);
+    p.l = __fma_rn(a.l, b.h, p.l);
+    return fast_two_sum(p.h, p.l);
+}
+__device__ __forceinline__ dd dd_div(dd a, dd b) {  // long division, three quotient digits
+    const double q1 = __ddiv_rn(a.h, b.h);
+    dd r = dd_add(a, dd_neg(dd_mul({q1, 0.0}, b)));
+    const double q2 = __ddiv_rn(r.h, b.h);
+    r = dd_add(r, dd_neg(dd_mul({q2, 0.0}, b)));
+    const double q3 = __ddiv_rn(r.h, b.h);
+    return dd_add(fast_two_sum(q1, q2), {q3, 0.0});
+}
+__device__ __forceinline__ double dd_val(dd a) { return a.h + a.l; }
+
+// The tableau: (d + 1) rows of W entries, hi and lo parts apart.
+struct Tab {
+    double* h;
+    double* l;
+    int W;
+    __device__ dd at(int r, int c) const { return {h[(size_t)r * W + c], l[(size_t)r * W + c]}; }
+    __device__ double hi(int r, int c) const { return h[(size_t)r * W + c]; }
+    __device__ void set(int r, int c, dd x) const {
+        h[(size_t)r * W + c] = x.h;
+        l[(size_t)r * W + c] = x.l;
+    }
+};
 
 struct LpArgs {
     const double* basis;  // [j][r][k], i x o x S
@@ -60,21 +128,22 @@ struct LpArgs {
 
 struct LpShared {
     int enter, leave, degen;
-    double piv;
+    dd piv;
 };
 
 // Pivot on row kp, column e: row kp /= T[kp][e], then every other row
 // (the objective row d included) loses its multiple of row kp.
-__device__ void lp_pivot(double* T, int* bas, double* fcol, int d, int W, int kp, int e, LpShared& sh) {
-    if (threadIdx.x == 0) sh.piv = T[(size_t)kp * W + e];
+__device__ void lp_pivot(const Tab& T, int* bas, dd* fcol, int d, int kp, int e, LpShared& sh) {
+    const int W = T.W;
+    if (threadIdx.x == 0) sh.piv = T.at(kp, e);
     __syncthreads();
-    for (int c = threadIdx.x; c < W; c += LNT) T[(size_t)kp * W + c] = c == e ? 1.0 : T[(size_t)kp * W + c] / sh.piv;
-    for (int r = threadIdx.x; r <= d; r += LNT) fcol[r] = r == kp ? 0.0 : T[(size_t)r * W + e];
+    for (int c = threadIdx.x; c < W; c += LNT) T.set(kp, c, c == e ? dd{1.0, 0.0} : dd_div(T.at(kp, c), sh.piv));
+    for (int r = threadIdx.x; r <= d; r += LNT) fcol[r] = r == kp ? dd{0.0, 0.0} : T.at(r, e);
     __syncthreads();
     for (int idx = threadIdx.x; idx < (d + 1) * W; idx += LNT) {
         const int r = idx / W, c = idx - r * W;
-        if (r == kp || fcol[r] == 0.0) continue;
-        T[idx] = c == e ? 0.0 : T[idx] - fcol[r] * T[(size_t)kp * W + c];
+        if (r == kp || (fcol[r].h == 0.0 && fcol[r].l == 0.0)) continue;
+        T.set(r, c, c == e ? dd{0.0, 0.0} : dd_add(T.at(r, c), dd_neg(dd_mul(fcol[r], T.at(kp, c)))));
     }
     if (threadIdx.x == 0) bas[kp] = e;
     __syncthreads();
@@ -86,11 +155,11 @@ __device__ void lp_pivot(double* T, int* bas, double* fcol, int d, int W, int kp
 // Pricing: the most negative reduced cost (Dantzig), ratio test: Harris's
 // two passes (the smallest ratio with the right-hand sides relaxed by
 // LP_HARRIS, then the largest pivot among the rows within it) -- few pivots
-// and no tiny pivots, so little rounding accumulates in the tableau.  After
-// more than d degenerate pivots in a row the phase switches to Bland's rule
-// (smallest entering index, smallest basic index among the tied rows whose
-// pivot is not tiny) until a pivot makes progress, which rules out cycling.
-__device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, double eps_rc, int max_iter,
+// and no tiny pivots.  After more than d degenerate pivots in a row the
+// phase switches to Bland's rule (smallest entering index, smallest basic
+// index among the tied rows whose pivot is not tiny) until a pivot makes
+// progress, which rules out cycling.  Decisions use the hi parts.
+__device__ int lp_phase(const Tab& T, int* bas, dd* fcol, int d, int m, double eps_rc, int max_iter,
                         LpShared& sh) {
     const int rhs = m + d;
     __shared__ double wval[LNT / 32];
@@ -103,7 +172,7 @@ __device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, 
         double bv = -eps_rc;
         int bi = INT_MAX;
         for (int c = threadIdx.x; c < m; c += LNT) {
-            const double x = T[(size_t)d * W + c];
+            const double x = T.hi(d, c);
             if (x < -eps_rc && (bland ? c < bi : (x < bv || (x == bv && c < bi)))) {
                 bv = x;
                 bi = c;
@@ -139,17 +208,16 @@ __device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, 
             const int lane = threadIdx.x;
             double q = INFINITY;
             for (int r = lane; r < d; r += 32) {
-                const double a = T[(size_t)r * W + e];
-                if (a > LP_EPS_PIV)
-                    q = fmin(q, (fmax(T[(size_t)r * W + rhs], 0.0) + (bland ? 0.0 : LP_HARRIS)) / a);
+                const double a = T.hi(r, e);
+                if (a > LP_EPS_PIV) q = fmin(q, (fmax(T.hi(r, rhs), 0.0) + (bland ? 0.0 : LP_HARRIS)) / a);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) q = fmin(q, __shfl_xor_sync(0xffffffffu, q, o));
             const double qtie = bland ? q + 1e-12 * (1.0 + q) : q;
             double amax = 0.0;
             for (int r = lane; r < d; r += 32) {
-                const double a = T[(size_t)r * W + e];
-                if (a > LP_EPS_PIV && fmax(T[(size_t)r * W + rhs], 0.0) / a <= qtie) amax = fmax(amax, a);
+                const double a = T.hi(r, e);
+                if (a > LP_EPS_PIV && fmax(T.hi(r, rhs), 0.0) / a <= qtie) amax = fmax(amax, a);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -157,8 +225,8 @@ __device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, 
             // smallest basic index among pivots not tiny next to the largest
             int best = INT_MAX, brow = -1;
             for (int r = lane; r < d; r += 32) {
-                const double a = T[(size_t)r * W + e];
-                if (!(a > LP_EPS_PIV) || fmax(T[(size_t)r * W + rhs], 0.0) / a > qtie) continue;
+                const double a = T.hi(r, e);
+                if (!(a > LP_EPS_PIV) || fmax(T.hi(r, rhs), 0.0) / a > qtie) continue;
                 const int key = bland ? (a >= 1e-3 * amax ? bas[r] : INT_MAX) : (a == amax ? r : INT_MAX);
                 if (key < best) {
                     best = key;
@@ -177,14 +245,14 @@ __device__ int lp_phase(double* T, int* bas, double* fcol, int d, int m, int W, 
             if (lane == 0) {
                 sh.leave = q == INFINITY ? -1 : brow;
                 if (brow >= 0) {
-                    const double step = fmax(T[(size_t)brow * W + rhs], 0.0) / T[(size_t)brow * W + e];
+                    const double step = fmax(T.hi(brow, rhs), 0.0) / T.hi(brow, e);
                     sh.degen = step <= 1e-12 ? sh.degen + 1 : 0;
                 }
             }
         }
         __syncthreads();
         if (sh.leave < 0) return 1;
-        lp_pivot(T, bas, fcol, d, W, sh.leave, e, sh);
+        lp_pivot(T, bas, fcol, d, sh.leave, e, sh);
     }
 }
 
@@ -202,75 +270,77 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
         for (int r = threadIdx.x; r < a.o; r += LNT) a.yx[(size_t)k * a.o + r] = NAN;
         return;
     }
-    double* T = smem;                        // (d + 1) x W; row d is the objective
-    double* cost = T + (size_t)(d + 1) * W;  // m: b of the dual (scaled)
-    double* fcol = cost + m;                 // d + 1
+    const size_t NT = (size_t)(d + 1) * W;
+    const Tab T{smem, smem + NT, W};         // row d is the objective
+    dd* cost = (dd*)(smem + 2 * NT);         // m: b of the dual (scaled)
+    dd* fcol = cost + m;                     // d + 1
     int* bas = (int*)(fcol + d + 1);         // d
     // primal constraint columns, unscaled: A[col][row] with row = z_0..z_{i-1}, t
     const int nbox0 = a.qu + a.qi;
-    for (int idx = threadIdx.x; idx < (d + 1) * W; idx += LNT) T[idx] = 0.0;
-    for (int c = threadIdx.x; c < m; c += LNT) cost[c] = 0.0;
+    for (size_t idx = threadIdx.x; idx < 2 * NT; idx += LNT) smem[idx] = 0.0;
+    for (int c = threadIdx.x; c < m; c += LNT) cost[c] = {0.0, 0.0};
     __syncthreads();
     for (int idx = threadIdx.x; idx < (a.zonly ? 0 : a.qu * a.i); idx += LNT) {  // U_u B_k e_j
         const int u = idx / a.i, j = idx - u * a.i;
         double s = 0.0;
         for (int r = 0; r < a.o; ++r) s = fma(a.U[(size_t)u * a.o + r], a.basis[((size_t)j * a.o + r) * a.S + k], s);
-        T[(size_t)j * W + u] = s;
+        T.h[(size_t)j * W + u] = s;
     }
     for (int u = threadIdx.x; u < a.qu; u += LNT) {
-        T[(size_t)a.i * W + u] = -1.0;  // the t coefficient
-        cost[u] = a.zonly ? 0.0 : a.v[u];
+        T.h[(size_t)a.i * W + u] = -1.0;  // the t coefficient
+        cost[u] = {a.zonly ? 0.0 : a.v[u], 0.0};
     }
     for (int idx = threadIdx.x; idx < a.qi * a.i; idx += LNT) {
         const int q = idx / a.i, j = idx - q * a.i;
-        T[(size_t)j * W + a.qu + q] = a.Iz[(size_t)q * a.i + j];
+        T.h[(size_t)j * W + a.qu + q] = a.Iz[(size_t)q * a.i + j];
     }
-    for (int q = threadIdx.x; q < a.qi; q += LNT) cost[a.qu + q] = a.iota[q];
+    for (int q = threadIdx.x; q < a.qi; q += LNT) cost[a.qu + q] = {a.iota[q], 0.0};
     if (threadIdx.x == 0) {  // finite box sides, in column order
         int c = nbox0;
         for (int j = 0; j < a.i; ++j) {
             if (isfinite(a.zhi[j])) {
-                T[(size_t)j * W + c] = 1.0;
-                cost[c++] = a.zhi[j];
+                T.h[(size_t)j * W + c] = 1.0;
+                cost[c++] = {a.zhi[j], 0.0};
             }
             if (isfinite(a.zlo[j])) {
-                T[(size_t)j * W + c] = -1.0;
-                cost[c++] = -a.zlo[j];
+                T.h[(size_t)j * W + c] = -1.0;
+                cost[c++] = {-a.zlo[j], 0.0};
             }
         }
     }
     __syncthreads();
-    // unit-norm columns; the t row is negated so that the right-hand side
+    // unit-norm columns (exact double-double products of the double data and
+    // the double scale); the t row is negated so that the right-hand side
     // -c = -e_t becomes +1 (all right-hand sides >= 0); artificial identity;
     // phase-1 objective: minimise the sum of the artificials
     for (int c = threadIdx.x; c < m; c += LNT) {
         double nrm = 0.0;
-        for (int r = 0; r < d; ++r) nrm = fma(T[(size_t)r * W + c], T[(size_t)r * W + c], nrm);
+        for (int r = 0; r < d; ++r) nrm = fma(T.hi(r, c), T.hi(r, c), nrm);
         nrm = sqrt(nrm);
         const double sc = nrm > 0.0 ? 1.0 / nrm : 1.0;
-        double colsum = 0.0;
+        dd colsum{0.0, 0.0};
         for (int r = 0; r < d; ++r) {
-            const double x = T[(size_t)r * W + c] * sc * (r == a.i ? -1.0 : 1.0);
-            T[(size_t)r * W + c] = x;
-            colsum += x;
+            const dd x = two_prod(T.hi(r, c) * (r == a.i ? -1.0 : 1.0), sc);
+            T.set(r, c, x);
+            colsum = dd_add(colsum, x);
         }
-        cost[c] *= sc;
-        T[(size_t)d * W + c] = -colsum;
+        cost[c] = two_prod(cost[c].h, sc);
+        T.set(d, c, dd_neg(colsum));
     }
     for (int r = threadIdx.x; r < d; r += LNT) {
-        T[(size_t)r * W + m + r] = 1.0;
-        T[(size_t)r * W + rhs] = r == a.i ? 1.0 : 0.0;
+        T.set(r, m + r, {1.0, 0.0});
+        T.set(r, rhs, {r == a.i ? 1.0 : 0.0, 0.0});
         bas[r] = m + r;
     }
-    if (threadIdx.x == 0) T[(size_t)d * W + rhs] = -1.0;
+    if (threadIdx.x == 0) T.set(d, rhs, {-1.0, 0.0});
     __syncthreads();
 
     int st = 0;  // KV_LP_OPTIMAL
     // phase 1 is bounded below by 0: a column without a pivot there is rounding
     // noise in its reduced cost, and the sum of artificials decides
-    int rc = lp_phase(T, bas, fcol, d, m, W, LP_EPS_RC, a.max_iter, sh);
-    if (rc == 2) st = 3;                                      // KV_LP_ITER
-    else if (-T[(size_t)d * W + rhs] > LP_EPS_FEAS) st = 1;  // KV_LP_FAILED
+    int rc = lp_phase(T, bas, fcol, d, m, LP_EPS_RC, a.max_iter, sh);
+    if (rc == 2) st = 3;                                  // KV_LP_ITER
+    else if (-dd_val(T.at(d, rhs)) > LP_EPS_FEAS) st = 1;  // KV_LP_FAILED
     if (st == 0) {
         // basic artificials at level zero leave the basis where a structural
         // column can replace them (else their row is redundant)
@@ -279,30 +349,29 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
             if (threadIdx.x == 0) sh.enter = INT_MAX;
             __syncthreads();
             for (int c = threadIdx.x; c < m; c += LNT)
-                if (fabs(T[(size_t)r * W + c]) > 1e-9) {
+                if (fabs(T.hi(r, c)) > 1e-9) {
                     atomicMin(&sh.enter, c);
                     break;
                 }
             __syncthreads();
-            if (sh.enter != INT_MAX) lp_pivot(T, bas, fcol, d, W, r, sh.enter, sh);
+            if (sh.enter != INT_MAX) lp_pivot(T, bas, fcol, d, r, sh.enter, sh);
         }
         // phase 2: the dual's costs, reduced against the current basis
         double cmax = 0.0;
-        for (int c = 0; c < m; ++c) cmax = fmax(cmax, fabs(cost[c]));
+        for (int c = 0; c < m; ++c) cmax = fmax(cmax, fabs(cost[c].h));
         for (int c = threadIdx.x; c < W; c += LNT) {
-            double x = c < m ? cost[c] : 0.0;
+            dd x = c < m ? cost[c] : dd{0.0, 0.0};
             for (int r = 0; r < d; ++r) {
                 const int bc = bas[r];
-                if (bc < m) x = fma(-cost[bc], T[(size_t)r * W + c], x);
+                if (bc < m) x = dd_add(x, dd_neg(dd_mul(cost[bc], T.at(r, c))));
             }
-            T[(size_t)d * W + c] = x;
+            T.set(d, c, x);
         }
         __syncthreads();
-        rc = lp_phase(T, bas, fcol, d, m, W, LP_EPS_RC * fmax(1.0, cmax), a.max_iter, sh);
+        rc = lp_phase(T, bas, fcol, d, m, LP_EPS_RC * fmax(1.0, cmax), a.max_iter, sh);
         if (rc == 1) st = 2;       // dual unbounded: the initial set is empty
         else if (rc == 2) st = 3;
     }
-    if (threadIdx.x == 0) a.status[k] = st;
     if (a.zonly) {  // the check LP is bounded (t >= 0): unbounded dual = empty set
         if (threadIdx.x == 0) *a.zflag = st == 0 ? 0 : (st == 2 ? 1 : 2);
         return;
@@ -311,24 +380,26 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
     // B_k is tiny next to the t coefficient two nearly parallel unsafe
     // columns can share the optimal basis and leave z* off the box by the
     // rounding of that ill-conditioned solve (the margin is unaffected)
-    for (int j = threadIdx.x; j < a.i; j += LNT)
-        fcol[j] = st == 0 ? fmin(fmax(-T[(size_t)d * W + m + j], a.zlo[j]), a.zhi[j]) : NAN;
+    double* zs = (double*)fcol;  // free now: 2 (d + 1) >= i doubles
     __syncthreads();
-    // y* = B_k z*; the tableau's constraint rows are free now: y* in row 0
-    double* ys = T;
+    for (int j = threadIdx.x; j < a.i; j += LNT)
+        zs[j] = st == 0 ? fmin(fmax(-dd_val(T.at(d, m + j)), a.zlo[j]), a.zhi[j]) : NAN;
+    __syncthreads();
+    // y* = B_k z*; the tableau's first row is free now
+    double* ys = T.h;
     for (int r = threadIdx.x; r < a.o; r += LNT) {
         double y = 0.0;
-        for (int j = 0; j < a.i; ++j) y = fma(a.basis[((size_t)j * a.o + r) * a.S + k], fcol[j], y);
+        for (int j = 0; j < a.i; ++j) y = fma(a.basis[((size_t)j * a.o + r) * a.S + k], zs[j], y);
         a.yx[(size_t)k * a.o + r] = y;
         if (r < W) ys[r] = y;
     }
-    for (int j = threadIdx.x; j < a.i; j += LNT) a.zx[(size_t)k * a.i + j] = fcol[j];
+    for (int j = threadIdx.x; j < a.i; j += LNT) a.zx[(size_t)k * a.i + j] = zs[j];
     __syncthreads();
     // The margin is the primal objective at z*, max_u (U_u y* - upsilon_u):
     // the value the reported counter-example attains.  The step checks
     // itself: that value must equal the dual objective (no duality gap) and
-    // z* must meet the extra initial rows; otherwise the tableau has lost
-    // too much to rounding and the step reports KV_LP_FAILED.
+    // z* must meet the extra initial rows; otherwise rounding has spoilt the
+    // tableau and the step reports KV_LP_FAILED.
     if (threadIdx.x == 0) {
         double t = -INFINITY;
         for (int u = 0; u < a.qu; ++u) {
@@ -337,14 +408,14 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
             t = fmax(t, s);
         }
         if (st == 0) {
-            const double gap = fabs(t - T[(size_t)d * W + rhs]);
+            const double gap = fabs(t - dd_val(T.at(d, rhs)));
             double zmax = 1.0;
             for (int j = 0; j < a.i; ++j) zmax = fmax(zmax, fmax(fabs(a.zlo[j]), fabs(a.zhi[j])));
             double viol = 0.0;
             for (int q = 0; q < a.qi; ++q) {
                 double s = -a.iota[q], nq = 0.0;
                 for (int j = 0; j < a.i; ++j) {
-                    s = fma(a.Iz[(size_t)q * a.i + j], fcol[j], s);
+                    s = fma(a.Iz[(size_t)q * a.i + j], zs[j], s);
                     nq = fma(a.Iz[(size_t)q * a.i + j], a.Iz[(size_t)q * a.i + j], nq);
                 }
                 if (nq > 0.0) viol = fmax(viol, s / sqrt(nq));
@@ -358,7 +429,7 @@ __global__ void __launch_bounds__(LNT) k_step_lp(LpArgs a) {
 
 size_t lp_smem_bytes(int i, int m) {
     const size_t d = (size_t)i + 1, W = (size_t)m + d + 1;
-    return ((d + 1) * W + (size_t)m + d + 1) * sizeof(double) + d * sizeof(int);
+    return (2 * (d + 1) * W + 2 * ((size_t)m + d + 1)) * sizeof(double) + d * sizeof(int);
 }
 
 // Two launches: the emptiness check of the initial set (one CTA; the unsafe
