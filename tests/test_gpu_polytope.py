@@ -25,7 +25,7 @@ def ctx():
         pytest.skip("no GPU")
     from paper_1804_01583_gb300 import build as kvbuild
     kvbuild.build()
-    c = kv.Context(16 << 30)
+    c = kv.Context(40 << 30)
     yield c
     c.close()
 
@@ -194,3 +194,39 @@ def test_lp_argument_errors(ctx):
     finally:
         ph.close()
         sysh.close()
+
+
+_FULL = {}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_random_csr_full_size_polygon(ctx, precision):
+    """The benchmark's LP leg at full size: the random-CSR query (n = 2e6,
+    i = 17, o = 2, m = 60, 2001 steps, PROPAGATE) with the unsafe triangle
+    and the generator budget; margins at every 40th step against the
+    oracle's LP on the oracle's basis (built by the transpose dynamics, two
+    runs, which the transpose pins tie to the forward basis)."""
+    if "ref" not in _FULL:
+        p64 = W.random_csr_problem(2_000_000, seed=0)
+        p64.simulate = "transpose"
+        r = oracle.run(p64)
+        B = np.stack([r["basis"][j] for j in range(p64.i)])
+        zlo = np.array([c.zlo for c in p64.columns])
+        zhi = np.array([c.zhi for c in p64.columns])
+        hi = oracle.bounds(B, zlo, zhi, np.full(2, np.inf))["hi"]
+        a, b = 0.4 * np.max(hi[0]), 0.4 * np.max(hi[1])
+        U = np.array([[-1.0, 0.0], [0.0, -1.0], [1.0, 1.0]])
+        v = np.array([-a, -b, 3.0 * (abs(a) + abs(b))])
+        Iz = np.zeros((1, p64.i))
+        Iz[0, :16] = 1.0
+        iota = np.array([4.0])
+        ks = np.arange(0, p64.steps + 1, 40)
+        ref = np.array([LP.step_lp(B[:, :, k].T, zlo, zhi, U, v, Iz, iota)[1] for k in ks])
+        _FULL["ref"] = (U, v, Iz, iota, ks, ref)
+    U, v, Iz, iota, ks, ref = _FULL["ref"]
+    p = W.random_csr_problem(2_000_000, seed=0, precision=precision)
+    _, got = gpu_lp(ctx, p, U, v, Iz, iota, expm_mode="propagate")
+    assert np.all(got["status"] == kv.KV_LP_OPTIMAL)
+    scale = np.max(np.abs(ref))
+    err = np.max(np.abs(got["margin"][ks] - ref)) / scale
+    assert err <= (1e-6 if precision == "fp32" else 1e-9), err
