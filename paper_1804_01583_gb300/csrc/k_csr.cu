@@ -409,44 +409,82 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
             x[k] = r < N ? Vl[r] : (T)0;
         }
     };
-    // this thread's products with basis vector l, reduced over the warp
-    auto dots = [&](const T (&x)[CR], int l) {
-        T at = 0, gt = 0;
+    // this thread's products with basis vector l
+    auto prod = [&](const T (&x)[CR], T& at, T& gt) {
+        at = 0;
+        gt = 0;
 #pragma unroll
         for (int k = 0; k < CR; ++k) {
             at = fma(x[k], wv[k], at);
             gt = fma(x[k], vv[k], gt);
         }
+    };
+    // the four sums of basis vectors l and l+1 (h1 and g of each) over the
+    // warp by a transposed butterfly: at the first two levels each lane
+    // hands half of what it holds to its partner, so the five levels cost 6
+    // additions instead of 20; lanes 0, 8, 16, 24 end with the four totals.
+    // FP32 form: float pairs (hi, lo) combined error-free; FP64: doubles.
+    auto reduce4 = [&](T a0, T g0, T a1, T g1, int l, bool two) {
+        const bool up = lane & 16, mid = lane & 8;
         if constexpr (std::is_same<T, float>::value) {
-            float ah = at, al = 0.f, gh = gt, gl = 0.f;
-            warp_sum_pair(ah, al);
-            warp_sum_pair(gh, gl);
-            if (lane == 0) {
-                wsumf[l][warp] = make_float2(ah, al);
-                wsumf[KV_MAX_M + 1 + l][warp] = make_float2(gh, gl);
+            float kh0 = up ? a1 : a0, kh1 = up ? g1 : g0, kl0 = 0.f, kl1 = 0.f;
+            const float s0 = up ? a0 : a1, s1 = up ? g0 : g1;
+            {
+                float t, e;
+                two_sum_f(kh0, __shfl_xor_sync(0xffffffffu, s0, 16), t, e);
+                kh0 = t;
+                kl0 = e;
+                two_sum_f(kh1, __shfl_xor_sync(0xffffffffu, s1, 16), t, e);
+                kh1 = t;
+                kl1 = e;
+            }
+            float h = mid ? kh1 : kh0, lo = mid ? kl1 : kl0;
+            {
+                const float sh = mid ? kh0 : kh1, sl = mid ? kl0 : kl1;
+                const float rh = __shfl_xor_sync(0xffffffffu, sh, 8);
+                const float rl = __shfl_xor_sync(0xffffffffu, sl, 8);
+                float t, e;
+                two_sum_f(h, rh, t, e);
+                h = t;
+                lo = __fadd_rn(__fadd_rn(lo, rl), e);
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                const float rh = __shfl_xor_sync(0xffffffffu, h, o);
+                const float rl = __shfl_xor_sync(0xffffffffu, lo, o);
+                float t, e;
+                two_sum_f(h, rh, t, e);
+                h = t;
+                lo = __fadd_rn(__fadd_rn(lo, rl), e);
+            }
+            if ((lane & 7) == 0 && (two || !up)) {
+                const int q = (up ? l + 1 : l) + (mid ? KV_MAX_M + 1 : 0);
+                wsumf[q][warp] = make_float2(h, lo);
             }
         } else {
-            double a = at, g = gt;
+            double k0 = up ? a1 : a0, k1 = up ? g1 : g0;
+            k0 += __shfl_xor_sync(0xffffffffu, up ? a0 : a1, 16);
+            k1 += __shfl_xor_sync(0xffffffffu, up ? g0 : g1, 16);
+            double x = (mid ? k1 : k0) + __shfl_xor_sync(0xffffffffu, mid ? k0 : k1, 8);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-                g += __shfl_xor_sync(0xffffffffu, g, o);
-            }
-            if (lane == 0) {
-                wsum[l][warp] = a;
-                wsum[KV_MAX_M + 1 + l][warp] = g;
+            for (int o = 4; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if ((lane & 7) == 0 && (two || !up)) {
+                const int q = (up ? l + 1 : l) + (mid ? KV_MAX_M + 1 : 0);
+                wsum[q][warp] = x;
             }
         }
     };
-    // two register buffers: the loads of vector l+1 are in flight while the
-    // products of vector l are formed and reduced
+    // two register buffers: the loads of the next vectors are in flight while
+    // the products of the current ones are formed and reduced
     load(xa, 0);
     for (int l = 0; l <= j; l += 2) {
-        if (l + 1 <= j) load(xb, l + 1);
-        dots(xa, l);
-        if (l + 1 > j) break;
+        const bool two = l + 1 <= j;
+        if (two) load(xb, l + 1);
+        T a0, g0, a1 = 0, g1 = 0;
+        prod(xa, a0, g0);
         if (l + 2 <= j) load(xa, l + 2);
-        dots(xb, l + 1);
+        if (two) prod(xb, a1, g1);
+        reduce4(a0, g0, a1, g1, l, two);
     }
     __syncthreads();
     const int K = j + 1;
