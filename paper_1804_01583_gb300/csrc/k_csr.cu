@@ -39,7 +39,7 @@ constexpr int CNT = 256;           // threads per block
 // no FP64 instruction per vector and can keep the rows per thread small)
 template <typename T>
 struct RowsPer {
-    static constexpr int v = 8;
+    static constexpr int v = 16;
 };
 template <>
 struct RowsPer<float> {
