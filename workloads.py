@@ -304,6 +304,61 @@ def oscillator(theta: float = 4.0) -> Problem:
                    name="oscillator")
 
 
+def paper_heat_factors(N: int, coef: float = 0.01, exchange: float = 0.5):
+    """The 1-D factors of the paper's heat model (Sec. 5.3: a unit cube,
+    every face insulated except x = 1, which exchanges heat with the ambient
+    (temperature 0) at constant `exchange`), discretised by cell-centred
+    finite volumes: N cells of width h = 1/N per axis, coupling coef/h^2
+    between neighbours, no flux through an insulated face.  At x = 1 the flux
+    -coef u_x = exchange u_b runs through the half cell next to the face;
+    eliminating the face value u_b leaves the last x-cell the diagonal term
+    -g/h with g = exchange (2 coef/h) / (2 coef/h + exchange).  Returns
+    (A_x, A_y, A_z) dense N x N: A = A_x (+) A_y (+) A_z (Kronecker sum, x
+    fastest), symmetric and negative definite."""
+    h = 1.0 / N
+    L = np.zeros((N, N))
+    for i in range(N - 1):
+        L[i, i + 1] = L[i + 1, i] = 1.0
+        L[i, i] -= 1.0
+        L[i + 1, i + 1] -= 1.0
+    Ay = (coef / h ** 2) * L
+    Ax = Ay.copy()
+    g = exchange * (2 * coef / h) / (2 * coef / h + exchange)
+    Ax[N - 1, N - 1] -= g / h
+    return Ax, Ay, Ay.copy()
+
+
+def paper_heat(N: int = 100, *, dt: float = 0.02, steps: int = 1000, m: int = 800, err_target: float = 0.0,
+               zlo: float = 0.9, zhi: float = 1.1, theta: float = math.inf, precision: str = "fp64",
+               coef: float = 0.01, exchange: float = 0.5) -> Problem:
+    """The paper's 3-D heat benchmark (Sec. 5.3) on N^3 cells: the model of
+    paper_heat_factors as a symmetric CSR matrix (7 entries per interior
+    row); the heated region x in [0, 0.4], y in [0, 0.2], z in [0, 0.1]
+    (cells whose centres lie in it) at a temperature in [zlo, zhi], one
+    column; the output is the temperature at the centre of the cube, the
+    mean of the 8 cells around it; T = 20 by dt = 0.02 (1000 steps)."""
+    import scipy.sparse as sp
+    Ax, Ay, Az = paper_heat_factors(N, coef, exchange)
+    I = sp.identity(N, format="csr")
+    A = (sp.kron(sp.kron(I, I), sp.csr_matrix(Ax)) + sp.kron(sp.kron(I, sp.csr_matrix(Ay)), I)
+         + sp.kron(sp.kron(sp.csr_matrix(Az), I), I)).tocsr()
+    A.sort_indices()
+    n = N ** 3
+    sysm = CsrSystem(n=n, row_ptr=A.indptr.astype(np.int64), col=A.indices.astype(np.int32),
+                     val=A.data.astype(np.float64), b=None, symmetric=True)
+    centres = (np.arange(N) + 0.5) / N
+    bx, by, bz = (int(np.sum(centres <= lim)) for lim in (0.4, 0.2, 0.1))
+    ix = np.arange(bx)
+    idx = (np.arange(bz)[:, None, None] * N * N + np.arange(by)[None, :, None] * N + ix[None, None, :]).ravel()
+    col = Column(kind="sparse", zlo=zlo, zhi=zhi, idx=np.sort(idx).astype(np.int64), val=np.ones(idx.size))
+    c = [N // 2 - 1, N // 2]
+    cells = [(z * N + y) * N + x for z in c for y in c for x in c]
+    rp, cc, cv = _c_rows([(cells, [0.125] * 8)])
+    return Problem(system=sysm, columns=[col], C_row_ptr=rp, C_col=cc, C_val=cv, theta=np.array([theta]),
+                   dt=dt, steps=steps, m=m, err_target=err_target, precision=precision,
+                   name=f"paper-heat3d-{N}^3")
+
+
 def replicated_blocks(h: int, *, seed: int = 0, dt: float = 0.1, steps: int = 300, m: int = 28,
                       theta: float = 0.45, precision: str = "fp64", simulate: str = "auto") -> Problem:
     """The replicated-helicopter shape of Sec. 5.2 with a stand-in block: the
