@@ -488,6 +488,43 @@ def error_control_bench(dev: int):
     return out
 
 
+def paper_heat_bench(dev: int):
+    """The paper's own 3-D heat experiment (Sec. 5.3): 100^3 cells of the
+    insulated cube with heat exchange at x = 1 (cell-centred reading), the
+    heated region [0,0.4]x[0,0.2]x[0,0.1], the centre output, T = 20 by 0.02,
+    Lemma-1 error control with target 1e-6 (Krylov dimension up to 800), CSR
+    Lanczos: the dimension the control picks (the paper reports 544 for its
+    discretisation), the bound, and the time per query."""
+    import torch
+    import paper_1804_01583_gb300 as kv
+    out = {}
+    ctx = kv.Context(8 << 30, device=dev)
+    try:
+        for prec in ("fp64", "fp32"):
+            p = W.paper_heat(100, precision=prec, err_target=1e-6)
+            sysh = kv.System(ctx, p.system, p.precision)
+            ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
+            ph.run(full=False)
+            torch.cuda.synchronize()
+            ctx.profile_enable(True)
+            t0 = time.perf_counter()
+            r = ph.run(full=True)
+            ms = (time.perf_counter() - t0) * 1e3
+            chk = sum(ctx.profile_read(nm)[1] for nm in ("error_expm", "error_bound"))
+            kry = sum(ctx.profile_read(nm)[1] for nm in ("csr_spmv", "csr_lanczos_update", "project"))
+            ctx.profile_enable(False)
+            out[prec] = {"m_used": int(r["m_used"][0]), "lemma1_bound": float(r["err_bound"][0]),
+                         "ms_per_query": ms, "checkpoint_ms": chk, "krylov_ms": kry,
+                         "peak_centre_temperature": float(np.max(r["hi"][0]))}
+            ph.close()
+            sysh.close()
+    finally:
+        ctx.close()
+    out["workload"] = ("paper heat3d 100^3 (insulated, exchange 0.5 at x = 1), centre output, dt 0.02, 1000 steps, "
+                       "m <= 800, target 1e-6; paper: k = 544")
+    return out
+
+
 def replicated_bench(dev: int, h: int = 20_000):
     """The replicated-block shape of Sec. 5.2 (n = 28 h, i = 8 h, o = 1, 300
     steps) at h = 20 000: one Krylov run of the transpose dynamics instead of
@@ -742,6 +779,7 @@ def main():
         line["batched"] = batched_bench(dev)
         line["error_control"] = error_control_bench(dev)
         line["replicated"] = replicated_bench(dev)
+        line["paper_heat"] = paper_heat_bench(dev)
     if args.csr and world == 1:
         line["csr_workload"] = csr_bench(args, dev)
     if args.serve and world == 1:
