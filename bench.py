@@ -488,7 +488,7 @@ def error_control_bench(dev: int):
     return out
 
 
-def paper_heat_bench(dev: int):
+def paper_heat_bench(dev: int, precisions=("fp64", "fp32")):
     """The paper's own 3-D heat experiment (Sec. 5.3): 100^3 cells of the
     insulated cube with heat exchange at x = 1 (cell-centred reading), the
     heated region [0,0.4]x[0,0.2]x[0,0.1], the centre output, T = 20 by 0.02,
@@ -500,7 +500,7 @@ def paper_heat_bench(dev: int):
     out = {}
     ctx = kv.Context(8 << 30, device=dev)
     try:
-        for prec in ("fp64", "fp32"):
+        for prec in precisions:
             p = W.paper_heat(100, precision=prec, err_target=1e-6)
             sysh = kv.System(ctx, p.system, p.precision)
             ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
@@ -723,6 +723,8 @@ def main():
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--csr-only", type=int, default=0, metavar="N",
                     help="only the random-CSR query (FP32, forward) at n = N (profiling case)")
+    ap.add_argument("--paper-heat-only", default="", choices=["", "fp64", "fp32"],
+                    help="only the paper's heat experiment (100^3, target 1e-6) in one precision (profiling case)")
     ap.add_argument("--serve-queries", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-pool-gb", type=int, default=160)
@@ -764,6 +766,15 @@ def main():
         torch.cuda.set_device(dev)
         print(json.dumps({"metric": "random-CSR query ms", "csr_workload":
                           csr_bench(args, dev, n=args.csr_only, legs=(("fp32", "forward"),))}))
+        return
+    if args.paper_heat_only:
+        import torch
+        from paper_1804_01583_gb300 import build as kvbuild
+        kvbuild.build()
+        dev = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(dev)
+        print(json.dumps({"metric": "paper heat query ms",
+                          "paper_heat": paper_heat_bench(dev, precisions=(args.paper_heat_only,))}))
         return
     if args.serve_only:
         import torch

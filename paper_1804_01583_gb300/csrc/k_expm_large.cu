@@ -18,11 +18,15 @@
 //      P_i = E^(2^i), U[:, 2^i + c] = P_i U[:, c] for c < 2^i, P_{i+1} = P_i^2;
 //   4. basis rows beta0 P U (o x (steps+1)) and the last row |U[k-1, :]|, the
 //      integrand of the Lemma-1 bound.
-// Every launch is sized for the largest dimension m and reads k from the
-// run's state; tiles beyond k return at once, and a checkpoint of a run that
-// has stopped does nothing.  The number of squaring launches is fixed
-// (SQ_LAUNCHES); those beyond the run's s copy instead, so the launch
-// sequence does not depend on device data (it can be captured in a graph).
+// Every launch is sized for the largest dimension m (for the checkpoint's
+// dimension at a checkpoint) and reads k from the run's state; tiles beyond k
+// return at once, and a checkpoint of a run that has stopped does nothing.
+// Products with at most 16 rows or columns (the first doubling stages, the
+// basis rows) run one thread per entry (k_dgemm_thin).  The number of
+// squaring launches is fixed (SQ_LAUNCHES); those beyond the run's s return
+// at once, the last one moving the result into the buffer the host reads
+// when s is odd, so the launch sequence does not depend on device data (it
+// can be captured in a graph).
 //
 // This is a different exponential from the paper's Pade (Sec. 4.1): the
 // same e^{t H} up to rounding, without a linear solve.
@@ -68,7 +72,7 @@ struct GemmArgs {
     KDim kd;
     int epi;          // 0: C = AB; 1: C = AB + lin; 2: C = beta0 AB (beta0 of the run)
     Lin4 lin;
-    const double* gate;  // squaring gate (per run, stride sG): q >= gate -> C = A (copy)
+    const double* gate;  // squaring gate (per run, stride sG): launches q >= gate do not square
     int64_t sG;
     int q;
 };
@@ -99,12 +103,20 @@ __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
         }
         return;
     }
-    if (g.gate && g.q >= (int)g.gate[z * g.sG]) {
-        for (int e = threadIdx.x; e < GT * GT; e += GNT) {
-            const int r = r0 + e / GT, c = c0 + e % GT;
-            if (r < M && c < N) C[(int64_t)r * g.ldc + c] = A[(int64_t)r * g.lda + c];
+    if (g.gate) {
+        const int s = (int)g.gate[z * g.sG];
+        if (g.q >= s) {
+            // the run's s squarings are done: the result stays in the buffer the
+            // last one wrote, and only the last launch moves it to the buffer the
+            // host reads next (SQ_LAUNCHES is even: needed when s is odd)
+            if (g.q == SQ_LAUNCHES - 1 && ((g.q - s) & 1) == 0) {
+                for (int e = threadIdx.x; e < GT * GT; e += GNT) {
+                    const int r = r0 + e / GT, c = c0 + e % GT;
+                    if (r < M && c < N) C[(int64_t)r * g.ldc + c] = A[(int64_t)r * g.lda + c];
+                }
+            }
+            return;
         }
-        return;
     }
     __shared__ double As[GT][GT + 1], Bs[GT][GT + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -264,13 +276,52 @@ int large_expm_batch(int m, int steps, int runs) {
     return (int)std::min<int64_t>(b, runs);
 }
 
+// Thin products (M or N at most 16: the first doubling stages and the basis
+// rows): one thread per output entry, four interleaved partial sums over K
+// added in a fixed order.  The 32 x 32 tiles of k_dgemm would spend almost
+// all of their FP64 work on zero padding there.  blockIdx.y = run.
+__global__ void __launch_bounds__(GNT) k_dgemm_thin(GemmArgs g) {
+    const int z = blockIdx.y;
+    const int k = kdim(g.kd, z);
+    if (k < 0) return;
+    const int M = g.M < 0 ? k : g.M, N = g.N < 0 ? k : g.N, K = g.K < 0 ? k : g.K;
+    const double* A = g.A + z * g.sA;
+    const double* B = g.B + z * g.sB;
+    double* C = g.C + z * g.sC;
+    const double beta0 = g.epi == 2 ? (g.kd.st + z)->beta0 : 1.0;
+    for (int64_t e = (int64_t)blockIdx.x * GNT + threadIdx.x; e < (int64_t)M * N; e += (int64_t)gridDim.x * GNT) {
+        const int r = (int)(e / N), c = (int)(e - (int64_t)r * N);
+        const double* a = A + (int64_t)r * g.lda;
+        const double* b = B + c;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int kk = 0;
+        for (; kk + 4 <= K; kk += 4) {
+            s0 = fma(a[kk], b[(int64_t)kk * g.ldb], s0);
+            s1 = fma(a[kk + 1], b[(int64_t)(kk + 1) * g.ldb], s1);
+            s2 = fma(a[kk + 2], b[(int64_t)(kk + 2) * g.ldb], s2);
+            s3 = fma(a[kk + 3], b[(int64_t)(kk + 3) * g.ldb], s3);
+        }
+        for (; kk < K; ++kk) s0 = fma(a[kk], b[(int64_t)kk * g.ldb], s0);
+        C[(int64_t)r * g.ldc + c] = ((s0 + s1) + (s2 + s3)) * beta0;  // k == 0: K = 0, zero rows
+    }
+}
+
 static int gemm(Prob* p, int nb, const double* A, int lda, int64_t sA, const double* B, int ldb, int64_t sB, double* C,
                 int ldc, int64_t sC, int M, int N, int K, KDim kd, int epi = 0, Lin4 lin = Lin4{},
                 const double* gate = nullptr, int64_t sG = 0, int q = 0) {
-    const int Mx = M < 0 ? p->m : M, Nx = N < 0 ? p->m : N;
-    dim3 grd((unsigned)((Nx + GT - 1) / GT), (unsigned)((Mx + GT - 1) / GT), (unsigned)nb);
+    // grid: the problem's largest dimension, or the checkpoint's when the
+    // host knows it (kd.dim > 0); the kernel reads each run's own dimension
+    const int kmax = kd.dim > 0 ? kd.dim : p->m;
+    const int Mx = M < 0 ? kmax : M, Nx = N < 0 ? kmax : N;
     GemmArgs g{A, lda, sA, B, ldb, sB, C, ldc, sC, M, N, K, kd, epi, lin, gate, sG, q};
-    k_dgemm<<<grd, GNT, 0, p->ctx->stream>>>(g);
+    if (epi != 1 && !gate && (Mx <= 16 || Nx <= 16)) {
+        int64_t gx = ((int64_t)Mx * Nx + GNT - 1) / GNT;
+        if (gx > 152 * 4) gx = 152 * 4;
+        k_dgemm_thin<<<dim3((unsigned)gx, (unsigned)nb), GNT, 0, p->ctx->stream>>>(g);
+    } else {
+        dim3 grd((unsigned)((Nx + GT - 1) / GT), (unsigned)((Mx + GT - 1) / GT), (unsigned)nb);
+        k_dgemm<<<grd, GNT, 0, p->ctx->stream>>>(g);
+    }
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;
 }
