@@ -324,7 +324,9 @@ __device__ void finish_vector(double nw2, const T* W, ColState* s, double* H, do
         const double beta = sqrt(nw2);
         H[(int64_t)(j + 1) * m + j] = beta;
         double nav2 = beta * beta;
-        for (int l = 0; l <= j; ++l) nav2 += H[(int64_t)l * m + j] * H[(int64_t)l * m + j];
+        // Lanczos: column j of H has entries in rows j-1 and j only (the rest
+        // stay zero), so one thread need not walk the whole column
+        for (int l = symmetric && j > 0 ? j - 1 : 0; l <= j; ++l) nav2 += H[(int64_t)l * m + j] * H[(int64_t)l * m + j];
         if (!(beta > 1e-12 * sqrt(nav2)) || !isfinite(beta)) {
             s->done = 1;
             s->m_used = j + 1;
