@@ -616,7 +616,7 @@ static int64_t row_blocks_t(int64_t N) {
 }
 static int64_t spmv_blocks(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
-    return b > 152 * 16 ? 152 * 16 : b;
+    return b > 152 * 8 ? 152 * 8 : b;
 }
 
 int64_t csr_scratch_slots(int64_t N, int m) {  // reduction partials per column
