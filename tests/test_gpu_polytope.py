@@ -230,3 +230,36 @@ def test_random_csr_full_size_polygon(ctx, precision):
     scale = np.max(np.abs(ref))
     err = np.max(np.abs(got["margin"][ks] - ref)) / scale
     assert err <= (1e-6 if precision == "fp32" else 1e-9), err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_grid_multi_column_polygon(ctx, precision):
+    """A grid (Lanczos) with a point source, a dense field and a box column and
+    two outputs, one of them the point cell itself; the early steps' basis
+    entries of the far columns are tiny (the ill-conditioned regime of the
+    LP).  Unsafe: a wedge in the output plane; initial rows: a budget on the
+    first two columns.  FP32 storage feeds the LP a basis within 1e-6."""
+    import math
+    dims = (24, 17, 9)
+    n = 24 * 17 * 9
+    rng = np.random.default_rng(3)
+    sysm = W.GridSystem(dims=dims, coef=0.01, h=tuple(1.0 / (d + 1) for d in dims))
+    src = W.grid_index(dims, (6, 6, 4))
+    cols = [W.Column(kind="sparse", zlo=-1.0, zhi=2.0, idx=np.array([src]), val=np.array([1.0])),
+            W.Column(kind="dense", zlo=0.0, zhi=0.5, dense=rng.standard_normal(n)),
+            W.Column(kind="box", zlo=0.9, zhi=1.1, box_lo=(0, 0, 0), box_hi=(4, 3, 2), value=2.0)]
+    rp, cc, cv = W._c_rows([([src], [1.0]), (np.arange(0, n, 7), rng.standard_normal(len(range(0, n, 7))))])
+    mk = lambda prec: W.Problem(system=sysm, columns=cols, C_row_ptr=rp, C_col=cc, C_val=cv,
+                                theta=np.array([math.inf, math.inf]), dt=0.02, steps=80, m=20, precision=prec)
+    U = np.array([[-1.0, 0.3], [0.5, -1.0]])
+    v = np.array([-0.4, 0.2]) + 0.6 * np.linalg.norm(U, axis=1)   # the wedge becomes reachable mid-horizon
+    Iz = np.array([[1.0, 1.0, 0.0]])
+    iota = np.array([1.5])
+    B, zlo, zhi, ref = oracle_lp(mk("fp64"), U, v, Iz, iota)
+    assert 0 < ref["viol_step"] < 80
+    _, got = gpu_lp(ctx, mk(precision), U, v, Iz, iota)
+    compare(got, ref, 1e-9 if precision == "fp64" else 1e-6, B, zlo, zhi, U, v, Iz, iota)
+    k = ref["viol_step"]
+    scale = np.max(np.abs(ref["margin"]))
+    if abs(ref["margin"][k]) > 1e-5 * scale and abs(ref["margin"][k - 1]) > 1e-5 * scale:
+        assert got["viol_step"] == k
