@@ -62,6 +62,10 @@ int kv_graph_create(kv_ctx* ctx, kv_prob* const* probs, int32_t n, kv_graph** ou
     kv_graph* g = new kv_graph();
     g->ctx = ctx;
     g->probs.assign(probs, probs + n);
+    // enqueueing under capture marks a problem as run; until the graph is
+    // launched its results are those of its previous runs, if any
+    std::vector<bool> ran_before(n);
+    for (int k = 0; k < n; ++k) ran_before[k] = probs[k]->ran;
     cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(fork, origin);
     for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(br[b], fork, 0);
@@ -70,6 +74,7 @@ int kv_graph_create(kv_ctx* ctx, kv_prob* const* probs, int32_t n, kv_graph** ou
         rc = kv_enqueue(probs[k]);
     }
     ctx->stream = origin;
+    for (int k = 0; k < n; ++k) probs[k]->ran = ran_before[k];
     for (int b = 0; b < nb && e == cudaSuccess; ++b) {
         e = cudaEventRecord(join[b], br[b]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, join[b], 0);
@@ -105,7 +110,10 @@ int kv_graph_launch(kv_graph* g) {
     KV_CHECK_CUDA(cudaSetDevice(g->ctx->device));
     KV_CHECK_CUDA(cudaGraphLaunch(g->exec, g->ctx->stream));
     g->ctx->launches += 1;
-    for (kv_prob* p : g->probs) KV_CHECK_CUDA(cudaEventRecord(p->done_ev, g->ctx->stream));
+    for (kv_prob* p : g->probs) {
+        KV_CHECK_CUDA(cudaEventRecord(p->done_ev, g->ctx->stream));
+        p->ran = true;
+    }
     return KV_OK;
 }
 

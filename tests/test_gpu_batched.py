@@ -72,3 +72,29 @@ def test_graph_fp64_results_match_oracle(ctx):
         h.close()
     for s in systems:
         s.close()
+
+
+def test_polytope_check_follows_graph_launches(ctx):
+    """A problem captured in a graph has not run until the graph is launched:
+    the per-step LP refuses it before, and after the launch gives the same
+    margins as after kv_run."""
+    q = W.oscillator()
+    q.C_row_ptr, q.C_col, q.C_val = W._c_rows([([0], [1.0]), ([1], [1.0]), ([2], [1.0])])
+    q.theta = np.full(3, np.inf)
+    U = np.array([[1.0, 0, 0], [-1.0, 0, 0]])
+    v = np.array([4.0, -4.0])
+    s = kv.System(ctx, q.system, q.precision)
+    h = kv.ProblemHandle(ctx, s, q)
+    g = kv.Graph(ctx, [h])
+    with pytest.raises(kv.KvError) as ei:
+        h.check_polytope(U, v, tol=1e-9)
+    assert ei.value.code == kv.KV_EINVAL
+    g.launch()
+    via_graph = h.check_polytope(U, v, tol=1e-9)
+    h.run()
+    direct = h.check_polytope(U, v, tol=1e-9)
+    assert via_graph["viol_step"] == direct["viol_step"] == 3
+    assert np.array_equal(via_graph["margin"], direct["margin"])
+    g.close()
+    h.close()
+    s.close()
