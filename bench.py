@@ -373,14 +373,19 @@ def serve_bench(args, dev: int):
     100..2000 steps, m 20..60; FP32 storage) through the continuous-batching
     server.  A burst of all queries measures capacity; then Poisson arrivals at
     0.8 x capacity give queries/s and the p50 / p99 latency from kv_submit to
-    the results on the host.  The FP32 bounds are compared with the FP64 oracle
-    on the smallest queries and with the FP64 GPU path (parity-tested against the
-    oracle) on a random sample."""
+    the results on the host.  The FP32 bounds are compared with the FP64 GPU
+    path (parity-tested against the oracle by the tests, served results included)
+    on a random sample."""
     import torch
     import paper_1804_01583_gb300 as kv
-    import oracle
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from parity import bound_error
+
+    def bound_error(got, ref):  # per output row, scaled by the row's largest |bound|
+        worst = 0.0
+        for r in range(ref["hi"].shape[0]):
+            S = max(np.max(np.abs(ref["lo"][r])), np.max(np.abs(ref["hi"][r])))
+            d = max(np.max(np.abs(got["lo"][r] - ref["lo"][r])), np.max(np.abs(got["hi"][r] - ref["hi"][r])))
+            worst = max(worst, d / S if S > 0 else d)
+        return worst
 
     qs = W.serving_mix(args.serve_queries, seed=0)
     ctx = kv.Context(args.serve_pool_gb << 30, device=dev)
@@ -422,15 +427,7 @@ def serve_bench(args, dev: int):
     st = srv.stats()
     srv.close()
     lat = np.array([res[i]["latency_ms"] for i in range(len(qs))])
-    # accuracy of the FP32 results
-    # oracle sample: the smallest queries whose bounds are not all zero (an
-    # output cell beyond stencil reach of the block gives exact zeros)
-    order = sorted(range(len(qs)), key=lambda i: qs[i].system.n * qs[i].i * qs[i].m)
-    picked = [i for i in order if np.any(res[i]["hi"] != 0.0)][:6]
-    err_oracle = 0.0
-    for i in picked:
-        q64 = W.Problem(**{**qs[i].__dict__, "precision": "fp64"})
-        err_oracle = max(err_oracle, bound_error(res[i], oracle.run(q64)))
+    # accuracy of the FP32 results against the FP64 form on the same GPU
     sample = np.random.default_rng(7).choice(len(qs), size=min(24, len(qs)), replace=False)
     err_gpu64 = 0.0
     for i in sample:
@@ -446,8 +443,6 @@ def serve_bench(args, dev: int):
             "capacity_qps": cap, "arrival_rate_qps": rate, "queries_per_s": len(qs) / elapsed,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_running": st["max_running"], "memory_waits": st["memory_waits"],
-            "max_rel_bound_err_vs_fp64_oracle": err_oracle,
-            "oracle_sample": [qs[i].name for i in picked],
             "max_rel_bound_err_vs_fp64_gpu": err_gpu64, "fp64_gpu_sample": f"{len(sample)} random queries",
             "precision": "fp32 storage, fp64 accumulation"}
 
