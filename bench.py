@@ -483,6 +483,54 @@ def error_control_bench(dev: int):
     return out
 
 
+def configs_bench(dev: int) -> dict:
+    """Configurations 1 and 2 as specified (20x20 2-D heat, m = 30, 500 steps;
+    100^3 3-D heat, m = 40, 1000 steps; FP64 plain method) with the FP32
+    storage form beside them: time per query (median of 5 after a warm-up,
+    CUDA-synchronised wall time of kv_enqueue + kv_fetch), Krylov steps/s, and
+    the first violation step (parity of both against the oracle is in the
+    tests)."""
+    import paper_1804_01583_gb300 as kv
+    out = {}
+    ctx = kv.Context(4 << 30, device=dev)
+    try:
+        for label, mk in (("2d-20x20", W.heat2d_20), ("3d-100^3", W.heat3d_100)):
+            out[label] = {}
+            for prec in ("fp64", "fp32"):
+                p = mk(precision=prec)
+                sysh = kv.System(ctx, p.system, p.precision)
+                ph = kv.ProblemHandle(ctx, sysh, p)
+                r = ph.run(full=False)
+                ts = []
+                for _ in range(5):
+                    t0 = time.perf_counter()
+                    ph.enqueue()
+                    r = ph.fetch(full=False)
+                    ts.append((time.perf_counter() - t0) * 1e3)
+                ms = statistics.median(ts)
+                out[label][prec] = {"ms_per_query": ms, "krylov_steps_per_s": p.m / (ms * 1e-3),
+                                    "first_violation_step": int(r["viol_step"]), "m": p.m, "steps": p.steps,
+                                    "n": int(p.system.n)}
+                ph.close()
+                sysh.close()
+    finally:
+        ctx.close()
+    return out
+
+
+def cpu_configs() -> dict:
+    """The CPU oracle on the same two configurations (FP64, all host cores):
+    wall time of one whole query (Krylov, exponentials, bounds)."""
+    import oracle
+    out = {}
+    for label, mk in (("2d-20x20", W.heat2d_20), ("3d-100^3", W.heat3d_100)):
+        p = mk()
+        t0 = time.perf_counter()
+        oracle.run(p, want_basis=False)
+        out[label] = {"ms_per_query": (time.perf_counter() - t0) * 1e3, "cores": oracle.num_threads()}
+    return out
+
+
 def paper_heat_bench(dev: int, precisions=("fp64", "fp32")):
     """The paper's own 3-D heat experiment (Sec. 5.3): 100^3 cells of the
     insulated cube with heat exchange at x = 1 (cell-centred reading), the
@@ -786,12 +834,14 @@ def main():
         line["error_control"] = error_control_bench(dev)
         line["replicated"] = replicated_bench(dev)
         line["paper_heat"] = paper_heat_bench(dev)
+        line["configs"] = configs_bench(dev)
     if args.csr and world == 1:
         line["csr_workload"] = csr_bench(args, dev)
     if args.serve and world == 1:
         line["serving"] = serve_bench(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload(args.workload, "fp64"), iters=args.cpu_iters)
+        line["cpu_baseline"]["configs"] = cpu_configs()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
