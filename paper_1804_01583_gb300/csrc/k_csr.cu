@@ -628,7 +628,9 @@ size_t csr_arnoldi_dev_bytes() { return sizeof(ArnoldiDev); }
 
 // ------------------------------------------------------- SpMM dispatch --
 // Grid-stride kernels get one full wave: the SMs times the blocks of CNT
-// threads that fit on one SM at the kernel's register count.
+// threads that fit on one SM at the kernel's register count.  Each kernel's
+// wave is found once, on the device of the first problem that sizes it (one
+// GPU model per process).
 template <typename K>
 static int64_t one_wave(K kernel, int device) {
     int nb = 0, nsm = 0;
