@@ -289,8 +289,8 @@ def run_gpu(args, rank: int, world: int):
     else:
         alg_bytes = None
     if p.precision == "fp64" and dom in ("stencil_update", "stencil_alpha"):
-        # the FP64 grid passes are bound by the FP64 pipe (9 and 8
-        # FP64 instructions per grid point; peak 2 per SM per clock)
+        # the FP64 grid passes are bound by the FP64 pipe (9 and 8 FP64
+        # instructions per grid point; peak 2 per SM per clock)
         dp = {"stencil_update": 9.0, "stencil_alpha": 8.0}[dom] * p.system.n
         dp_peak = 2.0 * 152 * 2.07e9 / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": dp / avg_s / 1e12, "peak": dp_peak,
