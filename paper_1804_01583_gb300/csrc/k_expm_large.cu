@@ -22,7 +22,11 @@
 // dimension at a checkpoint) and reads k from the run's state; tiles beyond k
 // return at once, and a checkpoint of a run that has stopped does nothing.
 // Products with at most 16 rows or columns (the first doubling stages, the
-// basis rows) run one thread per entry (k_dgemm_thin).  The number of
+// basis rows) run one thread per entry (k_dgemm_thin).  The Lanczos H is
+// tridiagonal and the Arnoldi H upper Hessenberg, so the Taylor products and
+// the first squarings are banded: each product is told the bands of its
+// operands (entries outside them are exact zeros) and its tiles skip the
+// K-tiles outside both, which only leaves out exact zero terms.  The number of
 // squaring launches is fixed (SQ_LAUNCHES); those beyond the run's s return
 // at once, the last one moving the result into the buffer the host reads
 // when s is odd, so the launch sequence does not depend on device data (it
@@ -32,6 +36,8 @@
 // same e^{t H} up to rounding, without a linear solve.
 #include <math.h>
 
+#include <algorithm>
+
 #include "kv_internal.h"
 
 namespace kv {
@@ -39,6 +45,17 @@ namespace kv {
 constexpr int GT = 32;          // GEMM tile: GT x GT outputs per CTA
 constexpr int GNT = 256;        // 16 x 16 threads, 2 x 2 outputs each
 constexpr int SQ_LAUNCHES = 32; // squarings enqueued (even); handles ||dt H||_1 up to 2^32
+
+// A(r, c) may be nonzero only for r - lo <= c <= r + up (BAND_DENSE: no band)
+constexpr int BAND_DENSE = 1 << 28;
+struct Band {
+    int lo, up;
+};
+__host__ __device__ constexpr Band dense_band() { return Band{BAND_DENSE, BAND_DENSE}; }
+static Band band_sum(Band a, Band b) {  // band of a product
+    return Band{std::min(a.lo + b.lo, BAND_DENSE), std::min(a.up + b.up, BAND_DENSE)};
+}
+static Band band_max(Band a, Band b) { return Band{std::max(a.lo, b.lo), std::max(a.up, b.up)}; }
 
 struct KDim {
     const ColState* st;  // the batch's first run; run z is st + z
@@ -75,6 +92,7 @@ struct GemmArgs {
     const double* gate;  // squaring gate (per run, stride sG): launches q >= gate do not square
     int64_t sG;
     int q;
+    Band ba, bb;      // bands of A and B
 };
 
 __device__ __forceinline__ double lin_at(const Lin4& l, int z, int r, int c) {
@@ -121,7 +139,10 @@ __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
     __shared__ double As[GT][GT + 1], Bs[GT][GT + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
-    for (int kk = 0; kk < K; kk += GT) {
+    // the inner indices l where both A(r0.., l) and B(l, c0..) may be nonzero
+    const int l_lo = max(0, max(r0 - g.ba.lo, c0 - g.bb.up));
+    const int l_hi = min(K - 1, min(r0 + GT - 1 + g.ba.up, c0 + GT - 1 + g.bb.lo));
+    for (int kk = (l_lo / GT) * GT; kk <= l_hi; kk += GT) {
         for (int e = threadIdx.x; e < GT * GT; e += GNT) {
             const int a = e / GT, b = e % GT;
             const int ar = r0 + a, ac = kk + b;
@@ -308,12 +329,13 @@ __global__ void __launch_bounds__(GNT) k_dgemm_thin(GemmArgs g) {
 
 static int gemm(Prob* p, int nb, const double* A, int lda, int64_t sA, const double* B, int ldb, int64_t sB, double* C,
                 int ldc, int64_t sC, int M, int N, int K, KDim kd, int epi = 0, Lin4 lin = Lin4{},
-                const double* gate = nullptr, int64_t sG = 0, int q = 0) {
+                const double* gate = nullptr, int64_t sG = 0, int q = 0, Band ba = dense_band(),
+                Band bb = dense_band()) {
     // grid: the problem's largest dimension, or the checkpoint's when the
     // host knows it (kd.dim > 0); the kernel reads each run's own dimension
     const int kmax = kd.dim > 0 ? kd.dim : p->m;
     const int Mx = M < 0 ? kmax : M, Nx = N < 0 ? kmax : N;
-    GemmArgs g{A, lda, sA, B, ldb, sB, C, ldc, sC, M, N, K, kd, epi, lin, gate, sG, q};
+    GemmArgs g{A, lda, sA, B, ldb, sB, C, ldc, sC, M, N, K, kd, epi, lin, gate, sG, q, ba, bb};
     if (epi != 1 && !gate && (Mx <= 16 || Nx <= 16)) {
         int64_t gx = ((int64_t)Mx * Nx + GNT - 1) / GNT;
         if (gx > 152 * 4) gx = 152 * 4;
@@ -352,9 +374,14 @@ static int expm_large_batch(Prob* p, int j0, int nb, int dim, bool write_basis) 
     k_lx_scaling<<<dim3(1, 1, (unsigned)nb), GNT, 0, st>>>(cs, X_, m, SQ_LAUNCHES, kd);
     k_lx_scale<<<ge, GNT, 0, st>>>(X, m, X_, scale, X_, kd);
     KV_CHECK_CUDA(cudaGetLastError());
-    int rc = gemm(p, nb, X, m, X_, X, m, X_, X2, m, X_, -1, -1, -1, kd);
-    if (!rc) rc = gemm(p, nb, X2, m, X_, X, m, X_, X3, m, X_, -1, -1, -1, kd);
-    if (!rc) rc = gemm(p, nb, X2, m, X_, X2, m, X_, X4, m, X_, -1, -1, -1, kd);
+    // band of H: tridiagonal when every run of the batch is a Lanczos run
+    bool lanczos = true;
+    for (int j = j0; j < j0 + nb; ++j) lanczos = lanczos && p->method[j] == KV_LANCZOS;
+    const Band b1 = lanczos ? Band{1, 1} : Band{1, BAND_DENSE};
+    const Band b2 = band_sum(b1, b1), b3 = band_sum(b2, b1), b4 = band_sum(b2, b2);
+    int rc = gemm(p, nb, X, m, X_, X, m, X_, X2, m, X_, -1, -1, -1, kd, 0, Lin4{}, nullptr, 0, 0, b1, b1);
+    if (!rc) rc = gemm(p, nb, X2, m, X_, X, m, X_, X3, m, X_, -1, -1, -1, kd, 0, Lin4{}, nullptr, 0, 0, b2, b1);
+    if (!rc) rc = gemm(p, nb, X2, m, X_, X2, m, X_, X4, m, X_, -1, -1, -1, kd, 0, Lin4{}, nullptr, 0, 0, b2, b2);
     if (rc) return rc;
     // Paterson-Stockmeyer: blocks B_i = c_{4i} I + c_{4i+1} X + c_{4i+2} X^2 + c_{4i+3} X^3
     double c[19];
@@ -368,15 +395,19 @@ static int expm_large_batch(Prob* p, int j0, int nb, int dim, bool write_basis) 
     KV_CHECK_CUDA(cudaGetLastError());
     double* cur = T0;
     double* nxt = T1;
+    Band bt = b2;  // band of B_4
     for (int i = 3; i >= 0; --i) {  // T = T X^4 + B_i
-        rc = gemm(p, nb, cur, m, X_, X4, m, X_, nxt, m, X_, -1, -1, -1, kd, 1, blk(i));
+        rc = gemm(p, nb, cur, m, X_, X4, m, X_, nxt, m, X_, -1, -1, -1, kd, 1, blk(i), nullptr, 0, 0, bt, b4);
         if (rc) return rc;
+        bt = band_max(band_sum(bt, b4), b3);
         std::swap(cur, nxt);
     }
-    // squarings (SQ_LAUNCHES is even: the result ends in `cur`)
+    // squarings (SQ_LAUNCHES is even: the result ends in `cur`); launch q
+    // squares only when q < s, so its operand has been squared q times
     for (int q = 0; q < SQ_LAUNCHES; ++q) {
-        rc = gemm(p, nb, cur, m, X_, cur, m, X_, nxt, m, X_, -1, -1, -1, kd, 0, Lin4{}, gate, X_, q);
+        rc = gemm(p, nb, cur, m, X_, cur, m, X_, nxt, m, X_, -1, -1, -1, kd, 0, Lin4{}, gate, X_, q, bt, bt);
         if (rc) return rc;
+        bt = band_sum(bt, bt);
         std::swap(cur, nxt);
     }
     // doubling over the output steps: P_0 = E (in cur), spare buffers X2 / X3
