@@ -22,8 +22,10 @@
 //
 // All scalars stay on the device; the last block of each pass finishes the
 // deterministic reduction and writes them.
+#include <errno.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <sys/stat.h>
 
 #include <string>
 #include <type_traits>
@@ -709,6 +711,16 @@ static std::string tune_cache_path() {
     return std::string(h ? h : "/tmp") + "/.cache/kv_autotune.txt";
 }
 
+// mkdir -p of the cache file's directory, without a shell (the path comes
+// from the environment); failures only mean the result is not cached.
+static void make_dirs(const std::string& dir) {
+    for (size_t k = 1; k <= dir.size(); ++k)
+        if (k == dir.size() || dir[k] == '/') {
+            const std::string d = dir.substr(0, k);
+            if (mkdir(d.c_str(), 0755) != 0 && errno != EEXIST) return;
+        }
+}
+
 static std::string tune_key(const Prob* p, int ncols) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, p->ctx->device);
@@ -831,8 +843,8 @@ static int autotune_t(Prob* p, int ncols, void* V) {
     KV_CHECK_CUDA(cudaGetLastError());
     p->spmm_G = bg;
     p->spmm_LPR = bl;
-    const std::string dir = path.substr(0, path.find_last_of('/'));
-    (void)!system(("mkdir -p '" + dir + "' 2>/dev/null").c_str());
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos && slash > 0) make_dirs(path.substr(0, slash));
     if (FILE* f = fopen(path.c_str(), "a")) {
         fprintf(f, "%s %d %d %.3f\n", key.c_str(), bg, bl, best * 1000.0 / 3.0);
         fclose(f);

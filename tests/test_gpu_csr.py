@@ -192,8 +192,9 @@ def test_spmm_and_spmv_paths(ctx, flags, precision):
 
 def test_autotuner_cache(ctx, tmp_path, monkeypatch):
     """The SpMM shape is timed once per (device, n, N, nnz, element size,
-    columns) and cached in KV_AUTOTUNE_CACHE; the second problem reuses it."""
-    path = tmp_path / "tune.txt"
+    columns) and cached in KV_AUTOTUNE_CACHE, whose missing directories are
+    created; the second problem reuses it."""
+    path = tmp_path / "cache" / "kv" / "tune.txt"
     monkeypatch.setenv("KV_AUTOTUNE_CACHE", str(path))
     p = W.random_csr_problem(120_000, seed=13, n_gen=7, o=1, c_width=500, dt=0.01, steps=50, m=8, precision="fp32")
     for _ in range(2):
