@@ -83,8 +83,9 @@ struct VecArgs {
 };
 
 // ------------------------------------------------------------------ SpMV --
+constexpr int SPMV_STAGE = 256;  // matrix entries per warp staged in shared memory
 template <typename T, bool ALPHA>
-__global__ void __launch_bounds__(CNT) k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(CNT, 6) k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                               const T* __restrict__ val, const double* __restrict__ b,
                                               VecArgs<T> V, int xslot, int wslot, int64_t n, int64_t N,
                                               const int* aug, ColState* st, double* H, int m, int j,
@@ -96,23 +97,41 @@ __global__ void __launch_bounds__(CNT) k_spmv(const int64_t* __restrict__ rp, co
     T* Wv = V.base + cidx * V.cstride + (int64_t)wslot * N;
     const double sj = s->s[j];
     const bool ag = aug[cidx] != 0;
+    // one lane per row; the entries of the warp's 32 rows are contiguous in
+    // the CSR arrays, so the warp stages them in shared memory with coalesced
+    // loads (SPMV_STAGE at a time) and each lane walks its own row there, in
+    // the order of the arrays
+    __shared__ T sv[CNT / 32][SPMV_STAGE];
+    __shared__ int32_t scol[CNT / 32][SPMV_STAGE];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double acc_alpha = 0.0;
-    for (int64_t r = (int64_t)blockIdx.x * CNT + threadIdx.x; r < N; r += (int64_t)gridDim.x * CNT) {
-        double y;
-        if (r < n) {
-            if constexpr (std::is_same<T, float>::value) {
-                Dot2f d;
-                for (int64_t e = rp[r]; e < rp[r + 1]; ++e) d.add_prod(val[e], X[col[e]]);
-                y = d.value();
-            } else {
-                double d = 0.0;
-                for (int64_t e = rp[r]; e < rp[r + 1]; ++e) d = fma(val[e], X[col[e]], d);
-                y = d;
+    // warp-uniform loop over the warp's first row: every lane reaches every
+    // shuffle and warp barrier
+    for (int64_t rb = (int64_t)blockIdx.x * CNT + (threadIdx.x & ~31); rb < N; rb += (int64_t)gridDim.x * CNT) {
+        const int64_t r = rb + lane;
+        const bool inrow = r < n;
+        // rows past n have the empty range at rp[n]
+        const int64_t e0 = rp[inrow ? r : n], e1 = inrow ? rp[r + 1] : e0;
+        const int64_t E0 = __shfl_sync(0xffffffffu, e0, 0), E1 = __shfl_sync(0xffffffffu, e1, 31);
+        typename AccOf<T>::type d;
+        for (int64_t base = E0; base < E1; base += SPMV_STAGE) {
+            const int cnt = (int)(E1 - base < SPMV_STAGE ? E1 - base : SPMV_STAGE);
+            for (int q = lane; q < cnt; q += 32) {
+                sv[w][q] = val[base + q];
+                scol[w][q] = col[base + q];
             }
+            __syncwarp();
+            const int lo = (int)((e0 > base ? e0 : base) - base);
+            const int hi = (int)((e1 < base + cnt ? e1 : base + cnt) - base);
+            for (int q = lo; q < hi; ++q) d.add_prod(sv[w][q], X[scol[w][q]]);
+            __syncwarp();
+        }
+        if (r >= N) continue;
+        double y = 0.0;  // the constant variable's row of A' is zero
+        if (inrow) {
+            y = d.value();
             if (ag && b) y = fma(b[r], (double)X[n], y);
             y *= sj;
-        } else {
-            y = 0.0;  // the constant variable's row of A' is zero
         }
         const T yt = (T)y;
         Wv[r] = yt;
@@ -620,6 +639,12 @@ static int64_t spmv_blocks(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
     return b > 152 * 8 ? 152 * 8 : b;
 }
+// k_spmv: one wave at the 6 blocks per SM its launch bounds guarantee (its
+// staging buffers and 40 registers a thread); at most spmv_blocks
+static int64_t spmv_grid(int64_t N) {
+    int64_t b = (N + CNT - 1) / CNT;
+    return b > 152 * 6 ? 152 * 6 : b;
+}
 
 int64_t csr_scratch_slots(int64_t N, int m) {  // reduction partials per column
     const int64_t nb = row_blocks(N) > spmv_blocks(N) ? row_blocks(N) : spmv_blocks(N);
@@ -910,12 +935,13 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
     double* partials = p->red.partials;
     unsigned* counters = p->d_counters;
     dim3 gs((unsigned)spmv_blocks(N), (unsigned)ncols), gr((unsigned)row_blocks_t<T>(N), (unsigned)ncols);
+    const dim3 gv((unsigned)spmv_grid(N), (unsigned)ncols);
     for (int it = 0; it < m; ++it) {
         if (lanczos) {
             const int vs = it % 3, ws = (it + 1) % 3, ps = (it + 2) % 3;
             {
                 LaunchScope ls(p->ctx, "csr_spmv");
-                k_spmv<T, true><<<gs, CNT, 0, st>>>(s->d_rp, s->d_col, (const T*)s->d_val, s->d_b, va, vs, ws, n, N,
+                k_spmv<T, true><<<gv, CNT, 0, st>>>(s->d_rp, s->d_col, (const T*)s->d_val, s->d_b, va, vs, ws, n, N,
                                                    aug, stp, H, m, it, partials, counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }
@@ -942,7 +968,7 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
                 KV_CHECK_CUDA(cudaGetLastError());
             } else {
                 LaunchScope ls(p->ctx, "csr_spmv");
-                k_spmv<T, false><<<gs, CNT, 0, st>>>(s->d_rp, s->d_col, (const T*)s->d_val, s->d_b, va, it, it + 1, n,
+                k_spmv<T, false><<<gv, CNT, 0, st>>>(s->d_rp, s->d_col, (const T*)s->d_val, s->d_b, va, it, it + 1, n,
                                                     N, aug, stp, H, m, it, partials, counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }
