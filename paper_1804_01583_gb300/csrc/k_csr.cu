@@ -369,7 +369,7 @@ __device__ void finish_vector(double nw2, const T* W, ColState* s, double* H, do
 
 // ------------------------------------------------------ Lanczos update --
 template <typename T, bool FIRST>
-__global__ void __launch_bounds__(CNT) k_lanczos3_update(VecArgs<T> V, int wslot, int vslot, int pslot, int64_t N,
+__global__ void __launch_bounds__(CNT, 6) k_lanczos3_update(VecArgs<T> V, int wslot, int vslot, int pslot, int64_t N,
                                                          ColState* st, double* Hall, double* Pall, CDesc cd, int m,
                                                          int j, double* partials, unsigned* counters, int64_t nbx) {
     const int cidx = blockIdx.y;
@@ -639,8 +639,8 @@ static int64_t spmv_blocks(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
     return b > 152 * 8 ? 152 * 8 : b;
 }
-// k_spmv: one wave at the 6 blocks per SM its launch bounds guarantee (its
-// staging buffers and 40 registers a thread); at most spmv_blocks
+// k_spmv and k_lanczos3_update: one wave at the 6 blocks per SM their launch
+// bounds guarantee (40 registers a thread); at most spmv_blocks
 static int64_t spmv_grid(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
     return b > 152 * 6 ? 152 * 6 : b;
@@ -948,10 +948,10 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
             {
                 LaunchScope ls(p->ctx, "csr_lanczos_update");
                 if (it == 0)
-                    k_lanczos3_update<T, true><<<gs, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
+                    k_lanczos3_update<T, true><<<gv, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
                                                                   counters, nbx);
                 else
-                    k_lanczos3_update<T, false><<<gs, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
+                    k_lanczos3_update<T, false><<<gv, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
                                                                    counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }
