@@ -2,8 +2,9 @@
 //
 // SpMV.  w = A' (s_j V_j) with A' = [[A, b], [0, 0]] when the state carries the
 // constant-1 variable (Sec. 2.1): row r < n gets sum_e val[e] x[col[e]] +
-// b[r] x[n], row n is zero.  One thread per row; the row sum is a double in
-// the FP64 form and an error-free float pair (Dot2) in the FP32 form.
+// b[r] x[n], row n is zero.  One lane per row, the warp's entries staged in
+// shared memory; the row sum is a double in the FP64 form and an error-free
+// float pair (Dot2) in the FP32 form.
 //
 // Arnoldi (Alg. 1) for general A, one iteration j per column as two passes
 // over the stored basis V_0..V_j (each V_l stored unnormalised, read scale
