@@ -1144,7 +1144,7 @@ int kv_check_polytope(kv_prob* p, const kv_polytope* unsafe, const kv_polytope* 
     double* dyx = dzx + (size_t)S * i;
     int* dstatus = (int*)(dyx + (size_t)S * o);
     int* dzflag = dstatus + S;  // the initial set's emptiness, from the first launch
-    std::vector<double> zx((size_t)S * i), yrow(o);
+    std::vector<double> zx((size_t)S * i);
     auto run = [&]() -> int {
         int e = upload(c, dU, U.data(), U.size() * 8);
         if (!e) e = upload(c, dv, v.data(), v.size() * 8);
