@@ -101,7 +101,10 @@ int admit(kv_server* s, Request* r, int slot) {
     return KV_OK;
 }
 
-void finish(kv_server* s, Request* r) {
+// Copies a finished query's results to host storage and releases its device
+// memory; returns its status, which the caller publishes under the mutex
+// (kv_poll reads the results only after seeing the status there).
+int finish(kv_server* s, Request* r) {
     set_stream_and(s, r->slot);
     const kv_problem_desc& d = r->q.desc;
     const size_t S = (size_t)d.steps + 1;
@@ -130,7 +133,7 @@ void finish(kv_server* s, Request* r) {
     r->prob = nullptr;
     r->sys = nullptr;
     r->t_done = Clock::now();
-    r->status = rc;
+    return rc;
 }
 
 void worker_loop(kv_server* s) {
@@ -143,8 +146,9 @@ void worker_loop(kv_server* s) {
             if (!r) continue;
             busy = true;
             if (cudaEventQuery(r->prob->done_ev) == cudaSuccess) {
-                finish(s, r);
+                const int rc = finish(s, r);
                 std::lock_guard<std::mutex> lk(s->mu);
+                r->status = rc;
                 s->running[k] = nullptr;
                 s->completed++;
             }
@@ -294,19 +298,16 @@ int kv_poll(kv_server* s, uint64_t ticket, kv_result* out, double* latency_ms) {
         }
         r = it->second;
         if (r->status == KV_ENOTREADY) return KV_ENOTREADY;
+        if (r->status == KV_OK && (!out->lo || !out->hi)) {  // the result stays pollable
+            kv::set_error("kv_poll: lo and hi are required");
+            return KV_EINVAL;
+        }
         s->all.erase(it);
     }
     const int rc = r->status;
     if (rc == KV_OK) {
-        const size_t no = r->lo.size();
-        if (!out->lo || !out->hi) {
-            delete r;
-            kv::set_error("kv_poll: lo and hi are required");
-            return KV_EINVAL;
-        }
         std::copy(r->lo.begin(), r->lo.end(), out->lo);
         std::copy(r->hi.begin(), r->hi.end(), out->hi);
-        (void)no;
         if (out->beta0) std::copy(r->beta0.begin(), r->beta0.end(), out->beta0);
         if (out->m_used) std::copy(r->m_used.begin(), r->m_used.end(), out->m_used);
         if (out->err_bound) std::copy(r->err_bound.begin(), r->err_bound.end(), out->err_bound);

@@ -145,3 +145,25 @@ def test_unknown_ticket(lib):
     assert rc == kv.KV_EINVAL
     s.close()
     ctx.close()
+
+
+def test_poll_without_outputs_keeps_the_result(lib):
+    """A finished query polled without lo/hi is refused (KV_EINVAL) and its
+    result stays pollable."""
+    ctx = kv.Context(1 << 20)
+    s = kv.Server(ctx, slots=1)
+    q = W.heat((8, 8), block=(2, 2), output="centre", dt=0.1, steps=4, m=4)
+    t = s.submit(q)
+    res = kv.kv_result()  # lo and hi left NULL
+    t0 = time.time()
+    while True:
+        rc = lib.kv_poll(s.h, t, res, None)
+        if rc != kv.KV_ENOTREADY:
+            break
+        assert time.time() - t0 < 60
+        time.sleep(0.001)
+    assert rc == kv.KV_EINVAL
+    r = wait_all(s, [t])[0]
+    assert r["lo"].shape == (1, 5) and np.all(r["hi"] >= r["lo"])
+    s.close()
+    ctx.close()
