@@ -2,6 +2,7 @@
 // systems, problems and the enqueue of the whole path on one stream.
 #include <math.h>
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -49,6 +50,7 @@ void Arena::init(char* base, size_t size) {
 
 void* Arena::alloc(size_t bytes) {
     if (bytes == 0) bytes = 1;
+    if (bytes > size_) return nullptr;  // also keeps the rounding below from wrapping
     bytes = (bytes + kAlign - 1) / kAlign * kAlign;
     for (auto it = free_.begin(); it != free_.end(); ++it) {
         if (it->second >= bytes) {
@@ -131,6 +133,7 @@ static void clear_profile(Ctx* c) {
 // ------------------------------------------------------------- helpers
 template <typename T>
 static int dalloc(Prob* p, T** out, size_t count) {
+    if (count > SIZE_MAX / sizeof(T)) return fail(KV_ENOMEM, "device allocation size overflows");
     void* q = p->ctx->arena.alloc(count * sizeof(T));
     if (!q) {
         return fail(KV_ENOMEM, "device pool exhausted: need %zu more bytes (largest free block %zu of %zu)",
@@ -704,7 +707,12 @@ static int prob_build(Ctx* c, Prob* p, const Sys* s, const kv_problem_desc* d, i
     } while (0)
     {
         p->nsets = vector_sets(s, p->i);
-        TRY(dalloc(p, (char**)&p->d_vec, (size_t)p->nvec * p->N * elem_size(precision) * p->nsets));
+        size_t vec_bytes = 0;  // nvec x N x element size x sets, checked for overflow
+        if (__builtin_mul_overflow((size_t)p->nvec, (size_t)p->N, &vec_bytes) ||
+            __builtin_mul_overflow(vec_bytes, (size_t)elem_size(precision), &vec_bytes) ||
+            __builtin_mul_overflow(vec_bytes, (size_t)p->nsets, &vec_bytes))
+            TRY(fail(KV_ENOMEM, "Krylov vectors: size overflows"));
+        TRY(dalloc(p, (char**)&p->d_vec, vec_bytes));
         if (s->kind == 1) {
             TRY(dalloc(p, &p->d_counters, (size_t)p->i));
             TRY(dalloc(p, &p->d_aug, (size_t)p->i));
