@@ -229,9 +229,12 @@ int kv_system_stencil(kv_ctx *ctx, kv_sys **out, int ndim, const int64_t dims[3]
 /* Sparse system in CSR form (row_ptr n+1 int64 starting at 0 and
  * non-decreasing, col int32 in [0, n), sorted within a row, val).  When
  * on_device is 0 the three arrays are host memory and are copied; when 1 they
- * are device pointers copied device-to-device.  value_precision (KV_FP64 or
- * KV_FP32) is the storage of the values and must match the precision of the
- * problems run on the system.  symmetric: the caller's promise that A is
+ * are device pointers copied device-to-device, after row_ptr and col have been
+ * copied to the host once and checked like host arrays (device arrays need
+ * value_precision KV_FP64).  value_precision (KV_FP64 or KV_FP32) is the
+ * storage of the values and must match the precision of the problems run on
+ * the system.  Errors: KV_EINVAL (malformed arrays, out-of-range or unsorted
+ * columns), KV_ENOMEM, KV_ECUDA.  symmetric: the caller's promise that A is
  * symmetric (enables Lanczos).  b: host, n entries, or NULL. */
 int kv_system_csr(kv_ctx *ctx, kv_sys **out, int64_t n, const int64_t *row_ptr, const int32_t *col,
                   const double *val, const double *b, int symmetric, int value_precision,

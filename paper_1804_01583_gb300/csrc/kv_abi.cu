@@ -310,10 +310,16 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
     if (n < 1 || n >= ((int64_t)1 << 31)) return fail(KV_EINVAL, "kv_system_csr: n out of range");
     if (value_precision != KV_FP64 && value_precision != KV_FP32)
         return fail(KV_EINVAL, "kv_system_csr: value_precision");
+    if (on_device && value_precision != KV_FP64)
+        return fail(KV_EINVAL, "kv_system_csr: device arrays need value_precision KV_FP64 (val is double)");
     int rc = with_device(c->device);
     if (rc) return rc;
+    // device arrays: the row pointers and column indices are checked on the
+    // host like host arrays (the kernels index with them), one copy of each
     std::vector<int64_t> hrp;
+    std::vector<int32_t> hcol;
     const int64_t* rp = row_ptr;
+    const int32_t* cl = col;
     if (on_device) {
         hrp.resize((size_t)n + 1);
         KV_CHECK_CUDA(cudaMemcpy(hrp.data(), row_ptr, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -323,14 +329,17 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
     for (int64_t r = 0; r < n; ++r)
         if (rp[r + 1] < rp[r]) return fail(KV_EINVAL, "kv_system_csr: row_ptr decreases at row %lld", (long long)r);
     const int64_t nnz = rp[n];
-    if (!on_device) {
-        for (int64_t r = 0; r < n; ++r) {
-            for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
-                if (col[e] < 0 || col[e] >= n)
-                    return fail(KV_EINVAL, "kv_system_csr: col[%lld] = %d out of range", (long long)e, col[e]);
-                if (e > rp[r] && col[e] <= col[e - 1])
-                    return fail(KV_EINVAL, "kv_system_csr: row %lld columns not strictly increasing", (long long)r);
-            }
+    if (on_device && nnz > 0) {
+        hcol.resize((size_t)nnz);
+        KV_CHECK_CUDA(cudaMemcpy(hcol.data(), col, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        cl = hcol.data();
+    }
+    for (int64_t r = 0; r < n; ++r) {
+        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+            if (cl[e] < 0 || cl[e] >= n)
+                return fail(KV_EINVAL, "kv_system_csr: col[%lld] = %d out of range", (long long)e, cl[e]);
+            if (e > rp[r] && cl[e] <= cl[e - 1])
+                return fail(KV_EINVAL, "kv_system_csr: row %lld columns not strictly increasing", (long long)r);
         }
     }
     kv_sys* s = new (std::nothrow) kv_sys();

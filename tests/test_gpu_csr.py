@@ -291,3 +291,38 @@ def test_many_output_rows_csr(ctx, method):
     got = run_gpu(ctx, p)
     ref = oracle.run(p)
     assert bound_error(got, ref) <= 1e-9
+
+
+def test_device_arrays_checked_like_host_arrays(ctx):
+    """kv_system_csr with device arrays (on_device = 1): a valid system is
+    accepted; an out-of-range or unsorted column index is rejected with
+    KV_EINVAL before any kernel reads it (the indices are checked on the
+    host); FP32 values are refused (the device values are doubles)."""
+    import ctypes as C
+    import torch
+    lib = kv.load()
+    s = W.random_csr(2000, seed=5)
+    rp = torch.tensor(s.row_ptr, dtype=torch.int64, device="cuda")
+    val = torch.tensor(s.val, dtype=torch.float64, device="cuda")
+
+    def make(col_host, precision=kv.KV_FP64):
+        col = torch.tensor(col_host, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        h = C.c_void_p()
+        rc = lib.kv_system_csr(ctx.h, C.byref(h), int(s.n), rp.data_ptr(), col.data_ptr(), val.data_ptr(), None, 0,
+                               precision, 1)
+        if rc == kv.KV_OK:
+            lib.kv_sys_destroy(h)
+        return rc
+
+    col = np.asarray(s.col, dtype=np.int32)
+    assert make(col) == kv.KV_OK
+    bad = col.copy()
+    bad[len(bad) // 2] = int(s.n)  # out of range
+    assert make(bad) == kv.KV_EINVAL
+    r = int(np.argmax(np.diff(s.row_ptr) >= 2))  # a row with two entries or more
+    uns = col.copy()
+    e0 = int(s.row_ptr[r])
+    uns[e0], uns[e0 + 1] = uns[e0 + 1], uns[e0]
+    assert make(uns) == kv.KV_EINVAL
+    assert make(col, kv.KV_FP32) == kv.KV_EINVAL
