@@ -185,7 +185,10 @@ typedef struct {
  *   m_used   i                             valid columns of H and P
  *   z_star   i                             counter-example z (unsafe only)
  *   err_bound i                            Lemma-1 bound at m_used, for the
- *                                          normalised start vector E_j/||E_j|| */
+ *                                          normalised start vector E_j/||E_j||
+ * H, P, beta0, m_used and err_bound are per Krylov run: i runs, or o runs
+ * under the transpose dynamics (kv_problem_runs gives the count; P is then
+ * i x krylov_m per run). */
 typedef struct {
     double *lo;
     double *hi;
