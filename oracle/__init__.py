@@ -56,7 +56,7 @@ class _Op(C.Structure):
     _fields_ = [("kind", C.c_int), ("ndim", C.c_int), ("dims", C.c_int64 * 3),
                 ("coef", C.c_double), ("h", C.c_double * 3), ("n", C.c_int64),
                 ("rp", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
-                ("b", C.c_void_p), ("aug", C.c_int), ("trans", C.c_int)]
+                ("b", C.c_void_p), ("aug", C.c_int), ("trans", C.c_int), ("face", C.c_void_p)]
 
 
 def _load():
@@ -113,6 +113,12 @@ class _OpHolder:
                 op.h[a] = float(system.h[a]) if a < op.ndim else 1.0
             op.coef = float(system.coef)
             op.n = int(np.prod(system.dims, dtype=np.int64))
+            face = getattr(system, "face", None)
+            if face is not None:
+                ff = np.ascontiguousarray(face, dtype=np.float64)
+                assert ff.shape == (2 * op.ndim,)
+                self.keep.append(ff)
+                op.face = _p(ff)
         else:
             op.kind = 1
             op.n = int(system.n)
@@ -226,10 +232,15 @@ def mu_bound(system, carries_constant: bool) -> float:
 
     Grid Laplacian (symmetric): the largest eigenvalue itself, the Kronecker
     sum of the 1-D Dirichlet second differences' largest eigenvalues
-    -(4/h^2) sin^2(pi / (2(N+1))).  CSR: the Gershgorin bound of the symmetric
+    -(4/h^2) sin^2(pi / (2(N+1))); with face coefficients gamma >= 0 the
+    Gershgorin bound (0 for coef >= 0).  CSR: the Gershgorin bound of the symmetric
     part, max_i a_ii + (sum_{j != i} |a_ij| + |a_ji|) / 2 (+ |b_i|/2, and the
     constant row sum |b_i|/2, for A')."""
     import math
+    if hasattr(system, "dims") and getattr(system, "face", None) is not None:
+        # a point's Gershgorin row: -sum over its neighbours of kappa - sum
+        # over its faces of gamma on the diagonal, sum of |kappa| off it
+        return float(sum(2.0 * (abs(k) - k) for k in (system.coef / (h * h) for h in system.h)))
     if hasattr(system, "dims"):
         return float(sum(-system.coef * 4.0 / (h * h) * math.sin(math.pi / (2.0 * (N + 1))) ** 2
                          for N, h in zip(system.dims, system.h)))

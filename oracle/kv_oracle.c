@@ -11,7 +11,8 @@
  * Everything is IEEE double precision (the paper sizes every buffer with
  * sizeof(double), Sec. 4.3), written in the order the paper states the steps:
  *
- *   ora_apply         y = A x, A a Dirichlet-0 grid Laplacian or a CSR matrix,
+ *   ora_apply         y = A x, A a grid Laplacian (Dirichlet-0, or a coefficient
+ *                     per face of the grid box) or a CSR matrix,
  *                     optionally augmented with the forcing column b and a zero
  *                     row (Sec. 2.1, affine-to-linear transformation).
  *   ora_lanczos       Lanczos with the output projection P = C V computed inside
@@ -60,6 +61,8 @@ typedef struct {
     const double *b;      /* forcing term, n entries, or NULL */
     int aug;              /* 1: the state carries the constant variable at index n */
     int trans;            /* 1: apply the transpose (A^T, or A'^T when aug) */
+    const double *face;   /* grid: gamma per face (x lo, x hi, y lo, y hi, z lo, z hi),
+                             2*ndim entries, or NULL for Dirichlet-0 */
 } ora_op;
 
 int ora_num_threads(void) {
@@ -86,7 +89,39 @@ int64_t ora_dim(const ora_op *op) { return op->n + (op->aug ? 1 : 0); }
 /* Second-order central differences: (A x)_p = coef * sum_axes
  * (x_{p-e} + x_{p+e} - 2 x_p) / h_axis^2, neighbours outside the grid are 0
  * (Dirichlet-0 boundary; semi-finite-difference model of Sec. 5.3). */
+/* The grid operator with a coefficient per face of the box (the heat models
+ * of Sec. 5.3 with insulated or heat-exchanging faces), term by term:
+ * (A x)_p = sum over the neighbours q inside the grid of coef/h_a^2 (x_q - x_p),
+ * minus gamma_f x_p for every face f the point p lies on. */
+static void grid_apply_faces(const ora_op *op, const double *x, double *y) {
+    const int64_t n3[3] = {op->dims[0], op->ndim >= 2 ? op->dims[1] : 1, op->ndim >= 3 ? op->dims[2] : 1};
+    const int64_t stride[3] = {1, n3[0], n3[0] * n3[1]};
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < n3[2]; z++) {
+        for (int64_t yy = 0; yy < n3[1]; yy++) {
+            for (int64_t xx = 0; xx < n3[0]; xx++) {
+                const int64_t coord[3] = {xx, yy, z};
+                const int64_t p = z * stride[2] + yy * stride[1] + xx;
+                const double c = x[p];
+                double acc = 0.0;
+                for (int a = 0; a < op->ndim; a++) {
+                    const double w = op->coef / (op->h[a] * op->h[a]);
+                    if (coord[a] > 0) acc += w * (x[p - stride[a]] - c);
+                    else acc -= op->face[2 * a] * c;
+                    if (coord[a] < n3[a] - 1) acc += w * (x[p + stride[a]] - c);
+                    else acc -= op->face[2 * a + 1] * c;
+                }
+                y[p] = acc;
+            }
+        }
+    }
+}
+
 static void grid_apply(const ora_op *op, const double *x, double *y) {
+    if (op->face) {
+        grid_apply_faces(op, x, y);
+        return;
+    }
     const int64_t nx = op->dims[0];
     const int64_t ny = op->ndim >= 2 ? op->dims[1] : 1;
     const int64_t nz = op->ndim >= 3 ? op->dims[2] : 1;

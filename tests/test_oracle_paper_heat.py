@@ -83,3 +83,64 @@ def test_heat_is_conserved_without_exchange():
     r = oracle.run(p)
     total = p.columns[0].idx.size
     assert np.allclose(r["basis"][0][0], total, rtol=1e-12, atol=0)
+
+
+def _kron_faces(dims, coef, h, face):
+    """Independent dense form of the grid operator with face coefficients: a
+    Kronecker sum of 1-D operators, each the insulated (Neumann) second
+    difference coef/h^2 [1, -2, 1] with end rows [-1, 1], minus gamma on its
+    two end points' diagonals."""
+    mats = []
+    for a, N in enumerate(dims):
+        k = coef / h[a] ** 2
+        T = np.zeros((N, N))
+        for i in range(N - 1):
+            T[i, i + 1] = T[i + 1, i] = k
+            T[i, i] -= k
+            T[i + 1, i + 1] -= k
+        T[0, 0] -= face[2 * a]
+        T[N - 1, N - 1] -= face[2 * a + 1]
+        parts = [np.eye(dims[b]) if b != a else T for b in reversed(range(len(dims)))]
+        K = parts[0]
+        for q in parts[1:]:
+            K = np.kron(K, q)
+        mats.append(K)
+    return sum(mats)
+
+
+@pytest.mark.parametrize("dims", [(6, 5), (5, 4, 3), (4, 6, 7)])
+def test_grid_apply_with_faces_matches_kronecker_sum(dims):
+    rng = np.random.default_rng(len(dims) + dims[0])
+    h = tuple(1.0 / d for d in dims)
+    face = tuple(float(v) for v in rng.uniform(0.0, 3.0, 2 * len(dims)))
+    sysm = W.GridSystem(dims=dims, coef=0.01, h=h, face=face)
+    x = rng.standard_normal(sysm.n)
+    A = _kron_faces(dims, 0.01, h, face)
+    assert np.allclose(oracle.apply(sysm, x), A @ x, rtol=1e-13, atol=1e-13)
+
+
+def test_grid_faces_at_the_dirichlet_value_give_the_dirichlet_operator():
+    dims, coef = (7, 6, 5), 0.01
+    h = tuple(1.0 / (d + 1) for d in dims)
+    face = tuple(coef / h[a // 2] ** 2 for a in range(6))
+    x = np.random.default_rng(3).standard_normal(7 * 6 * 5)
+    a = oracle.apply(W.GridSystem(dims=dims, coef=coef, h=h, face=face), x)
+    b = oracle.apply(W.GridSystem(dims=dims, coef=coef, h=h), x)
+    assert np.allclose(a, b, rtol=1e-13, atol=1e-13)
+
+
+def test_paper_heat_grid_is_the_paper_heat_csr_operator():
+    """The matrix-free form of the paper's heat model (insulated faces,
+    exchange at x = 1) is the CSR matrix paper_heat builds from the 1-D
+    factors, and the oracle's whole run on it gives the same outputs."""
+    N = 10
+    g = W.paper_heat_grid(N, dt=0.2, steps=50, m=40)
+    c = W.paper_heat(N, dt=0.2, steps=50, m=40)
+    x = np.random.default_rng(4).standard_normal(N ** 3)
+    assert np.allclose(oracle.apply(g.system, x), dense(c.system) @ x, rtol=1e-13, atol=1e-13)
+    assert np.array_equal(W.column_dense(g.columns[0], N ** 3, g.system.dims),
+                          W.column_dense(c.columns[0], N ** 3))
+    rg, rc = oracle.run(g), oracle.run(c)
+    S = np.max(np.abs(rc["hi"]))
+    assert np.max(np.abs(rg["hi"] - rc["hi"])) <= 1e-12 * S
+    assert oracle.mu_bound(g.system, False) == 0.0

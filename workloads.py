@@ -29,15 +29,21 @@ import numpy as np
 # --------------------------------------------------------------------------
 @dataclass
 class GridSystem:
-    """dx/dt = coef * Laplacian_h(x) (+ b), Dirichlet-0 outside the grid.
+    """dx/dt = coef * Laplacian_h(x) (+ b), Dirichlet-0 outside the grid
+    unless `face` gives a coefficient per face of the grid box.
 
     dims are (nx, ny) or (nx, ny, nz); x varies fastest in the flat index
-    idx = (z*ny + y)*nx + x.  h holds the grid spacing per axis.
+    idx = (z*ny + y)*nx + x.  h holds the grid spacing per axis.  face:
+    None, or 2*ndim values gamma_f >= 0 (x low, x high, y low, y high, z
+    low, z high): a point on face f gets -gamma_f x_p in place of the coupling
+    coef/h_a^2 (x_q - x_p) to its missing neighbour (coef/h_a^2 is the
+    Dirichlet-0 ghost, 0 an insulated face).
     """
     dims: Tuple[int, ...]
     coef: float
     h: Tuple[float, ...]
     b: Optional[np.ndarray] = None
+    face: Optional[Tuple[float, ...]] = None
 
     @property
     def ndim(self) -> int:
@@ -357,6 +363,37 @@ def paper_heat(N: int = 100, *, dt: float = 0.02, steps: int = 1000, m: int = 80
     return Problem(system=sysm, columns=[col], C_row_ptr=rp, C_col=cc, C_val=cv, theta=np.array([theta]),
                    dt=dt, steps=steps, m=m, err_target=err_target, precision=precision,
                    name=f"paper-heat3d-{N}^3")
+
+
+def paper_heat_exchange_face(N: int, coef: float = 0.01, exchange: float = 0.5) -> float:
+    """The face coefficient of the x = 1 face of the paper's heat model on N
+    cells per axis (Sec. 5.3, as in paper_heat_factors): g / h with
+    g = exchange (2 coef/h) / (2 coef/h + exchange), h = 1/N."""
+    h = 1.0 / N
+    return exchange * (2 * coef / h) / (2 * coef / h + exchange) / h
+
+
+def paper_heat_grid(N: int = 100, *, dt: float = 0.02, steps: int = 1000, m: int = 800, err_target: float = 0.0,
+                    zlo: float = 0.9, zhi: float = 1.1, theta: float = math.inf, precision: str = "fp64",
+                    coef: float = 0.01, exchange: float = 0.5) -> Problem:
+    """paper_heat as a matrix-free grid system: N^3 cells of width h = 1/N,
+    coupling coef/h^2, every face insulated (gamma = 0) except x = 1
+    (gamma = paper_heat_exchange_face); the heated region as one box column
+    (the cells whose centres lie in [0, 0.4] x [0, 0.2] x [0, 0.1]); the output
+    the mean of the 8 cells around the centre.  The same operator, column and
+    output as paper_heat."""
+    h = 1.0 / N
+    face = (0.0, paper_heat_exchange_face(N, coef, exchange), 0.0, 0.0, 0.0, 0.0)
+    sysm = GridSystem(dims=(N, N, N), coef=coef, h=(h, h, h), face=face)
+    centres = (np.arange(N) + 0.5) / N
+    bx, by, bz = (int(np.sum(centres <= lim)) for lim in (0.4, 0.2, 0.1))
+    col = Column(kind="box", zlo=zlo, zhi=zhi, box_lo=(0, 0, 0), box_hi=(bx, by, bz), value=1.0)
+    c = [N // 2 - 1, N // 2]
+    cells = [(z * N + y) * N + x for z in c for y in c for x in c]
+    rp, cc, cv = _c_rows([(cells, [0.125] * 8)])
+    return Problem(system=sysm, columns=[col], C_row_ptr=rp, C_col=cc, C_val=cv, theta=np.array([theta]),
+                   dt=dt, steps=steps, m=m, err_target=err_target, precision=precision,
+                   name=f"paper-heat3d-grid-{N}^3")
 
 
 def replicated_blocks(h: int, *, seed: int = 0, dt: float = 0.1, steps: int = 300, m: int = 28,
