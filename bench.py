@@ -200,6 +200,82 @@ def cpu_baseline(p, iters: int = 4):
 
 
 # ------------------------------------------------------------------ GPU arm
+GRID_KERNELS = ["lanczos_fused", "lanczos_fused64", "stencil_update", "stencil_alpha", "stencil_init", "expm_per_step",
+                "expm_propagate", "bounds", "bounds_finish"]
+
+
+def fp64_instr_per_launch(p) -> float:
+    """Algorithmic FP64 instructions of one single-pass FP64 iteration: the
+    update w = fx (l + r) + fy (d + u) + fz (m + p) + fc c + fa a takes 3
+    pair sums, 1 multiply and 4 fused multiply-adds a grid point (3 FMAs in
+    the first iteration, which has no v_{j-1}); averaged over a query's m
+    launches."""
+    return p.system.n * (7.0 + 8.0 * (p.m - 1)) / p.m
+
+
+def time_query(ctx, ph, stream, steps: int, warmup: int, torch, barrier=None, clocks=None):
+    """Device time of `steps` enqueues of one query (CUDA events on the
+    library stream) with per-kernel times from the library's own events."""
+    for _ in range(warmup):
+        ph.enqueue()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    ctx.profile_enable(True)
+    if clocks:
+        clocks.start()
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.mark(0)
+    ev0.record(stream)
+    for _ in range(steps):
+        ph.enqueue()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark(1)
+    if barrier:
+        barrier()
+    clk = clocks.stop() if clocks else None
+    ms_total = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    kern = {}
+    for name in GRID_KERNELS:
+        nl, tms = ctx.profile_read(name)
+        if nl:
+            kern[name] = (nl, tms)
+    ctx.profile_enable(False)
+    return ms_total, kern, launches, clk
+
+
+def roofline(dom: str, kern: dict, p, fp64_peak: float) -> dict:
+    """Roofline of the dominant kernel: algorithmic work per launch over its
+    average launch time (library events), against the measured peak."""
+    nl, tms = kern[dom]
+    avg_s = tms / nl * 1e-3
+    bpi = bytes_per_iteration(p)
+    hbm_peak, hbm_kind = peaks()
+    if dom == "lanczos_fused64":
+        instr = fp64_instr_per_launch(p)
+        ach = instr / avg_s / 1e12
+        pk = fp64_peak / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk, "unit": "T FP64-instr/s",
+                "frac": ach / pk,
+                "peak_kind": "measured in this run: kv_diag_fp64_rate (FP64 FMA chains on every SM, best of 5, "
+                             "CUDA events)",
+                "algorithmic_fp64_instr_per_launch": instr, "avg_launch_ms": avg_s * 1e3,
+                "algorithmic_bytes_per_launch": bpi, "hbm_achieved_gbs": bpi / avg_s / 1e9,
+                "hbm_frac": bpi / avg_s / 1e9 / hbm_peak, "traffic": profiled_traffic(dom, p)}
+    alg = {"lanczos_fused": bpi, "stencil_update": bpi, "stencil_alpha": bpi / 3.0}.get(dom)
+    ach = alg / avg_s / 1e9 if alg else None
+    return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+            "frac": (ach / hbm_peak) if ach else None, "peak_kind": hbm_kind + " (copy, burst)",
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3, "traffic": profiled_traffic(dom, p)}
+
+
 def run_gpu(args, rank: int, world: int):
     import torch
     import paper_1804_01583_gb300 as kv
@@ -208,6 +284,7 @@ def run_gpu(args, rank: int, world: int):
     kvbuild.build()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    fp64_peak, fp64_add = kv.diag_fp64_rate(dev)
     p = workload(args.workload, args.precision)
     pool_bytes = max(kv_bytes_guess(p), 1 << 30)
     stream = torch.cuda.Stream()
@@ -219,37 +296,8 @@ def run_gpu(args, rank: int, world: int):
         if world > 1:
             torch.distributed.barrier()
 
-    # warm-up
-    for _ in range(args.warmup):
-        ph.enqueue()
-    torch.cuda.synchronize()
-    # timed region (device events on the library stream)
-    launches0 = ctx.launch_count()
-    ctx.profile_enable(True)
-    clocks = ClockSampler(dev)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    clocks.mark(0)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        ph.enqueue()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clocks.mark(1)
-    barrier()
-    clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    launches = ctx.launch_count() - launches0
-    kern = {}
-    for name in ["lanczos_fused", "stencil_update", "stencil_alpha", "stencil_init", "expm_per_step", "expm_propagate",
-                 "bounds", "bounds_finish"]:
-        nl, tms = ctx.profile_read(name)
-        if nl:
-            kern[name] = (nl, tms)
-    ctx.profile_enable(False)
+    ms_total, kern, launches, clk = time_query(ctx, ph, stream, args.steps, args.warmup, torch, barrier,
+                                               ClockSampler(dev))
     res = ph.fetch(full=False)
     ph.close()
     sysh.close()
@@ -277,31 +325,7 @@ def run_gpu(args, rank: int, world: int):
     out_e2e = {"value": replica_throughput(p.m * bpi, e2e, world) / 1e9, "unit": "GB/s", "ms_per_step": e2e,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    peak, peak_kind = peaks()
-    # dominant kernel: largest share of the timed region
     dom = max(kern, key=lambda k: kern[k][1])
-    nl, tms = kern[dom]
-    avg_s = tms / nl * 1e-3
-    if dom in ("lanczos_fused", "stencil_update"):
-        alg_bytes = bpi  # reads v_j and v_{j-1}, writes w: 3 vectors of n elements
-    elif dom == "stencil_alpha":
-        alg_bytes = bpi / 3.0
-    else:
-        alg_bytes = None
-    if p.precision == "fp64" and dom in ("stencil_update", "stencil_alpha"):
-        # the FP64 grid passes are bound by the FP64 pipe (9 and 8 FP64
-        # instructions per grid point; peak 2 per SM per clock)
-        dp = {"stencil_update": 9.0, "stencil_alpha": 8.0}[dom] * p.system.n
-        dp_peak = 2.0 * 152 * 2.07e9 / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": dp / avg_s / 1e12, "peak": dp_peak,
-                "unit": "T FP64-instr/s", "frac": dp / avg_s / 1e12 / dp_peak,
-                "peak_kind": "derived: 2 FP64 instructions per SM per clock x 152 SMs x 2.07 GHz",
-                "algorithmic_fp64_instr_per_launch": dp, "traffic": None}
-    else:
-        achieved = alg_bytes / avg_s / 1e9 if alg_bytes else None
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind + " (copy, burst)",
-                "algorithmic_bytes_per_launch": alg_bytes, "traffic": profiled_traffic(dom, p)}
     kernels = {k: {"launches": v[0], "avg_ms": v[1] / v[0], "share": v[1] / ms_total} for k, v in kern.items()}
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -310,21 +334,28 @@ def run_gpu(args, rank: int, world: int):
         "data": "synthetic",
         "config": {"workload": p.name, "n": p.system.n, "krylov_m": p.m, "steps_per_query": p.steps,
                    "precision": p.precision, "expm": args.expm, "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "bytes_per_point_per_iteration": 3 * (8 if p.precision == "fp64" else 4)},
         "queries_per_s": world * 1e3 / ms_step,
-        "roofline": roof, "kernels": kernels, "e2e": out_e2e, "gpu_launches": launches,
-        "clocks": clk, "first_violation_step": res["viol_step"],
+        "roofline": roofline(dom, kern, p, fp64_peak), "kernels": kernels, "e2e": out_e2e,
+        "gpu_launches": launches, "clocks": clk, "first_violation_step": res["viol_step"],
         "lemma1_bound": float(res["err_bound"][0]),
+        "fp64_rate": {"fma_per_s": fp64_peak, "add_per_s": fp64_add, "sms": torch.cuda.get_device_properties(dev)
+                      .multi_processor_count},
     }
-    if args.compare_fp64 and p.precision != "fp64":
-        line["fp64_plain"] = time_other_precision(kv, ctx, args, "fp64", torch, stream)
+    if args.compare_fp64:
+        other = "fp32" if p.precision == "fp64" else "fp64"
+        sub = time_other_precision(kv, ctx, args, other, torch, stream, fp64_peak)
+        sub["speedup_over_fp64" if other == "fp32" else "speedup_of_fp32"] = (
+            ms_step / sub["ms_per_step"] if other == "fp32" else sub["ms_per_step"] / ms_step)
+        line["fp32_storage" if other == "fp32" else "fp64_plain"] = sub
     ctx.close()
     return line, p
 
 
-def time_other_precision(kv, ctx, args, precision, torch, stream):
-    """The same query in another storage precision on the same context
-    (context only; the headline value is the main form)."""
+def time_other_precision(kv, ctx, args, precision, torch, stream, fp64_peak):
+    """The same query in the other storage precision on the same context, with
+    its own kernel times and roofline."""
     q = workload(args.workload, precision)
     sysh = kv.System(ctx, q.system, q.precision)
     try:
@@ -332,21 +363,18 @@ def time_other_precision(kv, ctx, args, precision, torch, stream):
     except kv.KvError as e:
         sysh.close()
         return {"skipped": str(e)}
-    ph.enqueue()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    k = 2
-    e0.record(stream)
-    for _ in range(k):
-        ph.enqueue()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / k
+    k = max(2, args.steps)
+    ms_total, kern, launches, _ = time_query(ctx, ph, stream, k, max(1, args.warmup), torch)
     ph.close()
     sysh.close()
-    return {"precision": precision, "ms_per_step": ms, "value": q.m * bytes_per_iteration(q) / (ms * 1e-3) / 1e9,
-            "unit": "GB/s", "steps": k}
+    ms = ms_total / k
+    dom = max(kern, key=lambda x: kern[x][1])
+    return {"precision": precision, "dtype": "f32" if precision == "fp32" else "f64", "ms_per_step": ms,
+            "value": q.m * bytes_per_iteration(q) / (ms * 1e-3) / 1e9, "unit": "GB/s", "steps": k,
+            "bytes_per_point_per_iteration": 3 * (8 if precision == "fp64" else 4),
+            "roofline": roofline(dom, kern, q, fp64_peak),
+            "kernels": {x: {"launches": v[0], "avg_ms": v[1] / v[0], "share": v[1] / ms_total}
+                        for x, v in kern.items()}, "gpu_launches": launches}
 
 
 def profiled_traffic(kernel: str, p):
@@ -367,15 +395,38 @@ def profiled_traffic(kernel: str, p):
         return None
 
 
+SERVE_KINDS = ("heat2d", "heat3d", "csr")
+
+
+def serve_kind(q) -> str:
+    return next(k for k in SERVE_KINDS if f"-{k}" in q.name)
+
+
+def serve_oracle_sample(qs, per_kind: int = 6, seed: int = 7):
+    """Queries whose served results the CPU leg compares with the oracle:
+    `per_kind` of each kind, drawn with a seed among those the oracle runs in
+    about a second on the host (heat grids up to 250^3 points, CSR systems up
+    to 5e5 rows)."""
+    rng = np.random.default_rng(seed)
+    pick = []
+    for kind in SERVE_KINDS:
+        ok = [i for i, q in enumerate(qs) if serve_kind(q) == kind and
+              (q.system.n <= 250 ** 3 if kind != "csr" else q.system.n <= 500_000)]
+        pick += [int(i) for i in rng.choice(ok, size=min(per_kind, len(ok)), replace=False)]
+    return sorted(pick)
+
+
 def serve_bench(args, dev: int):
     """The serving stream: a seeded mix of queries (2D heat n = 1e4..4e6, 3D heat
     n = 1e6..6.4e7, random CSR n = 1e5..2e6 with 1..32 generators; horizons
     100..2000 steps, m 20..60; FP32 storage) through the continuous-batching
     server.  A burst of all queries measures capacity; then Poisson arrivals at
     0.8 x capacity give queries/s and the p50 / p99 latency from kv_submit to
-    the results on the host.  The FP32 bounds are compared with the FP64 GPU
-    path (parity-tested against the oracle by the tests, served results included)
-    on a random sample."""
+    the results on the host, overall and per query kind.  The same mix run one
+    query at a time without the server, in FP64 (the plain method) and in
+    FP32, gives the served form's speed-up.  The FP32 bounds are compared with
+    the FP64 GPU path on a random sample; the sampled served results are kept
+    for the CPU leg, which compares them with the oracle."""
     import torch
     import paper_1804_01583_gb300 as kv
 
@@ -427,6 +478,21 @@ def serve_bench(args, dev: int):
     st = srv.stats()
     srv.close()
     lat = np.array([res[i]["latency_ms"] for i in range(len(qs))])
+    kinds = [serve_kind(q) for q in qs]
+    per_kind = {}
+    for kind in SERVE_KINDS:
+        lk = np.array([lat[i] for i in range(len(qs)) if kinds[i] == kind])
+        per_kind[kind] = {"queries": int(lk.size), "p50_ms": float(np.percentile(lk, 50)),
+                          "p99_ms": float(np.percentile(lk, 99)), "max_ms": float(np.max(lk))}
+    # the same mix one query at a time through kv_run (no server): the plain
+    # FP64 method and the FP32 storage form
+    plain = {}
+    for prec in ("fp64", "fp32"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q in qs:
+            kv.solve(W.Problem(**{**q.__dict__, "precision": prec}), ctx, expm_mode="propagate")
+        plain[prec] = time.perf_counter() - t0
     # accuracy of the FP32 results against the FP64 form on the same GPU
     sample = np.random.default_rng(7).choice(len(qs), size=min(24, len(qs)), replace=False)
     err_gpu64 = 0.0
@@ -434,17 +500,46 @@ def serve_bench(args, dev: int):
         q64 = W.Problem(**{**qs[int(i)].__dict__, "precision": "fp64"})
         err_gpu64 = max(err_gpu64, bound_error(res[int(i)], kv.solve(q64, ctx, expm_mode="propagate")))
     ctx.close()
-    kinds = {"heat2d": 0, "heat3d": 0, "csr": 0}
-    for q in qs:
-        for kk in kinds:
-            if f"-{kk}" in q.name:
-                kinds[kk] += 1
-    return {"queries": len(qs), "mix": kinds, "slots": args.serve_slots, "pool_gb": args.serve_pool_gb,
-            "capacity_qps": cap, "arrival_rate_qps": rate, "queries_per_s": len(qs) / elapsed,
+    osample = serve_oracle_sample(qs)
+    SERVED_FOR_ORACLE.clear()
+    SERVED_FOR_ORACLE.extend((i, qs[i], res[i]) for i in osample)
+    return {"queries": len(qs), "mix": {kk: kinds.count(kk) for kk in SERVE_KINDS}, "slots": args.serve_slots,
+            "pool_gb": args.serve_pool_gb, "capacity_qps": cap, "arrival_rate_qps": rate,
+            "queries_per_s": len(qs) / elapsed,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "per_kind": per_kind,
             "max_running": st["max_running"], "memory_waits": st["memory_waits"],
+            "plain_fp64_sequential_s": plain["fp64"], "plain_fp32_sequential_s": plain["fp32"],
+            "served_makespan_s": makespan,
+            "speedup_over_plain_fp64": plain["fp64"] / makespan,
+            "speedup_over_plain_fp32": plain["fp32"] / makespan,
             "max_rel_bound_err_vs_fp64_gpu": err_gpu64, "fp64_gpu_sample": f"{len(sample)} random queries",
+            "oracle_sample": osample,
             "precision": "fp32 storage, fp64 accumulation"}
+
+
+# served results (index, query, result) that the CPU leg compares with the oracle
+SERVED_FOR_ORACLE: list = []
+
+
+def serve_oracle_errors() -> dict:
+    """CPU leg: the sampled served FP32 results against the FP64 oracle
+    (scale-normalised bound error per output row, as the parity tests)."""
+    import oracle
+    worst, per = 0.0, {}
+    t0 = time.perf_counter()
+    for i, q, got in SERVED_FOR_ORACLE:
+        ref = oracle.run(W.Problem(**{**q.__dict__, "precision": "fp64"}))
+        e = 0.0
+        for r in range(ref["hi"].shape[0]):
+            S = max(np.max(np.abs(ref["lo"][r])), np.max(np.abs(ref["hi"][r])))
+            d = max(np.max(np.abs(got["lo"][r] - ref["lo"][r])), np.max(np.abs(got["hi"][r] - ref["hi"][r])))
+            e = max(e, d / S if S > 0 else d)
+        kind = serve_kind(q)
+        per[kind] = max(per.get(kind, 0.0), e)
+        worst = max(worst, e)
+    return {"max_rel_bound_err_vs_fp64_oracle": worst, "per_kind": per, "queries": len(SERVED_FOR_ORACLE),
+            "oracle_s": time.perf_counter() - t0}
 
 
 def error_control_bench(dev: int):
@@ -743,9 +838,9 @@ def csr_bench(args, dev: int, n: int = 2_000_000, legs=None):
 
 
 def kv_bytes_guess(p) -> int:
-    # the larger of the FP32 form (three float vectors) and the FP64 two-pass
-    # form (two double vectors), which may run on the same context
-    return int(max(3 * 4, 2 * 8) * p.system.n * 1.02) + (512 << 20)
+    # the FP64 single-pass form (three double vectors); the FP32 form (three
+    # float vectors) runs on the same context after it
+    return int(3 * 8 * p.system.n * 1.02) + (512 << 20)
 
 
 def main():
@@ -755,7 +850,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kv", choices=["kv", "reference"])
     ap.add_argument("--workload", default="heat3d-1000", choices=["heat3d-1000", "heat3d-100", "heat2d-20", "heat3d-512"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--expm", default="per_step", choices=["per_step", "propagate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=24)
@@ -842,6 +937,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(workload(args.workload, "fp64"), iters=args.cpu_iters)
         line["cpu_baseline"]["configs"] = cpu_configs()
+        if "serving" in line and SERVED_FOR_ORACLE:
+            oe = serve_oracle_errors()
+            line["serving"]["max_rel_bound_err_vs_fp64_oracle"] = oe["max_rel_bound_err_vs_fp64_oracle"]
+            line["serving"]["oracle_check"] = oe
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -62,6 +62,17 @@ extern "C" {
                            pairs and summed in double; H, the exponential and
                            the bounds are double */
 
+#define KV_PREC_AUTO 2  /* kv_problem / kv_problem_bytes: KV_FP64 when the operator is
+                           symmetric and its largest-eigenvalue bound mu (the one of the
+                           error control) gives mu * steps * dt > -1 -- its slowest
+                           mode loses less than a factor e over the horizon, so FP32
+                           rounding of the stored Krylov vectors reaches the last
+                           outputs undamped (an insulated heat model: measured
+                           1.2e-6 .. 2.4e-6 with FP32 storage against the FP64 oracle)
+                           -- else KV_FP32.  CSR systems keep their value precision;
+                           KV_EINVAL when the rule asks for FP64 and the values are
+                           FP32.  kv_problem_precision reports the choice. */
+
 /* Krylov method */
 #define KV_AUTO 0       /* Lanczos when the system is symmetric and the column
                            does not carry the constant variable, else Arnoldi */
@@ -229,6 +240,24 @@ int kv_pool_stats(const kv_ctx *ctx, size_t *in_use, size_t *total);
 int kv_system_stencil(kv_ctx *ctx, kv_sys **out, int ndim, const int64_t dims[3], double coef,
                       const double h[3], const double *b);
 
+/* Matrix-free grid system with a coefficient per face of the grid box (the
+ * boundary models of Sec. 5.3).  face: host, 2*ndim entries (x low, x high,
+ * y low, y high[, z low, z high]), each finite and >= 0, or NULL for
+ * Dirichlet-0 (then identical to kv_system_stencil).  A grid point p on face
+ * f gets -face[f] v_p in place of the coupling coef/h_a^2 (v_q - v_p) to its
+ * missing neighbour q:
+ *     (A v)_p = sum over neighbours q in the grid of coef/h_a^2 (v_q - v_p)
+ *               - sum over the faces f that p lies on of face[f] v_p.
+ * face[f] = coef/h_a^2 is the Dirichlet-0 boundary of the vertex grid (the
+ * ghost value 0), 0 an insulated face, and for the paper's heat model (unit
+ * cube of N^3 cells, h = 1/N, insulated except x = 1 with heat exchange
+ * constant g0 toward ambient 0) face[1] = g / h with
+ * g = g0 (2 coef/h) / (2 coef/h + g0), the half cell between the last
+ * cell's centre and the face eliminated.  A is symmetric, so KV_AUTO picks
+ * Lanczos.  Errors: KV_EINVAL (bad sizes or face values), KV_ENOMEM, KV_ECUDA. */
+int kv_system_grid(kv_ctx *ctx, kv_sys **out, int ndim, const int64_t dims[3], double coef,
+                   const double h[3], const double *face, const double *b);
+
 /* Sparse system in CSR form (row_ptr n+1 int64 starting at 0 and
  * non-decreasing, col int32 in [0, n), sorted within a row, val).  When
  * on_device is 0 the three arrays are host memory and are copied; when 1 they
@@ -251,6 +280,10 @@ int kv_sys_destroy(kv_sys *sys);
 int kv_problem(kv_ctx *ctx, kv_prob **out, const kv_sys *sys, const kv_problem_desc *desc,
                int precision);
 int kv_prob_destroy(kv_prob *prob);
+
+/* Storage precision a problem runs in (KV_FP64 or KV_FP32; the choice made
+ * for KV_PREC_AUTO). */
+int kv_problem_precision(const kv_prob *prob, int32_t *precision);
 
 /* Number of Krylov runs of a problem (i, or o with the transpose dynamics)
  * and whether the transpose dynamics run: the length of the per-run arrays of
@@ -415,15 +448,21 @@ int kv_check_polytope(kv_prob *prob, const kv_polytope *unsafe, const kv_polytop
 
 /* Projected Lanczos on a small grid without any device allocation.  The paper
  * has no counterpart: this exists for callers that cannot allocate device
- * memory when they need a result -- code running while a CUDA graph is being
- * captured (cudaMalloc cannot be captured), real-time or embedded hosts that
- * reserve all device memory up front, callers inside another runtime's
- * allocator.  It runs the FP64 two-pass grid Lanczos iterations of kv_run for
- * one box column (value on box_lo <= idx < box_hi) on the grid of
- * kv_system_stencil (no forcing term) and writes H ((krylov_m+1) x krylov_m,
- * row-major), P (o x krylov_m: C v_l), beta0 (||E||) and m_used (valid
- * columns) to the caller's device buffers; C is given in CSR form with device
- * arrays (c_row_ptr o+1, c_col and c_val c_row_ptr[o] entries).  All working
+ * memory when they need a result -- real-time or embedded hosts that reserve
+ * all device memory up front and forbid allocation afterwards, callers running
+ * inside another runtime's allocator or memory-pool callback, which must not
+ * re-enter the driver's allocator.  It runs the FP64 two-pass grid Lanczos
+ * iterations of kv_run for one box column (value on box_lo <= idx < box_hi) on
+ * the grid of kv_system_stencil (Dirichlet-0, no forcing term) and writes H
+ * ((krylov_m+1) x krylov_m, row-major), P (o x krylov_m: C v_l), beta0
+ * (||E||) and m_used (valid columns) to the caller's device buffers.
+ * krylov_m is in [1, KV_MAX_M]: the main path's larger Lanczos limit serves
+ * its error control, which this entry point does not have.  C is given in
+ * CSR form with device arrays: c_row_ptr holds o+1 offsets, c_col and c_val
+ * hold c_row_ptr[o] entries each (the caller guarantees these lengths).  The
+ * first kernel checks what it can: offsets that do not start at 0 or that
+ * decrease, or a column index outside [0, n), end the call's work before
+ * anything is read through them, with m_used = -1 and H, P zero.  All working
  * memory (two Krylov vectors, reduction partials, column state, about
  * 4.2 MB) lives in one fixed device array that every GPU loading the library
  * holds until exit; nothing is allocated or freed.  Grids with more than
@@ -432,8 +471,11 @@ int kv_check_polytope(kv_prob *prob, const kv_polytope *unsafe, const kv_polytop
  * without waiting.  The array is shared by all calls on a device and keeps
  * the last call's contents: calls whose work overlaps on the GPU race on it.
  * The first call on a device looks up the array's address on that device;
- * make that first call before any stream capture begins.  Errors: KV_EINVAL,
- * KV_ECUDA. */
+ * make that first call before any stream capture begins.  That address is
+ * kept for the life of the process, so after cudaDeviceReset on a device this
+ * entry point must not be called on it again.  The calling thread's current
+ * device is the same after the call as before.  Errors: KV_EINVAL (NULL
+ * argument, bad sizes), KV_ECUDA. */
 int kv_grid_lanczos_noalloc(int device, void *stream, int ndim, const int64_t dims[3], double coef,
                             const double h[3], const int64_t box_lo[3], const int64_t box_hi[3], double value,
                             int32_t o, const int64_t *c_row_ptr, const int64_t *c_col, const double *c_val,
@@ -450,6 +492,16 @@ int kv_grid_lanczos_noalloc(int device, void *stream, int ndim, const int64_t di
  * (the expected outcome), KV_OK if it did not, KV_EINVAL for a bad argument,
  * KV_ECUDA on a CUDA error.  The device and any context on it stay usable. */
 int kv_diag_bounded_wait(int device, int64_t polls);
+
+/* The device's FP64 instruction rate, measured.  Not in the paper: the FP64
+ * grid iteration is bound by the FP64 pipe of this GPU (not by HBM), and its
+ * roofline takes this rate as the peak.  Runs eight independent chains of
+ * FP64 fused multiply-adds (then of FP64 additions) per thread on 8 blocks of
+ * 256 threads per SM and reports operations per second (one FMA or add of
+ * one thread = one operation) over the best of five timed launches.
+ * Allocates a small device buffer and a stream for the call and waits for
+ * them.  Errors: KV_EINVAL (NULL argument, bad device), KV_ECUDA. */
+int kv_diag_fp64_rate(int device, double *fma_per_s, double *add_per_s);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,8 @@ KV_MAX_M = 256
 KV_MAX_M_LANCZOS = 4096
 KV_FLAG_TWO_PASS = 1
 
-_PREC = {"fp64": KV_FP64, "fp32": KV_FP32}
+KV_PREC_AUTO = 2
+_PREC = {"fp64": KV_FP64, "fp32": KV_FP32, "auto": KV_PREC_AUTO}
 _METH = {"auto": KV_AUTO, "lanczos": KV_LANCZOS, "arnoldi": KV_ARNOLDI}
 _EXPM = {"per_step": KV_EXPM_PER_STEP, "propagate": KV_EXPM_PROPAGATE}
 KV_SIM_FORWARD, KV_SIM_TRANSPOSE, KV_SIM_AUTO = 0, 1, 2
@@ -84,9 +85,11 @@ class kv_lp_result(C.Structure):
 KV_LP_OPTIMAL, KV_LP_FAILED, KV_LP_EMPTY, KV_LP_ITER = 0, 1, 2, 3
 
 EXPORTED = ["kv_version", "kv_last_error", "kv_create", "kv_destroy", "kv_pool_stats", "kv_system_stencil",
+            "kv_system_grid",
             "kv_system_csr", "kv_sys_destroy", "kv_problem", "kv_prob_destroy", "kv_problem_bytes",
             "kv_enqueue", "kv_fetch", "kv_run", "kv_profile_enable", "kv_profile_read", "kv_launch_count",
-            "kv_problem_runs", "kv_diag_bounded_wait", "kv_check_polytope"]
+            "kv_problem_runs", "kv_diag_bounded_wait", "kv_check_polytope", "kv_diag_fp64_rate",
+            "kv_problem_precision"]
 
 _lib = None
 _lock = threading.Lock()
@@ -112,7 +115,10 @@ def load(path: Optional[str] = None):
         lib.kv_pool_stats.argtypes = [V, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         lib.kv_system_stencil.argtypes = [V, C.POINTER(V), I, C.POINTER(C.c_int64), C.c_double,
                                           C.POINTER(C.c_double), V]
+        lib.kv_system_grid.argtypes = [V, C.POINTER(V), I, C.POINTER(C.c_int64), C.c_double,
+                                       C.POINTER(C.c_double), V, V]
         lib.kv_system_csr.argtypes = [V, C.POINTER(V), C.c_int64, V, V, V, V, I, I, I]
+        lib.kv_diag_fp64_rate.argtypes = [I, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.kv_sys_destroy.argtypes = [V]
         lib.kv_problem.argtypes = [V, C.POINTER(V), V, C.POINTER(kv_problem_desc), I]
         lib.kv_prob_destroy.argtypes = [V]
@@ -203,7 +209,8 @@ class Context:
 
 
 class System:
-    """kv_system_stencil / kv_system_csr / kv_sys_destroy for a workloads system."""
+    """kv_system_stencil (kv_system_grid when the grid has face coefficients) /
+    kv_system_csr / kv_sys_destroy for a workloads system."""
 
     def __init__(self, ctx: Context, system, precision: str = "fp64"):
         self.ctx = ctx
@@ -215,13 +222,21 @@ class System:
             nd = len(system.dims)
             dims = (C.c_int64 * 3)(*[int(system.dims[a]) if a < nd else 1 for a in range(3)])
             hh = (C.c_double * 3)(*[float(system.h[a]) if a < nd else 1.0 for a in range(3)])
-            _check(lib.kv_system_stencil(ctx.h, C.byref(h), nd, dims, float(system.coef), hh, _ptr(bb)))
+            face = getattr(system, "face", None)
+            if face is None:
+                _check(lib.kv_system_stencil(ctx.h, C.byref(h), nd, dims, float(system.coef), hh, _ptr(bb)))
+            else:
+                ff = np.ascontiguousarray(face, dtype=np.float64)
+                if ff.shape != (2 * nd,):
+                    raise ValueError(f"face must hold {2 * nd} coefficients")
+                _check(lib.kv_system_grid(ctx.h, C.byref(h), nd, dims, float(system.coef), hh, _ptr(ff), _ptr(bb)))
         else:
             rp = np.ascontiguousarray(system.row_ptr, dtype=np.int64)
             col = np.ascontiguousarray(system.col, dtype=np.int32)
             val = np.ascontiguousarray(system.val, dtype=np.float64)
             _check(lib.kv_system_csr(ctx.h, C.byref(h), int(system.n), _ptr(rp), _ptr(col), _ptr(val), _ptr(bb),
-                                     1 if system.symmetric else 0, _PREC[precision], 0))
+                                     1 if system.symmetric else 0,
+                                     KV_FP64 if precision == "auto" else _PREC[precision], 0))
         self.h = h
         self.n = int(system.n)
 
@@ -301,6 +316,9 @@ class ProblemHandle:
         runs, tr = C.c_int32(), C.c_int32()
         _check(ctx._lib.kv_problem_runs(h, C.byref(runs), C.byref(tr)))
         self.runs, self.transposed = int(runs.value), bool(tr.value)
+        prec = C.c_int32()
+        _check(ctx._lib.kv_problem_precision(h, C.byref(prec)))
+        self.precision = "fp64" if prec.value == KV_FP64 else "fp32"
 
     def enqueue(self):
         _check(self.ctx._lib.kv_enqueue(self.h))
@@ -528,6 +546,14 @@ class Server:
 
 
 KV_NOALLOC_MAX_N = 262144
+
+
+def diag_fp64_rate(device: int = 0):
+    """kv_diag_fp64_rate: (FP64 FMA/s, FP64 add/s) measured on the device."""
+    lib = load()
+    f, a = C.c_double(), C.c_double()
+    _check(lib.kv_diag_fp64_rate(device, C.byref(f), C.byref(a)))
+    return f.value, a.value
 
 
 def grid_lanczos_noalloc(device: int, stream, ndim: int, dims, coef: float, h, box_lo, box_hi, value: float,

@@ -1,26 +1,34 @@
 // k_noalloc.cu -- grid Lanczos for small grids without any device allocation.
 //
 // Some callers cannot allocate device memory at the moment they need a
-// result: code running while a CUDA graph is being captured (cudaMalloc is
-// not capturable), real-time or embedded hosts that reserve all device
-// memory up front and forbid allocation afterwards, and callers inside another
-// runtime's allocator that must not take the driver's allocation lock.  For
-// them, kv_grid_lanczos_noalloc runs the projected Lanczos iterations on a
-// small grid with every piece of working memory -- the two Krylov vectors, the
-// reduction partials, the column state -- in one file-scope device array of
-// fixed size.  The caller passes the inputs and the output buffers; nothing
-// is allocated or freed, by this file or by any library it calls.
+// result: real-time or embedded hosts that reserve all device memory up front
+// and forbid allocation afterwards, and callers running inside another
+// runtime's allocator or memory-pool callback, which must not re-enter the
+// driver's allocator.  For them, kv_grid_lanczos_noalloc runs the projected
+// Lanczos iterations on a small grid with every piece of working memory -- the
+// two Krylov vectors, the reduction partials, the column state -- in one
+// file-scope device array of fixed size.  The caller passes the inputs and the
+// output buffers; nothing is allocated or freed, by this file or by any
+// library it calls.
 //
 // The kernels are a variant of the two-pass FP64 grid passes of the main
 // path (same arithmetic: alpha_j = v_j . A v_j, then w = A v_j - alpha_j v_j -
 // beta_j v_{j-1} stored over v_{j-1}), flattened to one thread per grid point
 // in a fixed grid of KV_NA_BLOCKS blocks so the scratch size is known.
 //
+// C comes as device arrays the host never sees, so the first kernel checks
+// them (offsets from 0, never decreasing; column indices inside the grid)
+// before anything reads the grid through them; rejected arrays end the call's
+// work with m_used = -1.
+//
 // The scratch array is shared by every call on a device and keeps the last
 // call's contents; calls that overlap on the GPU (on different streams, or
 // from different host threads) race on it.  The first call on a device looks
 // up the array's device address (cudaGetSymbolAddress) with that device
-// current; make that first call before any stream capture begins.
+// current; make that first call before any stream capture begins.  The
+// address is kept for the life of the process: after a reset of the device
+// (cudaDeviceReset) it is stale, so the entry point must not be called on that
+// device again in the same process.
 #include <mutex>
 
 #include "kv_internal.h"
@@ -56,10 +64,35 @@ __device__ __forceinline__ double na_stencil(const double* B, const NaGrid& g, i
     return g.kx * (l + r) + g.ky * (d + u) + g.kz * (b + f);  // the centre term is added by the caller
 }
 
-__device__ void na_gather_P(const CDesc& cd, const double* x, double scale, double* P, int m, int col, double* sh) {
+// Whether C's CSR arrays stay inside the grid of n points: the offsets start
+// at 0 and never decrease, and every column index lies in [0, n).  Run by all
+// threads of one block; only entries inside the given offsets are read.
+__device__ bool na_check_C(const CDesc& cd, int64_t n, int* bad) {
+    if (threadIdx.x == 0) *bad = (cd.o > 0 && cd.rp[0] != 0) ? 1 : 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < cd.o; r += NA_NT)
+        if (cd.rp[r + 1] < cd.rp[r]) *bad = 1;
+    __syncthreads();
+    if (!*bad && cd.o > 0) {
+        for (int64_t e = threadIdx.x; e < cd.rp[cd.o]; e += NA_NT) {
+            const int64_t c = cd.col[e];
+            if (c < 0 || c >= n) *bad = 1;
+        }
+    }
+    __syncthreads();
+    return *bad == 0;
+}
+
+// P[:, col] = scale * C x; entries whose column lies outside the grid are
+// skipped (the first kernel has rejected such arrays already)
+__device__ void na_gather_P(const CDesc& cd, const double* x, int64_t n, double scale, double* P, int m, int col,
+                            double* sh) {
     for (int r = 0; r < cd.o; ++r) {
         double v = 0.0;
-        for (int64_t e = cd.rp[r] + threadIdx.x; e < cd.rp[r + 1]; e += NA_NT) v += cd.val[e] * __ldcg(x + cd.col[e]);
+        for (int64_t e = cd.rp[r] + threadIdx.x; e < cd.rp[r + 1]; e += NA_NT) {
+            const int64_t c = cd.col[e];
+            if (c >= 0 && c < n) v += cd.val[e] * __ldcg(x + c);
+        }
         v = block_sum<NA_NT>(v, sh);
         if (threadIdx.x == 0) P[(int64_t)r * m + col] = scale * v;
     }
@@ -82,6 +115,8 @@ __global__ void __launch_bounds__(NA_NT) k_na_init(NaLayout* L, NaGrid g, int64_
     if (!grid_arrive(part, L->partials, &L->counter, blockIdx.x, gridDim.x, &flag)) return;
     const double tot = grid_finish<NA_NT>(L->partials, gridDim.x, &L->counter, sh);
     __shared__ double s0;
+    __shared__ int c_bad;
+    const bool c_ok = na_check_C(cd, g.n, &c_bad);
     if (threadIdx.x == 0) {
         const double b0 = sqrt(tot);
         ColState* st = &L->state;
@@ -98,10 +133,16 @@ __global__ void __launch_bounds__(NA_NT) k_na_init(NaLayout* L, NaGrid g, int64_
             st->s[0] = 1.0 / b0;
             s0 = 1.0 / b0;
         }
+        if (!c_ok) {  // nothing runs: the later kernels see done
+            st->done = 1;
+            st->m_used = -1;
+            st->status |= 2;
+        }
         *m_used_out = st->m_used;
     }
     __syncthreads();
-    na_gather_P(cd, B, s0, P, m, 0, sh);
+    if (!c_ok) return;
+    na_gather_P(cd, B, g.n, s0, P, m, 0, sh);
 }
 
 __global__ void __launch_bounds__(NA_NT) k_na_alpha(NaLayout* L, NaGrid g, int j, double* H, int m) {
@@ -166,7 +207,7 @@ __global__ void __launch_bounds__(NA_NT) k_na_update(NaLayout* L, NaGrid g, int 
         }
     }
     __syncthreads();
-    if (cont) na_gather_P(cd, A, snext, P, m, j + 1, sh);
+    if (cont) na_gather_P(cd, A, g.n, snext, P, m, j + 1, sh);
 }
 
 // device address of the scratch array, looked up once per device
@@ -200,7 +241,8 @@ extern "C" int kv_grid_lanczos_noalloc(int device, void* stream, int ndim, const
                                        const double* c_val, int32_t krylov_m, double* H, double* P, double* beta0,
                                        int32_t* m_used) {
     using namespace kv;
-    if (!dims || !h || !box_lo || !box_hi || !H || !P || !beta0 || !m_used || (o > 0 && !c_row_ptr)) {
+    if (!dims || !h || !box_lo || !box_hi || !H || !P || !beta0 || !m_used ||
+        (o > 0 && (!c_row_ptr || !c_col || !c_val))) {
         set_error("kv_grid_lanczos_noalloc: NULL argument");
         return KV_EINVAL;
     }
@@ -238,7 +280,9 @@ extern "C" int kv_grid_lanczos_noalloc(int device, void* stream, int ndim, const
     g.ky = coef / (h[1] * h[1]);
     g.kz = ndim == 3 ? coef / (h[2] * h[2]) : 0.0;
     g.kc = -2.0 * (g.kx + g.ky + g.kz);
-    cudaError_t e = cudaSetDevice(device);
+    // the caller's current device is made current again on return
+    DeviceGuard dg(device);
+    cudaError_t e = dg.err;
     if (e != cudaSuccess) {
         set_error("kv_grid_lanczos_noalloc: cudaSetDevice: %s", cudaGetErrorString(e));
         return KV_ECUDA;

@@ -1,6 +1,7 @@
 // k_stencil.cu -- matrix-free grid Laplacian Lanczos passes (Alg. 3 / Alg. 4).
 //
-// A = coef * (discrete Laplacian, spacing h per axis, Dirichlet-0).  One
+// A = coef * (discrete Laplacian, spacing h per axis) with a coefficient per
+// grid face (Dirichlet-0 unless the system says otherwise).  One
 // Lanczos iteration j runs as two passes over the grid:
 //   alpha pass:  alpha_j = v_j . A v_j                         (reads v_j)
 //   update pass: w = A v_j - alpha_j v_j - beta_j v_{j-1}, stored over v_{j-1};
@@ -50,6 +51,8 @@ static StencilGeom geom_of(const Sys* s) {
     g.ky = s->ndim >= 2 ? s->coef / (s->h[1] * s->h[1]) : 0.0;
     g.kz = s->ndim >= 3 ? s->coef / (s->h[2] * s->h[2]) : 0.0;
     g.kc = -2.0 * (g.kx + g.ky + g.kz);
+    const double kap[3] = {g.kx, g.ky, g.kz};
+    for (int f = 0; f < 6; ++f) g.rho[f] = kap[f >> 1] > 0.0 ? s->face[f] / kap[f >> 1] : 0.0;
     return g;
 }
 
@@ -114,8 +117,13 @@ __global__ void __launch_bounds__(SNT) k_stencil_init_box(T* __restrict__ B, Ste
             // and the indicator differs across exactly the two faces of the box
             // on each axis (towards the zero ghost where the box meets the
             // grid boundary), one edge per face cell.
+            // A face of the box on a face of the grid couples to the ghost
+            // with gamma = rho kappa instead of kappa.
             const double ex = (double)(hx - lx), ey = (double)(hy - ly), ez = (double)(hz - lz);
-            H0[0] = -2.0 * (g.kx * ey * ez + g.ky * ex * ez + g.kz * ex * ey) / (ex * ey * ez);
+            const double wx = g.kx * ((lx > 0 ? 1.0 : g.rho[0]) + (hx < g.nx ? 1.0 : g.rho[1]));
+            const double wy = g.ky * ((ly > 0 ? 1.0 : g.rho[2]) + (hy < g.ny ? 1.0 : g.rho[3]));
+            const double wz = g.kz * ((lz > 0 ? 1.0 : g.rho[4]) + (hz < g.nz ? 1.0 : g.rho[5]));
+            H0[0] = -(wx * ey * ez + wy * ex * ez + wz * ex * ey) / (ex * ey * ez);
         }
     }
     __syncthreads();
@@ -146,17 +154,28 @@ __global__ void __launch_bounds__(SNT) k_stencil_alpha(const T* __restrict__ B, 
         T c = B[idx];
         const bool hl = x > 0, hr = x < g.nx - 1, hd = y > 0, hu = y < g.ny - 1;
         for (int64_t z = z0; z < z1; ++z, idx += P2) {
-            const T cp = (z + 1 < g.nz) ? B[idx + P2] : (T)0;
-            const T l = hl ? B[idx - 1] : (T)0;
-            const T r = hr ? B[idx + 1] : (T)0;
-            const T d = hd ? B[idx - g.nx] : (T)0;
-            const T u = hu ? B[idx + g.nx] : (T)0;
+            const bool hm = z > 0, hp = z + 1 < g.nz;
+            const T cp = hp ? B[idx + P2] : (T)0;
             T av;
             if constexpr (std::is_same<T, float>::value) {
-                // difference form: neighbour - centre is exact for nearby values
-                av = kx * ((l - c) + (r - c)) + ky * ((d - c) + (u - c)) + kz * ((cm - c) + (cp - c));
+                // difference form: neighbour - centre is exact for nearby values;
+                // a face keeps the share rho of the ghost coupling (-rho c)
+                const float dl = hl ? B[idx - 1] - c : -(float)g.rho[0] * c;
+                const float dr = hr ? B[idx + 1] - c : -(float)g.rho[1] * c;
+                const float dd = hd ? B[idx - g.nx] - c : -(float)g.rho[2] * c;
+                const float du = hu ? B[idx + g.nx] - c : -(float)g.rho[3] * c;
+                const float dm = hm ? cm - c : -(float)g.rho[4] * c;
+                const float dp = hp ? cp - c : -(float)g.rho[5] * c;
+                av = kx * (dl + dr) + ky * (dd + du) + kz * (dm + dp);
             } else {
-                av = kx * (l + r) + ky * (d + u) + kz * (cm + cp) + kc * c;
+                // pair-sum form: a face's ghost value is (1 - rho) c (0: Dirichlet)
+                const T l = hl ? B[idx - 1] : (T)(1.0 - g.rho[0]) * c;
+                const T r = hr ? B[idx + 1] : (T)(1.0 - g.rho[1]) * c;
+                const T d = hd ? B[idx - g.nx] : (T)(1.0 - g.rho[2]) * c;
+                const T u = hu ? B[idx + g.nx] : (T)(1.0 - g.rho[3]) * c;
+                const T mz = hm ? cm : (T)(1.0 - g.rho[4]) * c;
+                const T pz = hp ? cp : (T)(1.0 - g.rho[5]) * c;
+                av = kx * (l + r) + ky * (d + u) + kz * (mz + pz) + kc * c;
             }
             acc.add_prod(c, av);
             cm = c;
@@ -206,14 +225,18 @@ __global__ void __launch_bounds__(SNT) k_stencil_update(const T* __restrict__ B,
         T c = B[idx];
         const bool hl = x > 0, hr = x < g.nx - 1, hd = y > 0, hu = y < g.ny - 1;
         for (int64_t z = z0; z < z1; ++z, idx += P2) {
-            const T cp = (z + 1 < g.nz) ? B[idx + P2] : (T)0;
-            const T l = hl ? B[idx - 1] : (T)0;
-            const T r = hr ? B[idx + 1] : (T)0;
-            const T d = hd ? B[idx - g.nx] : (T)0;
-            const T u = hu ? B[idx + g.nx] : (T)0;
+            const bool hm = z > 0, hp = z + 1 < g.nz;
+            const T cp = hp ? B[idx + P2] : (T)0;
             T w;
             if constexpr (std::is_same<T, float>::value) {
-                const float Lx = (l - c) + (r - c), Ly = (d - c) + (u - c), Lz = (cm - c) + (cp - c);
+                // difference form; a face keeps the share rho of the ghost coupling
+                const float dl = hl ? B[idx - 1] - c : -(float)g.rho[0] * c;
+                const float dr = hr ? B[idx + 1] - c : -(float)g.rho[1] * c;
+                const float dd = hd ? B[idx - g.nx] - c : -(float)g.rho[2] * c;
+                const float du = hu ? B[idx + g.nx] - c : -(float)g.rho[3] * c;
+                const float dm = hm ? cm - c : -(float)g.rho[4] * c;
+                const float dp = hp ? cp - c : -(float)g.rho[5] * c;
+                const float Lx = dl + dr, Ly = dd + du, Lz = dm + dp;
                 float acc2 = fx.lo * Lx;
                 acc2 = fmaf(fy.lo, Ly, acc2);
                 acc2 = fmaf(fz.lo, Lz, acc2);
@@ -226,7 +249,14 @@ __global__ void __launch_bounds__(SNT) k_stencil_update(const T* __restrict__ B,
                 if (!FIRST) acc2 = fmaf(fa.hi, A[idx], acc2);
                 w = acc2;
             } else {
-                w = ax * (l + r) + ay * (d + u) + az * (cm + cp) + bc * c;
+                // pair-sum form: a face's ghost value is (1 - rho) c (0: Dirichlet)
+                const T l = hl ? B[idx - 1] : (T)(1.0 - g.rho[0]) * c;
+                const T r = hr ? B[idx + 1] : (T)(1.0 - g.rho[1]) * c;
+                const T d = hd ? B[idx - g.nx] : (T)(1.0 - g.rho[2]) * c;
+                const T u = hu ? B[idx + g.nx] : (T)(1.0 - g.rho[3]) * c;
+                const T mz = hm ? cm : (T)(1.0 - g.rho[4]) * c;
+                const T pz = hp ? cp : (T)(1.0 - g.rho[5]) * c;
+                w = ax * (l + r) + ay * (d + u) + az * (mz + pz) + bc * c;
                 if (!FIRST) w += ba * A[idx];
             }
             A[idx] = w;

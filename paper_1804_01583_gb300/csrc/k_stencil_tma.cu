@@ -26,7 +26,9 @@
 // the x0+124 neighbour) and v_{j-1} into a shared-memory ring four planes
 // ahead of the compute (two CTAs per SM, so eight stages, about 140 KB, in
 // flight per SM); TMA fills coordinates outside the grid with zeros, which is
-// the Dirichlet-0 boundary.  Box rows are 512 bytes, so every float4 row load
+// the Dirichlet-0 boundary.  A grid face with its own coefficient gamma
+// (insulated, heat exchange) replaces the difference to that zero ghost by
+// -(gamma / kappa) c, and its edge term in w . A w by gamma w^2.  Box rows are 512 bytes, so every float4 row load
 // is conflict-free; the x neighbours of a thread's four points come from the
 // adjacent lanes (shuffles).  The x-1 neighbour of w comes from the next lane
 // (shuffle), y-1 from the warp's own other row or the shared w plane, z-1
@@ -49,6 +51,7 @@
 
 #include "kv_internal.h"
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace kv {
 
@@ -69,50 +72,6 @@ constexpr int ASTRIDE = ABYTES;
 constexpr int WSTRIDE = WC * WR * 4;
 constexpr int SMEM_MAIN = RB * BSTRIDE + RB * SSTRIDE + RA * ASTRIDE + 2 * WSTRIDE;
 constexpr int SMEM_TOTAL = SMEM_MAIN + 128 + 1024;  // + barriers + alignment slack
-constexpr long WAIT_LIMIT = 1L << 22;
-
-__device__ __forceinline__ unsigned saddr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, long limit = WAIT_LIMIT) {
-    for (long it = 0; it < limit; ++it)
-        if (mbar_try_wait(b, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-        "[%2];" ::"r"(saddr(dst)),
-        "l"((uint64_t)map), "r"(saddr(bar)), "r"(x), "r"(y), "r"(z)
-        : "memory");
-}
-
-// hi + lo += x with the rounding error of the float add kept in lo (TwoSum,
-// Knuth; six float operations, valid for any ordering of |hi| and |x|):
-// the per-thread sums over a chunk of planes stay float pairs, without
-// conversions or adds on the FP64 pipe inside the plane loop.
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
-    const float s = hi + x;
-    const float bp = s - hi;
-    const float e = (hi - (s - bp)) + (x - bp);
-    hi = s;
-    lo += e;
-}
-
 struct FusedArgs {
     float* W;          // output buffer (w = unnormalised v_{j+1})
     StencilGeom g;
@@ -127,6 +86,10 @@ struct FusedArgs {
     // narrow ones
     int nbx, nby;
     int sg_log2, nby_s;  // narrow tiles: 2^sg_log2 lanes per row pair; 0 = none
+    // grid faces (x low, x high, y low, y high, z low, z high), used when the
+    // system's boundary is not Dirichlet-0: rho = gamma / kappa, the share of
+    // the ghost coupling a face keeps, and gamma itself (the face term of w . A w)
+    float rho[6], gam[6];
 };
 
 // One CTA's tile and chunk of z planes.  LG = log2 of the lanes that share
@@ -137,7 +100,7 @@ struct FusedArgs {
 // compile-time constant, so the box offsets fold into the load instructions.
 // Returns false when a stage wait expired (the copies are drained and the
 // timeout reported); otherwise this thread's sums of w.w and -w.Aw.
-template <bool FIRST, int LG>
+template <bool FIRST, int LG, bool FACES>
 __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensorMap* mS, const CUtensorMap* mA,
                                            const FusedArgs& a, int tx, int ty, int tz, unsigned char* sm,
                                            int& abort_flag, double& sum_n, double& sum_e) {
@@ -198,6 +161,8 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
     const bool inner1 = inner_x && yin1;              // row r0 + 1 >= 1 always
     const bool xhi3 = xin && (xb + 3 == nx - 1);      // u = 3 on the high x face
     const bool yhi0 = (y0 - 1 + r0) == ny - 1, yhi1 = (y0 + r0) == ny - 1;
+    const bool ylo0 = (y0 - 1 + r0) == 0, ylo1 = (y0 + r0) == 0;
+    const bool xlo0 = xb == 0;                        // u = 0 on the low x face
 
     if (t == 0) {
         for (int q = 0; q <= DEPTH; ++q) mbar_init(bars + q, 1);
@@ -285,9 +250,24 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const float c = cc[u];
-                const float Lx = (xl[u] - c) + (xr[u] - c);
-                const float Ly = (dd[u] - c) + (uu[u] - c);
-                const float Lz = (mm[u] - c) + (pp[u] - c);
+                float Lx, Ly, Lz;
+                if (!FACES) {
+                    Lx = (xl[u] - c) + (xr[u] - c);
+                    Ly = (dd[u] - c) + (uu[u] - c);
+                    Lz = (mm[u] - c) + (pp[u] - c);
+                } else {
+                    // a face replaces the difference to the ghost by -rho c
+                    const bool ylo = h == 0 ? ylo0 : ylo1, yhi = h == 0 ? yhi0 : yhi1;
+                    const float dl = (u == 0 && xlo0) ? -a.rho[0] * c : xl[u] - c;
+                    const float dr = (u == 3 && xhi3) ? -a.rho[1] * c : xr[u] - c;
+                    const float dn = ylo ? -a.rho[2] * c : dd[u] - c;
+                    const float dup = yhi ? -a.rho[3] * c : uu[u] - c;
+                    const float dm = p == 0 ? -a.rho[4] * c : mm[u] - c;
+                    const float dp = p == nz - 1 ? -a.rho[5] * c : pp[u] - c;
+                    Lx = dl + dr;
+                    Ly = dn + dup;
+                    Lz = dm + dp;
+                }
                 float acc = fx * Lx;
                 acc = fmaf(fy, Ly, acc);
                 acc = fmaf(fz, Lz, acc);
@@ -335,10 +315,16 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
                 const float lf[4] = {h == 0 ? left0 : left1, w4.x, w4.y, w4.z};
                 const float uv[4] = {up.x, up.y, up.z, up.w};
                 const float zv[4] = {zp.x, zp.y, zp.z, zp.w};
+                const bool ylo = h == 0 ? ylo0 : ylo1;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const float w = wv[u];
-                    const float dx = w - lf[u], dy = w - uv[u], dz = w - zv[u];
+                    float dx = w - lf[u], dy = w - uv[u], dz = w - zv[u];
+                    if (FACES) {  // a low face's edge to the ghost is its own face term below
+                        if (u == 0 && xlo0) dx = 0.f;
+                        if (ylo) dy = 0.f;
+                        if (p == 0) dz = 0.f;
+                    }
                     tx = fmaf(dx, dx, tx);
                     ty = fmaf(dy, dy, ty);
                     tz = fmaf(dz, dz, tz);
@@ -346,13 +332,24 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
                 }
                 float* dst = a.W + woff + (h == 0 ? 0 : nx);
                 *reinterpret_cast<float4*>(dst) = w4;
-                // edges from the high faces to the zero ghost points
-                const float gy = ((h == 0 ? yhi0 : yhi1) ? ky : 0.f) + (zhi ? kz : 0.f);
-                if (gy != 0.f || xhi3) {
+                if (!FACES) {
+                    // edges from the high faces to the zero ghost points
+                    const float gy = ((h == 0 ? yhi0 : yhi1) ? ky : 0.f) + (zhi ? kz : 0.f);
+                    if (gy != 0.f || xhi3) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float gc = gy + ((u == 3 && xhi3) ? kx : 0.f);
+                            tg = fmaf(gc * wv[u], wv[u], tg);
+                        }
+                    }
+                } else {
+                    // every face: gamma_f w^2
+                    const float gy = ((h == 0 ? yhi0 : yhi1) ? a.gam[3] : 0.f) + (ylo ? a.gam[2] : 0.f) +
+                                     (zhi ? a.gam[5] : 0.f) + (p == 0 ? a.gam[4] : 0.f);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float gc = gy + ((u == 3 && xhi3) ? kx : 0.f);
-                        tg = fmaf(gc * wv[u], wv[u], tg);
+                        const float gc = gy + ((u == 3 && xhi3) ? a.gam[1] : 0.f) + ((u == 0 && xlo0) ? a.gam[0] : 0.f);
+                        if (gc != 0.f) tg = fmaf(gc * wv[u], wv[u], tg);
                     }
                 }
             }
@@ -388,7 +385,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap* mB, const CUtensor
 }
 
 
-template <bool FIRST, int LGN>
+template <bool FIRST, int LGN, bool FACES>
 __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_constant__ CUtensorMap mapB,
                                                              const __grid_constant__ CUtensorMap mapS,
                                                              const __grid_constant__ CUtensorMap mapA,
@@ -410,10 +407,11 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
     double sum_n, sum_e;
     bool ok;
     if (q < a.nbx * a.nby)
-        ok = fused_tile<FIRST, 5>(&mapB, &mapS, &mapA, a, q % a.nbx, q / a.nbx, tz, sm, abort_flag, sum_n, sum_e);
+        ok = fused_tile<FIRST, 5, FACES>(&mapB, &mapS, &mapA, a, q % a.nbx, q / a.nbx, tz, sm, abort_flag, sum_n,
+                                         sum_e);
     else
-        ok = fused_tile<FIRST, LGN>(&mapBn, &mapS, &mapAn, a, a.nbx, q - a.nbx * a.nby, tz, sm, abort_flag, sum_n,
-                                    sum_e);
+        ok = fused_tile<FIRST, LGN, FACES>(&mapBn, &mapS, &mapAn, a, a.nbx, q - a.nbx * a.nby, tz, sm, abort_flag,
+                                           sum_n, sum_e);
     if (!ok) return;
     const double alpha = a.H[(int64_t)a.j * a.m + a.j];
 
@@ -460,11 +458,7 @@ __global__ void __launch_bounds__(FNT, 2) k_lanczos_fused_tma(const __grid_const
 }
 
 // ---------------------------------------------------------------- host side
-typedef CUresult (*PfnEncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static PfnEncodeTiled encode_fn() {
+PfnEncodeTiled tensor_map_encoder() {
     static PfnEncodeTiled fn = nullptr;
     static bool tried = false;
     if (!tried) {
@@ -479,6 +473,23 @@ static PfnEncodeTiled encode_fn() {
     return fn;
 }
 
+int make_grid_map(CUtensorMap* m, void* base, int64_t nx, int64_t ny, int64_t nz, int elem_bytes, int box_w,
+                  int box_h) {
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t strides[2] = {(cuuint64_t)nx * elem_bytes, (cuuint64_t)nx * ny * elem_bytes};
+    cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = tensor_map_encoder()(m, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                      3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return KV_ECUDA;
+    }
+    return KV_OK;
+}
+
 // Whether the single-pass TMA iteration applies: FP32 grid, rows a multiple
 // of 16 bytes (TMA stride rule), extents that fit int coordinates.
 bool fused_tma_supported(const Prob* p) {
@@ -487,32 +498,30 @@ bool fused_tma_supported(const Prob* p) {
     const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
     if (nx % 4 != 0 || nx >= ((int64_t)1 << 30) || ny >= ((int64_t)1 << 30) || nz >= ((int64_t)1 << 30))
         return false;
-    return encode_fn() != nullptr;
+    return tensor_map_encoder() != nullptr;
 }
 
 static int make_map(CUtensorMap* m, void* base, const Sys* s, int box_w, int box_h) {
     const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
-    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-        return KV_ECUDA;
-    }
-    return KV_OK;
+    return make_grid_map(m, base, nx, ny, nz, 4, box_w, box_h);
 }
 
 // One-time shared-memory limit of the kernel (not allowed during capture).
 int fused_prepare() {
     static bool attr_set = false;
     if (!attr_set) {
-        const void* fns[] = {(const void*)k_lanczos_fused_tma<true, 2>,  (const void*)k_lanczos_fused_tma<true, 3>,
-                             (const void*)k_lanczos_fused_tma<true, 4>,  (const void*)k_lanczos_fused_tma<false, 2>,
-                             (const void*)k_lanczos_fused_tma<false, 3>, (const void*)k_lanczos_fused_tma<false, 4>};
+        const void* fns[] = {(const void*)k_lanczos_fused_tma<true, 2, false>,
+                             (const void*)k_lanczos_fused_tma<true, 3, false>,
+                             (const void*)k_lanczos_fused_tma<true, 4, false>,
+                             (const void*)k_lanczos_fused_tma<false, 2, false>,
+                             (const void*)k_lanczos_fused_tma<false, 3, false>,
+                             (const void*)k_lanczos_fused_tma<false, 4, false>,
+                             (const void*)k_lanczos_fused_tma<true, 2, true>,
+                             (const void*)k_lanczos_fused_tma<true, 3, true>,
+                             (const void*)k_lanczos_fused_tma<true, 4, true>,
+                             (const void*)k_lanczos_fused_tma<false, 2, true>,
+                             (const void*)k_lanczos_fused_tma<false, 3, true>,
+                             (const void*)k_lanczos_fused_tma<false, 4, true>};
         for (const void* fn : fns)
             KV_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL));
         attr_set = true;
@@ -545,14 +554,22 @@ static FusedGrid fused_grid(const Sys* s) {
     f.nby = (int)((ny + TYI - 1) / TYI);
     const int64_t ty_n = f.sg_log2 ? 16 * (32 >> f.sg_log2) - 1 : 1;
     f.nby_s = f.sg_log2 ? (int)((ny + ty_n - 1) / ty_n) : 0;
-    // z chunk: about 12 waves of 2 resident CTAs per SM, at least 16 planes
+    // z chunk: about 12 waves of 2 resident CTAs per SM, at least 16 planes;
+    // a small grid that would not fill one wave that way gets shorter chunks
+    // (at least 2 planes), enough of them for one wave
     const int64_t per_z = (int64_t)f.nbx * f.nby + f.nby_s;
-    const int64_t target = 152LL * 2 * 12;
+    const int64_t slots = 152LL * 2;
+    const int64_t target = slots * 12;
     int64_t nzc = (target + per_z - 1) / per_z;
     if (nzc < 1) nzc = 1;
     int64_t zc = (nz + nzc - 1) / nzc;
     if (zc < 16) zc = 16;
     if (zc > nz) zc = nz;
+    if (per_z * ((nz + zc - 1) / zc) < slots) {
+        const int64_t want = (slots + per_z - 1) / per_z;
+        zc = std::max<int64_t>(2, (nz + want - 1) / want);
+        if (zc > nz) zc = nz;
+    }
     f.zc = (int)zc;
     f.nzch = (int)((nz + zc - 1) / zc);
     f.n_norm = (int64_t)f.nbx * f.nby * f.nzch;
@@ -608,6 +625,13 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     a.m = p->m;
     a.j = it;
     a.red = p->red;
+    {
+        const double kap[3] = {g.kx, g.ky, g.kz};
+        for (int f = 0; f < 6; ++f) {
+            a.gam[f] = (float)s->face[f];
+            a.rho[f] = (float)(kap[f >> 1] > 0.0 ? s->face[f] / kap[f >> 1] : 0.0);
+        }
+    }
     rc = fused_prepare();
     if (rc) return rc;
     LaunchScope ls(p->ctx, "lanczos_fused");
@@ -615,8 +639,12 @@ int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, v
     // the narrow shape is a template argument (G = 4 when there are none:
     // that branch is then never taken)
     auto go = [&](auto first, auto lgn) {
-        k_lanczos_fused_tma<decltype(first)::value, decltype(lgn)::value>
-            <<<grd, FNT, SMEM_TOTAL, st>>>(mB, mS, mA, mBn, mAn, a);
+        if (s->faces)
+            k_lanczos_fused_tma<decltype(first)::value, decltype(lgn)::value, true>
+                <<<grd, FNT, SMEM_TOTAL, st>>>(mB, mS, mA, mBn, mAn, a);
+        else
+            k_lanczos_fused_tma<decltype(first)::value, decltype(lgn)::value, false>
+                <<<grd, FNT, SMEM_TOTAL, st>>>(mB, mS, mA, mBn, mAn, a);
     };
     using T = std::true_type;
     using F = std::false_type;
@@ -657,7 +685,8 @@ extern "C" int kv_diag_bounded_wait(int device, int64_t polls) {
         set_error("kv_diag_bounded_wait: polls must be in [1, %ld]", WAIT_LIMIT);
         return KV_EINVAL;
     }
-    if (cudaSetDevice(device) != cudaSuccess) {
+    DeviceGuard dg(device);
+    if (dg.err != cudaSuccess) {
         set_error("kv_diag_bounded_wait: device %d", device);
         return KV_EINVAL;
     }

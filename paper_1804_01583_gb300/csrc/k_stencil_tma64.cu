@@ -1,0 +1,671 @@
+// k_stencil_tma64.cu -- single-pass Lanczos iteration on the grid operator in
+// FP64 (FP64 storage of the Krylov vectors, FP64 arithmetic for the vectors).
+//
+// One launch performs iteration j of the projected Lanczos loop (Alg. 3 with
+// the Alg. 4 projection), like the FP32 kernel of k_stencil_tma.cu:
+//     w = A v_j - alpha_j v_j - beta_j v_{j-1}           (written to a third buffer)
+//     beta_{j+1}^2 = w . w,  alpha_{j+1} = (w . A w) / (w . w)
+//     P[:, j+1] = C w / beta_{j+1}
+// so each iteration reads v_j and v_{j-1} once and writes w once: 24 bytes a
+// grid point, the minimum of a three-vector FP64 Lanczos step.
+//
+// Where the time goes on this GPU: its FP64 pipe retires about two FP64
+// instructions per SM per clock (1/64 of FP32), so an FP64 iteration is bound
+// by its FP64 instruction count, not by HBM.  The vector w itself is computed
+// with FP64 instructions (the minimum for the 7-point update is 8 a point:
+// three neighbour-pair sums, one multiply, four fused multiply-adds).  The two
+// sums that need no FP64 result per point are taken off the FP64 pipe:
+//   - each w is split exactly into three floats (a1 + a2 + a3 = w, by integer
+//     operations on its bits: 24 + 24 + 5 significant bits);
+//   - w . w and the summation-by-parts form of w . A w,
+//         w . A w = - sum_a kappa_a sum_edges (w_p - w_q)^2 - sum_faces gamma_f sum w_p^2,
+//     are accumulated with error-free float transformations (TwoSum,
+//     TwoProduct by FMA), the differences w_p - w_q formed from the exact
+//     splits, so every term keeps about 47 significant bits and the sums are
+//     compensated; per-thread sums become doubles once at the end.
+//
+// Grid boundary: each face f of the box grid has a coefficient gamma_f >= 0,
+// and a point on face f gets -gamma_f v_p in place of the coupling to the
+// missing neighbour: gamma = kappa_a (= coef / h_a^2) is the Dirichlet-0
+// boundary of the vertex grid, gamma = 0 an insulated face, anything between
+// a heat exchange (Sec. 5.3).  TMA reads zeros outside the grid (the
+// Dirichlet ghost); other faces add s_j (kappa_a - gamma_f) v_p at their
+// points.
+//
+// Tiling: a CTA owns 126 (x) x 15 (y) points and marches over a chunk of z
+// planes.  w is evaluated on a 128 x 16 region (x0-2 .. x0+125, y0-1 ..
+// y0+14: the tile plus the low-x and low-y neighbours its backward differences
+// need); lane l of warp k owns the four columns 4l .. 4l+3 of rows 2k and
+// 2k+1.  v_j arrives by TMA (a 128 x 18 box and a 2-column side box for the
+// x0+126 neighbour) in a ring two planes ahead, v_{j-1} by plain coalesced
+// loads one plane ahead; the split of w's odd rows goes through shared memory
+// for the next warp's y-1 differences, the z-1 split stays in registers.
+//
+// Every mbarrier wait is bounded; on expiry the CTA sets the column's status
+// word (reported as KV_ETIMEOUT), drains its outstanding copies with bounded
+// waits and leaves.
+#include <cuda.h>
+
+#include <type_traits>
+
+#include "kv_internal.h"
+#include "reduce.cuh"
+#include "tma.cuh"
+
+namespace kv {
+
+constexpr int DNT = 256;
+constexpr int DTX = 126, DTY = 15;      // interior points of a tile
+constexpr int DWC = 128, DWR = 16;      // w region: x0-2 .. x0+125, y0-1 .. y0+14
+constexpr int DBW = 128, DBH = 18;      // v_j box: x0-2 .. x0+125, y0-2 .. y0+15 (1 KB rows)
+constexpr int DSW = 2;                  // v_j side box: x0+126 .. x0+127, same rows
+constexpr int DDEPTH = 2;               // planes of v_j in flight ahead of the compute
+constexpr int DRB = DDEPTH + 2;         // ring slots: planes p-1 .. p+DDEPTH
+constexpr int DBBYTES = DBW * DBH * 8;  // 18432
+constexpr int DSBYTES = DSW * DBH * 8;  // 288
+constexpr int DSSTRIDE = 384;
+constexpr int DWROWS = DWR / 2;         // odd rows of the region, read by the next warp
+constexpr int DWPLANE = 3 * DWROWS * DWC * 4;  // their splits (a1, a2, a3 planes of floats)
+constexpr int DSMEM_MAIN = DRB * (DBBYTES + DSSTRIDE) + 2 * DWPLANE;
+constexpr int DSMEM_TOTAL = DSMEM_MAIN + 128 + 1024;  // + barriers + alignment slack
+
+// ---------------------------------------------------------------- splits --
+// x 2^-sh = a1 + a2 + a3 exactly, from the bits of x: a1 carries the sign, the
+// exponent and the leading 24 significant bits, a2 the next 24 and a3 the
+// last 5 (as integers times powers of two, converted exactly).  sh is chosen
+// by the host so that every |x| 2^-sh stays below 2^8; values whose scaled
+// magnitude is below 2^-100 give zero: their squares lie more than 2^-180
+// below the sums they enter, which are at least 2^-80 of the largest term
+// wherever the iteration has not broken down.
+struct F3 {
+    float a1, a2, a3;
+};
+
+__device__ __forceinline__ F3 split3(double x, int sh) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - sh;  // biased exponent of x 2^-sh
+    F3 r;
+    if (e < 1023 - 100) {
+        r.a1 = r.a2 = r.a3 = 0.f;
+        return r;
+    }
+    // 2^(e-1023) with the sign of x, as float bits (e - 1023 >= -100 > -127)
+    const unsigned pbits = (hi & 0x80000000u) | ((unsigned)(e - 1023 + 127) << 23);
+    const float P = __uint_as_float(pbits);
+    // a1: the sign, the exponent and mantissa bits 51..29 (20 from hi, 3 from lo)
+    r.a1 = __uint_as_float(pbits | (__funnelshift_l(lo, hi, 3) & 0x7fffffu));
+    // bits 28..5 and 4..0 of the mantissa: integers, exact in float
+    const float m2 = __uint2float_rz((lo >> 5) & 0xffffffu);
+    const float m3 = __uint2float_rz(lo & 31u);
+    r.a2 = __fmul_rn(__fmul_rn(m2, 0x1p-47f), P);
+    r.a3 = __fmul_rn(__fmul_rn(m3, 0x1p-52f), P);
+    return r;
+}
+
+// a + b = s + e exactly (TwoSum, Knuth: six float operations, any magnitudes)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Compensated float-pair accumulator of non-negative terms t = th + tl
+// (hi + lo, the rounding errors of the additions kept in lo).
+struct Acc2 {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float th, float tl) {
+        float s, e;
+        two_sum(hi, th, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, tl));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// square of x = a1 + a2 + a3 as a float pair: a1^2 exactly (TwoProduct), the
+// cross terms 2 a1 (a2 + a3) and a2^2 in the low part (their rounding is
+// 2^-48 of x^2)
+__device__ __forceinline__ void sq3(const F3& x, float& th, float& tl) {
+    th = __fmul_rn(x.a1, x.a1);
+    const float e = __fmaf_rn(x.a1, x.a1, -th);
+    const float a23 = __fadd_rn(x.a2, x.a3);
+    tl = __fmaf_rn(__fadd_rn(x.a1, x.a1), a23, __fmaf_rn(x.a2, x.a2, e));
+}
+
+// (p - q)^2 as a float pair, p and q exact splits: the difference first as an
+// unevaluated pair dh + dl accurate to about 2^-47 of |p - q| (the leading
+// parts' difference and its error by TwoSum, the second parts' likewise),
+// then squared as in sq3
+__device__ __forceinline__ void sqdiff3(const F3& p, const F3& q, float& th, float& tl) {
+    float s1, e1, s2, e2, u, f, dh, g;
+    two_sum(p.a1, -q.a1, s1, e1);
+    two_sum(p.a2, -q.a2, s2, e2);
+    const float t3 = __fsub_rn(p.a3, q.a3);
+    two_sum(s2, e1, u, f);
+    two_sum(s1, u, dh, g);
+    const float dl = __fadd_rn(g, __fadd_rn(__fadd_rn(f, e2), t3));
+    th = __fmul_rn(dh, dh);
+    const float e = __fmaf_rn(dh, dh, -th);
+    tl = __fmaf_rn(__fadd_rn(dh, dh), dl, e);
+}
+
+// ------------------------------------------------------------------ kernel --
+struct Fused64Args {
+    double* W;          // output buffer (w = unnormalised v_{j+1})
+    const double* Aprev;  // v_{j-1} (unnormalised; unused in the first iteration)
+    StencilGeom g;
+    double gface[6];    // gamma per face: x low, x high, y low, y high, z low, z high
+    int zc;             // z planes per CTA
+    int nbx, nby;       // tiles per z chunk: nbx x nby
+    int sh;             // split scale: |w| 2^-sh < 2^8
+    ColState* st;
+    double* H;          // this column's (m+1) x m
+    double* P;          // this column's o x m
+    CDesc cd;
+    int m, j;
+    Reduce red;
+};
+
+// The point's face flags: bit 2a for the low face of axis a, 2a+1 for the high.
+__device__ __forceinline__ unsigned face_bits(int x, int y, int z, int nx, int ny, int nz) {
+    return (x == 0 ? 1u : 0u) | (x == nx - 1 ? 2u : 0u) | (y == 0 ? 4u : 0u) | (y == ny - 1 ? 8u : 0u) |
+           (z == 0 ? 16u : 0u) | (z == nz - 1 ? 32u : 0u);
+}
+
+// One CTA's tile and chunk of z planes.  Returns false when a stage wait
+// expired (the copies are drained and the timeout reported); otherwise this
+// thread's sums: sum_n = w . w and sum_e = -(w . A w), as doubles.
+template <bool FIRST, bool FACES>
+__device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtensorMap* mS, const Fused64Args& a,
+                                             int tx, int ty, int tz, unsigned char* sm, int& abort_flag,
+                                             double& sum_n, double& sum_e) {
+    double* sB = (double*)sm;
+    double* sS = (double*)(sm + DRB * DBBYTES);
+    float* sW = (float*)(sm + DRB * (DBBYTES + DSSTRIDE));
+    uint64_t* bars = (uint64_t*)(sm + DSMEM_MAIN);  // DDEPTH stage barriers + 1 prologue barrier
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const StencilGeom& g = a.g;
+    const int nx = (int)g.nx, ny = (int)g.ny, nz = (int)g.nz;
+    const int x0 = tx * DTX, y0 = ty * DTY;
+    const int z0 = tz * a.zc;
+    const int z1 = min(z0 + a.zc, nz);
+    const int p0 = z0 - 1;  // w planes p0 .. z1-1; the sums run over z0 .. z1-1
+    constexpr unsigned stage_bytes = (unsigned)(DBBYTES + DSBYTES);
+
+    // coefficients of w = s_j A v_j - alpha_j s_j v_j - beta_j s_{j-1} v_{j-1}
+    // in the pair-sum form: fx (l + r) + fy (d + u) + fz (m + p) + fc c + fa a
+    const double sj = a.st->s[a.j];
+    const double alpha = a.H[(int64_t)a.j * a.m + a.j];
+    const double fx = sj * g.kx, fy = sj * g.ky, fz = sj * g.kz;
+    const double fc = sj * (g.kc - alpha);
+    const double fa = FIRST ? 0.0 : -a.H[(int64_t)a.j * a.m + (a.j - 1)] * a.st->s[a.j - 1];
+    // the face terms: a point on face f adds s_j (kappa_a - gamma_f) c
+    double fdel[6];
+    if (FACES) {
+        const double kap[3] = {g.kx, g.ky, g.kz};
+#pragma unroll
+        for (int f = 0; f < 6; ++f) fdel[f] = sj * (kap[f >> 1] - a.gface[f]);
+    }
+
+    auto ring = [](int plane) { return ((plane % DRB) + DRB) % DRB; };
+    auto load_b = [&](int plane, uint64_t* bar) {  // v_j plane: main box + side box, same ring slot
+        const int k = ring(plane);
+        tma_load_3d(sB + (size_t)k * (DBBYTES / 8), mB, bar, x0 - 2, y0 - 2, plane);
+        tma_load_3d(sS + (size_t)k * (DSSTRIDE / 8), mS, bar, x0 + DTX, y0 - 2, plane);
+    };
+
+    // this thread's points: region rows r0, r0 + 1 (y = y0 - 1 + r), region
+    // columns 4 lane .. 4 lane + 3 (x = x0 - 2 + 4 lane + u)
+    const int r0 = 2 * warp;
+    const int xb = x0 - 2 + 4 * lane;
+    const int yr[2] = {y0 - 1 + r0, y0 + r0};
+    bool xin[4], xint[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        xin[u] = xb + u >= 0 && xb + u < nx;
+        xint[u] = xin[u] && (lane > 0 || u >= 2);  // interior columns: x >= x0
+    }
+    const bool yin[2] = {yr[0] >= 0 && yr[0] < ny, yr[1] < ny};
+    const bool yint[2] = {yin[0] && r0 >= 1, yin[1]};
+
+    if (t == 0) {
+        for (int q = 0; q <= DDEPTH; ++q) mbar_init(bars + q, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();
+    int issued_upto = p0 - 1;
+    if (t == 0) {
+        uint64_t* pro = bars + DDEPTH;
+        mbar_expect_tx(pro, 2 * stage_bytes);
+        load_b(p0 - 1, pro);
+        load_b(p0, pro);
+        for (int q = 0; q < DDEPTH && p0 + q <= z1 - 1; ++q) {  // stage q: B(q+1)
+            uint64_t* bar = bars + q;
+            mbar_expect_tx(bar, stage_bytes);
+            load_b(p0 + q + 1, bar);
+            issued_upto = p0 + q;
+        }
+    }
+
+    // v_{j-1} at this thread's points of plane p (plain loads, one plane ahead)
+    const int64_t plane = (int64_t)nx * ny;
+    double2 an[2][2];
+    auto load_a = [&](int p) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) an[h][k] = make_double2(0.0, 0.0);
+        if (FIRST || p < 0 || p >= nz) return;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!yin[h]) continue;
+            const double* row = a.Aprev + (int64_t)p * plane + (int64_t)yr[h] * nx;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (xin[2 * k] && xin[2 * k + 1]) an[h][k] = __ldcs(reinterpret_cast<const double2*>(row + xb + 2 * k));
+        }
+    };
+    load_a(p0);
+
+    F3 prev[2][4];  // split of w at plane p-1
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) prev[h][u] = F3{0.f, 0.f, 0.f};
+    Acc2 acc_n, acc_x, acc_y, acc_z;
+    Acc2 acc_f[6];  // FACES: sum of w^2 over each face's points (weighted by gamma at the end)
+    int pfail = -1;
+    int sbm = ring(p0 - 1), sbc = ring(p0), sbp = ring(p0 + 1), sst = 0;
+    unsigned sph = 0;
+    for (int p = p0; p <= z1 - 1; ++p) {
+        bool ok = true;
+        if (p == p0) ok = mbar_wait(bars + DDEPTH, 0);
+        ok = ok && mbar_wait(bars + sst, sph);
+        if (!ok) abort_flag = 1;  // acted on after the barrier below
+        const double* Bm = sB + (size_t)sbm * (DBBYTES / 8);
+        const double* Bc = sB + (size_t)sbc * (DBBYTES / 8);
+        const double* Bp = sB + (size_t)sbp * (DBBYTES / 8);
+        const double* Sc = sS + (size_t)sbc * (DSSTRIDE / 8);
+        float* Wp = sW + (p & 1) * (DWPLANE / 4);
+        const bool pin = p >= 0 && p < nz;
+
+        // ---- w on this thread's 2 x 4 points, stored, split
+        F3 cur[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = r0 + h;  // region row; box row r + 1 is its own y
+            const double* bd = Bc + r * DBW + 4 * lane;
+            const double* bc = bd + DBW;
+            const double* bu = bc + DBW;
+            double cc[4], dd[4], uu[4], mm[4], pp[4];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const double2 c2 = *reinterpret_cast<const double2*>(bc + 2 * k);
+                const double2 d2 = *reinterpret_cast<const double2*>(bd + 2 * k);
+                const double2 u2 = *reinterpret_cast<const double2*>(bu + 2 * k);
+                const double2 m2 = *reinterpret_cast<const double2*>(Bm + (r + 1) * DBW + 4 * lane + 2 * k);
+                const double2 p2 = *reinterpret_cast<const double2*>(Bp + (r + 1) * DBW + 4 * lane + 2 * k);
+                cc[2 * k] = c2.x, cc[2 * k + 1] = c2.y;
+                dd[2 * k] = d2.x, dd[2 * k + 1] = d2.y;
+                uu[2 * k] = u2.x, uu[2 * k + 1] = u2.y;
+                mm[2 * k] = m2.x, mm[2 * k + 1] = m2.y;
+                pp[2 * k] = p2.x, pp[2 * k + 1] = p2.y;
+            }
+            // x neighbours from the adjacent lanes; lane 0's left value only
+            // feeds w(x0-2), which nothing uses; lane 31's right one is column
+            // x0+126 of the side box
+            const double lft = __shfl_up_sync(0xffffffffu, cc[3], 1);
+            double rgt = __shfl_down_sync(0xffffffffu, cc[0], 1);
+            if (lane == 31) rgt = Sc[(r + 1) * DSW];
+            const double xl[4] = {lft, cc[0], cc[1], cc[2]};
+            const double xr[4] = {cc[1], cc[2], cc[3], rgt};
+            const double aa[4] = {an[h][0].x, an[h][0].y, an[h][1].x, an[h][1].y};
+            double wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                double w = fx * (xl[u] + xr[u]);
+                w = fma(fy, dd[u] + uu[u], w);
+                w = fma(fz, mm[u] + pp[u], w);
+                w = fma(fc, cc[u], w);
+                if (!FIRST) w = fma(fa, aa[u], w);
+                if (FACES) {
+                    const unsigned fb = face_bits(xb + u, yr[h], p, nx, ny, nz);
+                    if (fb) {
+                        double d = 0.0;
+#pragma unroll
+                        for (int f = 0; f < 6; ++f)
+                            if (fb & (1u << f)) d += fdel[f];
+                        w = fma(d, cc[u], w);
+                    }
+                }
+                wv[u] = (pin && yin[h] && xin[u]) ? w : 0.0;
+            }
+            // interior points of planes z0.. go to memory (x0 .. x0+125; pairs
+            // are inside or outside the grid together: nx is even)
+            if (p >= z0 && yint[h]) {
+                double* dst = a.W + (int64_t)p * plane + (int64_t)yr[h] * nx + xb;
+                if (xint[1] && xint[0]) *reinterpret_cast<double2*>(dst) = make_double2(wv[0], wv[1]);
+                if (xint[3]) *reinterpret_cast<double2*>(dst + 2) = make_double2(wv[2], wv[3]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cur[h][u] = split3(wv[u], a.sh);
+        }
+        load_a(p + 1);  // v_{j-1} of the next plane, in flight during the sums below
+        // the odd row's split for the next warp's y-1 differences
+        {
+            float* w1 = Wp + warp * DWC + 4 * lane;
+            *reinterpret_cast<float4*>(w1) = make_float4(cur[1][0].a1, cur[1][1].a1, cur[1][2].a1, cur[1][3].a1);
+            *reinterpret_cast<float4*>(w1 + DWROWS * DWC) =
+                make_float4(cur[1][0].a2, cur[1][1].a2, cur[1][2].a2, cur[1][3].a2);
+            *reinterpret_cast<float4*>(w1 + 2 * DWROWS * DWC) =
+                make_float4(cur[1][0].a3, cur[1][1].a3, cur[1][2].a3, cur[1][3].a3);
+        }
+        __syncthreads();  // splits visible; B(p-1) no longer read
+        if (abort_flag) {  // some thread's wait expired: the stage may be incomplete
+            pfail = p;
+            break;
+        }
+        if (t == 0 && p + DDEPTH <= z1 - 1) {
+            // stage p + DDEPTH (B(p + DDEPTH + 1)) reuses this stage's barrier
+            // and B(p-1)'s ring slot
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const int q = p + DDEPTH;
+            uint64_t* bar = bars + sst;
+            mbar_expect_tx(bar, stage_bytes);
+            load_b(q + 1, bar);
+            issued_upto = q;
+        }
+
+        // ---- interior of plane p: w . w and the edge terms of w . A w
+        if (p >= z0) {
+            F3 left[2], up[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                left[h].a1 = __shfl_up_sync(0xffffffffu, cur[h][3].a1, 1);
+                left[h].a2 = __shfl_up_sync(0xffffffffu, cur[h][3].a2, 1);
+                left[h].a3 = __shfl_up_sync(0xffffffffu, cur[h][3].a3, 1);
+            }
+            if (warp >= 1) {
+                const float* w1 = Wp + (warp - 1) * DWC + 4 * lane;
+                const float4 u1 = *reinterpret_cast<const float4*>(w1);
+                const float4 u2 = *reinterpret_cast<const float4*>(w1 + DWROWS * DWC);
+                const float4 u3 = *reinterpret_cast<const float4*>(w1 + 2 * DWROWS * DWC);
+                up[0] = F3{u1.x, u2.x, u3.x};
+                up[1] = F3{u1.y, u2.y, u3.y};
+                up[2] = F3{u1.z, u2.z, u3.z};
+                up[3] = F3{u1.w, u2.w, u3.w};
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) up[u] = F3{0.f, 0.f, 0.f};
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!yint[h]) continue;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!xint[u]) continue;
+                    const F3 w = cur[h][u];
+                    const F3 wl = u == 0 ? left[h] : cur[h][u - 1];
+                    const F3 wd = h == 0 ? up[u] : cur[0][u];
+                    const F3 wz = prev[h][u];
+                    float nh, nl, th, tl;
+                    sq3(w, nh, nl);
+                    acc_n.add(nh, nl);
+                    unsigned fb = 0;
+                    if (FACES) fb = face_bits(xb + u, yr[h], p, nx, ny, nz);
+                    // backward edges; on a low face the edge to the zero ghost
+                    // is the Dirichlet term, replaced by the face's own one
+                    if (!FACES || !(fb & 1u)) {
+                        sqdiff3(w, wl, th, tl);
+                        acc_x.add(th, tl);
+                    }
+                    if (!FACES || !(fb & 4u)) {
+                        sqdiff3(w, wd, th, tl);
+                        acc_y.add(th, tl);
+                    }
+                    if (!FACES || !(fb & 16u)) {
+                        sqdiff3(w, wz, th, tl);
+                        acc_z.add(th, tl);
+                    }
+                    if (!FACES) {
+                        // Dirichlet high faces: the edge to the zero ghost, weight kappa
+                        if (xb + u == nx - 1) acc_x.add(nh, nl);
+                        if (yr[h] == ny - 1) acc_y.add(nh, nl);
+                        if (p == nz - 1) acc_z.add(nh, nl);
+                    } else if (fb) {
+#pragma unroll
+                        for (int f = 0; f < 6; ++f)
+                            if (fb & (1u << f)) acc_f[f].add(nh, nl);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) prev[h][u] = cur[h][u];
+        sbm = sbc;
+        sbc = sbp;
+        sbp = sbp + 1 == DRB ? 0 : sbp + 1;
+        if (++sst == DDEPTH) {
+            sst = 0;
+            sph ^= 1u;
+        }
+    }
+    if (abort_flag) {
+        // drain this CTA's outstanding copies (bounded), report the timeout
+        if (t == 0) {
+            atomicOr(&a.st->status, 1);
+            if (pfail == p0) mbar_wait(bars + DDEPTH, 0);
+            for (int q = pfail; q <= issued_upto; ++q)
+                mbar_wait(bars + ((q - p0) % DDEPTH), (unsigned)(((q - p0) / DDEPTH) & 1));
+        }
+        __syncthreads();
+        return false;
+    }
+    const double s2 = ldexp(1.0, 2 * a.sh);
+    sum_n = acc_n.value() * s2;
+    double e = g.kx * acc_x.value() + g.ky * acc_y.value() + g.kz * acc_z.value();
+    if (FACES)
+#pragma unroll
+        for (int f = 0; f < 6; ++f) e = fma(a.gface[f], acc_f[f].value(), e);
+    sum_e = e * s2;
+    return true;
+}
+
+template <bool FIRST, bool FACES>
+__global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constant__ CUtensorMap mapB,
+                                                           const __grid_constant__ CUtensorMap mapS,
+                                                           Fused64Args a) {
+    if (a.st->done) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ double shred[DNT / 32];
+    __shared__ int flag, abort_flag;
+    const int t = threadIdx.x;
+    // 1-D grid, z chunk major; per chunk nbx x nby tiles, x fastest
+    const int bid = blockIdx.x;
+    const int per_z = a.nbx * a.nby;
+    const int tz = bid / per_z, q = bid - tz * per_z;
+    double sum_n, sum_e;
+    if (!fused64_tile<FIRST, FACES>(&mapB, &mapS, a, q % a.nbx, q / a.nbx, tz, sm, abort_flag, sum_n, sum_e))
+        return;
+    const double alpha = a.H[(int64_t)a.j * a.m + a.j];
+
+    // ---- deterministic grid reduction of (w.w, -w.Aw)
+    const double d_nrm = block_sum<DNT>(sum_n, shred);
+    const double d_edg = block_sum<DNT>(sum_e, shred);
+    const int64_t nb = gridDim.x;
+    const int64_t slot = bid;
+    if (t == 0) a.red.partials[nb + slot] = d_edg;
+    if (!grid_arrive(d_nrm, a.red.partials, a.red.counter, slot, nb, &flag)) return;
+    const double nw2 = grid_finish<DNT>(a.red.partials, nb, a.red.counter, shred);
+    const double edg = grid_finish<DNT>(a.red.partials + nb, nb, a.red.counter, shred);
+    __shared__ double snext;
+    __shared__ int cont;
+    if (t == 0) {
+        const int j = a.j, m = a.m;
+        const double beta = sqrt(nw2);
+        a.H[(int64_t)(j + 1) * m + j] = beta;
+        const double bj = FIRST ? 0.0 : a.H[(int64_t)j * m + (j - 1)];
+        const double nav = sqrt(alpha * alpha + bj * bj + beta * beta);  // ||A v_j||
+        if (!(beta > 1e-12 * nav) || !isfinite(beta) || !isfinite(edg)) {
+            a.st->done = 1;
+            a.st->m_used = j + 1;
+            cont = 0;
+        } else {
+            a.st->s[j + 1] = 1.0 / beta;
+            snext = 1.0 / beta;
+            if (j + 1 < m) {
+                a.H[(int64_t)j * m + (j + 1)] = beta;
+                a.H[(int64_t)(j + 1) * m + (j + 1)] = -edg / nw2;  // alpha_{j+1}
+            }
+            cont = (j + 1 < m) ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (!cont || a.cd.o > PROJ_INLINE_MAX) return;  // launch_project takes many rows
+    for (int r = 0; r < a.cd.o; ++r) {
+        double v = 0.0;
+        for (int64_t e = a.cd.rp[r] + t; e < a.cd.rp[r + 1]; e += DNT)
+            v += a.cd.val[e] * __ldcg(a.W + a.cd.col[e]);
+        v = block_sum<DNT>(v, shred);
+        if (t == 0) a.P[(int64_t)r * a.m + (a.j + 1)] = snext * v;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+// Whether the single-pass FP64 iteration applies: FP64 grid, rows a multiple
+// of 16 bytes (TMA stride rule: nx even), extents that fit int coordinates.
+bool fused64_supported(const Prob* p) {
+    const Sys* s = p->sys;
+    if (s->kind != 0 || p->prec != KV_FP64) return false;
+    const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
+    if (nx % 2 != 0 || nx >= ((int64_t)1 << 30) || ny >= ((int64_t)1 << 30) || nz >= ((int64_t)1 << 30))
+        return false;
+    return tensor_map_encoder() != nullptr;
+}
+
+int fused64_prepare() {
+    static bool attr_set = false;
+    if (!attr_set) {
+        const void* fns[] = {(const void*)k_lanczos_fused64<true, false>, (const void*)k_lanczos_fused64<false, false>,
+                             (const void*)k_lanczos_fused64<true, true>, (const void*)k_lanczos_fused64<false, true>};
+        for (const void* fn : fns)
+            KV_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, DSMEM_TOTAL));
+        attr_set = true;
+    }
+    return KV_OK;
+}
+
+// Grid of one launch: tiles of 126 x 15 points, z chunks of zc planes.  Each
+// chunk also computes w on the plane below it (the z-1 differences) and pays
+// a fixed start (barrier set-up, the first planes' copies, the reduction),
+// about two planes' worth, so the chunk length trades those against the tail
+// of the last wave: zc >= 2 minimises ceil(chunks x tiles / slots) x
+// (zc + 3), with two resident CTAs per SM.
+struct Fused64Grid {
+    int nbx, nby, zc, nzch;
+    int64_t blocks;
+};
+
+static Fused64Grid fused64_grid(const Sys* s, int sms) {
+    const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
+    Fused64Grid f{};
+    f.nbx = (int)((nx + DTX - 1) / DTX);
+    f.nby = (int)((ny + DTY - 1) / DTY);
+    const int64_t tiles = (int64_t)f.nbx * f.nby;
+    const int64_t slots = 2LL * (sms > 0 ? sms : 152);
+    int64_t best_zc = nz, best_cost = INT64_MAX;
+    for (int64_t zc = std::min<int64_t>(2, nz); zc <= nz; ++zc) {
+        const int64_t nch = (nz + zc - 1) / zc;
+        if (zc > 2 && (nz + zc - 2) / (zc - 1) == nch) continue;  // same chunk count as zc - 1
+        const int64_t waves = (nch * tiles + slots - 1) / slots;
+        const int64_t cost = waves * (zc + 3);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best_zc = zc;
+        }
+    }
+    f.zc = (int)best_zc;
+    f.nzch = (int)((nz + best_zc - 1) / best_zc);
+    f.blocks = tiles * f.nzch;
+    return f;
+}
+
+static int device_sms(int device) {
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) return 152;
+    if (!cached[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 152;
+        cached[device] = v;
+    }
+    return cached[device];
+}
+
+int fused64_blocks(const Prob* p) { return (int)fused64_grid(p->sys, device_sms(p->ctx->device)).blocks; }
+
+// The split scale: 2^sh above the largest |w| (|w_p| <= ||w|| <= ||A v_j||
+// <= the Gershgorin bound of A, since v_j has unit norm).
+static int split_shift(const StencilGeom& g, const double* gface) {
+    double bound = 4.0 * (g.kx + g.ky + g.kz);
+    for (int f = 0; f < 6; ++f) bound += gface[f];
+    int e = 0;
+    frexp(bound > 0.0 ? bound : 1.0, &e);  // bound < 2^e
+    return e + 1;
+}
+
+int launch_lanczos_fused64(Prob* p, int j, int it, const void* B, const void* Aprev, void* Wout) {
+    const Sys* s = p->sys;
+    StencilGeom g;
+    g.nx = s->dims[0];
+    g.ny = s->ndim >= 2 ? s->dims[1] : 1;
+    g.nz = s->ndim >= 3 ? s->dims[2] : 1;
+    g.kx = s->coef / (s->h[0] * s->h[0]);
+    g.ky = s->ndim >= 2 ? s->coef / (s->h[1] * s->h[1]) : 0.0;
+    g.kz = s->ndim >= 3 ? s->coef / (s->h[2] * s->h[2]) : 0.0;
+    g.kc = -2.0 * (g.kx + g.ky + g.kz);
+    const Fused64Grid f = fused64_grid(s, device_sms(p->ctx->device));
+    if (f.blocks < 1 || f.blocks > INT32_MAX) {
+        set_error("fused FP64 grid of %lld blocks", (long long)f.blocks);
+        return KV_EINVAL;
+    }
+    CUtensorMap mB, mS;
+    int rc = make_grid_map(&mB, const_cast<void*>(B), g.nx, g.ny, g.nz, 8, DBW, DBH);
+    if (!rc) rc = make_grid_map(&mS, const_cast<void*>(B), g.nx, g.ny, g.nz, 8, DSW, DBH);
+    if (rc) return rc;
+    Fused64Args a;
+    a.W = (double*)Wout;
+    a.Aprev = (const double*)Aprev;
+    a.g = g;
+    for (int q = 0; q < 6; ++q) a.gface[q] = s->face[q];
+    a.zc = f.zc;
+    a.nbx = f.nbx;
+    a.nby = f.nby;
+    a.sh = split_shift(g, s->face);
+    a.st = p->d_state + j;
+    a.H = p->d_H + (int64_t)j * (p->m + 1) * p->m;
+    a.P = p->d_P + (int64_t)j * p->o * p->m;
+    a.cd = CDesc{p->o, p->d_crp, p->d_ccol, p->d_cval};
+    a.m = p->m;
+    a.j = it;
+    a.red = p->red;
+    rc = fused64_prepare();
+    if (rc) return rc;
+    LaunchScope ls(p->ctx, "lanczos_fused64");
+    cudaStream_t st = p->ctx->stream;
+    const dim3 grd((unsigned)f.blocks);
+    if (s->faces) {
+        if (it == 0) k_lanczos_fused64<true, true><<<grd, DNT, DSMEM_TOTAL, st>>>(mB, mS, a);
+        else k_lanczos_fused64<false, true><<<grd, DNT, DSMEM_TOTAL, st>>>(mB, mS, a);
+    } else {
+        if (it == 0) k_lanczos_fused64<true, false><<<grd, DNT, DSMEM_TOTAL, st>>>(mB, mS, a);
+        else k_lanczos_fused64<false, false><<<grd, DNT, DSMEM_TOTAL, st>>>(mB, mS, a);
+    }
+    KV_CHECK_CUDA(cudaGetLastError());
+    return KV_OK;
+}
+
+}  // namespace kv

@@ -150,11 +150,6 @@ static int upload(Ctx* c, void* dst, const void* src, size_t bytes) {
     return KV_OK;
 }
 
-static int with_device(int device) {
-    KV_CHECK_CUDA(cudaSetDevice(device));
-    return KV_OK;
-}
-
 int64_t reduce_slots_needed(const Prob* p) {
     int64_t nb = 152 * 8;
     if (p->sys->kind == 0) {
@@ -165,6 +160,7 @@ int64_t reduce_slots_needed(const Prob* p) {
         int zc;
         nb = std::max<int64_t>(nb, stencil_blocks(g, &zc));
         if (p->fused) nb = std::max<int64_t>(nb, 2 * (int64_t)fused_tma_blocks(p, &zc));
+        if (p->fused64) nb = std::max<int64_t>(nb, 2 * (int64_t)fused64_blocks(p));
         return nb * (int64_t)(p->m + 2);
     }
     // CSR: one region of partials per column (all columns run together)
@@ -193,8 +189,8 @@ int kv_create(kv_ctx** out, int device, void* pool, size_t pool_bytes, void* str
     if (device < 0 || device >= ndev) return fail(KV_EINVAL, "kv_create: device %d of %d", device, ndev);
     if (pool && ((uintptr_t)pool % 256) != 0) return fail(KV_EINVAL, "kv_create: pool must be 256-byte aligned");
     if (pool_bytes < 4096) return fail(KV_EINVAL, "kv_create: pool_bytes too small");
-    int rc = with_device(device);
-    if (rc) return rc;
+    KV_WITH_DEVICE(device);
+    int rc = KV_OK;
     kv_ctx* c = new (std::nothrow) kv_ctx();
     if (!c) return fail(KV_ENOMEM, "kv_create: host allocation");
     c->device = device;
@@ -225,7 +221,7 @@ int kv_create(kv_ctx** out, int device, void* pool, size_t pool_bytes, void* str
 
 int kv_destroy(kv_ctx* c) {
     if (!c) return KV_OK;
-    cudaSetDevice(c->device);
+    ::kv::DeviceGuard kv_device_guard_(c->device);
     cudaStreamSynchronize(c->stream);
     clear_profile(c);
     for (auto e : c->spare_events) cudaEventDestroy(e);
@@ -250,6 +246,11 @@ int kv_launch_count(const kv_ctx* c, int64_t* launches) {
 
 int kv_system_stencil(kv_ctx* c, kv_sys** out, int ndim, const int64_t dims[3], double coef, const double h[3],
                       const double* b) {
+    return kv_system_grid(c, out, ndim, dims, coef, h, nullptr, b);
+}
+
+int kv_system_grid(kv_ctx* c, kv_sys** out, int ndim, const int64_t dims[3], double coef, const double h[3],
+                   const double* face, const double* b) {
     if (!c || !out || !dims || !h) return fail(KV_EINVAL, "kv_system_stencil: NULL argument");
     *out = nullptr;
     if (ndim != 2 && ndim != 3) return fail(KV_EINVAL, "kv_system_stencil: ndim must be 2 or 3");
@@ -261,11 +262,15 @@ int kv_system_stencil(kv_ctx* c, kv_sys** out, int ndim, const int64_t dims[3], 
         n *= dims[a];
     }
     if (!isfinite(coef)) return fail(KV_EINVAL, "kv_system_stencil: coef");
+    if (face)
+        for (int f = 0; f < 2 * ndim; ++f)
+            if (!isfinite(face[f]) || face[f] < 0.0)
+                return fail(KV_EINVAL, "kv_system_grid: face[%d] must be finite and >= 0", f);
     // launch-shape limits of the grid kernels: ceil(ny/8) and ceil(nz/8) blocks
     if (dims[1] > 524280 || (ndim == 3 && dims[2] > 524280))
         return fail(KV_EINVAL, "kv_system_stencil: ny and nz must be <= 524280");
-    int rc = with_device(c->device);
-    if (rc) return rc;
+    KV_WITH_DEVICE(c->device);
+    int rc = KV_OK;
     kv_sys* s = new (std::nothrow) kv_sys();
     if (!s) return fail(KV_ENOMEM, "host allocation");
     s->ctx = c;
@@ -278,12 +283,32 @@ int kv_system_stencil(kv_ctx* c, kv_sys** out, int ndim, const int64_t dims[3], 
     s->coef = coef;
     s->n = n;
     s->symmetric = true;
-    // largest eigenvalue of the Dirichlet-0 Laplacian: the Kronecker sum of the
-    // 1-D second differences' largest eigenvalues -(4/h^2) sin^2(pi / (2(N+1)))
-    s->mu = 0.0;
+    // the boundary: gamma per face, Dirichlet-0 (gamma = coef / h_a^2) unless given
+    s->faces = false;
     for (int a = 0; a < ndim; ++a) {
-        const double sn = sin(M_PI / (2.0 * (double)(s->dims[a] + 1)));
-        s->mu -= coef * 4.0 / (s->h[a] * s->h[a]) * sn * sn;
+        const double kap = coef / (s->h[a] * s->h[a]);
+        for (int side = 0; side < 2; ++side) {
+            s->face[2 * a + side] = face ? face[2 * a + side] : kap;
+            if (s->face[2 * a + side] != kap) s->faces = true;
+        }
+    }
+    s->mu = 0.0;
+    if (!s->faces) {
+        // largest eigenvalue of the Dirichlet-0 Laplacian: the Kronecker sum of the
+        // 1-D second differences' largest eigenvalues -(4/h^2) sin^2(pi / (2(N+1)))
+        for (int a = 0; a < ndim; ++a) {
+            const double sn = sin(M_PI / (2.0 * (double)(s->dims[a] + 1)));
+            s->mu -= coef * 4.0 / (s->h[a] * s->h[a]) * sn * sn;
+        }
+    } else {
+        // Gershgorin bound of the (symmetric) operator: a point's diagonal is
+        // -sum over its neighbours of kappa - sum over its faces of gamma, its
+        // off-diagonal sum that of |kappa|; with gamma >= 0 the largest row
+        // value is at most 2 sum_a (|kappa_a| - kappa_a) (0 for coef >= 0)
+        for (int a = 0; a < ndim; ++a) {
+            const double kap = coef / (s->h[a] * s->h[a]);
+            s->mu += 2.0 * (fabs(kap) - kap);
+        }
     }
     s->mu_aug = s->mu;
     if (b) {
@@ -312,8 +337,8 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
         return fail(KV_EINVAL, "kv_system_csr: value_precision");
     if (on_device && value_precision != KV_FP64)
         return fail(KV_EINVAL, "kv_system_csr: device arrays need value_precision KV_FP64 (val is double)");
-    int rc = with_device(c->device);
-    if (rc) return rc;
+    KV_WITH_DEVICE(c->device);
+    int rc = KV_OK;
     // device arrays: the row pointers and column indices are checked on the
     // host like host arrays (the kernels index with them), one copy of each
     std::vector<int64_t> hrp;
@@ -404,7 +429,7 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
 int kv_sys_destroy(kv_sys* s) {
     if (!s) return KV_OK;
     Ctx* c = s->ctx;
-    cudaSetDevice(c->device);
+    ::kv::DeviceGuard kv_device_guard_(c->device);
     cudaStreamSynchronize(c->stream);
     c->arena.free(s->d_rp);
     c->arena.free(s->d_col);
@@ -418,6 +443,28 @@ int kv_sys_destroy(kv_sys* s) {
 }
 
 // ---------------------------------------------------------------- problems
+// KV_PREC_AUTO: FP64 storage when the operator is symmetric and its largest
+// eigenvalue bound mu gives mu T > -1 over the horizon T = steps dt (its
+// slowest mode loses less than a factor e, so the rounding of FP32-stored
+// Krylov vectors in that mode reaches the last outputs undamped), else FP32.
+// A CSR system keeps the value precision it was created with: when the rule
+// asks for FP64 and the values are FP32 the problem is refused.
+static int resolve_precision(const Sys* s, const kv_problem_desc* d, int precision, int* out) {
+    *out = precision;
+    if (precision != KV_PREC_AUTO) return KV_OK;
+    const double T = d ? (double)d->steps * d->dt : 0.0;
+    const bool conserving = s->symmetric && s->mu * T > -1.0;
+    *out = conserving ? KV_FP64 : KV_FP32;
+    if (s->kind == 1) {
+        if (conserving && s->val_prec != KV_FP64)
+            return fail(KV_EINVAL, "KV_PREC_AUTO: the operator keeps a slow mode over the horizon (mu T = %g > -1), "
+                        "so FP32 storage does not meet its accuracy; create the CSR system with KV_FP64 values",
+                        s->mu * T);
+        *out = s->val_prec;
+    }
+    return KV_OK;
+}
+
 static int validate(const Sys* s, const kv_problem_desc* d, int precision) {
     if (!d) return fail(KV_EINVAL, "problem description is NULL");
     if (precision != KV_FP64 && precision != KV_FP32) return fail(KV_EINVAL, "precision");
@@ -603,7 +650,7 @@ static int vectors_needed(const Sys* s, const Prob* p) {
     int nv = 0;
     for (int j = 0; j < p->i; ++j) {
         int need = 0;
-        if (p->method[j] == KV_LANCZOS) need = (s->kind == 0 && !p->fused) ? 2 : 3;
+        if (p->method[j] == KV_LANCZOS) need = (s->kind == 0 && !p->fused && !p->fused64) ? 2 : 3;
         else need = p->m + 1;
         nv = std::max(nv, need);
     }
@@ -628,6 +675,7 @@ static size_t bytes_core(const Sys* s, const kv_problem_desc* d, int precision, 
     tmp.flags = d->flags;
     plan_methods(s, d, &tmp, bo);
     tmp.fused = !(d->flags & KV_FLAG_TWO_PASS) && fused_tma_supported(&tmp);
+    tmp.fused64 = !(d->flags & KV_FLAG_TWO_PASS) && fused64_supported(&tmp);
     const int64_t N = s->n + (std::count(tmp.aug.begin(), tmp.aug.end(), 1) ? 1 : 0);
     const int nv = vectors_needed(s, &tmp);
     tmp.N = N;
@@ -660,7 +708,9 @@ static size_t bytes_core(const Sys* s, const kv_problem_desc* d, int precision, 
 
 int kv_problem_bytes(const kv_sys* s, const kv_problem_desc* d, int precision, size_t* bytes) {
     if (!s || !d || !bytes) return fail(KV_EINVAL, "kv_problem_bytes: NULL argument");
-    int rc = validate(s, d, precision);
+    int rc = resolve_precision(s, d, precision, &precision);
+    if (rc) return rc;
+    rc = validate(s, d, precision);
     if (rc) return rc;
     if (!runs_transposed(d)) {
         *bytes = bytes_core(s, d, precision, BuildOpts{});
@@ -704,6 +754,7 @@ static int prob_build(Ctx* c, Prob* p, const Sys* s, const kv_problem_desc* d, i
     p->d_brow = bo.brow;
     plan_methods(s, d, p, bo);
     p->fused = !(d->flags & KV_FLAG_TWO_PASS) && fused_tma_supported(p);
+    p->fused64 = !(d->flags & KV_FLAG_TWO_PASS) && fused64_supported(p);
     p->N = s->n + (std::count(p->aug.begin(), p->aug.end(), 1) ? 1 : 0);
     p->nvec = vectors_needed(s, p);
     p->cols.assign(d->cols, d->cols + d->i);
@@ -934,10 +985,12 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
     if (!c || !out || !s) return fail(KV_EINVAL, "kv_problem: NULL argument");
     *out = nullptr;
     if (s->ctx != c) return fail(KV_EINVAL, "kv_problem: system belongs to another context");
-    int rc = validate(s, d, precision);
+    if (!d) return fail(KV_EINVAL, "kv_problem: NULL argument");
+    int rc = resolve_precision(s, d, precision, &precision);
     if (rc) return rc;
-    rc = with_device(c->device);
+    rc = validate(s, d, precision);
     if (rc) return rc;
+    KV_WITH_DEVICE(c->device);
     if (runs_transposed(d)) return build_transposed(c, out, s, d, precision);
     kv_prob* p = new (std::nothrow) kv_prob();
     if (!p) return fail(KV_ENOMEM, "host allocation");
@@ -950,6 +1003,12 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
     return KV_OK;
 }
 
+int kv_problem_precision(const kv_prob* p, int32_t* precision) {
+    if (!p || !precision) return fail(KV_EINVAL, "kv_problem_precision: NULL argument");
+    *precision = p->prec;
+    return KV_OK;
+}
+
 int kv_problem_runs(const kv_prob* p, int32_t* runs, int32_t* transposed) {
     if (!p || !runs || !transposed) return fail(KV_EINVAL, "kv_problem_runs: NULL argument");
     *runs = p->inner ? p->inner->i : p->i;
@@ -959,7 +1018,7 @@ int kv_problem_runs(const kv_prob* p, int32_t* runs, int32_t* transposed) {
 
 int kv_prob_destroy(kv_prob* p) {
     if (!p) return KV_OK;
-    cudaSetDevice(p->ctx->device);
+    ::kv::DeviceGuard kv_device_guard_(p->ctx->device);
     cudaStreamSynchronize(p->ctx->stream);
     if (p->inner) {
         free_prob(p->inner);
@@ -985,7 +1044,7 @@ static int run_column(Prob* p, int j) {
         if (!rc) rc = launch_init_norm(p, j, vec(0));
     }
     if (rc) return rc;
-    if (p->method[j] == KV_LANCZOS && s->kind == 0 && p->fused) {
+    if (p->method[j] == KV_LANCZOS && s->kind == 0 && (p->fused || p->fused64)) {
         // alpha_0 (closed form for a box column, else one read pass), then
         // one fused pass per iteration over three rotating buffers
         if (c.kind != KV_COL_BOX) {
@@ -993,7 +1052,10 @@ static int run_column(Prob* p, int j) {
             if (rc) return rc;
         }
         for (int it = 0; it < p->m; ++it) {
-            rc = launch_lanczos_fused(p, j, it, vec(it % 3), vec((it + 2) % 3), vec((it + 1) % 3));
+            if (p->fused64)
+                rc = launch_lanczos_fused64(p, j, it, vec(it % 3), vec((it + 2) % 3), vec((it + 1) % 3));
+            else
+                rc = launch_lanczos_fused(p, j, it, vec(it % 3), vec((it + 2) % 3), vec((it + 1) % 3));
             if (!rc) rc = launch_project(p, j, 1, vec((it + 1) % 3), 0, it + 1);
             if (!rc && is_checkpoint(p, it + 1)) rc = launch_error_check(p, j, 1, it + 1);
             if (rc) return rc;
@@ -1058,8 +1120,8 @@ static int enqueue_runs(Prob* p) {
 
 int kv_enqueue(kv_prob* p) {
     if (!p) return fail(KV_EINVAL, "kv_enqueue: NULL problem");
-    int rc = with_device(p->ctx->device);
-    if (rc) return rc;
+    KV_WITH_DEVICE(p->ctx->device);
+    int rc = KV_OK;
     if (p->inner) {
         // transpose dynamics: basis rows per output row, then transposed
         rc = enqueue_runs(p->inner);
@@ -1077,8 +1139,8 @@ int kv_enqueue(kv_prob* p) {
 
 int kv_fetch(kv_prob* p, kv_result* r) {
     if (!p || !r || !r->lo || !r->hi) return fail(KV_EINVAL, "kv_fetch: NULL argument");
-    int rc = with_device(p->ctx->device);
-    if (rc) return rc;
+    KV_WITH_DEVICE(p->ctx->device);
+    int rc = KV_OK;
     KV_CHECK_CUDA(cudaEventSynchronize(p->done_ev));
     const size_t S = (size_t)p->steps + 1;
     KV_CHECK_CUDA(cudaMemcpy(r->lo, p->d_lo, (size_t)p->o * S * 8, cudaMemcpyDeviceToHost));
@@ -1145,8 +1207,8 @@ int kv_check_polytope(kv_prob* p, const kv_polytope* unsafe, const kv_polytope* 
     if (lp_smem_bytes(i, m) > (size_t)dev_max)
         return fail(KV_EINVAL, "kv_check_polytope: the LP (i = %d, %d constraints) needs %zu bytes of shared memory, "
                     "the device allows %d", i, m, lp_smem_bytes(i, m), dev_max);
-    int rc = with_device(p->ctx->device);
-    if (rc) return rc;
+    KV_WITH_DEVICE(p->ctx->device);
+    int rc = KV_OK;
     Ctx* c = p->ctx;
     // one arena block: U, v, Iz, iota, margin, zx, yx (doubles), status (ints)
     const size_t nd = (size_t)qu * o + qu + (size_t)qi * i + qi + S + (size_t)S * i + (size_t)S * o;
@@ -1202,7 +1264,7 @@ int kv_run(kv_prob* p, kv_result* r) {
 
 int kv_profile_enable(kv_ctx* c, int enable) {
     if (!c) return fail(KV_EINVAL, "kv_profile_enable: NULL ctx");
-    cudaSetDevice(c->device);
+    ::kv::DeviceGuard kv_device_guard_(c->device);
     cudaStreamSynchronize(c->stream);
     clear_profile(c);
     c->profiling = enable != 0;
@@ -1211,7 +1273,7 @@ int kv_profile_enable(kv_ctx* c, int enable) {
 
 int kv_profile_read(kv_ctx* c, const char* name, int64_t* launches, double* total_ms) {
     if (!c || !name || !launches || !total_ms) return fail(KV_EINVAL, "kv_profile_read: NULL argument");
-    KV_CHECK_CUDA(cudaSetDevice(c->device));
+    KV_WITH_DEVICE(c->device);
     KV_CHECK_CUDA(cudaStreamSynchronize(c->stream));
     int64_t n = 0;
     double t = 0.0;

@@ -21,8 +21,9 @@ struct kv_graph {
 
 namespace kv {
 int prepare_for_capture(int device) {
-    const int rc = expm_prepare(device);
-    return rc ? rc : fused_prepare();
+    int rc = expm_prepare(device);
+    if (!rc) rc = fused_prepare();
+    return rc ? rc : fused64_prepare();
 }
 }  // namespace kv
 
@@ -45,7 +46,7 @@ int kv_graph_create(kv_ctx* ctx, kv_prob* const* probs, int32_t n, kv_graph** ou
         set_error("kv_graph_create: disable per-kernel profiling before capturing");
         return KV_EINVAL;
     }
-    KV_CHECK_CUDA(cudaSetDevice(ctx->device));
+    KV_WITH_DEVICE(ctx->device);
     int rc = prepare_for_capture(ctx->device);
     if (rc) return rc;
     KV_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -107,7 +108,7 @@ int kv_graph_launch(kv_graph* g) {
         set_error("kv_graph_launch: NULL graph");
         return KV_EINVAL;
     }
-    KV_CHECK_CUDA(cudaSetDevice(g->ctx->device));
+    KV_WITH_DEVICE(g->ctx->device);
     KV_CHECK_CUDA(cudaGraphLaunch(g->exec, g->ctx->stream));
     g->ctx->launches += 1;
     for (kv_prob* p : g->probs) {
@@ -119,7 +120,7 @@ int kv_graph_launch(kv_graph* g) {
 
 int kv_graph_destroy(kv_graph* g) {
     if (!g) return KV_OK;
-    cudaSetDevice(g->ctx->device);
+    ::kv::DeviceGuard kv_device_guard_(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);

@@ -28,6 +28,30 @@ void set_error(const char* fmt, ...);
         }                                                                          \
     } while (0)
 
+// Makes `device` current for the guard's scope and then makes the calling
+// thread's previous current device current again, so no call of the library
+// leaves the caller switched to another device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != device) err = cudaSetDevice(device);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+#define KV_WITH_DEVICE(dev)                                                                            \
+    ::kv::DeviceGuard kv_device_guard_(dev);                                                          \
+    if (kv_device_guard_.err != cudaSuccess) {                                                        \
+        ::kv::set_error("cudaSetDevice(%d) failed: %s", (int)(dev), cudaGetErrorString(kv_device_guard_.err)); \
+        return KV_ECUDA;                                                                               \
+    }
+
 // ------------------------------------------------------------------- arena
 // First-fit allocator over one device buffer; 256-byte granularity.  All
 // device memory of a context comes from here, so admission is a bookkeeping
@@ -81,6 +105,12 @@ struct Sys {
     int ndim = 0;
     int64_t dims[3] = {1, 1, 1};
     double coef = 0, h[3] = {1, 1, 1};
+    // grid boundary: gamma per face (x low, x high, y low, y high, z low, z
+    // high); a point on face f gets -gamma_f v_p in place of the coupling to
+    // the missing neighbour.  gamma = coef / h_a^2 on every face is the
+    // Dirichlet-0 boundary (faces == false); axes beyond ndim have 0.
+    double face[6] = {0, 0, 0, 0, 0, 0};
+    bool faces = false;
     int64_t n = 0, nnz = 0;
     int64_t* d_rp = nullptr;
     int32_t* d_col = nullptr;
@@ -126,6 +156,11 @@ struct Reduce {  // scratch of one deterministic grid reduction
 struct StencilGeom {
     int64_t nx, ny, nz;
     double kx, ky, kz, kc;  // kc = -2 (kx + ky + kz)
+    // per face (x low, x high, y low, y high, z low, z high): rho = gamma /
+    // kappa_axis, the share of the Dirichlet ghost coupling the face keeps
+    // (1: Dirichlet-0, 0: insulated); the ghost value of the pair-sum form is
+    // (1 - rho) v_p
+    double rho[6];
 };
 
 struct Prob {
@@ -138,7 +173,8 @@ struct Prob {
     int batched = 0;
     int flags = 0;
     double err_target = 0.0;     // > 0: a-posteriori error control (Alg. 2 / Alg. 4)
-    bool fused = false;          // single-pass TMA Lanczos iterations on the grid
+    bool fused = false;          // single-pass TMA Lanczos iterations on the grid (FP32)
+    bool fused64 = false;        // single-pass TMA Lanczos iterations on the grid (FP64)
     bool ran = false;            // enqueued at least once (the basis on the device is a result)
     std::vector<int> method;     // per column: KV_LANCZOS | KV_ARNOLDI
     std::vector<int> aug;        // per column: runs on A' (carries the constant)
@@ -205,6 +241,12 @@ int launch_stencil_update(Prob* p, int j, int it, const void* B, void* A);
 bool fused_tma_supported(const Prob* p);
 int fused_tma_blocks(const Prob* p, int* zc);
 int launch_lanczos_fused(Prob* p, int j, int it, const void* B, const void* A, void* W);
+
+// single-pass TMA Lanczos iteration, FP64 grids (k_stencil_tma64.cu)
+bool fused64_supported(const Prob* p);
+int fused64_blocks(const Prob* p);
+int fused64_prepare();
+int launch_lanczos_fused64(Prob* p, int j, int it, const void* B, const void* Aprev, void* W);
 
 // a-posteriori error bound (k_expm.cu): the exponentials of H_k at every
 // step for columns j0 .. j0+ncols-1 (dim = k), then the bound and the stop

@@ -225,7 +225,7 @@ int kv_server_create(kv_ctx* ctx, kv_server** out, int32_t slots) {
     s->ctx = ctx;
     s->ctx_stream = ctx->stream;
     s->nslots = slots;
-    cudaSetDevice(ctx->device);
+    ::kv::DeviceGuard kv_device_guard_(ctx->device);
     for (int k = 0; k < slots; ++k) {
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -247,7 +247,7 @@ int kv_server_destroy(kv_server* s) {
     s->stop.store(true);
     s->cv.notify_all();
     if (s->worker.joinable()) s->worker.join();
-    cudaSetDevice(s->ctx->device);
+    ::kv::DeviceGuard kv_device_guard_(s->ctx->device);
     for (auto& kv : s->all) delete kv.second;
     for (auto x : s->streams) cudaStreamSynchronize(x);
     s->ctx->stream = s->ctx_stream;
