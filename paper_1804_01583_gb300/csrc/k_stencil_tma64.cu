@@ -16,7 +16,7 @@
 // three neighbour-pair sums, one multiply, four fused multiply-adds).  The two
 // sums that need no FP64 result per point are taken off the FP64 pipe:
 //   - each w is split exactly into three floats (a1 + a2 + a3 = w, by integer
-//     operations on its bits: 24 + 24 + 5 significant bits);
+//     operations on its bits: 24 + 23 + 6 significant bits);
 //   - w . w and the summation-by-parts form of w . A w,
 //         w . A w = - sum_a kappa_a sum_edges (w_p - w_q)^2 - sum_faces gamma_f sum w_p^2,
 //     are accumulated with error-free float transformations (TwoSum,
@@ -35,11 +35,16 @@
 // Tiling: a CTA owns 126 (x) x 15 (y) points and marches over a chunk of z
 // planes.  w is evaluated on a 128 x 16 region (x0-2 .. x0+125, y0-1 ..
 // y0+14: the tile plus the low-x and low-y neighbours its backward differences
-// need); lane l of warp k owns the four columns 4l .. 4l+3 of rows 2k and
-// 2k+1.  v_j arrives by TMA (a 128 x 18 box and a 2-column side box for the
-// x0+126 neighbour) in a ring two planes ahead, v_{j-1} by plain coalesced
-// loads one plane ahead; the split of w's odd rows goes through shared memory
-// for the next warp's y-1 differences, the z-1 split stays in registers.
+// need); warp k owns rows 2k and 2k+1, lane l the columns 2l, 2l+1, 64+2l
+// and 65+2l, so every 16-byte load or store of a warp covers 512 contiguous
+// bytes (shared memory without bank conflicts, whole global sectors).  v_j
+// arrives by TMA (a 128 x 18 box and a 2-column side box for the x0+126
+// neighbour) in a ring two planes ahead, v_{j-1} by plain coalesced loads one
+// plane ahead.  Each plane of w also goes to a double-buffered shared plane,
+// and the sums of a plane run one iteration later from that copy (the z-1
+// split stays in registers), interleaved with the next plane's FP64 work:
+// every warp's instruction stream then mixes FP64 and float work, and the
+// FP64 pipe does not idle while the float sums run.
 //
 // Every mbarrier wait is bounded; on expiry the CTA sets the column's status
 // word (reported as KV_ETIMEOUT), drains its outstanding copies with bounded
@@ -64,15 +69,15 @@ constexpr int DRB = DDEPTH + 2;         // ring slots: planes p-1 .. p+DDEPTH
 constexpr int DBBYTES = DBW * DBH * 8;  // 18432
 constexpr int DSBYTES = DSW * DBH * 8;  // 288
 constexpr int DSSTRIDE = 384;
-constexpr int DWROWS = DWR / 2;         // odd rows of the region, read by the next warp
-constexpr int DWPLANE = 3 * DWROWS * DWC * 4;  // their splits (a1, a2, a3 planes of floats)
+constexpr int DWPLANE = DWC * DWR * 8;  // one plane of w (doubles), kept for the next iteration's sums
 constexpr int DSMEM_MAIN = DRB * (DBBYTES + DSSTRIDE) + 2 * DWPLANE;
 constexpr int DSMEM_TOTAL = DSMEM_MAIN + 128 + 1024;  // + barriers + alignment slack
 
 // ---------------------------------------------------------------- splits --
 // x 2^-sh = a1 + a2 + a3 exactly, from the bits of x: a1 carries the sign, the
-// exponent and the leading 24 significant bits, a2 the next 24 and a3 the
-// last 5 (as integers times powers of two, converted exactly).  sh is chosen
+// exponent and the leading 24 significant bits (mantissa bits 51..29), a2
+// bits 28..6 and a3 bits 5..0, each an integer below 2^23 converted exactly
+// (2^23 + m has m as its low mantissa bits) and scaled by powers of two.  sh is chosen
 // by the host so that every |x| 2^-sh stays below 2^8; values whose scaled
 // magnitude is below 2^-100 give zero: their squares lie more than 2^-180
 // below the sums they enter, which are at least 2^-80 of the largest term
@@ -80,6 +85,10 @@ constexpr int DSMEM_TOTAL = DSMEM_MAIN + 128 + 1024;  // + barriers + alignment 
 struct F3 {
     float a1, a2, a3;
 };
+
+__device__ __forceinline__ float small_uint_to_float(unsigned m) {  // exact for m < 2^23
+    return __fsub_rn(__uint_as_float(0x4B000000u | m), 8388608.0f);
+}
 
 __device__ __forceinline__ F3 split3(double x, int sh) {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
@@ -94,11 +103,8 @@ __device__ __forceinline__ F3 split3(double x, int sh) {
     const float P = __uint_as_float(pbits);
     // a1: the sign, the exponent and mantissa bits 51..29 (20 from hi, 3 from lo)
     r.a1 = __uint_as_float(pbits | (__funnelshift_l(lo, hi, 3) & 0x7fffffu));
-    // bits 28..5 and 4..0 of the mantissa: integers, exact in float
-    const float m2 = __uint2float_rz((lo >> 5) & 0xffffffu);
-    const float m3 = __uint2float_rz(lo & 31u);
-    r.a2 = __fmul_rn(__fmul_rn(m2, 0x1p-47f), P);
-    r.a3 = __fmul_rn(__fmul_rn(m3, 0x1p-52f), P);
+    r.a2 = __fmul_rn(__fmul_rn(small_uint_to_float((lo >> 6) & 0x7fffffu), 0x1p-46f), P);
+    r.a3 = __fmul_rn(__fmul_rn(small_uint_to_float(lo & 63u), 0x1p-52f), P);
     return r;
 }
 
@@ -181,7 +187,7 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
                                              double& sum_n, double& sum_e) {
     double* sB = (double*)sm;
     double* sS = (double*)(sm + DRB * DBBYTES);
-    float* sW = (float*)(sm + DRB * (DBBYTES + DSSTRIDE));
+    double* sW = (double*)(sm + DRB * (DBBYTES + DSSTRIDE));
     uint64_t* bars = (uint64_t*)(sm + DSMEM_MAIN);  // DDEPTH stage barriers + 1 prologue barrier
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const StencilGeom& g = a.g;
@@ -215,15 +221,17 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
     };
 
     // this thread's points: region rows r0, r0 + 1 (y = y0 - 1 + r), region
-    // columns 4 lane .. 4 lane + 3 (x = x0 - 2 + 4 lane + u)
+    // columns 2 lane, 2 lane + 1, 64 + 2 lane, 65 + 2 lane (x = x0 - 2 + column)
     const int r0 = 2 * warp;
-    const int xb = x0 - 2 + 4 * lane;
     const int yr[2] = {y0 - 1 + r0, y0 + r0};
+    int xu[4];
     bool xin[4], xint[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        xin[u] = xb + u >= 0 && xb + u < nx;
-        xint[u] = xin[u] && (lane > 0 || u >= 2);  // interior columns: x >= x0
+        const int c = (u < 2 ? 0 : 64) + 2 * lane + (u & 1);
+        xu[u] = x0 - 2 + c;
+        xin[u] = xu[u] >= 0 && xu[u] < nx;
+        xint[u] = xin[u] && c >= 2;  // interior columns: x >= x0
     }
     const bool yin[2] = {yr[0] >= 0 && yr[0] < ny, yr[1] < ny};
     const bool yint[2] = {yin[0] && r0 >= 1, yin[1]};
@@ -263,12 +271,12 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
             const double* row = a.Aprev + (int64_t)p * plane + (int64_t)yr[h] * nx;
 #pragma unroll
             for (int k = 0; k < 2; ++k)
-                if (xin[2 * k] && xin[2 * k + 1]) an[h][k] = __ldcs(reinterpret_cast<const double2*>(row + xb + 2 * k));
+                if (xin[2 * k]) an[h][k] = __ldcs(reinterpret_cast<const double2*>(row + xu[2 * k]));
         }
     };
     load_a(p0);
 
-    F3 prev[2][4];  // split of w at plane p-1
+    F3 prev[2][4];  // split of w at plane q-1 while the sums of plane q run
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -278,97 +286,175 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
     int pfail = -1;
     int sbm = ring(p0 - 1), sbc = ring(p0), sbp = ring(p0 + 1), sst = 0;
     unsigned sph = 0;
-    for (int p = p0; p <= z1 - 1; ++p) {
+    // Iteration p computes w on plane p (FP64) and, from the copy of w kept in
+    // shared memory, the sums of plane q = p - 1 (float and integer work), so
+    // each warp's instruction stream mixes both and the FP64 pipe stays fed.
+    // One more iteration after the last plane finishes its sums.
+    for (int p = p0; p <= z1; ++p) {
+        const bool wplane = p <= z1 - 1;
         bool ok = true;
-        if (p == p0) ok = mbar_wait(bars + DDEPTH, 0);
-        ok = ok && mbar_wait(bars + sst, sph);
-        if (!ok) abort_flag = 1;  // acted on after the barrier below
+        if (wplane) {
+            if (p == p0) ok = mbar_wait(bars + DDEPTH, 0);
+            ok = ok && mbar_wait(bars + sst, sph);
+        }
+        // No barrier here: each thread's own wait makes the stage visible to
+        // it; a failed wait is acted on after the barrier below.
+        if (!ok) abort_flag = 1;
         const double* Bm = sB + (size_t)sbm * (DBBYTES / 8);
         const double* Bc = sB + (size_t)sbc * (DBBYTES / 8);
         const double* Bp = sB + (size_t)sbp * (DBBYTES / 8);
         const double* Sc = sS + (size_t)sbc * (DSSTRIDE / 8);
-        float* Wp = sW + (p & 1) * (DWPLANE / 4);
+        double* Wp = sW + (p & 1) * (DWC * DWR);           // w of plane p (written here)
+        const double* Wq = sW + ((p + 1) & 1) * (DWC * DWR);  // w of plane q = p - 1
         const bool pin = p >= 0 && p < nz;
+        const int qz = p - 1;
 
-        // ---- w on this thread's 2 x 4 points, stored, split
-        F3 cur[2][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int r = r0 + h;  // region row; box row r + 1 is its own y
-            const double* bd = Bc + r * DBW + 4 * lane;
-            const double* bc = bd + DBW;
-            const double* bu = bc + DBW;
-            double cc[4], dd[4], uu[4], mm[4], pp[4];
+            // ---- w of plane p on row r (FP64)
+            if (wplane) {
+                double cc[4], dd[4], uu[4], mm[4], pp[4];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const double2 c2 = *reinterpret_cast<const double2*>(bc + 2 * k);
-                const double2 d2 = *reinterpret_cast<const double2*>(bd + 2 * k);
-                const double2 u2 = *reinterpret_cast<const double2*>(bu + 2 * k);
-                const double2 m2 = *reinterpret_cast<const double2*>(Bm + (r + 1) * DBW + 4 * lane + 2 * k);
-                const double2 p2 = *reinterpret_cast<const double2*>(Bp + (r + 1) * DBW + 4 * lane + 2 * k);
-                cc[2 * k] = c2.x, cc[2 * k + 1] = c2.y;
-                dd[2 * k] = d2.x, dd[2 * k + 1] = d2.y;
-                uu[2 * k] = u2.x, uu[2 * k + 1] = u2.y;
-                mm[2 * k] = m2.x, mm[2 * k + 1] = m2.y;
-                pp[2 * k] = p2.x, pp[2 * k + 1] = p2.y;
+                for (int k = 0; k < 2; ++k) {
+                    const int c0 = 64 * k + 2 * lane;
+                    const double2 c2 = *reinterpret_cast<const double2*>(Bc + (r + 1) * DBW + c0);
+                    const double2 d2 = *reinterpret_cast<const double2*>(Bc + r * DBW + c0);
+                    const double2 u2 = *reinterpret_cast<const double2*>(Bc + (r + 2) * DBW + c0);
+                    const double2 m2 = *reinterpret_cast<const double2*>(Bm + (r + 1) * DBW + c0);
+                    const double2 p2 = *reinterpret_cast<const double2*>(Bp + (r + 1) * DBW + c0);
+                    cc[2 * k] = c2.x, cc[2 * k + 1] = c2.y;
+                    dd[2 * k] = d2.x, dd[2 * k + 1] = d2.y;
+                    uu[2 * k] = u2.x, uu[2 * k + 1] = u2.y;
+                    mm[2 * k] = m2.x, mm[2 * k + 1] = m2.y;
+                    pp[2 * k] = p2.x, pp[2 * k + 1] = p2.y;
+                }
+                // x neighbours: column 2l+2 is lane l+1's first point (lane 0's
+                // third for lane 31), column 63+2l lane l-1's fourth (lane 31's
+                // second for lane 0), column 66+2l lane l+1's third (the side box
+                // for lane 31); lane 0's first left value only feeds w(x0-2),
+                // which nothing uses
+                const double l0 = __shfl_up_sync(0xffffffffu, cc[1], 1);
+                const double r1 = __shfl_sync(0xffffffffu, lane == 0 ? cc[2] : cc[0], (lane + 1) & 31);
+                const double l2 = __shfl_sync(0xffffffffu, lane == 31 ? cc[1] : cc[3], (lane + 31) & 31);
+                double r3 = __shfl_down_sync(0xffffffffu, cc[2], 1);
+                if (lane == 31) r3 = Sc[(r + 1) * DSW];
+                const double xl[4] = {l0, cc[0], l2, cc[2]};
+                const double xr[4] = {cc[1], r1, cc[3], r3};
+                const double aa[4] = {an[h][0].x, an[h][0].y, an[h][1].x, an[h][1].y};
+                double wv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    double w = fx * (xl[u] + xr[u]);
+                    w = fma(fy, dd[u] + uu[u], w);
+                    w = fma(fz, mm[u] + pp[u], w);
+                    w = fma(fc, cc[u], w);
+                    if (!FIRST) w = fma(fa, aa[u], w);
+                    if (FACES) {
+                        const unsigned fb = face_bits(xu[u], yr[h], p, nx, ny, nz);
+                        if (fb) {
+                            double d = 0.0;
+#pragma unroll
+                            for (int f = 0; f < 6; ++f)
+                                if (fb & (1u << f)) d += fdel[f];
+                            w = fma(d, cc[u], w);
+                        }
+                    }
+                    wv[u] = (pin && yin[h] && xin[u]) ? w : 0.0;
+                }
+                // interior points of planes z0.. go to memory (pairs are inside
+                // or outside the grid together: nx is even)
+                if (p >= z0 && yint[h]) {
+                    double* row = a.W + (int64_t)p * plane + (int64_t)yr[h] * nx;
+                    if (xint[0]) *reinterpret_cast<double2*>(row + xu[0]) = make_double2(wv[0], wv[1]);
+                    if (xint[2]) *reinterpret_cast<double2*>(row + xu[2]) = make_double2(wv[2], wv[3]);
+                }
+                *reinterpret_cast<double2*>(Wp + r * DWC + 2 * lane) = make_double2(wv[0], wv[1]);
+                *reinterpret_cast<double2*>(Wp + r * DWC + 64 + 2 * lane) = make_double2(wv[2], wv[3]);
             }
-            // x neighbours from the adjacent lanes; lane 0's left value only
-            // feeds w(x0-2), which nothing uses; lane 31's right one is column
-            // x0+126 of the side box
-            const double lft = __shfl_up_sync(0xffffffffu, cc[3], 1);
-            double rgt = __shfl_down_sync(0xffffffffu, cc[0], 1);
-            if (lane == 31) rgt = Sc[(r + 1) * DSW];
-            const double xl[4] = {lft, cc[0], cc[1], cc[2]};
-            const double xr[4] = {cc[1], cc[2], cc[3], rgt};
-            const double aa[4] = {an[h][0].x, an[h][0].y, an[h][1].x, an[h][1].y};
-            double wv[4];
+            // ---- the sums of plane q = p - 1 on row r (float and integer work)
+            if (qz >= p0) {
+                F3 cur[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                double w = fx * (xl[u] + xr[u]);
-                w = fma(fy, dd[u] + uu[u], w);
-                w = fma(fz, mm[u] + pp[u], w);
-                w = fma(fc, cc[u], w);
-                if (!FIRST) w = fma(fa, aa[u], w);
-                if (FACES) {
-                    const unsigned fb = face_bits(xb + u, yr[h], p, nx, ny, nz);
-                    if (fb) {
-                        double d = 0.0;
+                for (int k = 0; k < 2; ++k) {
+                    const double2 v2 = *reinterpret_cast<const double2*>(Wq + r * DWC + 64 * k + 2 * lane);
+                    cur[2 * k] = split3(v2.x, a.sh);
+                    cur[2 * k + 1] = split3(v2.y, a.sh);
+                }
+                if (qz >= z0 && yint[h]) {
+                    // x-1: column 2l-1 is lane l-1's second point, column 63+2l
+                    // lane l-1's fourth (lane 31's second for lane 0); y-1: the row
+                    // below (another warp's row for h = 0); z-1: plane q-1
+                    F3 left[4], up[4];
+                    left[1] = cur[0];
+                    left[3] = cur[2];
+                    left[0].a1 = __shfl_up_sync(0xffffffffu, cur[1].a1, 1);
+                    left[0].a2 = __shfl_up_sync(0xffffffffu, cur[1].a2, 1);
+                    left[0].a3 = __shfl_up_sync(0xffffffffu, cur[1].a3, 1);
+                    const F3 snd = lane == 31 ? cur[1] : cur[3];
+                    left[2].a1 = __shfl_sync(0xffffffffu, snd.a1, (lane + 31) & 31);
+                    left[2].a2 = __shfl_sync(0xffffffffu, snd.a2, (lane + 31) & 31);
+                    left[2].a3 = __shfl_sync(0xffffffffu, snd.a3, (lane + 31) & 31);
+                    if (h == 1) {
+                        // row r0 of plane q: its split has just been kept in prev[0]
 #pragma unroll
-                        for (int f = 0; f < 6; ++f)
-                            if (fb & (1u << f)) d += fdel[f];
-                        w = fma(d, cc[u], w);
+                        for (int u = 0; u < 4; ++u) up[u] = prev[0][u];
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const double2 v2 =
+                                *reinterpret_cast<const double2*>(Wq + (r - 1) * DWC + 64 * k + 2 * lane);
+                            up[2 * k] = split3(v2.x, a.sh);
+                            up[2 * k + 1] = split3(v2.y, a.sh);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (!xint[u]) continue;
+                        const F3 w = cur[u];
+                        float nh, nl, th, tl;
+                        sq3(w, nh, nl);
+                        acc_n.add(nh, nl);
+                        unsigned fb = 0;
+                        if (FACES) fb = face_bits(xu[u], yr[h], qz, nx, ny, nz);
+                        // backward edges; on a low face the edge to the zero ghost
+                        // is the Dirichlet term, replaced by the face's own one
+                        if (!FACES || !(fb & 1u)) {
+                            sqdiff3(w, left[u], th, tl);
+                            acc_x.add(th, tl);
+                        }
+                        if (!FACES || !(fb & 4u)) {
+                            sqdiff3(w, up[u], th, tl);
+                            acc_y.add(th, tl);
+                        }
+                        if (!FACES || !(fb & 16u)) {
+                            sqdiff3(w, prev[h][u], th, tl);
+                            acc_z.add(th, tl);
+                        }
+                        if (!FACES) {
+                            // Dirichlet high faces: the edge to the zero ghost, weight kappa
+                            if (xu[u] == nx - 1) acc_x.add(nh, nl);
+                            if (yr[h] == ny - 1) acc_y.add(nh, nl);
+                            if (qz == nz - 1) acc_z.add(nh, nl);
+                        } else if (fb) {
+#pragma unroll
+                            for (int f = 0; f < 6; ++f)
+                                if (fb & (1u << f)) acc_f[f].add(nh, nl);
+                        }
                     }
                 }
-                wv[u] = (pin && yin[h] && xin[u]) ? w : 0.0;
-            }
-            // interior points of planes z0.. go to memory (x0 .. x0+125; pairs
-            // are inside or outside the grid together: nx is even)
-            if (p >= z0 && yint[h]) {
-                double* dst = a.W + (int64_t)p * plane + (int64_t)yr[h] * nx + xb;
-                if (xint[1] && xint[0]) *reinterpret_cast<double2*>(dst) = make_double2(wv[0], wv[1]);
-                if (xint[3]) *reinterpret_cast<double2*>(dst + 2) = make_double2(wv[2], wv[3]);
-            }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) cur[h][u] = split3(wv[u], a.sh);
+                for (int u = 0; u < 4; ++u) prev[h][u] = cur[u];
+            }
         }
-        load_a(p + 1);  // v_{j-1} of the next plane, in flight during the sums below
-        // the odd row's split for the next warp's y-1 differences
-        {
-            float* w1 = Wp + warp * DWC + 4 * lane;
-            *reinterpret_cast<float4*>(w1) = make_float4(cur[1][0].a1, cur[1][1].a1, cur[1][2].a1, cur[1][3].a1);
-            *reinterpret_cast<float4*>(w1 + DWROWS * DWC) =
-                make_float4(cur[1][0].a2, cur[1][1].a2, cur[1][2].a2, cur[1][3].a2);
-            *reinterpret_cast<float4*>(w1 + 2 * DWROWS * DWC) =
-                make_float4(cur[1][0].a3, cur[1][1].a3, cur[1][2].a3, cur[1][3].a3);
-        }
-        __syncthreads();  // splits visible; B(p-1) no longer read
+        if (wplane) load_a(p + 1);  // v_{j-1} of the next plane, in flight meanwhile
+        __syncthreads();  // w of plane p visible; plane q's copy and B(p-1) no longer read
         if (abort_flag) {  // some thread's wait expired: the stage may be incomplete
             pfail = p;
             break;
         }
         if (t == 0 && p + DDEPTH <= z1 - 1) {
-            // stage p + DDEPTH (B(p + DDEPTH + 1)) reuses this stage's barrier
-            // and B(p-1)'s ring slot
+            // stage p + DDEPTH reuses this stage's barrier and B(p-1)'s slot
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             const int q = p + DDEPTH;
             uint64_t* bar = bars + sst;
@@ -376,75 +462,6 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
             load_b(q + 1, bar);
             issued_upto = q;
         }
-
-        // ---- interior of plane p: w . w and the edge terms of w . A w
-        if (p >= z0) {
-            F3 left[2], up[4];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                left[h].a1 = __shfl_up_sync(0xffffffffu, cur[h][3].a1, 1);
-                left[h].a2 = __shfl_up_sync(0xffffffffu, cur[h][3].a2, 1);
-                left[h].a3 = __shfl_up_sync(0xffffffffu, cur[h][3].a3, 1);
-            }
-            if (warp >= 1) {
-                const float* w1 = Wp + (warp - 1) * DWC + 4 * lane;
-                const float4 u1 = *reinterpret_cast<const float4*>(w1);
-                const float4 u2 = *reinterpret_cast<const float4*>(w1 + DWROWS * DWC);
-                const float4 u3 = *reinterpret_cast<const float4*>(w1 + 2 * DWROWS * DWC);
-                up[0] = F3{u1.x, u2.x, u3.x};
-                up[1] = F3{u1.y, u2.y, u3.y};
-                up[2] = F3{u1.z, u2.z, u3.z};
-                up[3] = F3{u1.w, u2.w, u3.w};
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) up[u] = F3{0.f, 0.f, 0.f};
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (!yint[h]) continue;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (!xint[u]) continue;
-                    const F3 w = cur[h][u];
-                    const F3 wl = u == 0 ? left[h] : cur[h][u - 1];
-                    const F3 wd = h == 0 ? up[u] : cur[0][u];
-                    const F3 wz = prev[h][u];
-                    float nh, nl, th, tl;
-                    sq3(w, nh, nl);
-                    acc_n.add(nh, nl);
-                    unsigned fb = 0;
-                    if (FACES) fb = face_bits(xb + u, yr[h], p, nx, ny, nz);
-                    // backward edges; on a low face the edge to the zero ghost
-                    // is the Dirichlet term, replaced by the face's own one
-                    if (!FACES || !(fb & 1u)) {
-                        sqdiff3(w, wl, th, tl);
-                        acc_x.add(th, tl);
-                    }
-                    if (!FACES || !(fb & 4u)) {
-                        sqdiff3(w, wd, th, tl);
-                        acc_y.add(th, tl);
-                    }
-                    if (!FACES || !(fb & 16u)) {
-                        sqdiff3(w, wz, th, tl);
-                        acc_z.add(th, tl);
-                    }
-                    if (!FACES) {
-                        // Dirichlet high faces: the edge to the zero ghost, weight kappa
-                        if (xb + u == nx - 1) acc_x.add(nh, nl);
-                        if (yr[h] == ny - 1) acc_y.add(nh, nl);
-                        if (p == nz - 1) acc_z.add(nh, nl);
-                    } else if (fb) {
-#pragma unroll
-                        for (int f = 0; f < 6; ++f)
-                            if (fb & (1u << f)) acc_f[f].add(nh, nl);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) prev[h][u] = cur[h][u];
         sbm = sbc;
         sbc = sbp;
         sbp = sbp + 1 == DRB ? 0 : sbp + 1;
