@@ -626,22 +626,29 @@ def cpu_configs() -> dict:
     return out
 
 
-def paper_heat_bench(dev: int, precisions=("fp64", "fp32")):
-    """The paper's own 3-D heat experiment (Sec. 5.3): 100^3 cells of the
-    insulated cube with heat exchange at x = 1 (cell-centred reading), the
-    heated region [0,0.4]x[0,0.2]x[0,0.1], the centre output, T = 20 by 0.02,
-    Lemma-1 error control with target 1e-6 (Krylov dimension up to 800), CSR
-    Lanczos: the dimension the control picks (the paper reports 544 for its
-    discretisation), the bound, and the time per query."""
+def paper_heat_bench(dev: int, precisions=("fp64", "fp32"), forms=("grid", "csr", "grid1000")):
+    """The paper's own 3-D heat model (Sec. 5.3): the insulated cube with heat
+    exchange at x = 1 (cell-centred reading), the heated region
+    [0,0.4]x[0,0.2]x[0,0.1], the centre output, T = 20 by 0.02.
+      * 100^3 with the Lemma-1 error control (target 1e-6, Krylov dimension up
+        to 800), through the matrix-free grid path (FP64 and FP32 storage) and
+        the CSR path (FP64): the dimension the control picks (the paper
+        reports 544), the bound, the time per query and its Krylov and
+        checkpoint parts;
+      * 1000^3 (n = 1e9, the paper's largest run) through the grid path at a
+        fixed Krylov dimension 30, FP64 and FP32: time per query and per
+        iteration, and the Lemma-1 bound that dimension reaches (the paper's
+        run needed k = 5932, beyond this library's Lanczos limit of 4096)."""
     import torch
     import paper_1804_01583_gb300 as kv
     out = {}
-    ctx = kv.Context(8 << 30, device=dev)
-    try:
-        for prec in precisions:
-            p = W.paper_heat(100, precision=prec, err_target=1e-6)
-            sysh = kv.System(ctx, p.system, p.precision)
-            ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
+    kry_names = ("lanczos_fused64", "lanczos_fused", "stencil_alpha", "stencil_update", "stencil_init", "csr_spmv",
+                 "csr_lanczos_update", "project")
+
+    def timed(ctx, p, **kw):
+        sysh = kv.System(ctx, p.system, p.precision)
+        ph = kv.ProblemHandle(ctx, sysh, p, **kw)
+        try:
             ph.run(full=False)
             torch.cuda.synchronize()
             ctx.profile_enable(True)
@@ -649,17 +656,38 @@ def paper_heat_bench(dev: int, precisions=("fp64", "fp32")):
             r = ph.run(full=True)
             ms = (time.perf_counter() - t0) * 1e3
             chk = sum(ctx.profile_read(nm)[1] for nm in ("error_expm", "error_bound"))
-            kry = sum(ctx.profile_read(nm)[1] for nm in ("csr_spmv", "csr_lanczos_update", "project"))
+            kry = {nm: ctx.profile_read(nm) for nm in kry_names}
             ctx.profile_enable(False)
-            out[prec] = {"m_used": int(r["m_used"][0]), "lemma1_bound": float(r["err_bound"][0]),
-                         "ms_per_query": ms, "checkpoint_ms": chk, "krylov_ms": kry,
-                         "peak_centre_temperature": float(np.max(r["hi"][0]))}
+            kms = sum(v[1] for v in kry.values())
+            launches = sum(v[0] for nm, v in kry.items() if nm.startswith(("lanczos", "stencil_update", "csr_spmv")))
+            return {"m_used": int(r["m_used"][0]), "lemma1_bound": float(r["err_bound"][0]),
+                    "ms_per_query": ms, "checkpoint_ms": chk, "krylov_ms": kms,
+                    "krylov_ms_per_iteration": kms / max(1, launches),
+                    "peak_centre_temperature": float(np.max(r["hi"][0])), "storage": ph.precision}
+        finally:
             ph.close()
             sysh.close()
+
+    ctx = kv.Context(8 << 30, device=dev)
+    try:
+        if "grid" in forms:
+            for prec in precisions:
+                out[f"grid_100_{prec}"] = timed(ctx, W.paper_heat_grid(100, precision=prec, err_target=1e-6),
+                                                expm_mode="propagate")
+        if "csr" in forms:
+            out["csr_100_fp64"] = timed(ctx, W.paper_heat(100, precision="fp64", err_target=1e-6),
+                                        expm_mode="propagate")
     finally:
         ctx.close()
-    out["workload"] = ("paper heat3d 100^3 (insulated, exchange 0.5 at x = 1), centre output, dt 0.02, 1000 steps, "
-                       "m <= 800, target 1e-6; paper: k = 544")
+    if "grid1000" in forms:
+        ctx = kv.Context(26 << 30, device=dev)
+        try:
+            for prec in precisions:
+                out[f"grid_1000_{prec}"] = timed(ctx, W.paper_heat_grid(1000, precision=prec, m=30))
+        finally:
+            ctx.close()
+    out["workload"] = ("paper heat3d (insulated, exchange 0.5 at x = 1), centre output, dt 0.02, 1000 steps; "
+                       "100^3: m <= 800, target 1e-6 (paper: k = 544); 1000^3: m = 30 fixed")
     return out
 
 
@@ -861,6 +889,8 @@ def main():
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--csr-only", type=int, default=0, metavar="N",
                     help="only the random-CSR query (FP32, forward) at n = N (profiling case)")
+    ap.add_argument("--paper-heat-form", default="grid,csr,grid1000",
+                    help="forms of the paper-heat leg: grid (100^3), csr (100^3), grid1000 (1000^3)")
     ap.add_argument("--paper-heat-only", default="", choices=["", "fp64", "fp32"],
                     help="only the paper's heat experiment (100^3, target 1e-6) in one precision (profiling case)")
     ap.add_argument("--serve-queries", type=int, default=512)
@@ -912,7 +942,8 @@ def main():
         dev = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(dev)
         print(json.dumps({"metric": "paper heat query ms",
-                          "paper_heat": paper_heat_bench(dev, precisions=(args.paper_heat_only,))}))
+                          "paper_heat": paper_heat_bench(dev, precisions=(args.paper_heat_only,),
+                                                         forms=tuple(args.paper_heat_form.split(",")))}))
         return
     if args.serve_only:
         import torch

@@ -493,6 +493,17 @@ int kv_grid_lanczos_noalloc(int device, void *stream, int ndim, const int64_t di
  * KV_ECUDA on a CUDA error.  The device and any context on it stay usable. */
 int kv_diag_bounded_wait(int device, int64_t polls);
 
+#ifdef KV_DEBUG
+/* Debug build only (compiled with -DKV_DEBUG; not in the paper): overwrite
+ * entry e of a forward problem's device copy of the output matrix's column
+ * indices with `value`, which the host validation of kv_problem would have
+ * refused, so that a test can check that the device-side bounds checks skip
+ * such an index instead of reading through it (kv_fetch then returns
+ * KV_EINVAL).  Waits for the context stream first.  Errors: KV_EINVAL (NULL
+ * problem, a transposed problem, e outside C's entries), KV_ECUDA. */
+int kv_debug_set_c_col(kv_prob *prob, int64_t e, int64_t value);
+#endif
+
 /* The device's FP64 instruction rate, measured.  Not in the paper: the FP64
  * grid iteration is bound by the FP64 pipe of this GPU (not by HBM), and its
  * roofline takes this rate as the peak.  Runs eight independent chains of

@@ -17,7 +17,8 @@ from typing import Dict, Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libkv.so")
+# KV_LIBRARY: another build of the library (the debug build of build.py)
+LIB_PATH = os.environ.get("KV_LIBRARY") or os.path.join(_HERE, "_build", "libkv.so")
 
 KV_OK, KV_EINVAL, KV_ENOMEM, KV_ECUDA, KV_ETIMEOUT, KV_EBUSY, KV_ENOTREADY = range(7)
 KV_FP64, KV_FP32 = 0, 1
@@ -546,6 +547,18 @@ class Server:
 
 
 KV_NOALLOC_MAX_N = 262144
+
+
+def debug_set_c_col(ph: "ProblemHandle", e: int, value: int) -> None:
+    """kv_debug_set_c_col (debug build only): overwrite entry e of the
+    problem's device copy of C's column indices."""
+    lib = load()
+    if not hasattr(lib, "kv_debug_set_c_col"):
+        raise RuntimeError("kv_debug_set_c_col exists in the debug build only (build(debug=True), KV_LIBRARY)")
+    f = lib.kv_debug_set_c_col
+    f.argtypes = [C.c_void_p, C.c_int64, C.c_int64]
+    f.restype = C.c_int
+    _check(f(ph.h, int(e), int(value)))
 
 
 def diag_fp64_rate(device: int = 0):

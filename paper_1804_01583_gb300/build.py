@@ -16,6 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkv.so")
+# the debug build (-DKV_DEBUG: device-side index checks on the matrix and the
+# scattered columns, a test hook), in a directory of its own
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 SOURCES = ["kv_abi.cu", "k_stencil.cu", "k_vector.cu", "k_expm.cu", "k_bounds.cu", "k_csr.cu", "k_stencil_tma.cu", "k_stencil_tma64.cu",
            "k_noalloc.cu", "kv_serve.cu", "kv_graph.cu", "k_lognorm.cu",
            "k_expm_large.cu", "k_csr_transpose.cu", "k_lp.cu", "k_diag.cu"]
@@ -41,15 +44,17 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files if os.path.exists(f))
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, debug: bool = False) -> str:
+    bdir = BUILD_DEBUG if debug else BUILD
+    lib = os.path.join(bdir, "libkv.so")
+    os.makedirs(bdir, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
     cc = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DKV_DEBUG"] if debug else [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -60,13 +65,13 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

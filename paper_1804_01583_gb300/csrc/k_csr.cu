@@ -124,7 +124,18 @@ __global__ void __launch_bounds__(CNT, 6) k_spmv(const int64_t* __restrict__ rp,
             __syncwarp();
             const int lo = (int)((e0 > base ? e0 : base) - base);
             const int hi = (int)((e1 < base + cnt ? e1 : base + cnt) - base);
-            for (int q = lo; q < hi; ++q) d.add_prod(sv[w][q], X[scol[w][q]]);
+            // unrolled so that several gathers of the row are in flight at once
+#pragma unroll 4
+            for (int q = lo; q < hi; ++q) {
+#ifdef KV_DEBUG
+                // debug build: a matrix column outside [0, n) is skipped, not read
+                if (scol[w][q] < 0 || scol[w][q] >= n) {
+                    atomicOr(&s->status, KV_ST_INDEX);
+                    continue;
+                }
+#endif
+                d.add_prod(sv[w][q], X[scol[w][q]]);
+            }
             __syncwarp();
         }
         if (r >= N) continue;
@@ -231,6 +242,15 @@ __global__ void __launch_bounds__(CNT) k_spmm(const int64_t* __restrict__ rp, co
     // x_k[c] for the G columns: one G-wide load (interleaved) or G loads
     // (column-major; dead slots read the group's first column)
     auto gather = [&](int c, T(&x)[G]) {
+#ifdef KV_DEBUG
+        // debug build: a matrix column outside [0, n) is skipped, not read
+        if (c < 0 || c >= n) {
+            atomicOr(&const_cast<ColState*>(st)[cg0].status, KV_ST_INDEX);
+#pragma unroll
+            for (int k = 0; k < G; ++k) x[k] = (T)0;
+            return;
+        }
+#endif
         if constexpr (IL) {
             load_row<T, G>(xg + (int64_t)c * G, x);
         } else {
@@ -271,7 +291,7 @@ __global__ void __launch_bounds__(CNT) k_spmm(const int64_t* __restrict__ rp, co
                 __syncwarp();
                 const int lo = (int)((e0 > base ? e0 : base) - base);
                 const int hi = (int)((e1 < base + cnt ? e1 : base + cnt) - base);
-#pragma unroll 4
+#pragma unroll 8
                 for (int q = lo; q < hi; ++q) {
                     T x[G];
                     gather(scol[w][q], x);
@@ -283,7 +303,7 @@ __global__ void __launch_bounds__(CNT) k_spmm(const int64_t* __restrict__ rp, co
             }
         } else {
             const int64_t e0 = inrow ? rp[r] : 0, e1 = inrow ? rp[r + 1] : 0;
-#pragma unroll 4
+#pragma unroll 8
             for (int64_t e = e0 + sub; e < e1; e += LP) {
                 T x[G];
                 gather(col[e], x);
@@ -328,9 +348,9 @@ __global__ void __launch_bounds__(CNT) k_interleave(VecArgs<T> V, int xslot, int
 
 // gather of C x by a whole block; result in thread 0
 template <typename T>
-__device__ double cgather(const CDesc& cd, int r, const T* x, double* sh) {
+__device__ double cgather(const CDesc& cd, int r, const T* x, double* sh, int* status) {
     double v = 0.0;
-    for (int64_t e = cd.rp[r] + threadIdx.x; e < cd.rp[r + 1]; e += CNT) v += cd.val[e] * (double)__ldcg(x + cd.col[e]);
+    for (int64_t e = cd.rp[r] + threadIdx.x; e < cd.rp[r + 1]; e += CNT) v += c_entry(cd, e, x, status);
     return block_sum<CNT>(v, sh);
 }
 
@@ -350,6 +370,7 @@ __device__ void finish_vector(double nw2, const T* W, ColState* s, double* H, do
         // stay zero), so one thread need not walk the whole column
         for (int l = symmetric && j > 0 ? j - 1 : 0; l <= j; ++l) nav2 += H[(int64_t)l * m + j] * H[(int64_t)l * m + j];
         if (!(beta > 1e-12 * sqrt(nav2)) || !isfinite(beta)) {
+            if (!isfinite(beta)) s->status |= KV_ST_NONFINITE;
             s->done = 1;
             s->m_used = j + 1;
             cont = 0;
@@ -363,14 +384,14 @@ __device__ void finish_vector(double nw2, const T* W, ColState* s, double* H, do
     __syncthreads();
     if (!cont || cd.o > PROJ_INLINE_MAX) return;  // launch_project takes many rows
     for (int r = 0; r < cd.o; ++r) {
-        const double v = cgather<T>(cd, r, W, sh);
+        const double v = cgather<T>(cd, r, W, sh, &s->status);
         if (threadIdx.x == 0) P[(int64_t)r * m + (j + 1)] = snext * v;
     }
 }
 
 // ------------------------------------------------------ Lanczos update --
 template <typename T, bool FIRST>
-__global__ void __launch_bounds__(CNT, 6) k_lanczos3_update(VecArgs<T> V, int wslot, int vslot, int pslot, int64_t N,
+__global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int wslot, int vslot, int pslot, int64_t N,
                                                          ColState* st, double* Hall, double* Pall, CDesc cd, int m,
                                                          int j, double* partials, unsigned* counters, int64_t nbx) {
     const int cidx = blockIdx.y;
@@ -384,7 +405,28 @@ __global__ void __launch_bounds__(CNT, 6) k_lanczos3_update(VecArgs<T> V, int ws
     const double ca = -alpha * s->s[j];
     const double cb = FIRST ? 0.0 : -H[(int64_t)j * m + (j - 1)] * s->s[j - 1];
     typename AccOf<T>::type acc;
-    for (int64_t r = (int64_t)blockIdx.x * CNT + threadIdx.x; r < N; r += (int64_t)gridDim.x * CNT) {
+    // four rows per thread per round, all their loads issued before the
+    // arithmetic (the three vectors are distinct buffers)
+    const int64_t stride = (int64_t)gridDim.x * CNT;
+    int64_t r = (int64_t)blockIdx.x * CNT + threadIdx.x;
+    for (; r + 3 * stride < N; r += 4 * stride) {
+        T wv[4], vj[4], vp[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wv[k] = Wv[r + k * stride];
+            vj[k] = __ldcs(Vj + r + k * stride);
+            vp[k] = FIRST ? (T)0 : __ldcs(Vp + r + k * stride);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double w = fma(ca, (double)vj[k], (double)wv[k]);
+            if (!FIRST) w = fma(cb, (double)vp[k], w);
+            const T wt = (T)w;
+            Wv[r + k * stride] = wt;
+            acc.add_prod(wt, wt);
+        }
+    }
+    for (; r < N; r += stride) {
         double w = fma(ca, (double)Vj[r], (double)Wv[r]);
         if (!FIRST) w = fma(cb, (double)Vp[r], w);
         const T wt = (T)w;
@@ -640,11 +682,17 @@ static int64_t spmv_blocks(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
     return b > 152 * 8 ? 152 * 8 : b;
 }
-// k_spmv and k_lanczos3_update: one wave at the 6 blocks per SM their launch
-// bounds guarantee (40 registers a thread); at most spmv_blocks
+// k_spmv: one wave at the 6 blocks per SM its launch bounds guarantee (40
+// registers a thread); at most spmv_blocks
 static int64_t spmv_grid(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
     return b > 152 * 6 ? 152 * 6 : b;
+}
+// k_lanczos3_update: one wave at its 4 blocks per SM (four rows a thread in
+// flight need the registers)
+static int64_t update_grid(int64_t N) {
+    int64_t b = (N + CNT - 1) / CNT;
+    return b > 152 * 4 ? 152 * 4 : b;
 }
 
 int64_t csr_scratch_slots(int64_t N, int m) {  // reduction partials per column
@@ -927,7 +975,7 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
     cudaStream_t st = p->ctx->stream;
     VecArgs<T> va{(T*)V, (int64_t)p->nvec * N};
     const int m = p->m;
-    CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval};
+    CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval, p->N};
     ColState* stp = p->d_state + j0;
     double* H = p->d_H + (int64_t)j0 * (m + 1) * m;
     double* P = p->d_P + (int64_t)j0 * p->o * m;
@@ -936,7 +984,7 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
     double* partials = p->red.partials;
     unsigned* counters = p->d_counters;
     dim3 gs((unsigned)spmv_blocks(N), (unsigned)ncols), gr((unsigned)row_blocks_t<T>(N), (unsigned)ncols);
-    const dim3 gv((unsigned)spmv_grid(N), (unsigned)ncols);
+    const dim3 gv((unsigned)spmv_grid(N), (unsigned)ncols), gu((unsigned)update_grid(N), (unsigned)ncols);
     for (int it = 0; it < m; ++it) {
         if (lanczos) {
             const int vs = it % 3, ws = (it + 1) % 3, ps = (it + 2) % 3;
@@ -949,10 +997,10 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
             {
                 LaunchScope ls(p->ctx, "csr_lanczos_update");
                 if (it == 0)
-                    k_lanczos3_update<T, true><<<gv, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
+                    k_lanczos3_update<T, true><<<gu, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
                                                                   counters, nbx);
                 else
-                    k_lanczos3_update<T, false><<<gv, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
+                    k_lanczos3_update<T, false><<<gu, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
                                                                    counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }

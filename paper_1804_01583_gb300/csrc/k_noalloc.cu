@@ -301,7 +301,7 @@ extern "C" int kv_grid_lanczos_noalloc(int device, void* stream, int ndim, const
         return KV_ECUDA;
     }
     const int64_t lz = ndim == 3 ? box_lo[2] : 0, hz = ndim == 3 ? box_hi[2] : 1;
-    CDesc cd{o, c_row_ptr, c_col, c_val};
+    CDesc cd{o, c_row_ptr, c_col, c_val, g.n};
     k_na_init<<<NA_BLOCKS, NA_NT, 0, s>>>(L, g, box_lo[0], box_lo[1], lz, box_hi[0], box_hi[1], hz, value, cd, m, P,
                                           beta0, m_used);
     for (int j = 0; j < m; ++j) {

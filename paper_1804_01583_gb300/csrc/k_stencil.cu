@@ -58,10 +58,10 @@ static StencilGeom geom_of(const Sys* s) {
 
 // gather of C x for row r by the whole (last) block; result in thread 0
 template <typename T>
-__device__ double c_gather_row(const CDesc& cd, int r, const T* x, double* sh) {
+__device__ double c_gather_row(const CDesc& cd, int r, const T* x, double* sh, int* status) {
     double v = 0.0;
     const int t = threadIdx.x + threadIdx.y * blockDim.x;
-    for (int64_t e = cd.rp[r] + t; e < cd.rp[r + 1]; e += SNT) v += cd.val[e] * (double)__ldcg(x + cd.col[e]);
+    for (int64_t e = cd.rp[r] + t; e < cd.rp[r + 1]; e += SNT) v += c_entry(cd, e, x, status);
     return block_sum<SNT>(v, sh);
 }
 
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(SNT) k_stencil_init_box(T* __restrict__ B, Ste
     __syncthreads();
     if (cd.o > PROJ_INLINE_MAX) return;  // launch_project takes the rows
     for (int r = 0; r < cd.o; ++r) {
-        const double v = c_gather_row<T>(cd, r, B, sh);
+        const double v = c_gather_row<T>(cd, r, B, sh, &st->status);
         if (t == 0) P[(int64_t)r * m + 0] = s0 * v;
     }
 }
@@ -190,6 +190,11 @@ __global__ void __launch_bounds__(SNT) k_stencil_alpha(const T* __restrict__ B, 
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         const double s = st->s[j];
         H[(int64_t)j * m + j] = s * s * tot;  // alpha_j
+        if (!isfinite(tot)) {
+            st->status |= KV_ST_NONFINITE;
+            st->done = 1;
+            st->m_used = j;
+        }
     }
 }
 
@@ -279,6 +284,7 @@ __global__ void __launch_bounds__(SNT) k_stencil_update(const T* __restrict__ B,
         const double bj = FIRST ? 0.0 : H[(int64_t)j * m + (j - 1)];
         const double nav = sqrt(alpha * alpha + bj * bj + beta * beta);  // ||A v_j||
         if (!(beta > 1e-12 * nav) || !isfinite(beta)) {
+            if (!isfinite(beta)) st->status |= KV_ST_NONFINITE;
             st->done = 1;
             st->m_used = j + 1;
             cont = 0;
@@ -292,13 +298,13 @@ __global__ void __launch_bounds__(SNT) k_stencil_update(const T* __restrict__ B,
     __syncthreads();
     if (!cont || cd.o > PROJ_INLINE_MAX) return;
     for (int r = 0; r < cd.o; ++r) {
-        const double v = c_gather_row<T>(cd, r, A, sh);
+        const double v = c_gather_row<T>(cd, r, A, sh, &st->status);
         if (t == 0) P[(int64_t)r * m + (j + 1)] = snext * v;
     }
 }
 
 // --------------------------------------------------------------- launchers
-static CDesc cdesc(const Prob* p) { return CDesc{p->o, p->d_crp, p->d_ccol, p->d_cval}; }
+static CDesc cdesc(const Prob* p) { return CDesc{p->o, p->d_crp, p->d_ccol, p->d_cval, p->N}; }
 
 int launch_stencil_init_box(Prob* p, int j, void* B) {
     const StencilGeom g = geom_of(p->sys);

@@ -528,6 +528,7 @@ __global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constan
         const double bj = FIRST ? 0.0 : a.H[(int64_t)j * m + (j - 1)];
         const double nav = sqrt(alpha * alpha + bj * bj + beta * beta);  // ||A v_j||
         if (!(beta > 1e-12 * nav) || !isfinite(beta) || !isfinite(edg)) {
+            if (!isfinite(beta) || !isfinite(edg)) a.st->status |= KV_ST_NONFINITE;
             a.st->done = 1;
             a.st->m_used = j + 1;
             cont = 0;
@@ -546,7 +547,7 @@ __global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constan
     for (int r = 0; r < a.cd.o; ++r) {
         double v = 0.0;
         for (int64_t e = a.cd.rp[r] + t; e < a.cd.rp[r + 1]; e += DNT)
-            v += a.cd.val[e] * __ldcg(a.W + a.cd.col[e]);
+            v += c_entry(a.cd, e, a.W, &a.st->status);
         v = block_sum<DNT>(v, shred);
         if (t == 0) a.P[(int64_t)r * a.m + (a.j + 1)] = snext * v;
     }
@@ -665,7 +666,7 @@ int launch_lanczos_fused64(Prob* p, int j, int it, const void* B, const void* Ap
     a.st = p->d_state + j;
     a.H = p->d_H + (int64_t)j * (p->m + 1) * p->m;
     a.P = p->d_P + (int64_t)j * p->o * p->m;
-    a.cd = CDesc{p->o, p->d_crp, p->d_ccol, p->d_cval};
+    a.cd = CDesc{p->o, p->d_crp, p->d_ccol, p->d_cval, p->N};
     a.m = p->m;
     a.j = it;
     a.red = p->red;

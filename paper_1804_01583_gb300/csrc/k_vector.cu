@@ -13,9 +13,17 @@ constexpr int VNT = 256;
 
 template <typename T>
 __global__ void k_scatter(T* __restrict__ B, const int64_t* __restrict__ idx, const double* __restrict__ val,
-                          int64_t nnz) {
-    for (int64_t e = (int64_t)blockIdx.x * VNT + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * VNT)
+                          int64_t nnz, int64_t N, int* status) {
+    for (int64_t e = (int64_t)blockIdx.x * VNT + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * VNT) {
+#ifdef KV_DEBUG
+        // debug build: an index outside the vector is skipped, not written
+        if (idx[e] < 0 || idx[e] >= N) {
+            atomicOr(status, KV_ST_INDEX);
+            continue;
+        }
+#endif
         B[idx[e]] = (T)val[e];
+    }
 }
 
 template <typename T>
@@ -42,7 +50,7 @@ __global__ void __launch_bounds__(VNT) k_init_norm(const T* __restrict__ B, int6
         const double b0 = sqrt(tot);
         st->beta0 = b0;
         st->m_used = m;
-        st->status = 0;
+        st->status = isfinite(b0) ? 0 : KV_ST_NONFINITE;
         if (!(b0 > 0.0) || !isfinite(b0)) {
             st->done = 1;
             st->m_used = 0;
@@ -58,7 +66,7 @@ __global__ void __launch_bounds__(VNT) k_init_norm(const T* __restrict__ B, int6
     for (int r = 0; r < cd.o; ++r) {
         double v = 0.0;
         for (int64_t e = cd.rp[r] + threadIdx.x; e < cd.rp[r + 1]; e += VNT)
-            v += cd.val[e] * (double)__ldcg(B + cd.col[e]);
+            v += c_entry(cd, e, B, &st->status);
         v = block_sum<VNT>(v, sh);
         if (threadIdx.x == 0) P[(int64_t)r * m] = s0 * v;
     }
@@ -68,10 +76,10 @@ __global__ void __launch_bounds__(VNT) k_init_norm(const T* __restrict__ B, int6
 // columns of a launch group (blockIdx.y); a column that stopped before jcol
 // is skipped (its P columns past m_used are not used)
 template <typename T>
-__global__ void __launch_bounds__(VNT) k_project(const T* w0, int64_t cstride, const ColState* st, CDesc cd,
+__global__ void __launch_bounds__(VNT) k_project(const T* w0, int64_t cstride, ColState* st, CDesc cd,
                                                  double* P0, int64_t pstride, int m, int jcol) {
     const int c = blockIdx.y;
-    const ColState* s = st + c;
+    ColState* s = st + c;
     if (s->done && s->m_used <= jcol) return;
     const T* W = w0 + c * cstride;
     double* P = P0 + c * pstride;
@@ -80,7 +88,7 @@ __global__ void __launch_bounds__(VNT) k_project(const T* w0, int64_t cstride, c
     const int64_t nw = (int64_t)gridDim.x * (VNT / 32);
     for (int64_t r = (int64_t)blockIdx.x * (VNT / 32) + (threadIdx.x >> 5); r < cd.o; r += nw) {
         double v = 0.0;
-        for (int64_t e = cd.rp[r] + lane; e < cd.rp[r + 1]; e += 32) v += cd.val[e] * (double)__ldcg(W + cd.col[e]);
+        for (int64_t e = cd.rp[r] + lane; e < cd.rp[r + 1]; e += 32) v += c_entry(cd, e, W, &s->status);
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) P[r * m + jcol] = sc * v;
     }
@@ -89,7 +97,7 @@ __global__ void __launch_bounds__(VNT) k_project(const T* w0, int64_t cstride, c
 int launch_project(Prob* p, int j0, int ncols, const void* w0, int64_t cstride, int jcol) {
     if (p->o <= PROJ_INLINE_MAX || jcol >= p->m) return KV_OK;
     LaunchScope ls(p->ctx, "project");
-    CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval};
+    CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval, p->N};
     int64_t g = ((int64_t)p->o + (VNT / 32) - 1) / (VNT / 32);
     if (g > 152 * 16) g = 152 * 16;
     const dim3 grd((unsigned)g, (unsigned)ncols);
@@ -118,9 +126,11 @@ int launch_scatter(Prob* p, int j, void* B) {
     if (nnz == 0) return KV_OK;
     LaunchScope ls(p->ctx, "scatter");
     if (p->prec == KV_FP32)
-        k_scatter<float><<<grid_for(nnz), VNT, 0, p->ctx->stream>>>((float*)B, p->d_sidx[j], p->d_sval[j], nnz);
+        k_scatter<float><<<grid_for(nnz), VNT, 0, p->ctx->stream>>>((float*)B, p->d_sidx[j], p->d_sval[j], nnz, p->N,
+                                                                    &p->d_state[j].status);
     else
-        k_scatter<double><<<grid_for(nnz), VNT, 0, p->ctx->stream>>>((double*)B, p->d_sidx[j], p->d_sval[j], nnz);
+        k_scatter<double><<<grid_for(nnz), VNT, 0, p->ctx->stream>>>((double*)B, p->d_sidx[j], p->d_sval[j], nnz,
+                                                                     p->N, &p->d_state[j].status);
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;
 }
@@ -139,7 +149,7 @@ int launch_init_norm(Prob* p, int j, void* B) {
     {
         LaunchScope ls(p->ctx, "init_norm");
         const int g = grid_for(p->N);
-        CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval};
+        CDesc cd{p->o, p->d_crp, p->d_ccol, p->d_cval, p->N};
         ColState* st = p->d_state + j;
         double* P = p->d_P + (int64_t)j * p->o * p->m;
         if (p->prec == KV_FP32)

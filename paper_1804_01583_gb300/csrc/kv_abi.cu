@@ -1003,6 +1003,20 @@ int kv_problem(kv_ctx* c, kv_prob** out, const kv_sys* s, const kv_problem_desc*
     return KV_OK;
 }
 
+#ifdef KV_DEBUG
+int kv_debug_set_c_col(kv_prob* p, int64_t e, int64_t value) {
+    if (!p) return fail(KV_EINVAL, "kv_debug_set_c_col: NULL problem");
+    if (p->inner) return fail(KV_EINVAL, "kv_debug_set_c_col: forward problems only");
+    KV_WITH_DEVICE(p->ctx->device);
+    KV_CHECK_CUDA(cudaStreamSynchronize(p->ctx->stream));
+    int64_t cnnz = 0;
+    KV_CHECK_CUDA(cudaMemcpy(&cnnz, p->d_crp + p->o, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (e < 0 || e >= cnnz) return fail(KV_EINVAL, "kv_debug_set_c_col: entry %lld of %lld", (long long)e, (long long)cnnz);
+    KV_CHECK_CUDA(cudaMemcpy(p->d_ccol + e, &value, sizeof(int64_t), cudaMemcpyHostToDevice));
+    return KV_OK;
+}
+#endif
+
 int kv_problem_precision(const kv_prob* p, int32_t* precision) {
     if (!p || !precision) return fail(KV_EINVAL, "kv_problem_precision: NULL argument");
     *precision = p->prec;
@@ -1170,7 +1184,13 @@ int kv_fetch(kv_prob* p, kv_result* r) {
         if (r->z_star) KV_CHECK_CUDA(cudaMemcpy(r->z_star, p->d_zstar, (size_t)p->i * 8, cudaMemcpyDeviceToHost));
     }
     if (r->err_bound) KV_CHECK_CUDA(cudaMemcpy(r->err_bound, q->d_err, (size_t)q->i * 8, cudaMemcpyDeviceToHost));
-    if (status) return fail(KV_ETIMEOUT, "a device-side wait gave up (status %d)", status);
+    if (status & KV_ST_TIMEOUT) return fail(KV_ETIMEOUT, "a device-side wait gave up (status %d)", status);
+    if (status & KV_ST_INDEX)
+        return fail(KV_EINVAL, "a device-side bounds check skipped an index outside its vector (status %d): the "
+                    "results are incomplete", status);
+    if (status & KV_ST_NONFINITE)
+        return fail(KV_EINVAL, "a Krylov scalar (the norm of a column, alpha or beta) is not finite (status %d): "
+                    "the system or the initial set holds a NaN or overflows", status);
     return KV_OK;
 }
 

@@ -146,7 +146,25 @@ struct CDesc {  // output matrix C in CSR form on the device
     const int64_t* rp;
     const int64_t* col;
     const double* val;
+    int64_t n;  // length of the vectors C is applied to (column indices lie in [0, n))
 };
+
+// ColState::status bits, reported by kv_fetch
+constexpr int KV_ST_TIMEOUT = 1;    // a bounded device wait expired
+constexpr int KV_ST_INDEX = 2;      // an index outside its vector was skipped, not read
+constexpr int KV_ST_NONFINITE = 4;  // alpha or beta of an iteration is not finite
+
+// One term of C_r . x: an entry whose column lies outside the vector is
+// skipped (not read) and recorded in *status.
+template <typename T>
+__device__ __forceinline__ double c_entry(const CDesc& cd, int64_t e, const T* x, int* status) {
+    const int64_t c = cd.col[e];
+    if (c < 0 || c >= cd.n) {
+        atomicOr(status, KV_ST_INDEX);
+        return 0.0;
+    }
+    return cd.val[e] * (double)__ldcg(x + c);
+}
 
 struct Reduce {  // scratch of one deterministic grid reduction
     double* partials;

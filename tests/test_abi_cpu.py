@@ -18,6 +18,8 @@ def declared_entry_points():
         if f.endswith(".h"):
             src = open(os.path.join(ROOT, "include", f)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            # entry points of the debug build only
+            src = re.sub(r"#ifdef KV_DEBUG.*?#endif", "", src, flags=re.S)
             names |= set(re.findall(r"\b(kv_[a-z0-9_]+)\s*\(", src))
     return sorted(names)
 
