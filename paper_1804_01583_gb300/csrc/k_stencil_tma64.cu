@@ -161,6 +161,8 @@ struct Fused64Args {
     const double* Aprev;  // v_{j-1} (unnormalised; unused in the first iteration)
     StencilGeom g;
     double gface[6];    // gamma per face: x low, x high, y low, y high, z low, z high
+    float gfh[6], gfl[6];  // the same as float pairs (gamma = gfh + gfl to 2^-48), the face terms' weights
+    double kmg[6];      // kappa_axis - gamma per face: a face point adds s_j (kappa - gamma) v_p to w
     int zc;             // z planes per CTA
     int nbx, nby;       // tiles per z chunk: nbx x nby
     int sh;             // split scale: |w| 2^-sh < 2^8
@@ -205,13 +207,6 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
     const double fx = sj * g.kx, fy = sj * g.ky, fz = sj * g.kz;
     const double fc = sj * (g.kc - alpha);
     const double fa = FIRST ? 0.0 : -a.H[(int64_t)a.j * a.m + (a.j - 1)] * a.st->s[a.j - 1];
-    // the face terms: a point on face f adds s_j (kappa_a - gamma_f) c
-    double fdel[6];
-    if (FACES) {
-        const double kap[3] = {g.kx, g.ky, g.kz};
-#pragma unroll
-        for (int f = 0; f < 6; ++f) fdel[f] = sj * (kap[f >> 1] - a.gface[f]);
-    }
 
     auto ring = [](int plane) { return ((plane % DRB) + DRB) % DRB; };
     auto load_b = [&](int plane, uint64_t* bar) {  // v_j plane: main box + side box, same ring slot
@@ -282,7 +277,7 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
 #pragma unroll
         for (int u = 0; u < 4; ++u) prev[h][u] = F3{0.f, 0.f, 0.f};
     Acc2 acc_n, acc_x, acc_y, acc_z;
-    Acc2 acc_f[6];  // FACES: sum of w^2 over each face's points (weighted by gamma at the end)
+    Acc2 acc_g;  // FACES: sum of gamma_f w^2 over the faces' points
     int pfail = -1;
     int sbm = ring(p0 - 1), sbc = ring(p0), sbp = ring(p0 + 1), sst = 0;
     unsigned sph = 0;
@@ -352,12 +347,12 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
                     if (!FIRST) w = fma(fa, aa[u], w);
                     if (FACES) {
                         const unsigned fb = face_bits(xu[u], yr[h], p, nx, ny, nz);
-                        if (fb) {
+                        if (fb) {  // a point on face f adds s_j (kappa - gamma_f) c
                             double d = 0.0;
 #pragma unroll
                             for (int f = 0; f < 6; ++f)
-                                if (fb & (1u << f)) d += fdel[f];
-                            w = fma(d, cc[u], w);
+                                if (fb & (1u << f)) d += a.kmg[f];
+                            w = fma(sj * d, cc[u], w);
                         }
                     }
                     wv[u] = (pin && yin[h] && xin[u]) ? w : 0.0;
@@ -437,9 +432,16 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
                             if (yr[h] == ny - 1) acc_y.add(nh, nl);
                             if (qz == nz - 1) acc_z.add(nh, nl);
                         } else if (fb) {
+                            // gamma_f w^2 with gamma as a float pair: the product
+                            // keeps about 47 bits, like every other term
 #pragma unroll
                             for (int f = 0; f < 6; ++f)
-                                if (fb & (1u << f)) acc_f[f].add(nh, nl);
+                                if (fb & (1u << f)) {
+                                    const float gh = a.gfh[f], gl = a.gfl[f];
+                                    const float pp = __fmul_rn(gh, nh);
+                                    const float pe = __fmaf_rn(gh, nh, -pp);
+                                    acc_g.add(pp, __fmaf_rn(gh, nl, __fmaf_rn(gl, nh, pe)));
+                                }
                         }
                     }
                 }
@@ -484,9 +486,7 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
     const double s2 = ldexp(1.0, 2 * a.sh);
     sum_n = acc_n.value() * s2;
     double e = g.kx * acc_x.value() + g.ky * acc_y.value() + g.kz * acc_z.value();
-    if (FACES)
-#pragma unroll
-        for (int f = 0; f < 6; ++f) e = fma(a.gface[f], acc_f[f].value(), e);
+    if (FACES) e += acc_g.value();
     sum_e = e * s2;
     return true;
 }
@@ -658,7 +658,13 @@ int launch_lanczos_fused64(Prob* p, int j, int it, const void* B, const void* Ap
     a.W = (double*)Wout;
     a.Aprev = (const double*)Aprev;
     a.g = g;
-    for (int q = 0; q < 6; ++q) a.gface[q] = s->face[q];
+    for (int q = 0; q < 6; ++q) {
+        a.gface[q] = s->face[q];
+        a.gfh[q] = (float)s->face[q];
+        a.gfl[q] = (float)(s->face[q] - (double)a.gfh[q]);
+        const double kap = q < 2 ? g.kx : (q < 4 ? g.ky : g.kz);
+        a.kmg[q] = kap - s->face[q];
+    }
     a.zc = f.zc;
     a.nbx = f.nbx;
     a.nby = f.nby;
