@@ -170,20 +170,30 @@ __global__ void __launch_bounds__(CNT, 6) k_spmv(const int64_t* __restrict__ rp,
 // one contiguous G-wide load (one 32-byte sector for 32 bytes) instead of G
 // scattered ones.  k_interleave builds xi for every group from the
 // column-major vectors just before the SpMM.
+// One 32-byte read-only load (ld.global.nc.v8.b32, sm_100 and later): a
+// lane's gather of a 32-byte row is one request instead of two 16-byte ones,
+// and a warp's divergent gather costs the L1 about as much per request
+// whatever its width up to 32 bytes.  The address is 32-byte aligned.
+__device__ __forceinline__ void ld_nc_256(const void* p, uint32_t (&u)[8]) {
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+                 : "l"(p));
+}
+
 template <typename T, int G>
 __device__ __forceinline__ void load_row(const T* __restrict__ src, T (&x)[G]) {
     static_assert((G * sizeof(T)) % 16 == 0, "interleaved rows are whole 16-byte words");
-    constexpr int W = (int)(G * sizeof(T) / 16);
-    const uint4* s4 = reinterpret_cast<const uint4*>(src);
-    uint4 w[W];
+    constexpr int BYTES = (int)(G * sizeof(T));
+    if constexpr (BYTES % 32 == 0) {  // rows of 32 or 64 bytes: 32-byte loads
+        constexpr int W = BYTES / 32;
+        uint32_t u[W][8];
 #pragma unroll
-    for (int q = 0; q < W; ++q) w[q] = __ldg(s4 + q);
+        for (int q = 0; q < W; ++q) ld_nc_256(reinterpret_cast<const char*>(src) + 32 * q, u[q]);
 #pragma unroll
-    for (int q = 0; q < W; ++q) {
-        T t[16 / sizeof(T)];
-        memcpy(t, &w[q], 16);
-#pragma unroll
-        for (int u = 0; u < (int)(16 / sizeof(T)); ++u) x[q * (16 / sizeof(T)) + u] = t[u];
+        for (int q = 0; q < W; ++q) memcpy(&x[q * (32 / sizeof(T))], u[q], 32);
+    } else {  // 16-byte rows
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(src));
+        memcpy(&x[0], &w, 16);
     }
 }
 
@@ -356,19 +366,27 @@ __device__ double cgather(const CDesc& cd, int r, const T* x, double* sh, int* s
 
 // Shared epilogue of every pass that produces w = unnormalised v_{j+1}:
 // beta = ||w||, breakdown test against ||A v_j||^2 = sum_l H[l][j]^2 + beta^2,
-// scale, H entries, P column.  Runs in the last block, all threads.
+// scale, H entries, P column.  Runs in the last block, all threads.  hcol2 >= 0
+// is sum_l H[l][j]^2 already known to the caller (else read from H); cw, when
+// given, holds C w for the o rows of C (already reduced over the grid), else
+// the block gathers it.
 template <typename T>
 __device__ void finish_vector(double nw2, const T* W, ColState* s, double* H, double* P, const CDesc& cd, int m,
-                              int j, bool symmetric, double* sh) {
+                              int j, bool symmetric, double* sh, double hcol2 = -1.0, const double* cw = nullptr) {
     __shared__ double snext;
     __shared__ int cont;
     if (threadIdx.x == 0) {
         const double beta = sqrt(nw2);
         H[(int64_t)(j + 1) * m + j] = beta;
         double nav2 = beta * beta;
-        // Lanczos: column j of H has entries in rows j-1 and j only (the rest
-        // stay zero), so one thread need not walk the whole column
-        for (int l = symmetric && j > 0 ? j - 1 : 0; l <= j; ++l) nav2 += H[(int64_t)l * m + j] * H[(int64_t)l * m + j];
+        if (hcol2 >= 0.0) {
+            nav2 += hcol2;
+        } else {
+            // Lanczos: column j of H has entries in rows j-1 and j only (the
+            // rest stay zero), so one thread need not walk the whole column
+            for (int l = symmetric && j > 0 ? j - 1 : 0; l <= j; ++l)
+                nav2 += H[(int64_t)l * m + j] * H[(int64_t)l * m + j];
+        }
         if (!(beta > 1e-12 * sqrt(nav2)) || !isfinite(beta)) {
             if (!isfinite(beta)) s->status |= KV_ST_NONFINITE;
             s->done = 1;
@@ -383,17 +401,28 @@ __device__ void finish_vector(double nw2, const T* W, ColState* s, double* H, do
     }
     __syncthreads();
     if (!cont || cd.o > PROJ_INLINE_MAX) return;  // launch_project takes many rows
+    if (cw) {
+        if (threadIdx.x < cd.o) P[(int64_t)threadIdx.x * m + (j + 1)] = snext * cw[threadIdx.x];
+        return;
+    }
     for (int r = 0; r < cd.o; ++r) {
         const double v = cgather<T>(cd, r, W, sh, &s->status);
         if (threadIdx.x == 0) P[(int64_t)r * m + (j + 1)] = snext * v;
     }
 }
 
+// C w of the Lanczos update folded into its grid reduction: with at most
+// CINL_ROWS rows and CNT entries in C, each block adds up the entries whose
+// column it wrote itself, and the last block only sums the blocks' shares
+// (no gather after the grid reduction).
+constexpr int CINL_ROWS = 4;
+
 // ------------------------------------------------------ Lanczos update --
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int wslot, int vslot, int pslot, int64_t N,
-                                                         ColState* st, double* Hall, double* Pall, CDesc cd, int m,
-                                                         int j, double* partials, unsigned* counters, int64_t nbx) {
+                                                         ColState* st, double* Hall, double* Pall, CDesc cd, int cinl,
+                                                         int m, int j, double* partials, unsigned* counters,
+                                                         int64_t nbx) {
     const int cidx = blockIdx.y;
     ColState* s = st + cidx;
     if (s->done) return;
@@ -403,7 +432,8 @@ __global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int ws
     const T* Vp = V.base + cidx * V.cstride + (int64_t)pslot * N;
     const double alpha = H[(int64_t)j * m + j];
     const double ca = -alpha * s->s[j];
-    const double cb = FIRST ? 0.0 : -H[(int64_t)j * m + (j - 1)] * s->s[j - 1];
+    const double hb = FIRST ? 0.0 : H[(int64_t)j * m + (j - 1)];  // beta_j = H[j-1][j]
+    const double cb = -hb * (FIRST ? 0.0 : s->s[j - 1]);
     typename AccOf<T>::type acc;
     // four rows per thread per round, all their loads issued before the
     // arithmetic (the three vectors are distinct buffers)
@@ -435,10 +465,49 @@ __global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int ws
     }
     __shared__ double sh[CNT / 32];
     __shared__ int flag;
-    const double part = block_sum<CNT>(acc.value(), sh);
-    if (!grid_arrive(part, partials + cidx * nbx, counters + cidx, blockIdx.x, gridDim.x, &flag)) return;
-    const double tot = grid_finish<CNT>(partials + cidx * nbx, gridDim.x, counters + cidx, sh);
-    finish_vector<T>(tot, Wv, s, H, Pall + (int64_t)cidx * cd.o * m, cd, m, j, true, sh);
+    __shared__ double cw[CINL_ROWS];
+    const double part = block_sum<CNT>(acc.value(), sh);  // its barriers also publish the block's W
+    // column region: ||w||^2 partials, then (cinl) one row of partials per row of C
+    double* preg = partials + (int64_t)cidx * nbx * (cinl ? 1 + CINL_ROWS : 1);
+    if (cinl) {
+        // row c of W was written by block (c mod stride) / CNT
+        const int64_t e0 = cd.rp[0], ne = cd.rp[cd.o] - e0;
+        double v = 0.0;
+        int row = -1;
+        if (threadIdx.x < ne) {
+            const int64_t e = e0 + threadIdx.x, c = cd.col[e];
+            if (c < 0 || c >= cd.n) {
+                if (blockIdx.x == 0) atomicOr(&s->status, KV_ST_INDEX);  // skipped, not read
+            } else if ((c % stride) / CNT == blockIdx.x) {
+                row = 0;
+                while (cd.rp[row + 1] <= e) ++row;
+                v = cd.val[e] * (double)__ldcg(Wv + c);
+            }
+        }
+        if (__syncthreads_or(row >= 0)) {
+            for (int q = 0; q < cd.o; ++q) {
+                const double r = block_sum<CNT>(row == q ? v : 0.0, sh);
+                if (threadIdx.x == 0) preg[(int64_t)(1 + q) * nbx + blockIdx.x] = r;
+            }
+        } else if (threadIdx.x == 0) {
+            for (int q = 0; q < cd.o; ++q) preg[(int64_t)(1 + q) * nbx + blockIdx.x] = 0.0;
+        }
+        // thread 0 wrote every partial of the block: grid_arrive's fence covers them
+    }
+    if (!grid_arrive(part, preg, counters + cidx, blockIdx.x, gridDim.x, &flag)) return;
+    const double tot = grid_finish<CNT>(preg, gridDim.x, counters + cidx, sh);
+    if (cinl) {
+        for (int q = 0; q < cd.o; ++q) {
+            double v = 0.0;
+            for (int64_t b = threadIdx.x; b < gridDim.x; b += CNT) v += __ldcg(preg + (int64_t)(1 + q) * nbx + b);
+            v = block_sum<CNT>(v, sh);
+            if (threadIdx.x == 0) cw[q] = v;
+        }
+        __syncthreads();
+    }
+    // the column of H above beta: alpha_j and beta_j, both already here
+    finish_vector<T>(tot, Wv, s, H, Pall + (int64_t)cidx * cd.o * m, cd, m, j, true, sh, alpha * alpha + hb * hb,
+                     cinl ? cw : nullptr);
 }
 
 // --------------------------------------------------------- Arnoldi dots --
@@ -985,6 +1054,9 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
     unsigned* counters = p->d_counters;
     dim3 gs((unsigned)spmv_blocks(N), (unsigned)ncols), gr((unsigned)row_blocks_t<T>(N), (unsigned)ncols);
     const dim3 gv((unsigned)spmv_grid(N), (unsigned)ncols), gu((unsigned)update_grid(N), (unsigned)ncols);
+    // C w inside the update's reduction: few rows and entries, and room for
+    // 1 + CINL_ROWS rows of partials in a column's 2 (m + 1) (csr_scratch_slots)
+    const int cinl = p->o >= 1 && p->o <= CINL_ROWS && p->c_nnz <= CNT && 1 + CINL_ROWS <= 2 * (m + 1) ? 1 : 0;
     for (int it = 0; it < m; ++it) {
         if (lanczos) {
             const int vs = it % 3, ws = (it + 1) % 3, ps = (it + 2) % 3;
@@ -997,11 +1069,11 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
             {
                 LaunchScope ls(p->ctx, "csr_lanczos_update");
                 if (it == 0)
-                    k_lanczos3_update<T, true><<<gu, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
-                                                                  counters, nbx);
+                    k_lanczos3_update<T, true><<<gu, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, cinl, m, it,
+                                                                  partials, counters, nbx);
                 else
-                    k_lanczos3_update<T, false><<<gu, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, m, it, partials,
-                                                                   counters, nbx);
+                    k_lanczos3_update<T, false><<<gu, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, cinl, m, it,
+                                                                   partials, counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }
             const int rc = launch_project(p, j0, ncols, (T*)V + (int64_t)ws * N, va.cstride, it + 1);

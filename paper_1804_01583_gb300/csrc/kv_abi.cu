@@ -760,6 +760,7 @@ static int prob_build(Ctx* c, Prob* p, const Sys* s, const kv_problem_desc* d, i
     p->cols.assign(d->cols, d->cols + d->i);
     const int64_t S = d->steps + 1;
     const int64_t cnnz = d->c_row_ptr[d->o];
+    p->c_nnz = cnnz;
 #define TRY(x)               \
     do {                     \
         rc = (x);            \

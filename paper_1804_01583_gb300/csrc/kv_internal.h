@@ -202,6 +202,7 @@ struct Prob {
     std::vector<double*> d_sval;
     std::vector<double*> d_dense;
     // device arrays
+    int64_t c_nnz = 0;  // entries of C (host copy of d_crp[o])
     int64_t* d_crp = nullptr;
     int64_t* d_ccol = nullptr;
     double* d_cval = nullptr;
