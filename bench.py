@@ -634,7 +634,7 @@ def cpu_configs() -> dict:
     return out
 
 
-def paper_heat_bench(dev: int, precisions=("fp64", "fp32"), forms=("grid", "csr", "grid1000")):
+def paper_heat_bench(dev: int, precisions=("fp64", "fp32"), forms=("grid", "csr", "grid1000"), pool_gb: int = 0):
     """The paper's own 3-D heat model (Sec. 5.3): the insulated cube with heat
     exchange at x = 1 (cell-centred reading), the heated region
     [0,0.4]x[0,0.2]x[0,0.1], the centre output, T = 20 by 0.02.
@@ -676,7 +676,7 @@ def paper_heat_bench(dev: int, precisions=("fp64", "fp32"), forms=("grid", "csr"
             ph.close()
             sysh.close()
 
-    ctx = kv.Context(8 << 30, device=dev)
+    ctx = kv.Context((pool_gb or 8) << 30, device=dev)
     try:
         if "grid" in forms:
             for prec in precisions:
@@ -831,7 +831,7 @@ def csr_bench(args, dev: int, n: int = 2_000_000, legs=None):
     for prec, sim in legs or (("fp64", "forward"), ("fp32", "forward"), ("fp64", "transpose"), ("fp32", "transpose")):
         p = W.random_csr_problem(n, seed=0, precision=prec)
         p.simulate = sim
-        ctx = kv.Context(40 << 30, device=dev)
+        ctx = kv.Context((getattr(args, "pool_gb", 0) or 40) << 30, device=dev)
         sysh = kv.System(ctx, p.system, p.precision)
         ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
         ph.enqueue()
@@ -901,6 +901,8 @@ def main():
                     help="forms of the paper-heat leg: grid (100^3), csr (100^3), grid1000 (1000^3)")
     ap.add_argument("--paper-heat-only", default="", choices=["", "fp64", "fp32"],
                     help="only the paper's heat experiment (100^3, target 1e-6) in one precision (profiling case)")
+    ap.add_argument("--pool-gb", type=int, default=0,
+                    help="device pool of the --csr-only and --paper-heat-only cases (GB; profiling runs keep it small)")
     ap.add_argument("--serve-queries", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-pool-gb", type=int, default=160)
@@ -951,7 +953,8 @@ def main():
         torch.cuda.set_device(dev)
         print(json.dumps({"metric": "paper heat query ms",
                           "paper_heat": paper_heat_bench(dev, precisions=(args.paper_heat_only,),
-                                                         forms=tuple(args.paper_heat_form.split(",")))}))
+                                                         forms=tuple(args.paper_heat_form.split(",")),
+                                                         pool_gb=args.pool_gb)}))
         return
     if args.serve_only:
         import torch

@@ -146,7 +146,12 @@ def heat(dims: Sequence[int], *, coef: float = 0.01, block: Sequence[int],
     Initial set: the corner block [0, block) per axis at temperature
     u in [zlo, zhi] (one generator, one Krylov run); everything else 0.
     output = "centre": the cell N//2 on every axis;
-    output = "centre8": the mean of the 2^ndim cells {N//2-1, N//2}^ndim.
+    output = "centre8": the mean of the 2^ndim cells {N//2-1, N//2}^ndim;
+    output = "edge": the cell just past the block's far corner (block[a] on
+    every axis), one stencil application per axis from the block, so the
+    Krylov space reaches it after ndim steps (the centre lies beyond the
+    reach of m stencil applications on large grids, where the projected
+    output is exactly 0).
     """
     dims = tuple(int(d) for d in dims)
     h = tuple(1.0 / (d + 1) for d in dims)
@@ -158,6 +163,8 @@ def heat(dims: Sequence[int], *, coef: float = 0.01, block: Sequence[int],
     elif output == "centre8":
         import itertools
         cells = list(itertools.product(*[(d // 2 - 1, d // 2) for d in dims]))
+    elif output == "edge":
+        cells = [tuple(min(int(b), d - 1) for b, d in zip(block, dims))]
     else:
         raise ValueError(output)
     w = 1.0 / len(cells)
@@ -511,8 +518,11 @@ def serving_mix(n_queries: int = 512, seed: int = 0, *, side2d=(100, 2000), side
                 csr_n=(100_000, 2_000_000), csr_sizes: int = 5, gens=(1, 32), steps=(100, 2000), m=(20, 60),
                 precision: str = "fp32", simulate: str = "auto") -> List[Problem]:
     """A seeded mix of verification queries, one third each:
-      * 2D heat, side log-uniform in side2d (n = side^2), block side/4, centre output, dt 0.1;
-      * 3D heat, side log-uniform in side3d, block side/10, centre output, dt 0.02;
+      * 2D heat, side log-uniform in side2d (n = side^2), block side/4, dt 0.1;
+      * 3D heat, side log-uniform in side3d, block side/10, dt 0.02;
+      (heat outputs: the cell just past the block's far corner, so that every
+      query's projected output is nonzero; the grid centre is out of the
+      Krylov space's reach at these m);
       * random CSR systems of random_csr (sizes log-spaced in csr_n, `csr_sizes`
         distinct systems shared by the queries), `gens` unit generators plus the
         fixed column, two +-1 output rows, dt 0.01;
@@ -530,12 +540,12 @@ def serving_mix(n_queries: int = 512, seed: int = 0, *, side2d=(100, 2000), side
         if kind == 0:
             side = int(round(math.exp(rng.uniform(math.log(side2d[0]), math.log(side2d[1])))))
             b = max(side // 4, 1)
-            out.append(heat((side, side), block=(b, b), output="centre", dt=0.1, steps=st, m=mm,
+            out.append(heat((side, side), block=(b, b), output="edge", dt=0.1, steps=st, m=mm,
                             precision=precision, name=f"q{q}-heat2d-{side}"))
         elif kind == 1:
             side = int(round(math.exp(rng.uniform(math.log(side3d[0]), math.log(side3d[1])))))
             b = max(side // 10, 1)
-            out.append(heat((side, side, side), block=(b, b, b), output="centre", dt=0.02, steps=st, m=mm,
+            out.append(heat((side, side, side), block=(b, b, b), output="edge", dt=0.02, steps=st, m=mm,
                             precision=precision, name=f"q{q}-heat3d-{side}"))
         else:
             n = sizes[int(rng.integers(len(sizes)))]
