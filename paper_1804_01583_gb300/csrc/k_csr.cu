@@ -91,6 +91,8 @@ __global__ void __launch_bounds__(CNT, 6) k_spmv(const int64_t* __restrict__ rp,
                                               VecArgs<T> V, int xslot, int wslot, int64_t n, int64_t N,
                                               const int* aug, ColState* st, double* H, int m, int j,
                                               double* partials, unsigned* counters, int64_t nbx) {
+    dep_wait();  // every input comes from the kernel before
+    dep_release();
     const int cidx = blockIdx.y;
     ColState* s = st + cidx;
     if (s->done) return;
@@ -423,6 +425,8 @@ __global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int ws
                                                          ColState* st, double* Hall, double* Pall, CDesc cd, int cinl,
                                                          int m, int j, double* partials, unsigned* counters,
                                                          int64_t nbx) {
+    dep_wait();  // every input comes from the kernel before
+    dep_release();
     const int cidx = blockIdx.y;
     ColState* s = st + cidx;
     if (s->done) return;
@@ -1060,21 +1064,23 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
     for (int it = 0; it < m; ++it) {
         if (lanczos) {
             const int vs = it % 3, ws = (it + 1) % 3, ps = (it + 2) % 3;
+            // the pair runs as a programmatic dependent chain: each launch is
+            // set up while the kernel before it runs (paper heat, 100^3,
+            // 1600 short launches a query: 102.8 -> 100.5 ms).  The Arnoldi
+            // chain below is launched plainly: its long multi-wave kernels
+            // gained nothing and lost 1 % with it.
             {
                 LaunchScope ls(p->ctx, "csr_spmv");
-                k_spmv<T, true><<<gv, CNT, 0, st>>>(s->d_rp, s->d_col, (const T*)s->d_val, s->d_b, va, vs, ws, n, N,
-                                                   aug, stp, H, m, it, partials, counters, nbx);
-                KV_CHECK_CUDA(cudaGetLastError());
+                KV_CHECK_CUDA(launch_dep(dep_launch_ok(p->ctx), k_spmv<T, true>, gv, dim3(CNT), 0, st, s->d_rp,
+                                         s->d_col, (const T*)s->d_val, s->d_b, va, vs, ws, n, N, aug, stp, H, m, it,
+                                         partials, counters, nbx));
             }
             {
                 LaunchScope ls(p->ctx, "csr_lanczos_update");
-                if (it == 0)
-                    k_lanczos3_update<T, true><<<gu, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, cinl, m, it,
-                                                                  partials, counters, nbx);
-                else
-                    k_lanczos3_update<T, false><<<gu, CNT, 0, st>>>(va, ws, vs, ps, N, stp, H, P, cd, cinl, m, it,
-                                                                   partials, counters, nbx);
-                KV_CHECK_CUDA(cudaGetLastError());
+                KV_CHECK_CUDA(launch_dep(dep_launch_ok(p->ctx), it == 0 ? k_lanczos3_update<T, true>
+                                                                        : k_lanczos3_update<T, false>,
+                                         gu, dim3(CNT), 0, st, va, ws, vs, ps, N, stp, H, P, cd, cinl, m, it,
+                                         partials, counters, nbx));
             }
             const int rc = launch_project(p, j0, ncols, (T*)V + (int64_t)ws * N, va.cstride, it + 1);
             if (rc) return rc;

@@ -4,6 +4,7 @@
 #include <stdarg.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -98,6 +99,14 @@ size_t Arena::largest_free() const {
 }
 
 // ----------------------------------------------------------- launch scope
+bool dep_launch_ok(const Ctx* c) {
+    static const bool env_on = [] {
+        const char* e = getenv("KV_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return env_on && !c->profiling && !c->capturing;
+}
+
 LaunchScope::LaunchScope(Ctx* c, const char* name) : ctx(c) {
     ctx->launches++;
     if (!ctx->profiling) return;

@@ -67,6 +67,7 @@ int kv_graph_create(kv_ctx* ctx, kv_prob* const* probs, int32_t n, kv_graph** ou
     // launched its results are those of its previous runs, if any
     std::vector<bool> ran_before(n);
     for (int k = 0; k < n; ++k) ran_before[k] = probs[k]->ran;
+    ctx->capturing = true;  // plain launches inside the graph
     cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(fork, origin);
     for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(br[b], fork, 0);
@@ -82,6 +83,7 @@ int kv_graph_create(kv_ctx* ctx, kv_prob* const* probs, int32_t n, kv_graph** ou
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+    ctx->capturing = false;
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess && rc == KV_OK) e = cudaGraphInstantiate(&g->exec, graph, 0);
     g->graph = graph;

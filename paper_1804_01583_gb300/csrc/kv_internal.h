@@ -82,6 +82,7 @@ struct Ctx {
     Arena arena;
     int64_t launches = 0;
     bool profiling = false;
+    bool capturing = false;  // inside kv_graph_create's stream capture
     struct Rec {
         std::string name;
         cudaEvent_t a, b;
@@ -89,6 +90,46 @@ struct Ctx {
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> spare_events;
 };
+
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  A kernel
+// of a dependent chain (each reads what the one before it in the stream
+// wrote) starts with dep_wait(), which returns once the previous kernel has
+// completed and its writes are visible, then calls dep_release(), which lets
+// the next kernel be launched as soon as every block of this one has
+// started, so the next grid's launch and ramp overlap this grid's run instead
+// of following its end.  Both are no-ops in a kernel launched without the
+// attribute.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Whether a launch on the context's stream may carry the attribute: not
+// while profiling (events between the launches) or capturing a graph, and
+// not when the environment variable KV_PDL is 0.
+bool dep_launch_ok(const Ctx* c);
+
+// kern<<<grid, block, smem, s>>>(args...), with the programmatic-serialisation
+// attribute when pdl (dep_launch_ok of the context, and no event or other
+// stream work of the caller between this launch and the kernel before);
+// kern must begin with dep_wait().
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    if (!pdl) {
+        kern<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 // Records one launch: bumps the launch counter and, when profiling, brackets
 // the launch with events on the context stream.

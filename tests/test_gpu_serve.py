@@ -78,18 +78,29 @@ def test_results_identical_alone_and_in_mix(lib):
     ctx3.close()
 
 
-def test_served_fp32_error_against_fp64_oracle(lib):
+def test_served_error_against_fp64_oracle(lib):
+    """The served mix (CSR queries in FP32 storage, heat queries in FP64)
+    against the FP64 oracle: within 1e-6 (FP32 storage) and 1e-9 (FP64).
+    The heat queries forced to FP32 storage stay under the floor documented
+    for the Lanczos recurrence with float vectors (3e-6; 1.0e-6 measured on
+    q1 here), which is why the mix serves them in FP64."""
     qs = small_mix(8, seed=11)
     ctx = kv.Context(8 << 30)
     s = kv.Server(ctx, slots=4)
     res = wait_all(s, [s.submit(q) for q in qs])
     s.close()
-    ctx.close()
+    n_heat = 0
     for q, r in zip(qs, res):
         q64 = W.Problem(**{**q.__dict__, "precision": "fp64"})
         ref = oracle.run(q64)
-        assert bound_error(r, ref) <= 1e-6, q.name
+        assert bound_error(r, ref) <= (1e-9 if q.precision == "fp64" else 1e-6), q.name
         assert r["latency_ms"] > 0
+        if "heat" in q.name:
+            n_heat += 1
+            r32 = kv.solve(W.Problem(**{**q.__dict__, "precision": "fp32"}), ctx)
+            assert bound_error(r32, ref) <= 3e-6, q.name
+    ctx.close()
+    assert n_heat > 0
 
 
 def test_admission_waits_for_memory(lib):

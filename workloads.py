@@ -516,13 +516,13 @@ def column_dense(col: Column, n: int, dims: Optional[Sequence[int]] = None) -> n
 # --------------------------------------------------------------------------
 def serving_mix(n_queries: int = 512, seed: int = 0, *, side2d=(100, 2000), side3d=(100, 400),
                 csr_n=(100_000, 2_000_000), csr_sizes: int = 5, gens=(1, 32), steps=(100, 2000), m=(20, 60),
-                precision: str = "fp32", simulate: str = "auto") -> List[Problem]:
+                precision: str = "fp32", heat_precision: str = "fp64", simulate: str = "auto") -> List[Problem]:
     """A seeded mix of verification queries, one third each:
       * 2D heat, side log-uniform in side2d (n = side^2), block side/4, dt 0.1;
       * 3D heat, side log-uniform in side3d, block side/10, dt 0.02;
       (heat outputs: the cell just past the block's far corner, so that every
-      query's projected output is nonzero; the grid centre is out of the
-      Krylov space's reach at these m);
+      query's projected output is nonzero, the grid centre being out of the
+      Krylov space's reach at these m; storage `heat_precision`);
       * random CSR systems of random_csr (sizes log-spaced in csr_n, `csr_sizes`
         distinct systems shared by the queries), `gens` unit generators plus the
         fixed column, two +-1 output rows, dt 0.01;
@@ -541,12 +541,12 @@ def serving_mix(n_queries: int = 512, seed: int = 0, *, side2d=(100, 2000), side
             side = int(round(math.exp(rng.uniform(math.log(side2d[0]), math.log(side2d[1])))))
             b = max(side // 4, 1)
             out.append(heat((side, side), block=(b, b), output="edge", dt=0.1, steps=st, m=mm,
-                            precision=precision, name=f"q{q}-heat2d-{side}"))
+                            precision=heat_precision, name=f"q{q}-heat2d-{side}"))
         elif kind == 1:
             side = int(round(math.exp(rng.uniform(math.log(side3d[0]), math.log(side3d[1])))))
             b = max(side // 10, 1)
             out.append(heat((side, side, side), block=(b, b, b), output="edge", dt=0.02, steps=st, m=mm,
-                            precision=precision, name=f"q{q}-heat3d-{side}"))
+                            precision=heat_precision, name=f"q{q}-heat3d-{side}"))
         else:
             n = sizes[int(rng.integers(len(sizes)))]
             if n not in cache:
