@@ -585,7 +585,8 @@ def error_control_bench(dev: int):
             r = ph.run(full=True)
             ms = (time.perf_counter() - t0) * 1e3
             chk = sum(ctx.profile_read(nm)[1] for nm in ("error_expm", "error_bound"))
-            kry = sum(ctx.profile_read(nm)[1] for nm in ("lanczos_fused", "stencil_alpha", "stencil_update"))
+            kry = sum(ctx.profile_read(nm)[1] for nm in ("lanczos_fused", "lanczos_fused64", "stencil_alpha",
+                                                         "stencil_update"))
             ctx.profile_enable(False)
             out[label] = {"m_used": int(r["m_used"][0]), "lemma1_bound": float(r["err_bound"][0]),
                           "ms_per_query": ms, "checkpoint_ms": chk, "krylov_ms": kry}

@@ -606,6 +606,24 @@ static Fused64Grid fused64_grid(const Sys* s, int sms) {
             best_zc = zc;
         }
     }
+    // Within one wave the FP64 pipe of an SM is shared by its CTAs, so two
+    // short chunks on one SM take as long as one chunk of twice the planes,
+    // plus a second halo; count the CTAs per SM instead (a lone CTA keeps the
+    // pipe less busy: taken as 0.8 of a pair's rate).
+    if ((nz + best_zc - 1) / best_zc * tiles <= slots) {
+        const int64_t sm = slots / 2;
+        double best = 1e300;
+        for (int64_t zc = std::min<int64_t>(2, nz); zc <= nz; ++zc) {
+            const int64_t nch = (nz + zc - 1) / zc;
+            if (zc > 2 && (nz + zc - 2) / (zc - 1) == nch) continue;
+            const int64_t per = (nch * tiles + sm - 1) / sm;
+            const double cost = (double)(per * (zc + 3)) / (per == 1 ? 0.8 : 1.0);
+            if (cost < best) {
+                best = cost;
+                best_zc = zc;
+            }
+        }
+    }
     f.zc = (int)best_zc;
     f.nzch = (int)((nz + best_zc - 1) / best_zc);
     f.blocks = tiles * f.nzch;
