@@ -1,0 +1,118 @@
+// splits.cuh -- exact three-float splits of doubles and the compensated
+// float-pair arithmetic built on them, for sums of squares and products of
+// FP64 values formed on the FP32 pipe (on this GPU the FP64 pipe retires
+// about 1/64 of the FP32 rate, so an FP64 kernel that needs a dot product per
+// element spends fewer FP64 cycles this way: each term keeps about 47
+// significant bits and the sums are compensated, as accurate as FP64
+// accumulation).
+#pragma once
+
+#include <stdint.h>
+
+namespace kv {
+
+// x 2^-sh = a1 + a2 + a3 exactly, from the bits of x: a1 carries the sign, the
+// exponent and the leading 24 significant bits (mantissa bits 51..29), a2
+// bits 28..6 and a3 bits 5..0, each an integer below 2^23 converted exactly
+// (2^23 + m has m as its low mantissa bits) and scaled by powers of two.  sh is chosen
+// by the host so that every |x| 2^-sh stays below 2^8; values whose scaled
+// magnitude is below 2^-100 give zero: their squares lie more than 2^-180
+// below the sums they enter, which are at least 2^-80 of the largest term
+// wherever the iteration has not broken down.
+struct F3 {
+    float a1, a2, a3;
+};
+
+__device__ __forceinline__ float small_uint_to_float(unsigned m) {  // exact for m < 2^23
+    return __fsub_rn(__uint_as_float(0x4B000000u | m), 8388608.0f);
+}
+
+__device__ __forceinline__ F3 split3(double x, int sh) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - sh;  // biased exponent of x 2^-sh
+    F3 r;
+    if (e < 1023 - 100) {
+        r.a1 = r.a2 = r.a3 = 0.f;
+        return r;
+    }
+    // 2^(e-1023) with the sign of x, as float bits (e - 1023 >= -100 > -127)
+    const unsigned pbits = (hi & 0x80000000u) | ((unsigned)(e - 1023 + 127) << 23);
+    const float P = __uint_as_float(pbits);
+    // a1: the sign, the exponent and mantissa bits 51..29 (20 from hi, 3 from lo)
+    r.a1 = __uint_as_float(pbits | (__funnelshift_l(lo, hi, 3) & 0x7fffffu));
+    r.a2 = __fmul_rn(__fmul_rn(small_uint_to_float((lo >> 6) & 0x7fffffu), 0x1p-46f), P);
+    r.a3 = __fmul_rn(__fmul_rn(small_uint_to_float(lo & 63u), 0x1p-52f), P);
+    return r;
+}
+
+// split3 for values whose bound the caller cannot vouch for: *bad is set
+// when |x| 2^-sh reaches 2^8 (or x is not finite), where split3 would give
+// garbage; the caller then reports the sum as not finite
+__device__ __forceinline__ F3 split3_checked(double x, int sh, bool* bad) {
+    const int e = (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu) - sh;
+    if (e >= 1023 + 8) {
+        *bad = true;
+        return F3{0.f, 0.f, 0.f};
+    }
+    return split3(x, sh);
+}
+
+// a + b = s + e exactly (TwoSum, Knuth: six float operations, any magnitudes)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Compensated float-pair accumulator of terms t = th + tl (hi + lo, the
+// rounding errors of the additions kept in lo).
+struct Acc2 {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float th, float tl) {
+        float s, e;
+        two_sum(hi, th, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, tl));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// square of x = a1 + a2 + a3 as a float pair: a1^2 exactly (TwoProduct), the
+// cross terms 2 a1 (a2 + a3) and a2^2 in the low part (their rounding is
+// 2^-48 of x^2)
+__device__ __forceinline__ void sq3(const F3& x, float& th, float& tl) {
+    th = __fmul_rn(x.a1, x.a1);
+    const float e = __fmaf_rn(x.a1, x.a1, -th);
+    const float a23 = __fadd_rn(x.a2, x.a3);
+    tl = __fmaf_rn(__fadd_rn(x.a1, x.a1), a23, __fmaf_rn(x.a2, x.a2, e));
+}
+
+// (p - q)^2 as a float pair, p and q exact splits: the difference first as an
+// unevaluated pair dh + dl accurate to about 2^-47 of |p - q| (the leading
+// parts' difference and its error by TwoSum, the second parts' likewise),
+// then squared as in sq3
+__device__ __forceinline__ void sqdiff3(const F3& p, const F3& q, float& th, float& tl) {
+    float s1, e1, s2, e2, u, f, dh, g;
+    two_sum(p.a1, -q.a1, s1, e1);
+    two_sum(p.a2, -q.a2, s2, e2);
+    const float t3 = __fsub_rn(p.a3, q.a3);
+    two_sum(s2, e1, u, f);
+    two_sum(s1, u, dh, g);
+    const float dl = __fadd_rn(g, __fadd_rn(__fadd_rn(f, e2), t3));
+    th = __fmul_rn(dh, dh);
+    const float e = __fmaf_rn(dh, dh, -th);
+    tl = __fmaf_rn(__fadd_rn(dh, dh), dl, e);
+}
+
+// x y as a float pair (th + tl) from the exact splits of x and y: the
+// leading product exactly (TwoProduct), the cross terms of the first two
+// parts and the products with the third parts in the low word; the terms
+// left out are below 2^-70 of |x y|
+__device__ __forceinline__ void prod3(const F3& x, const F3& y, float& th, float& tl) {
+    th = __fmul_rn(x.a1, y.a1);
+    const float e = __fmaf_rn(x.a1, y.a1, -th);
+    const float c = __fmaf_rn(x.a1, __fadd_rn(y.a2, y.a3), __fmul_rn(__fadd_rn(x.a2, x.a3), y.a1));
+    tl = __fadd_rn(__fmaf_rn(x.a2, y.a2, e), c);
+}
+
+}  // namespace kv

@@ -17,6 +17,7 @@ import sys
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -59,6 +60,35 @@ def test_overflowing_operator_is_reported(ctx, precision):
     q = W.heat2d_20(steps=10)
     got = kv.solve(q, ctx)
     assert got["m_used"][0] == q.m
+
+
+def test_overflowing_csr_lanczos_is_reported(ctx):
+    """Symmetric CSR, FP64, every entry 1e308: A v overflows.  The FP64
+    Lanczos sums are formed from exact float splits scaled by the operator's
+    largest absolute row sum; here that sum overflows too, so the sums fall
+    back to FP64 accumulation, and the non-finite alpha is reported.  (With a
+    finite row sum, |A v| and |w| stay within it, which is what the split
+    scale relies on.)  The context stays usable."""
+    n = 4
+    rp = np.arange(0, n * n + 1, n, dtype=np.int64)
+    cols = np.tile(np.arange(n, dtype=np.int32), n)
+    sysm = W.CsrSystem(n=n, row_ptr=rp, col=cols, val=np.full(n * n, 1e308), symmetric=True)
+    col = W.Column(kind="sparse", zlo=0.9, zhi=1.1, idx=np.arange(n), val=np.ones(n))
+    crp, cc, cv = W._c_rows([([0], [1.0])])
+    p = W.Problem(system=sysm, columns=[col], C_row_ptr=crp, C_col=cc, C_val=cv, theta=np.array([np.inf]),
+                  dt=0.1, steps=5, m=3, precision="fp64")
+    sysh = kv.System(ctx, p.system, "fp64")
+    ph = kv.ProblemHandle(ctx, sysh, p)
+    try:
+        with pytest.raises(kv.KvError) as ei:
+            ph.run()
+        assert ei.value.code == kv.KV_EINVAL and "not finite" in str(ei.value)
+    finally:
+        ph.close()
+        sysh.close()
+    base = W.paper_heat(6, dt=0.1, steps=5, m=6)
+    from parity import bound_error
+    assert bound_error(kv.solve(base, ctx), oracle.run(base)) <= 1e-9
 
 
 _CHILD = r"""
