@@ -33,7 +33,6 @@
 
 #include "kv_internal.h"
 #include "reduce.cuh"
-#include "splits.cuh"
 
 namespace kv {
 
@@ -72,7 +71,6 @@ __device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
     }
 }
 constexpr int CCHUNK_MIN = CNT * 8;  // smallest rows per block (sizes the partials)
-constexpr int SPLIT_OFF = 1 << 20;   // split scale meaning: keep FP64 sums
 
 struct ArnoldiDev {  // per-column device scratch of the Arnoldi passes
     double g[KV_MAX_M + 1][KV_MAX_M + 1];  // Gram matrix of the stored basis (normalised)
@@ -87,16 +85,12 @@ struct VecArgs {
 
 // ------------------------------------------------------------------ SpMV --
 constexpr int SPMV_STAGE = 256;  // matrix entries per warp staged in shared memory
-// blocks per SM the launch bounds guarantee (the FP64 alpha form holds its
-// float splits in 48 registers)
 template <typename T, bool ALPHA>
-constexpr int spmv_bps() { return std::is_same<T, double>::value && ALPHA ? 5 : 6; }
-template <typename T, bool ALPHA>
-__global__ void __launch_bounds__(CNT, spmv_bps<T, ALPHA>()) k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(CNT, 6) k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                               const T* __restrict__ val, const double* __restrict__ b,
                                               VecArgs<T> V, int xslot, int wslot, int64_t n, int64_t N,
                                               const int* aug, ColState* st, double* H, int m, int j,
-                                              double* partials, unsigned* counters, int64_t nbx, int shA) {
+                                              double* partials, unsigned* counters, int64_t nbx) {
     dep_wait();  // every input comes from the kernel before
     dep_release();
     const int cidx = blockIdx.y;
@@ -106,14 +100,6 @@ __global__ void __launch_bounds__(CNT, spmv_bps<T, ALPHA>()) k_spmv(const int64_
     T* Wv = V.base + cidx * V.cstride + (int64_t)wslot * N;
     const double sj = s->s[j];
     const bool ag = aug[cidx] != 0;
-    // FP64 form: alpha_j = s_j sum_r X[r] y[r] from exact float splits of
-    // X[r] (|X[r]| <= ||X|| = 1/s_j < 2^shx) and y[r] = s_j (A X)[r]
-    // (|y| <= ||A||_inf < 2^shA), off the FP64 pipe (splits.cuh); shA =
-    // SPLIT_OFF (an operator whose row sums overflow) keeps FP64 sums
-    const bool SPLIT = std::is_same<T, double>::value && shA != SPLIT_OFF;
-    const int shx = 1023 - (int)(((unsigned)__double2hiint(sj) >> 20) & 0x7ffu);
-    Acc2 acc_split;
-    bool bad = false;
     // one lane per row; the entries of the warp's 32 rows are contiguous in
     // the CSR arrays, so the warp stages them in shared memory with coalesced
     // loads (SPMV_STAGE at a time) and each lane walks its own row there, in
@@ -163,19 +149,9 @@ __global__ void __launch_bounds__(CNT, spmv_bps<T, ALPHA>()) k_spmv(const int64_
         }
         const T yt = (T)y;
         Wv[r] = yt;
-        if (ALPHA) {
-            if (SPLIT) {
-                float th, tl;
-                prod3(split3_checked((double)X[r], shx, &bad), split3_checked((double)yt, shA, &bad), th, tl);
-                acc_split.add(th, tl);
-            } else {
-                acc_alpha = fma(sj * (double)X[r], (double)yt, acc_alpha);
-            }
-        }
+        if (ALPHA) acc_alpha = fma(sj * (double)X[r], (double)yt, acc_alpha);
     }
     if (!ALPHA) return;
-    if (SPLIT)  // back to the scale of alpha: s_j 2^(shx + shA); NaN flags a value past its bound
-        acc_alpha = bad ? nan("") : sj * ldexp(acc_split.value(), shx + shA);
     __shared__ double sh[CNT / 32];
     __shared__ int flag;
     const double part = block_sum<CNT>(acc_alpha, sh);
@@ -448,7 +424,7 @@ template <typename T, bool FIRST>
 __global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int wslot, int vslot, int pslot, int64_t N,
                                                          ColState* st, double* Hall, double* Pall, CDesc cd, int cinl,
                                                          int m, int j, double* partials, unsigned* counters,
-                                                         int64_t nbx, int shA) {
+                                                         int64_t nbx) {
     dep_wait();  // every input comes from the kernel before
     dep_release();
     const int cidx = blockIdx.y;
@@ -463,22 +439,6 @@ __global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int ws
     const double hb = FIRST ? 0.0 : H[(int64_t)j * m + (j - 1)];  // beta_j = H[j-1][j]
     const double cb = -hb * (FIRST ? 0.0 : s->s[j - 1]);
     typename AccOf<T>::type acc;
-    // FP64 form: ||w||^2 from exact float splits of w (|w| <= ||A v_j|| <=
-    // ||A||_inf < 2^shA), off the FP64 pipe (splits.cuh); values below
-    // 2^(shA-100) drop out of the sum, which matters only where ||w|| is
-    // below 2^-58 ||A||_inf, under the rounding noise of FP64 arithmetic on A
-    const bool SPLIT = std::is_same<T, double>::value && shA != SPLIT_OFF;
-    Acc2 acc_split;
-    bool bad = false;
-    auto add_sq = [&](T wt) {
-        if (SPLIT) {
-            float th, tl;
-            sq3(split3_checked((double)wt, shA, &bad), th, tl);
-            acc_split.add(th, tl);
-        } else {
-            acc.add_prod(wt, wt);
-        }
-    };
     // four rows per thread per round, all their loads issued before the
     // arithmetic (the three vectors are distinct buffers)
     const int64_t stride = (int64_t)gridDim.x * CNT;
@@ -497,7 +457,7 @@ __global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int ws
             if (!FIRST) w = fma(cb, (double)vp[k], w);
             const T wt = (T)w;
             Wv[r + k * stride] = wt;
-            add_sq(wt);
+            acc.add_prod(wt, wt);
         }
     }
     for (; r < N; r += stride) {
@@ -505,14 +465,12 @@ __global__ void __launch_bounds__(CNT, 4) k_lanczos3_update(VecArgs<T> V, int ws
         if (!FIRST) w = fma(cb, (double)Vp[r], w);
         const T wt = (T)w;
         Wv[r] = wt;
-        add_sq(wt);
+        acc.add_prod(wt, wt);
     }
     __shared__ double sh[CNT / 32];
     __shared__ int flag;
     __shared__ double cw[CINL_ROWS];
-    // NaN flags a value past its bound (or not finite): the norm is then reported as not finite
-    const double mine = SPLIT ? (bad ? nan("") : ldexp(acc_split.value(), 2 * shA)) : acc.value();
-    const double part = block_sum<CNT>(mine, sh);  // its barriers also publish the block's W
+    const double part = block_sum<CNT>(acc.value(), sh);  // its barriers also publish the block's W
     // column region: ||w||^2 partials, then (cinl) one row of partials per row of C
     double* preg = partials + (int64_t)cidx * nbx * (cinl ? 1 + CINL_ROWS : 1);
     if (cinl) {
@@ -797,11 +755,11 @@ static int64_t spmv_blocks(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
     return b > 152 * 8 ? 152 * 8 : b;
 }
-// k_spmv: one wave at the blocks per SM its launch bounds guarantee; at most
-// spmv_blocks
-static int64_t spmv_grid(int64_t N, int bps) {
+// k_spmv: one wave at the 6 blocks per SM its launch bounds guarantee (40
+// registers a thread); at most spmv_blocks
+static int64_t spmv_grid(int64_t N) {
     int64_t b = (N + CNT - 1) / CNT;
-    return b > 152 * bps ? 152 * bps : b;
+    return b > 152 * 6 ? 152 * 6 : b;
 }
 // k_lanczos3_update: one wave at its 4 blocks per SM (four rows a thread in
 // flight need the registers)
@@ -1099,12 +1057,7 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
     double* partials = p->red.partials;
     unsigned* counters = p->d_counters;
     dim3 gs((unsigned)spmv_blocks(N), (unsigned)ncols), gr((unsigned)row_blocks_t<T>(N), (unsigned)ncols);
-    const dim3 gv((unsigned)spmv_grid(N, lanczos ? spmv_bps<T, true>() : spmv_bps<T, false>()), (unsigned)ncols);
-    const dim3 gu((unsigned)update_grid(N), (unsigned)ncols);
-    // the split scale of the FP64 Lanczos sums: ||A||_inf < 2^shA
-    int shA = 0;
-    if (!std::isfinite(s->row_abs_max)) shA = SPLIT_OFF;
-    else if (s->row_abs_max > 0.0) frexp(s->row_abs_max, &shA);
+    const dim3 gv((unsigned)spmv_grid(N), (unsigned)ncols), gu((unsigned)update_grid(N), (unsigned)ncols);
     // C w inside the update's reduction: few rows and entries, and room for
     // 1 + CINL_ROWS rows of partials in a column's 2 (m + 1) (csr_scratch_slots)
     const int cinl = p->o >= 1 && p->o <= CINL_ROWS && p->c_nnz <= CNT && 1 + CINL_ROWS <= 2 * (m + 1) ? 1 : 0;
@@ -1120,14 +1073,14 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
                 LaunchScope ls(p->ctx, "csr_spmv");
                 KV_CHECK_CUDA(launch_dep(dep_launch_ok(p->ctx), k_spmv<T, true>, gv, dim3(CNT), 0, st, s->d_rp,
                                          s->d_col, (const T*)s->d_val, s->d_b, va, vs, ws, n, N, aug, stp, H, m, it,
-                                         partials, counters, nbx, shA));
+                                         partials, counters, nbx));
             }
             {
                 LaunchScope ls(p->ctx, "csr_lanczos_update");
                 KV_CHECK_CUDA(launch_dep(dep_launch_ok(p->ctx), it == 0 ? k_lanczos3_update<T, true>
                                                                         : k_lanczos3_update<T, false>,
                                          gu, dim3(CNT), 0, st, va, ws, vs, ps, N, stp, H, P, cd, cinl, m, it,
-                                         partials, counters, nbx, shA));
+                                         partials, counters, nbx));
             }
             const int rc = launch_project(p, j0, ncols, (T*)V + (int64_t)ws * N, va.cstride, it + 1);
             if (rc) return rc;
@@ -1143,7 +1096,7 @@ static int run_csr_column_t(Prob* p, int j0, int ncols, void* V, ArnoldiDev* ad,
             } else {
                 LaunchScope ls(p->ctx, "csr_spmv");
                 k_spmv<T, false><<<gv, CNT, 0, st>>>(s->d_rp, s->d_col, (const T*)s->d_val, s->d_b, va, it, it + 1, n,
-                                                    N, aug, stp, H, m, it, partials, counters, nbx, 0);
+                                                    N, aug, stp, H, m, it, partials, counters, nbx);
                 KV_CHECK_CUDA(cudaGetLastError());
             }
             if (p->d_brow) {  // A'^T of the transpose dynamics: its last row b . x

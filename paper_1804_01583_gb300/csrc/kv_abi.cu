@@ -422,7 +422,7 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
         delete s;
         return fail(KV_ECUDA, "kv_system_csr: upload failed: %s", cudaGetErrorString(e));
     }
-    rc = csr_lognorm_bounds(s, b, &s->mu, &s->mu_aug, &s->row_abs_max);
+    rc = csr_lognorm_bounds(s, b, &s->mu, &s->mu_aug);
     if (rc) {
         c->arena.free(s->d_rp);
         c->arena.free(s->d_col);

@@ -162,9 +162,6 @@ struct Sys {
     // upper bounds of the largest eigenvalue of (A + A^T)/2, for A and for
     // A' = [[A, b], [0, 0]] (Lemma 1 of Sec. 4.2 takes e^{max(mu,0) T})
     double mu = 0.0, mu_aug = 0.0;
-    // max_i sum_j |a'_ij| (CSR, rounded up): for symmetric A a bound of
-    // ||A v|| over unit v, the scale of the FP64 Lanczos sums' float splits
-    double row_abs_max = 0.0;
     // A^T in CSR form (non-symmetric CSR only), built on first use by a
     // problem that runs the transpose dynamics (Sec. 4.1)
     int64_t* d_rpT = nullptr;
@@ -326,7 +323,7 @@ inline bool is_checkpoint(const Prob* p, int k) {
 }
 int launch_error_final(Prob* p);
 // Gershgorin bound of the symmetric part of a CSR matrix (k_lognorm.cu)
-int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug, double* row_abs_max);
+int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug);
 
 // transpose dynamics (k_csr_transpose.cu)
 int csr_build_transpose(Sys* s);

@@ -1,10 +1,8 @@
 // splits.cuh -- exact three-float splits of doubles and the compensated
-// float-pair arithmetic built on them, for sums of squares and products of
-// FP64 values formed on the FP32 pipe (on this GPU the FP64 pipe retires
-// about 1/64 of the FP32 rate, so an FP64 kernel that needs a dot product per
-// element spends fewer FP64 cycles this way: each term keeps about 47
-// significant bits and the sums are compensated, as accurate as FP64
-// accumulation).
+// float-pair arithmetic built on them, for the sums of squares of the FP64
+// grid iteration formed on the FP32 pipe (on this GPU the FP64 pipe retires
+// about 1/64 of the FP32 rate; each term keeps about 47 significant bits and
+// the sums are compensated, as accurate as FP64 accumulation).
 #pragma once
 
 #include <stdint.h>
@@ -43,18 +41,6 @@ __device__ __forceinline__ F3 split3(double x, int sh) {
     r.a2 = __fmul_rn(__fmul_rn(small_uint_to_float((lo >> 6) & 0x7fffffu), 0x1p-46f), P);
     r.a3 = __fmul_rn(__fmul_rn(small_uint_to_float(lo & 63u), 0x1p-52f), P);
     return r;
-}
-
-// split3 for values whose bound the caller cannot vouch for: *bad is set
-// when |x| 2^-sh reaches 2^8 (or x is not finite), where split3 would give
-// garbage; the caller then reports the sum as not finite
-__device__ __forceinline__ F3 split3_checked(double x, int sh, bool* bad) {
-    const int e = (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu) - sh;
-    if (e >= 1023 + 8) {
-        *bad = true;
-        return F3{0.f, 0.f, 0.f};
-    }
-    return split3(x, sh);
 }
 
 // a + b = s + e exactly (TwoSum, Knuth: six float operations, any magnitudes)
@@ -102,17 +88,6 @@ __device__ __forceinline__ void sqdiff3(const F3& p, const F3& q, float& th, flo
     th = __fmul_rn(dh, dh);
     const float e = __fmaf_rn(dh, dh, -th);
     tl = __fmaf_rn(__fadd_rn(dh, dh), dl, e);
-}
-
-// x y as a float pair (th + tl) from the exact splits of x and y: the
-// leading product exactly (TwoProduct), the cross terms of the first two
-// parts and the products with the third parts in the low word; the terms
-// left out are below 2^-70 of |x y|
-__device__ __forceinline__ void prod3(const F3& x, const F3& y, float& th, float& tl) {
-    th = __fmul_rn(x.a1, y.a1);
-    const float e = __fmaf_rn(x.a1, y.a1, -th);
-    const float c = __fmaf_rn(x.a1, __fadd_rn(y.a2, y.a3), __fmul_rn(__fadd_rn(x.a2, x.a3), y.a1));
-    tl = __fadd_rn(__fmaf_rn(x.a2, y.a2, e), c);
 }
 
 }  // namespace kv

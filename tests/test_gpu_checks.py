@@ -63,12 +63,9 @@ def test_overflowing_operator_is_reported(ctx, precision):
 
 
 def test_overflowing_csr_lanczos_is_reported(ctx):
-    """Symmetric CSR, FP64, every entry 1e308: A v overflows.  The FP64
-    Lanczos sums are formed from exact float splits scaled by the operator's
-    largest absolute row sum; here that sum overflows too, so the sums fall
-    back to FP64 accumulation, and the non-finite alpha is reported.  (With a
-    finite row sum, |A v| and |w| stay within it, which is what the split
-    scale relies on.)  The context stays usable."""
+    """Symmetric CSR, FP64, every entry 1e308: A v overflows in the CSR
+    Lanczos pair, and the non-finite alpha and beta are reported instead of
+    passing as a breakdown.  The context stays usable."""
     n = 4
     rp = np.arange(0, n * n + 1, n, dtype=np.int64)
     cols = np.tile(np.arange(n, dtype=np.int32), n)
