@@ -251,6 +251,9 @@ def time_query(ctx, ph, stream, steps: int, warmup: int, torch, barrier=None, cl
     return ms_total, kern, launches, clk
 
 
+FP64_NOMINAL_TIPS = 0.625  # nominal FP64 rate of the part, T instructions/s (1.25 TFLOP/s dense)
+
+
 def roofline(dom: str, kern: dict, p, fp64_peak: float) -> dict:
     """Roofline of the dominant kernel: algorithmic work per launch over its
     average launch time (library events), against the measured peak."""
@@ -266,6 +269,9 @@ def roofline(dom: str, kern: dict, p, fp64_peak: float) -> dict:
                 "frac": ach / pk,
                 "peak_kind": "measured in this run: kv_diag_fp64_rate (FP64 FMA chains on every SM, best of 5, "
                              "CUDA events)",
+                "peak_nominal": FP64_NOMINAL_TIPS, "frac_nominal": ach / FP64_NOMINAL_TIPS,
+                "peak_nominal_kind": "1.25 TFLOP/s dense FP64 (the part's nominal figure) = 0.625 T FP64 "
+                                     "instructions/s (one FMA, add or multiply each)",
                 "algorithmic_fp64_instr_per_launch": instr, "avg_launch_ms": avg_s * 1e3,
                 "algorithmic_bytes_per_launch": bpi, "hbm_achieved_gbs": bpi / avg_s / 1e9,
                 "hbm_frac": bpi / avg_s / 1e9 / hbm_peak, "traffic": profiled_traffic(dom, p)}
