@@ -104,19 +104,21 @@ __device__ __forceinline__ double lin_at(const Lin4& l, int z, int r, int c) {
     return v;
 }
 
+template <int TL>
 __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
+    constexpr int O = TL / 16;  // outputs per thread along each axis (16 x 16 threads)
     const int z = blockIdx.z;
     const int k = kdim(g.kd, z);
     if (k < 0) return;
     const int M = g.M < 0 ? k : g.M, N = g.N < 0 ? k : g.N, K = g.K < 0 ? k : g.K;
-    const int r0 = blockIdx.y * GT, c0 = blockIdx.x * GT;
+    const int r0 = blockIdx.y * TL, c0 = blockIdx.x * TL;
     if (r0 >= M || c0 >= N) return;
     const double* A = g.A + z * g.sA;
     const double* B = g.B + z * g.sB;
     double* C = g.C + z * g.sC;
     if (k == 0) {  // zero run: zero outputs (basis rows)
-        for (int e = threadIdx.x; e < GT * GT; e += GNT) {
-            const int r = r0 + e / GT, c = c0 + e % GT;
+        for (int e = threadIdx.x; e < TL * TL; e += GNT) {
+            const int r = r0 + e / TL, c = c0 + e % TL;
             if (r < M && c < N) C[(int64_t)r * g.ldc + c] = 0.0;
         }
         return;
@@ -128,23 +130,27 @@ __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
             // last one wrote, and only the last launch moves it to the buffer the
             // host reads next (SQ_LAUNCHES is even: needed when s is odd)
             if (g.q == SQ_LAUNCHES - 1 && ((g.q - s) & 1) == 0) {
-                for (int e = threadIdx.x; e < GT * GT; e += GNT) {
-                    const int r = r0 + e / GT, c = c0 + e % GT;
+                for (int e = threadIdx.x; e < TL * TL; e += GNT) {
+                    const int r = r0 + e / TL, c = c0 + e % TL;
                     if (r < M && c < N) C[(int64_t)r * g.ldc + c] = A[(int64_t)r * g.lda + c];
                 }
             }
             return;
         }
     }
-    __shared__ double As[GT][GT + 1], Bs[GT][GT + 1];
+    __shared__ double As[TL][TL + 1], Bs[TL][TL + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
+    double acc[O][O];
+#pragma unroll
+    for (int i = 0; i < O; ++i)
+#pragma unroll
+        for (int jj = 0; jj < O; ++jj) acc[i][jj] = 0.0;
     // the inner indices l where both A(r0.., l) and B(l, c0..) may be nonzero
     const int l_lo = max(0, max(r0 - g.ba.lo, c0 - g.bb.up));
-    const int l_hi = min(K - 1, min(r0 + GT - 1 + g.ba.up, c0 + GT - 1 + g.bb.lo));
-    for (int kk = (l_lo / GT) * GT; kk <= l_hi; kk += GT) {
-        for (int e = threadIdx.x; e < GT * GT; e += GNT) {
-            const int a = e / GT, b = e % GT;
+    const int l_hi = min(K - 1, min(r0 + TL - 1 + g.ba.up, c0 + TL - 1 + g.bb.lo));
+    for (int kk = (l_lo / TL) * TL; kk <= l_hi; kk += TL) {
+        for (int e = threadIdx.x; e < TL * TL; e += GNT) {
+            const int a = e / TL, b = e % TL;
             const int ar = r0 + a, ac = kk + b;
             As[a][b] = (ar < M && ac < K) ? A[(int64_t)ar * g.lda + ac] : 0.0;
             const int br = kk + a, bc = c0 + b;
@@ -152,25 +158,28 @@ __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
         }
         __syncthreads();
 #pragma unroll 8
-        for (int l = 0; l < GT; ++l) {
-            const double a0 = As[2 * ty][l], a1 = As[2 * ty + 1][l];
-            const double b0 = Bs[l][2 * tx], b1 = Bs[l][2 * tx + 1];
-            acc00 = fma(a0, b0, acc00);
-            acc01 = fma(a0, b1, acc01);
-            acc10 = fma(a1, b0, acc10);
-            acc11 = fma(a1, b1, acc11);
+        for (int l = 0; l < TL; ++l) {
+            double av[O], bv[O];
+#pragma unroll
+            for (int i = 0; i < O; ++i) {
+                av[i] = As[O * ty + i][l];
+                bv[i] = Bs[l][O * tx + i];
+            }
+#pragma unroll
+            for (int i = 0; i < O; ++i)
+#pragma unroll
+                for (int jj = 0; jj < O; ++jj) acc[i][jj] = fma(av[i], bv[jj], acc[i][jj]);
         }
         __syncthreads();
     }
-    const double accs[2][2] = {{acc00, acc01}, {acc10, acc11}};
     const double beta0 = g.epi == 2 ? (g.kd.st + z)->beta0 : 1.0;
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < O; ++i)
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int r = r0 + 2 * ty + i, c = c0 + 2 * tx + jj;
+        for (int jj = 0; jj < O; ++jj) {
+            const int r = r0 + O * ty + i, c = c0 + O * tx + jj;
             if (r >= M || c >= N) continue;
-            double v = accs[i][jj];
+            double v = acc[i][jj];
             if (g.epi == 1) v += lin_at(g.lin, z, r, c);
             if (g.epi == 2) v *= beta0;
             C[(int64_t)r * g.ldc + c] = v;
@@ -327,6 +336,14 @@ __global__ void __launch_bounds__(GNT) k_dgemm_thin(GemmArgs g) {
     }
 }
 
+// The FP64 pipe of an SM is shared by its resident CTAs, so a product takes
+// about (CTAs on the busiest SM) x (work of one CTA): ceil(tiles / SMs) x
+// tile^2 (times K, the same for both tile sizes).
+static int64_t waves_x_work(int M, int N, int nb, int tl) {
+    const int64_t tiles = (int64_t)((N + tl - 1) / tl) * ((M + tl - 1) / tl) * nb;
+    return (tiles + 151) / 152 * tl * tl;
+}
+
 static int gemm(Prob* p, int nb, const double* A, int lda, int64_t sA, const double* B, int ldb, int64_t sB, double* C,
                 int ldc, int64_t sC, int M, int N, int K, KDim kd, int epi = 0, Lin4 lin = Lin4{},
                 const double* gate = nullptr, int64_t sG = 0, int q = 0, Band ba = dense_band(),
@@ -340,9 +357,14 @@ static int gemm(Prob* p, int nb, const double* A, int lda, int64_t sA, const dou
         int64_t gx = ((int64_t)Mx * Nx + GNT - 1) / GNT;
         if (gx > 152 * 4) gx = 152 * 4;
         k_dgemm_thin<<<dim3((unsigned)gx, (unsigned)nb), GNT, 0, p->ctx->stream>>>(g);
+    } else if (waves_x_work(Mx, Nx, nb, 16) < waves_x_work(Mx, Nx, nb, GT)) {
+        // 16 x 16 tiles where they spread the FP64 work more evenly over the
+        // SMs (each output is summed over K in the same order: the same result)
+        dim3 grd((unsigned)((Nx + 15) / 16), (unsigned)((Mx + 15) / 16), (unsigned)nb);
+        k_dgemm<16><<<grd, GNT, 0, p->ctx->stream>>>(g);
     } else {
         dim3 grd((unsigned)((Nx + GT - 1) / GT), (unsigned)((Mx + GT - 1) / GT), (unsigned)nb);
-        k_dgemm<<<grd, GNT, 0, p->ctx->stream>>>(g);
+        k_dgemm<GT><<<grd, GNT, 0, p->ctx->stream>>>(g);
     }
     KV_CHECK_CUDA(cudaGetLastError());
     return KV_OK;

@@ -178,14 +178,16 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
         for (int h = 0; h < 2; ++h)
 #pragma unroll
             for (int k = 0; k < 2; ++k) an[h][k] = make_double2(0.0, 0.0);
-        if (FIRST || p < 0 || p >= nz) return;
+        if constexpr (!FIRST) {  // the first iteration has no v_{j-1}
+            if (p < 0 || p >= nz) return;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (!yin[h]) continue;
-            const double* row = a.Aprev + (int64_t)p * plane + (int64_t)yr[h] * nx;
+            for (int h = 0; h < 2; ++h) {
+                if (!yin[h]) continue;
+                const double* row = a.Aprev + (int64_t)p * plane + (int64_t)yr[h] * nx;
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
-                if (xin[2 * k]) an[h][k] = __ldcs(reinterpret_cast<const double2*>(row + xu[2 * k]));
+                for (int k = 0; k < 2; ++k)
+                    if (xin[2 * k]) an[h][k] = __ldcs(reinterpret_cast<const double2*>(row + xu[2 * k]));
+            }
         }
     };
     load_a(p0);
