@@ -93,6 +93,7 @@ struct GemmArgs {
     int64_t sG;
     int q;
     Band ba, bb;      // bands of A and B
+    int qlast;        // the last squaring launch (it moves the result when s is odd)
 };
 
 __device__ __forceinline__ double lin_at(const Lin4& l, int z, int r, int c) {
@@ -128,8 +129,8 @@ __global__ void __launch_bounds__(GNT) k_dgemm(GemmArgs g) {
         if (g.q >= s) {
             // the run's s squarings are done: the result stays in the buffer the
             // last one wrote, and only the last launch moves it to the buffer the
-            // host reads next (SQ_LAUNCHES is even: needed when s is odd)
-            if (g.q == SQ_LAUNCHES - 1 && ((g.q - s) & 1) == 0) {
+            // host reads next (the launch count is even: needed when s is odd)
+            if (g.q == g.qlast && ((g.q - s) & 1) == 0) {
                 for (int e = threadIdx.x; e < TL * TL; e += GNT) {
                     const int r = r0 + e / TL, c = c0 + e % TL;
                     if (r < M && c < N) C[(int64_t)r * g.ldc + c] = A[(int64_t)r * g.lda + c];
@@ -246,13 +247,21 @@ __global__ void __launch_bounds__(GNT) k_lx_scaling(const double* cs, int64_t sC
     const double inv_fact19 = 1.0 / 121645100408832000.0;  // 19! is exactly representable
     int s = 0;
     double r = nrm;
-    while (s < smax) {
+    bool met = false;
+    while (true) {
         double p = 1.0;
         for (int e = 0; e < 19; ++e) p *= r;
-        if (r < 20.0 && p * inv_fact19 / (1.0 - r / 20.0) <= 0x1p-53) break;
+        if (r < 20.0 && p * inv_fact19 / (1.0 - r / 20.0) <= 0x1p-53) {
+            met = true;
+            break;
+        }
+        if (s == smax) break;
         r *= 0.5;
         ++s;
     }
+    // more squarings needed than launched (a norm bound that did not hold, or
+    // a norm beyond 2^32): reported, not truncated silently
+    if (!met) atomicOr(&const_cast<ColState*>(kd.st + z)->status, KV_ST_SCALING);
     double* out = const_cast<double*>(c) + m;
     out[0] = (double)s;      // the squaring gate
     out[1] = ldexp(1.0, -s);  // the scale
@@ -347,12 +356,12 @@ static int64_t waves_x_work(int M, int N, int nb, int tl) {
 static int gemm(Prob* p, int nb, const double* A, int lda, int64_t sA, const double* B, int ldb, int64_t sB, double* C,
                 int ldc, int64_t sC, int M, int N, int K, KDim kd, int epi = 0, Lin4 lin = Lin4{},
                 const double* gate = nullptr, int64_t sG = 0, int q = 0, Band ba = dense_band(),
-                Band bb = dense_band()) {
+                Band bb = dense_band(), int qlast = SQ_LAUNCHES - 1) {
     // grid: the problem's largest dimension, or the checkpoint's when the
     // host knows it (kd.dim > 0); the kernel reads each run's own dimension
     const int kmax = kd.dim > 0 ? kd.dim : p->m;
     const int Mx = M < 0 ? kmax : M, Nx = N < 0 ? kmax : N;
-    GemmArgs g{A, lda, sA, B, ldb, sB, C, ldc, sC, M, N, K, kd, epi, lin, gate, sG, q, ba, bb};
+    GemmArgs g{A, lda, sA, B, ldb, sB, C, ldc, sC, M, N, K, kd, epi, lin, gate, sG, q, ba, bb, qlast};
     if (epi != 1 && !gate && (Mx <= 16 || Nx <= 16)) {
         int64_t gx = ((int64_t)Mx * Nx + GNT - 1) / GNT;
         if (gx > 152 * 4) gx = 152 * 4;
@@ -393,12 +402,24 @@ static int expm_large_batch(Prob* p, int j0, int nb, int dim, bool write_basis) 
     const dim3 ge(eb, 1, (unsigned)nb);
     k_lx_load<<<ge, GNT, 0, st>>>(p->d_H + (int64_t)j0 * sH, m, sH, X, m, X_, p->dt, kd);
     k_lx_colsum<<<dim3((unsigned)((m + 7) / 8), 1, (unsigned)nb), GNT, 0, st>>>(X, m, X_, cs, X_, kd);
-    k_lx_scaling<<<dim3(1, 1, (unsigned)nb), GNT, 0, st>>>(cs, X_, m, SQ_LAUNCHES, kd);
-    k_lx_scale<<<ge, GNT, 0, st>>>(X, m, X_, scale, X_, kd);
-    KV_CHECK_CUDA(cudaGetLastError());
     // band of H: tridiagonal when every run of the batch is a Lanczos run
     bool lanczos = true;
     for (int j = j0; j < j0 + nb; ++j) lanczos = lanczos && p->method[j] == KV_LANCZOS;
+    // squaring launches: the Lanczos H has ||H_k||_1 <= 3 ||A||_2 (its alpha
+    // are Rayleigh quotients and its beta norms of A v for unit v), and the
+    // Taylor test passes for ||X||_1 <= 1, so with a bound of ||A||_2 at most
+    // ceil(log2(3 dt bound)) squarings are needed (one more for rounding);
+    // otherwise SQ_LAUNCHES.  The count is even (the result ends in `cur`).
+    int L = SQ_LAUNCHES;
+    if (lanczos && std::isfinite(p->sys->norm2_bound)) {
+        const double nrm = 3.0 * p->dt * p->sys->norm2_bound * (1.0 + 1e-9);
+        const int e = nrm > 1.0 ? (int)std::ceil(std::log2(nrm)) : 0;
+        L = std::min(SQ_LAUNCHES, std::max(2, e + 1));
+        L += L & 1;
+    }
+    k_lx_scaling<<<dim3(1, 1, (unsigned)nb), GNT, 0, st>>>(cs, X_, m, L, kd);
+    k_lx_scale<<<ge, GNT, 0, st>>>(X, m, X_, scale, X_, kd);
+    KV_CHECK_CUDA(cudaGetLastError());
     const Band b1 = lanczos ? Band{1, 1} : Band{1, BAND_DENSE};
     const Band b2 = band_sum(b1, b1), b3 = band_sum(b2, b1), b4 = band_sum(b2, b2);
     int rc = gemm(p, nb, X, m, X_, X, m, X_, X2, m, X_, -1, -1, -1, kd, 0, Lin4{}, nullptr, 0, 0, b1, b1);
@@ -424,10 +445,10 @@ static int expm_large_batch(Prob* p, int j0, int nb, int dim, bool write_basis) 
         bt = band_max(band_sum(bt, b4), b3);
         std::swap(cur, nxt);
     }
-    // squarings (SQ_LAUNCHES is even: the result ends in `cur`); launch q
-    // squares only when q < s, so its operand has been squared q times
-    for (int q = 0; q < SQ_LAUNCHES; ++q) {
-        rc = gemm(p, nb, cur, m, X_, cur, m, X_, nxt, m, X_, -1, -1, -1, kd, 0, Lin4{}, gate, X_, q, bt, bt);
+    // squarings (L is even: the result ends in `cur`); launch q squares
+    // only when q < s, so its operand has been squared q times
+    for (int q = 0; q < L; ++q) {
+        rc = gemm(p, nb, cur, m, X_, cur, m, X_, nxt, m, X_, -1, -1, -1, kd, 0, Lin4{}, gate, X_, q, bt, bt, L - 1);
         if (rc) return rc;
         bt = band_sum(bt, bt);
         std::swap(cur, nxt);

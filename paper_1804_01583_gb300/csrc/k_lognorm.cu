@@ -2,6 +2,9 @@
 // CSR matrix, the e^{max(mu,0) T} factor of the a-posteriori bound of
 // Lemma 1 (Sec. 4.2; the lemma's nu(B) for B = -A is -mu(A)).
 //
+// The same pass returns max_i sum_j |a'_ij| (rounded up), for a symmetric A
+// a bound of ||A||_2 that sizes the squarings of the Lanczos exponentials.
+//
 // Gershgorin on the symmetric part: every eigenvalue of (A + A^T)/2 lies in a
 // disc around a_ii of radius sum_{j != i} |a_ij + a_ji| / 2, so
 //   mu <= max_i  a_ii + (sum_{j != i} |a_ij| + sum_{j != i} |a_ji|) / 2,
@@ -39,6 +42,7 @@ struct LnScratch {
     unsigned long long amax_bits, bmax_bits;  // non-negative doubles: raw bits order like values
     unsigned long long g_key, ga_key;         // order keys of max_i g_i and max_i g'_i
     unsigned long long bsum;                  // fixed-point sum of |b_i| / bmax
+    unsigned long long rsum_bits;             // max_i sum_j |a'_ij| (non-negative double bits)
 };
 
 template <typename T>
@@ -88,6 +92,7 @@ __global__ void __launch_bounds__(LNT) k_ln_rows(const int64_t* rp, const int32_
     const int64_t warps = (int64_t)gridDim.x * (LNT / 32);
     const double amax = __longlong_as_double((long long)sc->amax_bits);
     unsigned long long gk = 0ULL, gak = 0ULL;
+    double rmax = 0.0;  // the largest absolute row sum, rounded up
     for (int64_t r = (int64_t)blockIdx.x * (LNT / 32) + (threadIdx.x >> 5); r < n; r += warps) {
         double d = 0.0, off = 0.0;
         for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
@@ -104,19 +109,22 @@ __global__ void __launch_bounds__(LNT) k_ln_rows(const int64_t* rp, const int32_
             const double g = __dadd_ru(d, __dmul_ru(0.5, __dadd_ru(off, cs)));
             gk = max(gk, order_key(g));
             if (b) gak = max(gak, order_key(__dadd_ru(g, __dmul_ru(0.5, fabs(b[r])))));
+            rmax = fmax(rmax, __dadd_ru(__dadd_ru(fabs(d), off), b ? fabs(b[r]) : 0.0));
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         gk = max(gk, __shfl_xor_sync(0xffffffffu, gk, o));
         gak = max(gak, __shfl_xor_sync(0xffffffffu, gak, o));
+        rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     }
     if (lane == 0) {
         atomicMax(&sc->g_key, gk);
         if (b) atomicMax(&sc->ga_key, gak);
+        atomicMax(&sc->rsum_bits, (unsigned long long)__double_as_longlong(rmax));
     }
 }
 
-int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug) {
+int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug, double* row_abs_max) {
     Ctx* c = s->ctx;
     LnScratch* sc = (LnScratch*)c->arena.alloc(sizeof(LnScratch));
     unsigned long long* csum = (unsigned long long*)c->arena.alloc((size_t)s->n * sizeof(unsigned long long));
@@ -157,6 +165,7 @@ int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug)
     }
     *mu = from_order_key(h.g_key);
     *mu_aug = *mu;
+    memcpy(row_abs_max, &h.rsum_bits, sizeof(double));
     if (b_host) {
         double bmax;
         memcpy(&bmax, &h.bmax_bits, sizeof(bmax));

@@ -320,6 +320,12 @@ int kv_system_grid(kv_ctx* c, kv_sys** out, int ndim, const int64_t dims[3], dou
         }
     }
     s->mu_aug = s->mu;
+    if (!b) {  // Gershgorin: |diagonal| + off-diagonal sum <= 4 sum_a |kappa_a| + sum_f gamma_f
+        double nb = 0.0;
+        for (int a = 0; a < ndim; ++a) nb += 4.0 * fabs(coef / (s->h[a] * s->h[a]));
+        for (int f = 0; f < 6; ++f) nb += s->face[f];
+        s->norm2_bound = nb * (1.0 + 1e-12);
+    }
     if (b) {
         s->d_b = (double*)c->arena.alloc((size_t)n * sizeof(double));
         if (!s->d_b) {
@@ -422,7 +428,9 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
         delete s;
         return fail(KV_ECUDA, "kv_system_csr: upload failed: %s", cudaGetErrorString(e));
     }
-    rc = csr_lognorm_bounds(s, b, &s->mu, &s->mu_aug);
+    double rmax = INFINITY;
+    rc = csr_lognorm_bounds(s, b, &s->mu, &s->mu_aug, &rmax);
+    if (!rc && s->symmetric && !b) s->norm2_bound = rmax;  // ||A||_2 <= ||A||_inf for symmetric A
     if (rc) {
         c->arena.free(s->d_rp);
         c->arena.free(s->d_col);
@@ -1201,6 +1209,9 @@ int kv_fetch(kv_prob* p, kv_result* r) {
     if (status & KV_ST_NONFINITE)
         return fail(KV_EINVAL, "a Krylov scalar (the norm of a column, alpha or beta) is not finite (status %d): "
                     "the system or the initial set holds a NaN or overflows", status);
+    if (status & KV_ST_SCALING)
+        return fail(KV_EINVAL, "an exponential of H needed more squarings than the operator's norm bound allowed "
+                    "(status %d)", status);
     return KV_OK;
 }
 

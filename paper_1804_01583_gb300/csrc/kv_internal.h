@@ -162,6 +162,11 @@ struct Sys {
     // upper bounds of the largest eigenvalue of (A + A^T)/2, for A and for
     // A' = [[A, b], [0, 0]] (Lemma 1 of Sec. 4.2 takes e^{max(mu,0) T})
     double mu = 0.0, mu_aug = 0.0;
+    // a bound of ||A||_2 for a symmetric operator (Gershgorin: the largest
+    // absolute row sum, rounded up), +inf where none is known; it bounds
+    // ||H_k||_1 <= 3 ||A||_2 for the Lanczos H and so the squarings of its
+    // exponential
+    double norm2_bound = INFINITY;
     // A^T in CSR form (non-symmetric CSR only), built on first use by a
     // problem that runs the transpose dynamics (Sec. 4.1)
     int64_t* d_rpT = nullptr;
@@ -194,6 +199,7 @@ struct CDesc {  // output matrix C in CSR form on the device
 constexpr int KV_ST_TIMEOUT = 1;    // a bounded device wait expired
 constexpr int KV_ST_INDEX = 2;      // an index outside its vector was skipped, not read
 constexpr int KV_ST_NONFINITE = 4;  // alpha or beta of an iteration is not finite
+constexpr int KV_ST_SCALING = 8;    // an exponential needed more squarings than were launched
 
 // One term of C_r . x: an entry whose column lies outside the vector is
 // skipped (not read) and recorded in *status.
@@ -323,7 +329,7 @@ inline bool is_checkpoint(const Prob* p, int k) {
 }
 int launch_error_final(Prob* p);
 // Gershgorin bound of the symmetric part of a CSR matrix (k_lognorm.cu)
-int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug);
+int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug, double* row_abs_max);
 
 // transpose dynamics (k_csr_transpose.cu)
 int csr_build_transpose(Sys* s);

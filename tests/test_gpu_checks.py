@@ -88,6 +88,26 @@ def test_overflowing_csr_lanczos_is_reported(ctx):
     assert bound_error(kv.solve(base, ctx), oracle.run(base)) <= 1e-9
 
 
+def test_exponential_scaling_beyond_its_range_is_reported(ctx):
+    """The global-memory exponential scales dt H by up to 2^32 (32 squaring
+    launches, fewer when a bound of ||A|| limits them): a step so long that
+    ||dt H||_1 needs more is reported, not truncated.  A step inside the
+    range gives the oracle's bounds."""
+    p = W.heat2d_20(steps=4, dt=1e9)
+    sysh = kv.System(ctx, p.system, p.precision)
+    ph = kv.ProblemHandle(ctx, sysh, p, expm_mode="propagate")
+    try:
+        with pytest.raises(kv.KvError) as ei:
+            ph.run()
+        assert ei.value.code == kv.KV_EINVAL and "squarings" in str(ei.value)
+    finally:
+        ph.close()
+        sysh.close()
+    from parity import bound_error
+    q = W.heat2d_20(steps=40, dt=5.0)
+    assert bound_error(kv.solve(q, ctx, expm_mode="propagate"), oracle.run(q)) <= 1e-9
+
+
 _CHILD = r"""
 import json, sys
 sys.path.insert(0, sys.argv[1])
