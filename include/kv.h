@@ -299,7 +299,14 @@ int kv_problem_bytes(const kv_sys *sys, const kv_problem_desc *desc, int precisi
  * the device until kv_fetch. */
 int kv_enqueue(kv_prob *prob);
 
-/* Wait for the problem's work and copy its results to the host. */
+/* Wait for the problem's work and copy its results to the host.  The results
+ * are copied in every case; the status word the kernels set turns into the
+ * return code: KV_ETIMEOUT (a bounded device wait expired), KV_EINVAL (an
+ * index outside its vector was skipped by a device-side check; a Krylov
+ * scalar was not finite, i.e. the system or the initial set holds a NaN or
+ * overflows; or an exponential of H needed more scaling squarings than were
+ * launched, i.e. ||dt H||_1 beyond 2^32 or beyond the operator's norm bound),
+ * KV_ECUDA (a CUDA error). */
 int kv_fetch(kv_prob *prob, kv_result *res);
 
 /* kv_enqueue + kv_fetch. */
