@@ -326,3 +326,34 @@ def test_device_arrays_checked_like_host_arrays(ctx):
     uns[e0], uns[e0 + 1] = uns[e0 + 1], uns[e0]
     assert make(uns) == kv.KV_EINVAL
     assert make(col, kv.KV_FP32) == kv.KV_EINVAL
+
+
+_PDL_CHILD = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import workloads as W
+import paper_1804_01583_gb300 as kv
+p = W.paper_heat(12, dt=0.1, steps=30, m=40)
+got = kv.solve(p, kv.Context(1 << 28), expm_mode="propagate")
+print("RESULT " + json.dumps({"lo": got["lo"].tolist(), "hi": got["hi"].tolist(), "H": got["H"][0].tolist()}))
+"""
+
+
+def test_dependent_launches_change_no_result(ctx):
+    """The CSR Lanczos pair runs as a programmatic dependent chain (each
+    kernel waits for the one before it on the device, KV_PDL=0 turns the
+    attribute off): the results are bit-identical either way."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for pdl in ("1", "0"):
+        r = subprocess.run([sys.executable, "-c", _PDL_CHILD, os.path.join(root, "tests")], cwd=root,
+                           env=dict(os.environ, KV_PDL=pdl), capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        outs.append(json.loads(next(s for s in r.stdout.splitlines() if s.startswith("RESULT "))[7:]))
+    assert outs[0] == outs[1]
+    ref = oracle.run(W.paper_heat(12, dt=0.1, steps=30, m=40))
+    got = {k: np.array(v) for k, v in outs[0].items()}
+    assert bound_error(got, ref) <= 1e-9
