@@ -917,8 +917,10 @@ def main():
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-csr", dest="csr", action="store_false")
     ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--csr-precision", default="fp32", choices=["fp32", "fp64"],
+                    help="storage of the --csr-only query")
     ap.add_argument("--csr-only", type=int, default=0, metavar="N",
-                    help="only the random-CSR query (FP32, forward) at n = N (profiling case)")
+                    help="only the random-CSR query (forward, --csr-precision) at n = N (profiling case)")
     ap.add_argument("--paper-heat-form", default="grid,csr,grid1000",
                     help="forms of the paper-heat leg: grid (100^3), csr (100^3), grid1000 (1000^3)")
     ap.add_argument("--paper-heat-only", default="", choices=["", "fp64", "fp32"],
@@ -965,7 +967,7 @@ def main():
         dev = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(dev)
         print(json.dumps({"metric": "random-CSR query ms", "csr_workload":
-                          csr_bench(args, dev, n=args.csr_only, legs=(("fp32", "forward"),))}))
+                          csr_bench(args, dev, n=args.csr_only, legs=((args.csr_precision, "forward"),))}))
         return
     if args.paper_heat_only:
         import torch

@@ -18,6 +18,12 @@
 // (CGS2) without re-reading V for it; Alg. 1 uses modified Gram-Schmidt, which
 // gives the same H and P in exact arithmetic.
 //
+// The FP64 form forms the dots pass's products from exact float splits on
+// the FP32 pipe (that pass is otherwise bound by the FP64 pipe); the update
+// and the Lanczos passes keep FP64 arithmetic (moving their few FP64
+// instructions off the pipe made them slower: latency, not the pipe, sets
+// their time).
+//
 // Lanczos (Alg. 3) for symmetric CSR: SpMV fused with alpha_j = v_j . A v_j,
 // then w = A v_j - alpha_j v_j - beta_j v_{j-1} over three rotating buffers.
 //
@@ -33,16 +39,18 @@
 
 #include "kv_internal.h"
 #include "reduce.cuh"
+#include "splits.cuh"
 
 namespace kv {
 
 constexpr int CNT = 256;           // threads per block
-// rows per thread in the dots pass (the FP32 form reduces each basis
-// vector's per-thread partials across the warp as float pairs, so it needs
-// no FP64 instruction per vector and can keep the rows per thread small)
+// rows per thread in the dots pass: 16 for the FP32 form (each basis
+// vector's per-thread partials reduced across the warp as float pairs, so no
+// FP64 instruction per vector), 8 for the FP64 form (its float splits of w and
+// v_j take the registers of a second row set; 8 rows keep two blocks per SM)
 template <typename T>
 struct RowsPer {
-    static constexpr int v = 16;
+    static constexpr int v = 8;
 };
 template <>
 struct RowsPer<float> {
@@ -540,6 +548,35 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
         wv[k] = r < N ? W[r] : (T)0;
         vv[k] = r < N ? Vj[r] : (T)0;
     }
+    // FP64 form: the products are formed on the FP32 pipe from exact float
+    // splits (splits.cuh; this pass is bound by the FP64 pipe otherwise), each
+    // value x held as x1 + x2 (24 exact leading bits, the rest rounded to a
+    // float: 2^-48 of x) at a power-of-two scale: basis vector l by 2^(1-E(s_l))
+    // (|V_l| <= ||V_l|| = 1/s_l), v_j likewise, w by the warp's largest
+    // exponent.  Per (basis vector, warp) the float-pair sums become doubles
+    // once, rescaled.
+    constexpr bool SPLIT = std::is_same<T, double>::value;
+    auto exp_of = [](double x) { return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu); };
+    auto sh_of_scale = [&](double sc) { return 1 - (exp_of(sc) - 1023); };  // 1/sc < 2^result
+    float wh[SPLIT ? CR : 1], wl[SPLIT ? CR : 1], vh[SPLIT ? CR : 1], vl[SPLIT ? CR : 1];
+    int shw = 0, shv = 0;
+    if constexpr (SPLIT) {
+        int ew = 0;
+#pragma unroll
+        for (int k = 0; k < CR; ++k) ew = max(ew, exp_of(wv[k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ew = max(ew, __shfl_xor_sync(0xffffffffu, ew, o));
+        shw = ew - 1023 + 1;  // |w| < 2^shw over the warp
+        shv = sh_of_scale(s->s[j]);
+#pragma unroll
+        for (int k = 0; k < CR; ++k) {
+            const F3 a = split3((double)wv[k], shw), b = split3((double)vv[k], shv);
+            wh[k] = a.a1;
+            wl[k] = __fadd_rn(a.a2, a.a3);
+            vh[k] = b.a1;
+            vl[k] = __fadd_rn(b.a2, b.a3);
+        }
+    }
     auto load = [&](T (&x)[CR], int l) {
         const T* Vl = Vc + (int64_t)l * N;
 #pragma unroll
@@ -613,17 +650,92 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
             }
         }
     };
+    // FP64 form: this thread's products with basis vector l as float pairs
+    // (TwoProduct of the leading parts, the cross terms in the low word,
+    // compensated additions)
+    auto prod_split = [&](const T (&x)[CR], int shx, float& ah, float& al, float& gh, float& gl) {
+        ah = al = gh = gl = 0.f;
+#pragma unroll
+        for (int k = 0; k < CR; ++k) {
+            const F3 xs = split3((double)x[k], shx);
+            const float x1 = xs.a1, x2 = __fadd_rn(xs.a2, xs.a3);
+            float t, e;
+            const float pa = __fmul_rn(x1, wh[k]);
+            const float ea = __fmaf_rn(x1, wh[k], -pa);
+            const float ca = __fmaf_rn(x1, wl[k], __fmul_rn(x2, wh[k]));
+            two_sum(ah, pa, t, e);
+            ah = t;
+            al = __fadd_rn(al, __fadd_rn(e, __fadd_rn(ea, ca)));
+            const float pg = __fmul_rn(x1, vh[k]);
+            const float eg = __fmaf_rn(x1, vh[k], -pg);
+            const float cg = __fmaf_rn(x1, vl[k], __fmul_rn(x2, vh[k]));
+            two_sum(gh, pg, t, e);
+            gh = t;
+            gl = __fadd_rn(gl, __fadd_rn(e, __fadd_rn(eg, cg)));
+        }
+    };
+    // the same transposed butterfly as reduce4 on float pairs; the four totals
+    // become doubles at their scales in wsum
+    auto reduce4p = [&](float ah0, float al0, float gh0, float gl0, float ah1, float al1, float gh1, float gl1,
+                        int l, bool two, int shx0, int shx1) {
+        const bool up = lane & 16, mid = lane & 8;
+        float kh0 = up ? ah1 : ah0, kl0 = up ? al1 : al0, kh1 = up ? gh1 : gh0, kl1 = up ? gl1 : gl0;
+        const float s0h = up ? ah0 : ah1, s0l = up ? al0 : al1, s1h = up ? gh0 : gh1, s1l = up ? gl0 : gl1;
+        {
+            float t, e;
+            const float r0h = __shfl_xor_sync(0xffffffffu, s0h, 16), r0l = __shfl_xor_sync(0xffffffffu, s0l, 16);
+            const float r1h = __shfl_xor_sync(0xffffffffu, s1h, 16), r1l = __shfl_xor_sync(0xffffffffu, s1l, 16);
+            two_sum_f(kh0, r0h, t, e);
+            kh0 = t;
+            kl0 = __fadd_rn(__fadd_rn(kl0, r0l), e);
+            two_sum_f(kh1, r1h, t, e);
+            kh1 = t;
+            kl1 = __fadd_rn(__fadd_rn(kl1, r1l), e);
+        }
+        float h = mid ? kh1 : kh0, lo = mid ? kl1 : kl0;
+        {
+            const float sh = mid ? kh0 : kh1, sl = mid ? kl0 : kl1;
+            const float rh = __shfl_xor_sync(0xffffffffu, sh, 8);
+            const float rl = __shfl_xor_sync(0xffffffffu, sl, 8);
+            float t, e;
+            two_sum_f(h, rh, t, e);
+            h = t;
+            lo = __fadd_rn(__fadd_rn(lo, rl), e);
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            const float rh = __shfl_xor_sync(0xffffffffu, h, o);
+            const float rl = __shfl_xor_sync(0xffffffffu, lo, o);
+            float t, e;
+            two_sum_f(h, rh, t, e);
+            h = t;
+            lo = __fadd_rn(__fadd_rn(lo, rl), e);
+        }
+        if ((lane & 7) == 0 && (two || !up)) {
+            const int q = (up ? l + 1 : l) + (mid ? KV_MAX_M + 1 : 0);
+            wsum[q][warp] = ldexp((double)h + (double)lo, (up ? shx1 : shx0) + (mid ? shv : shw));
+        }
+    };
     // two register buffers: the loads of the next vectors are in flight while
     // the products of the current ones are formed and reduced
     load(xa, 0);
     for (int l = 0; l <= j; l += 2) {
         const bool two = l + 1 <= j;
         if (two) load(xb, l + 1);
-        T a0, g0, a1 = 0, g1 = 0;
-        prod(xa, a0, g0);
-        if (l + 2 <= j) load(xa, l + 2);
-        if (two) prod(xb, a1, g1);
-        reduce4(a0, g0, a1, g1, l, two);
+        if constexpr (SPLIT) {
+            const int shx0 = sh_of_scale(s->s[l]), shx1 = two ? sh_of_scale(s->s[l + 1]) : 0;
+            float ah0, al0, gh0, gl0, ah1 = 0.f, al1 = 0.f, gh1 = 0.f, gl1 = 0.f;
+            prod_split(xa, shx0, ah0, al0, gh0, gl0);
+            if (l + 2 <= j) load(xa, l + 2);
+            if (two) prod_split(xb, shx1, ah1, al1, gh1, gl1);
+            reduce4p(ah0, al0, gh0, gl0, ah1, al1, gh1, gl1, l, two, shx0, shx1);
+        } else {
+            T a0, g0, a1 = 0, g1 = 0;
+            prod(xa, a0, g0);
+            if (l + 2 <= j) load(xa, l + 2);
+            if (two) prod(xb, a1, g1);
+            reduce4(a0, g0, a1, g1, l, two);
+        }
     }
     __syncthreads();
     const int K = j + 1;

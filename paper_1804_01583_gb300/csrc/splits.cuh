@@ -1,8 +1,9 @@
 // splits.cuh -- exact three-float splits of doubles and the compensated
-// float-pair arithmetic built on them, for the sums of squares of the FP64
-// grid iteration formed on the FP32 pipe (on this GPU the FP64 pipe retires
-// about 1/64 of the FP32 rate; each term keeps about 47 significant bits and
-// the sums are compensated, as accurate as FP64 accumulation).
+// float-pair arithmetic built on them, for the FP64 sums that run on the FP32
+// pipe: the sums of squares of the FP64 grid iteration and the dot products
+// of the FP64 Arnoldi pass (on this GPU the FP64 pipe retires about 1/64 of
+// the FP32 rate; each term keeps about 47 significant bits and the sums are
+// compensated, as accurate as FP64 accumulation).
 #pragma once
 
 #include <stdint.h>
