@@ -14,7 +14,10 @@
  *      (Alg. 4, Sec. 4.3).
  *   3. The basis matrix C e^{A t_k} E_j ~ ||E_j|| P e^{H t_k} e_1 for every
  *      step t_k = k dt, k = 0..steps (Eq. approx-formula, Sec. 4.2), with a
- *      batched FP64 Pade-13 scaling-and-squaring exponential of H.
+ *      batched FP64 scaling-and-squaring exponential of H (Pade-13 in shared
+ *      memory up to dimension 64; above it, and for KV_EXPM_PROPAGATE, a
+ *      degree-18 Taylor sum in global-memory GEMMs: the same e^{tH} up to
+ *      rounding).
  *   4. Per step and output row r, the interval [lo, hi] of y_r = C_r x over
  *      the box z_j in [zlo_j, zhi_j], the first step whose upper bound reaches
  *      the unsafe half-space y_r >= theta_r, and the maximising box vertex as
