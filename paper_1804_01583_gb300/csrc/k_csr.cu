@@ -548,10 +548,10 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
         wv[k] = r < N ? W[r] : (T)0;
         vv[k] = r < N ? Vj[r] : (T)0;
     }
-    // FP64 form: the products are formed on the FP32 pipe from exact float
-    // splits (splits.cuh; this pass is bound by the FP64 pipe otherwise), each
-    // value x held as x1 + x2 (24 exact leading bits, the rest rounded to a
-    // float: 2^-48 of x) at a power-of-two scale: basis vector l by 2^(1-E(s_l))
+    // FP64 form: the products are formed on the FP32 pipe from float splits
+    // (splits.cuh; this pass is bound by the FP64 pipe otherwise), each value
+    // x held as x1 + x2 (24 exact leading bits, the rest rounded to a float:
+    // 2^-48 of x) at a power-of-two scale: basis vector l by 2^(1-E(s_l))
     // (|V_l| <= ||V_l|| = 1/s_l), v_j likewise, w by the warp's largest
     // exponent.  Per (basis vector, warp) the float-pair sums become doubles
     // once, rescaled.
@@ -570,11 +570,11 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
         shv = sh_of_scale(s->s[j]);
 #pragma unroll
         for (int k = 0; k < CR; ++k) {
-            const F3 a = split3((double)wv[k], shw), b = split3((double)vv[k], shv);
+            const F2 a = split2((double)wv[k], shw), b = split2((double)vv[k], shv);
             wh[k] = a.a1;
-            wl[k] = __fadd_rn(a.a2, a.a3);
+            wl[k] = a.a2;
             vh[k] = b.a1;
-            vl[k] = __fadd_rn(b.a2, b.a3);
+            vl[k] = b.a2;
         }
     }
     auto load = [&](T (&x)[CR], int l) {
@@ -657,8 +657,8 @@ __global__ void __launch_bounds__(CNT) k_arnoldi_dots(VecArgs<T> V, int64_t N, C
         ah = al = gh = gl = 0.f;
 #pragma unroll
         for (int k = 0; k < CR; ++k) {
-            const F3 xs = split3((double)x[k], shx);
-            const float x1 = xs.a1, x2 = __fadd_rn(xs.a2, xs.a3);
+            const F2 xs = split2((double)x[k], shx);
+            const float x1 = xs.a1, x2 = xs.a2;
             float t, e;
             const float pa = __fmul_rn(x1, wh[k]);
             const float ea = __fmaf_rn(x1, wh[k], -pa);

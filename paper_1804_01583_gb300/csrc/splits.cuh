@@ -44,6 +44,31 @@ __device__ __forceinline__ F3 split3(double x, int sh) {
     return r;
 }
 
+// x 2^-sh = a1 + a2 with a1 exact (the sign, the exponent and mantissa bits
+// 51..29, as in split3) and a2 the remaining 29 bits rounded to a float
+// (|a2 - rest| <= 2^-48 |x 2^-sh|): the two-part form for products, where
+// 2^-48 is below what FP64 accumulation keeps anyway.  Same preconditions
+// and flush as split3.
+struct F2 {
+    float a1, a2;
+};
+__device__ __forceinline__ F2 split2(double x, int sh) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - sh;
+    F2 r;
+    if (e < 1023 - 100) {
+        r.a1 = r.a2 = 0.f;
+        return r;
+    }
+    const unsigned sgn = hi & 0x80000000u;
+    const unsigned pbits = sgn | ((unsigned)(e - 1023 + 127) << 23);
+    r.a1 = __uint_as_float(pbits | (__funnelshift_l(lo, hi, 3) & 0x7fffffu));
+    // bits 28..0 of the mantissa: (lo mod 2^29) 2^-29 in [0, 1), times 2^(e-1023-23)
+    const float P23 = __uint_as_float(sgn | ((unsigned)(e - 1023 - 23 + 127) << 23));
+    r.a2 = __fmul_rn(__fmul_rn(__uint2float_rn(lo & 0x1fffffffu), 0x1p-29f), P23);
+    return r;
+}
+
 // a + b = s + e exactly (TwoSum, Knuth: six float operations, any magnitudes)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
