@@ -530,6 +530,8 @@ def serve_bench(args, dev: int):
                                  "p50_ms": float(np.percentile(lat_half, 50)),
                                  "p99_ms": float(np.percentile(lat_half, 99))},
             "max_running": st["max_running"], "memory_waits": st["memory_waits"],
+            "csr_systems": {"built": st["systems_built"], "reused": st["systems_reused"],
+                            "released_early": st["systems_released"]},
             "plain_fp64_sequential_s": plain["fp64"], "plain_served_precisions_sequential_s": plain["served"],
             "plain_fp32_sequential_s": plain["fp32"],
             "served_makespan_s": makespan,

@@ -354,14 +354,25 @@ int kv_graph_destroy(kv_graph *graph);
  * stream, so the work of different queries overlaps on the device; on
  * completion its results are copied to host storage and its device memory
  * and slot are released.  Results are identical to kv_run on the same query
- * (deterministic reductions; no state is shared between queries). */
+ * (deterministic reductions; queries share nothing but the read-only device
+ * copy of a CSR system, below). */
 typedef struct kv_server kv_server;
 
-/* One query: a system (as for kv_system_stencil / kv_system_csr, host
+/* One query: a system (as for kv_system_stencil, kv_system_grid or kv_system_csr, host
  * arrays) and a problem description with its precision.  The kv_column array
  * is copied by kv_submit; every other host array the query references (CSR
- * arrays, b, column idx/val/dense arrays, C arrays, theta) must stay valid
- * until kv_poll has returned something other than KV_ENOTREADY for it. */
+ * arrays, b, face, column idx/val/dense arrays, C arrays, theta) must stay valid,
+ * with unchanged contents, until kv_poll has returned something other than
+ * KV_ENOTREADY for it.
+ *
+ * CSR queries that name the same row_ptr, col, val and b pointers with the
+ * same n, symmetric and precision share one device copy of the system: it is
+ * built (kv_system_csr: validation, upload, the log-norm bound) when the first
+ * of them is admitted and released when the last of them queued or running
+ * finishes, or earlier when the pool cannot hold an admission and no running
+ * query uses it (it is then rebuilt for the next query naming it).  Equal
+ * pointers are taken to mean equal contents, which the rule above guarantees
+ * while any of the queries is unpolled.  A shared copy changes no result. */
 typedef struct {
     int32_t kind;               /* 0: grid system, 1: CSR system */
     int32_t ndim;               /* grid: 2 or 3 */
@@ -376,6 +387,8 @@ typedef struct {
     const double *b;            /* host, n entries, or NULL */
     kv_problem_desc desc;       /* the problem */
     int32_t precision;          /* KV_FP64 | KV_FP32 (CSR values stored likewise) */
+    const double *face;         /* grid: host, 2 ndim face coefficients as for kv_system_grid,
+                                   or NULL for the Dirichlet-0 boundary of kv_system_stencil */
 } kv_query;
 
 /* Start a server on ctx with `slots` concurrent queries (1..256).  While the
@@ -403,6 +416,12 @@ int kv_poll(kv_server *server, uint64_t ticket, kv_result *res, double *latency_
  * running at once, and admissions deferred because the pool was full. */
 int kv_server_stats(kv_server *server, int64_t *admitted, int64_t *completed, int64_t *pending,
                     int32_t *max_running, int64_t *memory_waits);
+
+/* Shared CSR systems: device copies built, admissions that used a copy already
+ * on the device, copies released early to make room, and copies on the device
+ * now.  Any pointer may be NULL.  Thread-safe.  Errors: KV_EINVAL (NULL server). */
+int kv_server_system_stats(kv_server *server, int64_t *built, int64_t *reused, int64_t *released,
+                           int64_t *resident);
 
 /* Polyhedral initial and unsafe sets (Sec. 2.1, over the projected basis of
  * Sec. 3.1-3.2).  The closed-form bounds of kv_run treat each output row as

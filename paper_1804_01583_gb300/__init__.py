@@ -438,7 +438,7 @@ class kv_query(C.Structure):
     _fields_ = [("kind", C.c_int32), ("ndim", C.c_int32), ("dims", C.c_int64 * 3), ("coef", C.c_double),
                 ("h", C.c_double * 3), ("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
                 ("val", C.c_void_p), ("symmetric", C.c_int32), ("b", C.c_void_p), ("desc", kv_problem_desc),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("face", C.c_void_p)]
 
 
 def _load_server(lib):
@@ -451,7 +451,9 @@ def _load_server(lib):
     lib.kv_poll.argtypes = [V, C.c_uint64, C.POINTER(kv_result), C.POINTER(C.c_double)]
     lib.kv_server_stats.argtypes = [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
-    for f in (lib.kv_server_create, lib.kv_server_destroy, lib.kv_submit, lib.kv_poll, lib.kv_server_stats):
+    lib.kv_server_system_stats.argtypes = [V] + [C.POINTER(C.c_int64)] * 4
+    for f in (lib.kv_server_create, lib.kv_server_destroy, lib.kv_submit, lib.kv_poll, lib.kv_server_stats,
+              lib.kv_server_system_stats):
         f.restype = C.c_int
     lib._server_ready = True
 
@@ -468,18 +470,55 @@ class Server:
         _check(self._lib.kv_server_create(ctx.h, C.byref(h), int(slots)))
         self.h = h
         self._keep: Dict[int, tuple] = {}
+        # converted host arrays per system object while a query names it, so
+        # that queries on one CSR system pass the same pointers and share its
+        # device copy: id -> [system, arrays, queries]
+        self._arrays: Dict[int, list] = {}
+
+    def _system_arrays(self, s) -> tuple:
+        ent = self._arrays.get(id(s))
+        if ent is None:
+            b = getattr(s, "b", None)
+            bb = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+            if hasattr(s, "dims"):
+                face = getattr(s, "face", None)
+                ff = None if face is None else np.ascontiguousarray(face, dtype=np.float64)
+                if ff is not None and ff.shape != (2 * len(s.dims),):
+                    raise ValueError(f"face must hold {2 * len(s.dims)} coefficients")
+                arrs = (bb, ff)
+            else:
+                arrs = (bb, np.ascontiguousarray(s.row_ptr, dtype=np.int64),
+                        np.ascontiguousarray(s.col, dtype=np.int32), np.ascontiguousarray(s.val, dtype=np.float64))
+            ent = self._arrays[id(s)] = [s, arrs, 0]
+        ent[2] += 1
+        return ent[1]
+
+    def _release_arrays(self, s):
+        ent = self._arrays.get(id(s))
+        if ent is not None:
+            ent[2] -= 1
+            if ent[2] == 0:
+                del self._arrays[id(s)]
 
     def submit(self, problem, *, expm_mode: str = "propagate", flags: int = 0) -> int:
-        keep: list = []
-        q = kv_query()
         s = problem.system
-        b = getattr(s, "b", None)
-        if b is not None:
-            bb = np.ascontiguousarray(b, dtype=np.float64)
-            keep.append(bb)
-            q.b = _ptr(bb)
+        arrs = self._system_arrays(s)
+        try:
+            q, keep, t = self._submit(problem, s, arrs, expm_mode, flags)
+        except Exception:
+            self._release_arrays(s)
+            raise
+        self._keep[t] = (q, keep, problem)
+        return t
+
+    def _submit(self, problem, s, arrs, expm_mode, flags):
+        keep: list = [a for a in arrs if a is not None]
+        q = kv_query()
+        if arrs[0] is not None:
+            q.b = _ptr(arrs[0])
         if hasattr(s, "dims"):
             q.kind = 0
+            q.face = _ptr(arrs[1])
             q.ndim = len(s.dims)
             for a in range(3):
                 q.dims[a] = int(s.dims[a]) if a < q.ndim else 1
@@ -487,10 +526,7 @@ class Server:
             q.coef = float(s.coef)
         else:
             q.kind = 1
-            rp = np.ascontiguousarray(s.row_ptr, dtype=np.int64)
-            col = np.ascontiguousarray(s.col, dtype=np.int32)
-            val = np.ascontiguousarray(s.val, dtype=np.float64)
-            keep += [rp, col, val]
+            rp, col, val = arrs[1:]
             q.n = int(s.n)
             q.row_ptr, q.col, q.val = _ptr(rp), _ptr(col), _ptr(val)
             q.symmetric = 1 if s.symmetric else 0
@@ -498,8 +534,7 @@ class Server:
         q.precision = _PREC[problem.precision]
         t = C.c_uint64()
         _check(self._lib.kv_submit(self.h, C.byref(q), C.byref(t)))
-        self._keep[t.value] = (q, keep, problem)
-        return t.value
+        return q, keep, t.value
 
     def poll(self, ticket: int) -> Optional[Dict]:
         """None while queued or running; the results once finished (raises
@@ -518,6 +553,7 @@ class Server:
         if rc == KV_ENOTREADY:
             return None
         del self._keep[ticket]
+        self._release_arrays(p.system)
         _check(rc)
         out["viol_step"] = int(r.first_violation_step)
         out["viol_row"] = int(r.violation_row)
@@ -531,8 +567,11 @@ class Server:
         a, c, pnd, mw = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
         mr = C.c_int32()
         _check(self._lib.kv_server_stats(self.h, C.byref(a), C.byref(c), C.byref(pnd), C.byref(mr), C.byref(mw)))
+        b, u, r, n = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(self._lib.kv_server_system_stats(self.h, C.byref(b), C.byref(u), C.byref(r), C.byref(n)))
         return dict(admitted=a.value, completed=c.value, pending=pnd.value, max_running=mr.value,
-                    memory_waits=mw.value)
+                    memory_waits=mw.value, systems_built=b.value, systems_reused=u.value,
+                    systems_released=r.value, systems_resident=n.value)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -10,11 +10,22 @@
 // slot's completion event has fired, copies the results to host storage,
 // releases the query's device memory and frees the slot for the next query.
 // kv_poll hands a finished query's results to the caller.
+//
+// CSR systems are shared: queries naming the same host arrays (row_ptr, col,
+// val, b) with the same n, symmetry and precision use one device copy, built
+// when the first of them is admitted and kept while any query naming it is
+// queued or running.  Building a CSR system (validation, upload, value
+// conversion, the log-norm pass of Sec. 4.2) is host work of the worker
+// thread, up to about a tenth of a second at n = 2e6, so a system that many
+// queries verify is built once.  When the pool cannot hold an admission, the
+// copies that no running query uses are released first and rebuilt on demand.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -24,6 +35,17 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// Identity of a shared CSR system: the host arrays and the sizes and flags
+// kv_system_csr takes.
+using CsrKey = std::tuple<int64_t, const void*, const void*, const void*, const void*, int32_t, int32_t>;
+
+struct SharedSys {
+    kv_sys* sys = nullptr;  // device copy, nullptr until built (or after release); written by
+                            // the worker under the server mutex
+    int64_t refs = 0;       // queued + running queries naming it (under the server mutex)
+    int64_t running = 0;    // running queries using the copy (worker thread only)
+};
 
 struct Request {
     uint64_t ticket = 0;
@@ -38,7 +60,9 @@ struct Request {
     int32_t viol_step = -1, viol_row = -1;
     double ystar = 0.0;
     // while running
-    kv_sys* sys = nullptr;
+    kv_sys* sys = nullptr;  // owned by the request for grid systems, else shared->sys
+    SharedSys* shared = nullptr;
+    std::map<CsrKey, SharedSys>::iterator shared_it;
     kv_prob* prob = nullptr;
     int slot = -1;
 };
@@ -53,12 +77,14 @@ struct kv_server {
     std::vector<Request*> running;  // per slot
     std::deque<Request*> pending;
     std::unordered_map<uint64_t, Request*> all;
+    std::map<CsrKey, SharedSys> systems;  // shared CSR systems, under mu
     std::mutex mu;
     std::condition_variable cv;
     std::thread worker;
     std::atomic<bool> stop{false};
     uint64_t next_ticket = 1;
     int64_t admitted = 0, completed = 0, waits_for_memory = 0;
+    int64_t systems_built = 0, systems_reused = 0, systems_released = 0;
     int max_running = 0;
 };
 
@@ -69,32 +95,91 @@ int set_stream_and(kv_server* s, int slot) {
     return KV_OK;
 }
 
-// Create the query's system and problem on the slot's stream and enqueue it.
-// Returns KV_OK, KV_ENOMEM (does not fit now) or another error.
+// Drops r's reference to its shared CSR system; the last reference releases
+// the device copy and the entry.
+void drop_shared(kv_server* s, Request* r) {
+    kv_sys* dead = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (--r->shared->refs == 0) {
+            dead = r->shared->sys;
+            s->systems.erase(r->shared_it);
+        }
+    }
+    r->shared = nullptr;
+    kv_sys_destroy(dead);
+}
+
+// Releases the device copies of the shared systems that no running query uses,
+// except `keep`; a query naming one rebuilds it on admission.  Returns how many
+// copies were released.
+int release_idle_systems(kv_server* s, const SharedSys* keep) {
+    std::vector<kv_sys*> idle;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto& kv : s->systems) {
+            SharedSys& e = kv.second;
+            if (&e != keep && e.sys && e.running == 0) {
+                idle.push_back(e.sys);
+                e.sys = nullptr;
+            }
+        }
+        s->systems_released += (int64_t)idle.size();
+    }
+    for (kv_sys* x : idle) kv_sys_destroy(x);
+    return (int)idle.size();
+}
+
+// Create (or take the shared copy of) the query's system and its problem on
+// the slot's stream and enqueue it.  Returns KV_OK, KV_ENOMEM (does not fit
+// now) or another error; on an error the request holds no device memory but
+// its shared system's copy, which stays for the next attempt.
 int admit(kv_server* s, Request* r, int slot) {
     set_stream_and(s, slot);
     const kv_query& q = r->q;
     int rc;
-    if (q.kind == 0)
-        rc = kv_system_stencil(s->ctx, &r->sys, q.ndim, q.dims, q.coef, q.h, q.b);
-    else
-        rc = kv_system_csr(s->ctx, &r->sys, q.n, q.row_ptr, q.col, q.val, q.b, q.symmetric, q.precision, 0);
-    if (rc) return rc;
+    bool reused = false;
+    if (q.kind == 0) {
+        rc = q.face ? kv_system_grid(s->ctx, &r->sys, q.ndim, q.dims, q.coef, q.h, q.face, q.b)
+                    : kv_system_stencil(s->ctx, &r->sys, q.ndim, q.dims, q.coef, q.h, q.b);
+        if (rc) return rc;
+    } else {
+        SharedSys* e = r->shared;
+        reused = e->sys != nullptr;
+        if (!reused) {
+            kv_sys* built = nullptr;
+            rc = kv_system_csr(s->ctx, &built, q.n, q.row_ptr, q.col, q.val, q.b, q.symmetric, q.precision, 0);
+            if (rc) return rc;
+            std::lock_guard<std::mutex> lk(s->mu);
+            e->sys = built;
+            s->systems_built++;
+        }
+        r->sys = e->sys;
+    }
+    auto release = [&]() {
+        if (!r->shared) kv_sys_destroy(r->sys);
+        r->sys = nullptr;
+    };
     kv_problem_desc d = q.desc;
     d.cols = r->cols.data();
     rc = kv_problem(s->ctx, &r->prob, r->sys, &d, q.precision);
     if (rc) {
-        kv_sys_destroy(r->sys);
-        r->sys = nullptr;
+        release();
         return rc;
     }
     rc = kv_enqueue(r->prob);
     if (rc) {
         kv_prob_destroy(r->prob);
-        kv_sys_destroy(r->sys);
         r->prob = nullptr;
-        r->sys = nullptr;
+        release();
         return rc;
+    }
+    if (r->shared) {
+        r->shared->running++;
+        if (reused) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->systems_reused++;
+        }
     }
     r->slot = slot;
     r->t_admit = Clock::now();
@@ -129,8 +214,13 @@ int finish(kv_server* s, Request* r) {
     r->viol_row = res.violation_row;
     r->ystar = res.y_star;
     kv_prob_destroy(r->prob);
-    kv_sys_destroy(r->sys);
     r->prob = nullptr;
+    if (r->shared) {
+        r->shared->running--;
+        drop_shared(s, r);
+    } else {
+        kv_sys_destroy(r->sys);
+    }
     r->sys = nullptr;
     r->t_done = Clock::now();
     return rc;
@@ -168,8 +258,9 @@ void worker_loop(kv_server* s) {
                 if (slot < 0) break;
                 r = s->pending.front();
             }
-            const int rc = admit(s, r, slot);
-            std::lock_guard<std::mutex> lk(s->mu);
+            int rc = admit(s, r, slot);
+            if (rc == KV_ENOMEM && release_idle_systems(s, r->shared) > 0) rc = admit(s, r, slot);
+            std::unique_lock<std::mutex> lk(s->mu);
             if (rc == KV_OK) {
                 s->pending.pop_front();
                 s->running[slot] = r;
@@ -188,8 +279,13 @@ void worker_loop(kv_server* s) {
             }
             // cannot run even on an idle device, or another error: fail it
             s->pending.pop_front();
-            r->status = rc;
             r->error = kv_last_error();
+            if (r->shared) {
+                lk.unlock();
+                drop_shared(s, r);
+                lk.lock();
+            }
+            r->status = rc;
             r->t_done = Clock::now();
             s->completed++;
         }
@@ -250,6 +346,8 @@ int kv_server_destroy(kv_server* s) {
     ::kv::DeviceGuard kv_device_guard_(s->ctx->device);
     for (auto& kv : s->all) delete kv.second;
     for (auto x : s->streams) cudaStreamSynchronize(x);
+    for (auto& kv : s->systems) kv_sys_destroy(kv.second.sys);  // none once every query has finished
+    s->systems.clear();
     s->ctx->stream = s->ctx_stream;
     for (auto x : s->streams) cudaStreamDestroy(x);
     delete s;
@@ -274,6 +372,12 @@ int kv_submit(kv_server* s, const kv_query* q, uint64_t* ticket) {
         delete r;
         kv::set_error("kv_submit: server is shutting down");
         return KV_EBUSY;
+    }
+    if (q->kind == 1) {
+        const CsrKey key{q->n, q->row_ptr, q->col, q->val, q->b, q->symmetric, q->precision};
+        r->shared_it = s->systems.try_emplace(key).first;
+        r->shared = &r->shared_it->second;
+        r->shared->refs++;
     }
     r->ticket = s->next_ticket++;
     s->all[r->ticket] = r;
@@ -335,6 +439,22 @@ int kv_server_stats(kv_server* s, int64_t* admitted, int64_t* completed, int64_t
     if (pending) *pending = (int64_t)s->pending.size();
     if (max_running) *max_running = s->max_running;
     if (memory_waits) *memory_waits = s->waits_for_memory;
+    return KV_OK;
+}
+
+int kv_server_system_stats(kv_server* s, int64_t* built, int64_t* reused, int64_t* released, int64_t* resident) {
+    if (!s) {
+        kv::set_error("kv_server_system_stats: NULL server");
+        return KV_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (built) *built = s->systems_built;
+    if (reused) *reused = s->systems_reused;
+    if (released) *released = s->systems_released;
+    if (resident) {
+        *resident = 0;
+        for (auto& kv : s->systems) *resident += kv.second.sys != nullptr;
+    }
     return KV_OK;
 }
 

@@ -178,3 +178,79 @@ def test_poll_without_outputs_keeps_the_result(lib):
     assert r["lo"].shape == (1, 5) and np.all(r["hi"] >= r["lo"])
     s.close()
     ctx.close()
+
+
+def test_csr_queries_share_one_system_copy(lib):
+    """Queries on one CSR system (direct and transpose dynamics, FP32 and FP64
+    storage) submitted together: one device copy per storage precision is
+    built, the other admissions reuse it, nothing stays resident after they
+    finish, and every result equals kv_run's on a system of its own."""
+    sysm = W.random_csr(6000, seed=77)
+    qs = [W.csr_problem_on(sysm, seed=s, n_gen=g, o=2, c_width=500, dt=0.01, steps=80, m=16, precision=p)
+          for s, (g, p) in enumerate([(1, "fp32"), (12, "fp32"), (3, "fp64"), (1, "fp32"), (20, "fp64"),
+                                      (5, "fp32")])]
+    ctx = kv.Context(2 << 30)
+    s = kv.Server(ctx, slots=4)
+    res = wait_all(s, [s.submit(q) for q in qs])
+    st = s.stats()
+    s.close()
+    assert st["completed"] == len(qs)
+    assert st["systems_built"] == 2 and st["systems_reused"] == len(qs) - 2, st
+    assert st["systems_released"] == 0 and st["systems_resident"] == 0, st
+    for q, r in zip(qs, res):
+        ref = kv.solve(q, ctx, expm_mode="propagate")
+        assert np.array_equal(ref["lo"], r["lo"]) and np.array_equal(ref["hi"], r["hi"]), q.name
+    ctx.close()
+
+
+def test_idle_shared_system_released_when_the_pool_is_full(lib):
+    """One slot and a pool that holds one CSR system and a query but not two
+    systems: after the first query on A, A stays for the third query (also on
+    A), and the query on B finds the pool full; A's idle copy is released to
+    admit it and rebuilt for the third query.  All results equal kv_run's."""
+    A = W.random_csr(60000, seed=5)
+    B = W.random_csr(60000, seed=6)
+    qa = W.csr_problem_on(A, seed=1, n_gen=1, o=2, c_width=500, dt=0.01, steps=40, m=8, precision="fp32")
+    qb = W.csr_problem_on(B, seed=2, n_gen=1, o=2, c_width=500, dt=0.01, steps=40, m=8, precision="fp32")
+    qa2 = W.csr_problem_on(A, seed=3, n_gen=1, o=2, c_width=500, dt=0.01, steps=40, m=8, precision="fp32")
+    # size the pool from the probe: the larger system, the larger problem, half a system of slack
+    probe = kv.Context(1 << 30)
+    used0 = probe.pool_stats()[0]
+    sys_bytes, prob_bytes = 0, 0
+    for q in (qa, qb, qa2):
+        h = kv.System(probe, q.system, precision=q.precision)
+        sys_bytes = max(sys_bytes, probe.pool_stats()[0] - used0)
+        prob_bytes = max(prob_bytes, kv.problem_bytes(h, q, expm_mode="propagate"))
+        h.close()
+    probe.close()
+    pool = sys_bytes + prob_bytes + sys_bytes // 2 + (1 << 20)
+    ctx = kv.Context(pool)
+    s = kv.Server(ctx, slots=1)
+    res = wait_all(s, [s.submit(q) for q in (qa, qb, qa2)])
+    st = s.stats()
+    s.close()
+    assert st["completed"] == 3 and st["systems_released"] >= 1, (st, sys_bytes, prob_bytes)
+    assert st["systems_resident"] == 0
+    ctx2 = kv.Context(1 << 30)
+    for q, r in zip((qa, qb, qa2), res):
+        ref = kv.solve(q, ctx2, expm_mode="propagate")
+        assert np.array_equal(ref["lo"], r["lo"]) and np.array_equal(ref["hi"], r["hi"])
+    ctx2.close()
+    ctx.close()
+
+
+def test_served_grid_with_face_coefficients(lib):
+    """A grid system with face coefficients (the paper's heat model: insulated
+    faces and one exchange face) is served as that system: the result equals
+    kv_run's and differs from the Dirichlet-0 grid of the same sizes."""
+    q = W.paper_heat_grid(24, dt=0.02, steps=60, m=24)
+    d0 = W.Problem(**{**q.__dict__, "system": W.GridSystem(dims=q.system.dims, coef=q.system.coef,
+                                                            h=q.system.h)})
+    ctx = kv.Context(1 << 30)
+    s = kv.Server(ctx, slots=2)
+    r, rd = wait_all(s, [s.submit(q), s.submit(d0)])
+    s.close()
+    ref = kv.solve(q, ctx, expm_mode="propagate")
+    ctx.close()
+    assert np.array_equal(ref["lo"], r["lo"]) and np.array_equal(ref["hi"], r["hi"])
+    assert not np.array_equal(rd["hi"], r["hi"])
