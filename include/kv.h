@@ -262,13 +262,16 @@ int kv_system_grid(kv_ctx *ctx, kv_sys **out, int ndim, const int64_t dims[3], d
                    const double h[3], const double *face, const double *b);
 
 /* Sparse system in CSR form (row_ptr n+1 int64 starting at 0 and
- * non-decreasing, col int32 in [0, n), sorted within a row, val).  When
- * on_device is 0 the three arrays are host memory and are copied; when 1 they
- * are device pointers copied device-to-device, after row_ptr and col have been
- * copied to the host once and checked like host arrays (device arrays need
- * value_precision KV_FP64).  value_precision (KV_FP64 or KV_FP32) is the
- * storage of the values and must match the precision of the problems run on
- * the system.  Errors: KV_EINVAL (malformed arrays, out-of-range or unsorted
+ * non-decreasing, col int32 in [0, n), strictly increasing within a row, val
+ * doubles).  When on_device is 0 the three arrays are host memory and are
+ * copied; when 1 they are device pointers copied device-to-device.  row_ptr is
+ * checked on the host (device arrays: after one copy to the host); the column
+ * indices are checked on the device after the copy, before any kernel reads
+ * through them, and an error names the first offending entry in storage
+ * order.  value_precision (KV_FP64 or KV_FP32) is the storage of the values
+ * and must match the precision of the problems run on the system; KV_FP32
+ * rounds each double to the nearest float on the device (host values pass
+ * through a staging buffer of at most 32 MB from the pool).  Errors: KV_EINVAL (malformed arrays, out-of-range or unsorted
  * columns), KV_ENOMEM, KV_ECUDA.  symmetric: the caller's promise that A is
  * symmetric (enables Lanczos).  b: host, n entries, or NULL. */
 int kv_system_csr(kv_ctx *ctx, kv_sys **out, int64_t n, const int64_t *row_ptr, const int32_t *col,

@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "libkv.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 SOURCES = ["kv_abi.cu", "k_stencil.cu", "k_vector.cu", "k_expm.cu", "k_bounds.cu", "k_csr.cu", "k_stencil_tma.cu", "k_stencil_tma64.cu",
            "k_noalloc.cu", "kv_serve.cu", "kv_graph.cu", "k_lognorm.cu",
-           "k_expm_large.cu", "k_csr_transpose.cu", "k_lp.cu", "k_diag.cu"]
+           "k_expm_large.cu", "k_csr_transpose.cu", "k_csr_check.cu", "k_lp.cu", "k_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]

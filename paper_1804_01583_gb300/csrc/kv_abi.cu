@@ -350,16 +350,12 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
     if (n < 1 || n >= ((int64_t)1 << 31)) return fail(KV_EINVAL, "kv_system_csr: n out of range");
     if (value_precision != KV_FP64 && value_precision != KV_FP32)
         return fail(KV_EINVAL, "kv_system_csr: value_precision");
-    if (on_device && value_precision != KV_FP64)
-        return fail(KV_EINVAL, "kv_system_csr: device arrays need value_precision KV_FP64 (val is double)");
     KV_WITH_DEVICE(c->device);
     int rc = KV_OK;
-    // device arrays: the row pointers and column indices are checked on the
-    // host like host arrays (the kernels index with them), one copy of each
+    // the row pointers bound every read of the other arrays and size the
+    // allocations: checked on the host (device arrays: one copy to the host)
     std::vector<int64_t> hrp;
-    std::vector<int32_t> hcol;
     const int64_t* rp = row_ptr;
-    const int32_t* cl = col;
     if (on_device) {
         hrp.resize((size_t)n + 1);
         KV_CHECK_CUDA(cudaMemcpy(hrp.data(), row_ptr, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -369,19 +365,6 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
     for (int64_t r = 0; r < n; ++r)
         if (rp[r + 1] < rp[r]) return fail(KV_EINVAL, "kv_system_csr: row_ptr decreases at row %lld", (long long)r);
     const int64_t nnz = rp[n];
-    if (on_device && nnz > 0) {
-        hcol.resize((size_t)nnz);
-        KV_CHECK_CUDA(cudaMemcpy(hcol.data(), col, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        cl = hcol.data();
-    }
-    for (int64_t r = 0; r < n; ++r) {
-        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
-            if (cl[e] < 0 || cl[e] >= n)
-                return fail(KV_EINVAL, "kv_system_csr: col[%lld] = %d out of range", (long long)e, cl[e]);
-            if (e > rp[r] && cl[e] <= cl[e - 1])
-                return fail(KV_EINVAL, "kv_system_csr: row %lld columns not strictly increasing", (long long)r);
-        }
-    }
     kv_sys* s = new (std::nothrow) kv_sys();
     if (!s) return fail(KV_ENOMEM, "host allocation");
     s->ctx = c;
@@ -395,48 +378,82 @@ int kv_system_csr(kv_ctx* c, kv_sys** out, int64_t n, const int64_t* row_ptr, co
     s->d_col = (int32_t*)c->arena.alloc((size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t));
     s->d_val = c->arena.alloc(std::max<size_t>(vb, 8));
     if (b) s->d_b = (double*)c->arena.alloc((size_t)n * sizeof(double));
-    if (!s->d_rp || !s->d_col || !s->d_val || (b && !s->d_b)) {
+    unsigned long long* d_bad = (unsigned long long*)c->arena.alloc(sizeof(unsigned long long));
+    auto release = [&]() {
         c->arena.free(s->d_rp);
         c->arena.free(s->d_col);
         c->arena.free(s->d_val);
         c->arena.free(s->d_b);
+        c->arena.free(d_bad);
         delete s;
+    };
+    if (!s->d_rp || !s->d_col || !s->d_val || (b && !s->d_b) || !d_bad) {
+        release();
         return fail(KV_ENOMEM, "kv_system_csr: pool cannot hold the matrix (%lld nnz)", (long long)nnz);
     }
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    cudaError_t e = cudaMemcpyAsync(s->d_rp, row_ptr, (size_t)(n + 1) * sizeof(int64_t), kind, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_col, col, (size_t)nnz * sizeof(int32_t), kind, c->stream);
-    if (e == cudaSuccess) {
-        if (value_precision == KV_FP64) {
-            e = cudaMemcpyAsync(s->d_val, val, (size_t)nnz * sizeof(double), kind, c->stream);
-        } else if (!on_device) {
-            std::vector<float> f((size_t)nnz);
-            for (int64_t q = 0; q < nnz; ++q) f[q] = (float)val[q];
-            e = cudaMemcpyAsync(s->d_val, f.data(), (size_t)nnz * sizeof(float), kind, c->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        } else {
-            e = cudaErrorInvalidValue;
+    // FP32 values from doubles: a staging buffer for host doubles, the largest
+    // of a few sizes the pool holds
+    double* stage = nullptr;
+    int64_t stage_n = 0;
+    if (value_precision == KV_FP32 && !on_device && nnz > 0) {
+        for (int64_t want : {(int64_t)1 << 22, (int64_t)1 << 19, (int64_t)1 << 16}) {
+            stage_n = std::min<int64_t>(want, nnz);
+            stage = (double*)c->arena.alloc((size_t)stage_n * sizeof(double));
+            if (stage) break;
+        }
+        if (!stage) {
+            release();
+            return fail(KV_ENOMEM, "kv_system_csr: pool cannot hold the value staging buffer");
         }
     }
-    if (e == cudaSuccess && b) e = cudaMemcpyAsync(s->d_b, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaStream_t st = c->stream;
+    cudaError_t e = cudaMemcpyAsync(s->d_rp, row_ptr, (size_t)(n + 1) * sizeof(int64_t), kind, st);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(s->d_col, col, (size_t)nnz * sizeof(int32_t), kind, st);
+    if (e == cudaSuccess) e = csr_check_cols_async(s->d_rp, s->d_col, n, d_bad, st);
+    if (e == cudaSuccess && nnz > 0) {
+        if (value_precision == KV_FP64) {
+            e = cudaMemcpyAsync(s->d_val, val, (size_t)nnz * sizeof(double), kind, st);
+        } else if (on_device) {
+            e = round_to_float_async(val, (float*)s->d_val, nnz, st);
+        } else {
+            for (int64_t q = 0; q < nnz && e == cudaSuccess; q += stage_n) {
+                const int64_t cnt = std::min<int64_t>(stage_n, nnz - q);
+                e = cudaMemcpyAsync(stage, val + q, (size_t)cnt * sizeof(double), cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) e = round_to_float_async(stage, (float*)s->d_val + q, cnt, st);
+            }
+        }
+    }
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(s->d_b, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st);
+    unsigned long long first_bad = ~0ULL;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&first_bad, d_bad, sizeof(first_bad), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    c->arena.free(stage);
     if (e != cudaSuccess) {
-        c->arena.free(s->d_rp);
-        c->arena.free(s->d_col);
-        c->arena.free(s->d_val);
-        c->arena.free(s->d_b);
-        delete s;
+        release();
         return fail(KV_ECUDA, "kv_system_csr: upload failed: %s", cudaGetErrorString(e));
     }
+    if (first_bad != ~0ULL) {  // the first offending entry in storage order
+        const int64_t at = (int64_t)first_bad;
+        const int64_t r = (int64_t)(std::upper_bound(rp, rp + n + 1, at) - rp) - 1;
+        int32_t v = 0;
+        if (on_device)
+            e = cudaMemcpy(&v, col + at, sizeof(v), cudaMemcpyDeviceToHost);
+        else
+            v = col[at];
+        release();
+        if (e != cudaSuccess) return fail(KV_ECUDA, "kv_system_csr: %s", cudaGetErrorString(e));
+        if (v < 0 || (int64_t)v >= n)
+            return fail(KV_EINVAL, "kv_system_csr: col[%lld] = %d out of range", (long long)at, v);
+        return fail(KV_EINVAL, "kv_system_csr: row %lld columns not strictly increasing", (long long)r);
+    }
+    c->arena.free(d_bad);
+    d_bad = nullptr;
     double rmax = INFINITY;
     rc = csr_lognorm_bounds(s, b, &s->mu, &s->mu_aug, &rmax);
     if (!rc && s->symmetric && !b) s->norm2_bound = rmax;  // ||A||_2 <= ||A||_inf for symmetric A
     if (rc) {
-        c->arena.free(s->d_rp);
-        c->arena.free(s->d_col);
-        c->arena.free(s->d_val);
-        c->arena.free(s->d_b);
-        delete s;
+        release();
         return rc;
     }
     *out = s;

@@ -333,6 +333,11 @@ int csr_lognorm_bounds(Sys* s, const double* b_host, double* mu, double* mu_aug,
 
 // transpose dynamics (k_csr_transpose.cu)
 int csr_build_transpose(Sys* s);
+// k_csr_check.cu: the column checks of kv_system_csr (smallest offending entry
+// index to *d_first_bad, all ones when none) and the FP32 rounding of values
+cudaError_t csr_check_cols_async(const int64_t* d_rp, const int32_t* d_col, int64_t n, unsigned long long* d_first_bad,
+                                 cudaStream_t st);
+cudaError_t round_to_float_async(const double* src, float* dst, int64_t cnt, cudaStream_t st);
 int row_dot_blocks();
 int launch_row_dot(Prob* p, int j0, int ncols, void* V, int xslot, int wslot, int it);
 int launch_basis_transpose(const Prob* inner, double* out, cudaStream_t st);

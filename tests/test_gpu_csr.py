@@ -295,9 +295,10 @@ def test_many_output_rows_csr(ctx, method):
 
 def test_device_arrays_checked_like_host_arrays(ctx):
     """kv_system_csr with device arrays (on_device = 1): a valid system is
-    accepted; an out-of-range or unsorted column index is rejected with
+    accepted, in FP64 and in FP32 storage (the device doubles rounded on the
+    device); an out-of-range or unsorted column index is rejected with
     KV_EINVAL before any kernel reads it (the indices are checked on the
-    host); FP32 values are refused (the device values are doubles)."""
+    device right after the copy)."""
     import ctypes as C
     import torch
     lib = kv.load()
@@ -325,7 +326,7 @@ def test_device_arrays_checked_like_host_arrays(ctx):
     e0 = int(s.row_ptr[r])
     uns[e0], uns[e0 + 1] = uns[e0 + 1], uns[e0]
     assert make(uns) == kv.KV_EINVAL
-    assert make(col, kv.KV_FP32) == kv.KV_EINVAL
+    assert make(col, kv.KV_FP32) == kv.KV_OK
 
 
 _PDL_CHILD = r"""
@@ -357,3 +358,52 @@ def test_dependent_launches_change_no_result(ctx):
     ref = oracle.run(W.paper_heat(12, dt=0.1, steps=30, m=40))
     got = {k: np.array(v) for k, v in outs[0].items()}
     assert bound_error(got, ref) <= 1e-9
+
+
+def test_fp32_storage_rounds_like_the_host(ctx):
+    """FP32 storage rounds each double to the nearest float on the device:
+    the same bounds as a system whose values were rounded to float on the host
+    beforehand (numpy's round-to-nearest-even cast), for host and device
+    arrays."""
+    import ctypes as C
+    import torch
+    p = W.random_csr_problem(30000, seed=9, n_gen=3, o=2, c_width=200, dt=0.01, steps=30, m=12, precision="fp32")
+    rounded = W.CsrSystem(n=p.system.n, row_ptr=p.system.row_ptr, col=p.system.col,
+                          val=p.system.val.astype(np.float32).astype(np.float64), b=p.system.b)
+    assert not np.array_equal(rounded.val, p.system.val)
+    a = kv.solve(p, ctx)
+    b = kv.solve(W.Problem(**{**p.__dict__, "system": rounded}), ctx)
+    assert np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["hi"], b["hi"])
+    # device arrays, FP32 storage: the same stored floats
+    lib = kv.load()
+    s = p.system
+    rp = torch.tensor(s.row_ptr, dtype=torch.int64, device="cuda")
+    col = torch.tensor(np.asarray(s.col, dtype=np.int32), device="cuda")
+    val = torch.tensor(s.val, dtype=torch.float64, device="cuda")
+    bb = np.ascontiguousarray(s.b, dtype=np.float64)
+    torch.cuda.synchronize()
+    h = C.c_void_p()
+    kv._check(lib.kv_system_csr(ctx.h, C.byref(h), int(s.n), rp.data_ptr(), col.data_ptr(), val.data_ptr(),
+                                bb.ctypes.data, 0, kv.KV_FP32, 1))
+    sysh = kv.System.__new__(kv.System)
+    sysh.ctx, sysh.h, sysh.n = ctx, h, int(s.n)
+    ph = kv.ProblemHandle(ctx, sysh, p)
+    c = ph.run()
+    ph.close()
+    sysh.close()
+    assert np.array_equal(a["lo"], c["lo"]) and np.array_equal(a["hi"], c["hi"])
+
+
+def test_first_malformed_entry_is_reported(ctx):
+    """Two malformed entries: the error names the first in storage order (an
+    unsorted pair in row 1 before an out-of-range index in row 3)."""
+    rp = np.array([0, 2, 4, 5, 7], dtype=np.int64)
+    col = np.array([0, 3, 2, 1, 2, 0, 9], dtype=np.int32)
+    bad = W.CsrSystem(n=4, row_ptr=rp, col=col, val=np.ones(7))
+    with pytest.raises(kv.KvError) as ei:
+        kv.System(ctx, bad)
+    assert ei.value.code == kv.KV_EINVAL and "row 1 " in str(ei.value), str(ei.value)
+    col2 = np.array([0, 3, 1, 2, 2, 0, 9], dtype=np.int32)
+    with pytest.raises(kv.KvError) as ei:
+        kv.System(ctx, W.CsrSystem(n=4, row_ptr=rp, col=col2, val=np.ones(7)))
+    assert "col[6] = 9 out of range" in str(ei.value), str(ei.value)
