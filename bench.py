@@ -206,11 +206,11 @@ GRID_KERNELS = ["lanczos_fused", "lanczos_fused64", "stencil_update", "stencil_a
 
 def fp64_instr_per_launch(p) -> float:
     """Algorithmic FP64 instructions of one single-pass FP64 iteration: the
-    update w = fx (l + r) + fy (d + u) + fz (m + p) + fc c + fa a takes 3
-    pair sums, 1 multiply and 4 fused multiply-adds a grid point (3 FMAs in
-    the first iteration, which has no v_{j-1}); averaged over a query's m
-    launches."""
-    return p.system.n * (7.0 + 8.0 * (p.m - 1)) / p.m
+    update stored as w / (s_j kappa_x) = (l + r) + ry (d + u) + rz (m + p)
+    + rc c + ra a takes 3 pair sums and 4 fused multiply-adds a grid point (3
+    FMAs in the first iteration, which has no v_{j-1}); averaged over a
+    query's m launches."""
+    return p.system.n * (6.0 + 7.0 * (p.m - 1)) / p.m
 
 
 def time_query(ctx, ph, stream, steps: int, warmup: int, torch, barrier=None, clocks=None):

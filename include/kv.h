@@ -257,7 +257,10 @@ int kv_system_stencil(kv_ctx *ctx, kv_sys **out, int ndim, const int64_t dims[3]
  * constant g0 toward ambient 0) face[1] = g / h with
  * g = g0 (2 coef/h) / (2 coef/h + g0), the half cell between the last
  * cell's centre and the face eliminated.  A is symmetric, so KV_AUTO picks
- * Lanczos.  Errors: KV_EINVAL (bad sizes or face values), KV_ENOMEM, KV_ECUDA. */
+ * Lanczos.  Face coefficients need coef > 0 (the kernels hold each as its
+ * share face[f] / (coef/h_a^2) of the coupling it replaces).  Errors:
+ * KV_EINVAL (bad sizes, face values, or a face array with coef <= 0),
+ * KV_ENOMEM, KV_ECUDA. */
 int kv_system_grid(kv_ctx *ctx, kv_sys **out, int ndim, const int64_t dims[3], double coef,
                    const double h[3], const double *face, const double *b);
 

@@ -12,9 +12,12 @@
 // Where the time goes on this GPU: its FP64 pipe retires about two FP64
 // instructions per SM per clock (1/64 of FP32), so an FP64 iteration is bound
 // by its FP64 instruction count, not by HBM.  The vector w itself is computed
-// with FP64 instructions (the minimum for the 7-point update is 8 a point:
-// three neighbour-pair sums, one multiply, four fused multiply-adds).  The two
-// sums that need no FP64 result per point are taken off the FP64 pipe:
+// with FP64 instructions: 8 a point for the 7-point update (three
+// neighbour-pair sums, one multiply, four fused multiply-adds), or 7 in the
+// unit form, which stores w divided by s_j kappa_x (s_j the lazy scale of
+// v_j's buffer) so that the x pair needs no multiply; the factor enters
+// beta_{j+1} and the buffer's scale.  The two sums that need no FP64 result
+// per point are taken off the FP64 pipe:
 //   - each w is split exactly into three floats (a1 + a2 + a3 = w, by integer
 //     operations on its bits: 24 + 23 + 6 significant bits);
 //   - w . w and the summation-by-parts form of w . A w,
@@ -50,6 +53,7 @@
 // word (reported as KV_ETIMEOUT), drains its outstanding copies with bounded
 // waits and leaves.
 #include <cuda.h>
+#include <stdlib.h>
 
 #include <type_traits>
 
@@ -76,15 +80,19 @@ constexpr int DSMEM_TOTAL = DSMEM_MAIN + 128 + 1024;  // + barriers + alignment 
 
 // ------------------------------------------------------------------ kernel --
 struct Fused64Args {
-    double* W;          // output buffer (w = unnormalised v_{j+1})
+    double* W;          // output buffer: w (unnormalised v_{j+1}), or w / (s_j kappa_x) in the unit form
     const double* Aprev;  // v_{j-1} (unnormalised; unused in the first iteration)
     StencilGeom g;
     double gface[6];    // gamma per face: x low, x high, y low, y high, z low, z high
     float gfh[6], gfl[6];  // the same as float pairs (gamma = gfh + gfl to 2^-48), the face terms' weights
     double kmg[6];      // kappa_axis - gamma per face: a face point adds s_j (kappa - gamma) v_p to w
+    double kmgx[6];     // the same divided by kappa_x, for the unit form
+    double ry, rz;      // kappa_y / kappa_x, kappa_z / kappa_x (unit form)
+    double ikx;         // 1 / kappa_x (unit form)
+    double wbound;      // bound of |w| for a unit v_j (4 sum |kappa| + sum gamma >= ||A||_2)
+    int unit_ok;        // the unit form may be used (kappa_x > 0, bounded drift)
     int zc;             // z planes per CTA
     int nbx, nby;       // tiles per z chunk: nbx x nby
-    int sh;             // split scale: |w| 2^-sh < 2^8
     ColState* st;
     double* H;          // this column's (m+1) x m
     double* P;          // this column's o x m
@@ -92,6 +100,18 @@ struct Fused64Args {
     int m, j;
     Reduce red;
 };
+
+// Whether iteration j stores w' = w / (s_j kappa_x) (7 FP64 instructions a
+// point) or w itself (8).  In the unit form each stored buffer is the previous
+// one times beta_{j+1} / kappa_x, so the buffers' magnitudes drift by up to
+// log2(3 wbound / kappa_x) bits an iteration (the host allows the form only
+// below 64); once s_j kappa_x leaves (2^-250, 2^250) one iteration stores w,
+// whose norm is beta_{j+1}, and the drift starts again from there.  Every
+// thread of the launch reads the same s_j, so the choice is uniform.
+__device__ __forceinline__ bool fused64_unit(const Fused64Args& a) {
+    const double f = a.st->s[a.j] * a.g.kx;
+    return a.unit_ok && f > 0x1p-250 && f < 0x1p250;
+}
 
 // The point's face flags: bit 2a for the low face of axis a, 2a+1 for the high.
 __device__ __forceinline__ unsigned face_bits(int x, int y, int z, int nx, int ny, int nz) {
@@ -102,7 +122,7 @@ __device__ __forceinline__ unsigned face_bits(int x, int y, int z, int nx, int n
 // One CTA's tile and chunk of z planes.  Returns false when a stage wait
 // expired (the copies are drained and the timeout reported); otherwise this
 // thread's sums: sum_n = w . w and sum_e = -(w . A w), as doubles.
-template <bool FIRST, bool FACES>
+template <bool FIRST, bool FACES, bool UNIT>
 __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtensorMap* mS, const Fused64Args& a,
                                              int tx, int ty, int tz, unsigned char* sm, int& abort_flag,
                                              double& sum_n, double& sum_e) {
@@ -119,13 +139,29 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
     const int p0 = z0 - 1;  // w planes p0 .. z1-1; the sums run over z0 .. z1-1
     constexpr unsigned stage_bytes = (unsigned)(DBBYTES + DSBYTES);
 
-    // coefficients of w = s_j A v_j - alpha_j s_j v_j - beta_j s_{j-1} v_{j-1}
-    // in the pair-sum form: fx (l + r) + fy (d + u) + fz (m + p) + fc c + fa a
+    // w = s_j A v_j - alpha_j s_j v_j - beta_j s_{j-1} v_{j-1} in the
+    // pair-sum form fx (l + r) + fy (d + u) + fz (m + p) + fc c + fa a
+    // (3 additions, a multiply and 4 FMAs), or in the unit form divided by
+    // fx = s_j kappa_x: (l + r) + ry (d + u) + rz (m + p) + rc c + ra a
+    // (3 additions and 4 FMAs); the factor then goes into beta_{j+1} and the
+    // scale of the stored buffer (Alg. 3's normalisation, applied lazily)
     const double sj = a.st->s[a.j];
     const double alpha = a.H[(int64_t)a.j * a.m + a.j];
-    const double fx = sj * g.kx, fy = sj * g.ky, fz = sj * g.kz;
-    const double fc = sj * (g.kc - alpha);
+    const double fx = sj * g.kx;
     const double fa = FIRST ? 0.0 : -a.H[(int64_t)a.j * a.m + (a.j - 1)] * a.st->s[a.j - 1];
+    const double cy = UNIT ? a.ry : sj * g.ky;
+    const double cz = UNIT ? a.rz : sj * g.kz;
+    const double cc0 = UNIT ? (g.kc - alpha) * a.ikx : sj * (g.kc - alpha);
+    const double ca = UNIT ? fa / fx : fa;
+    // split scale: |stored w| 2^-sh < 2^8, from |w| <= wbound (3 wbound with
+    // the orthogonality the recurrence has lost)
+    int sh = 1;
+    {
+        const double q = UNIT ? a.wbound / fx : a.wbound;
+        int e = 0;
+        if (q > 0.0 && q < INFINITY) frexp(q, &e);  // q < 2^e
+        sh = e + 1;
+    }
 
     auto ring = [](int plane) { return ((plane % DRB) + DRB) % DRB; };
     auto load_b = [&](int plane, uint64_t* bar) {  // v_j plane: main box + side box, same ring slot
@@ -261,19 +297,20 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
                 double wv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    double w = fx * (xl[u] + xr[u]);
-                    w = fma(fy, dd[u] + uu[u], w);
-                    w = fma(fz, mm[u] + pp[u], w);
-                    w = fma(fc, cc[u], w);
-                    if (!FIRST) w = fma(fa, aa[u], w);
+                    double w = xl[u] + xr[u];
+                    if (!UNIT) w *= fx;
+                    w = fma(cy, dd[u] + uu[u], w);
+                    w = fma(cz, mm[u] + pp[u], w);
+                    w = fma(cc0, cc[u], w);
+                    if (!FIRST) w = fma(ca, aa[u], w);
                     if (FACES) {
                         const unsigned fb = face_bits(xu[u], yr[h], p, nx, ny, nz);
-                        if (fb) {  // a point on face f adds s_j (kappa - gamma_f) c
+                        if (fb) {  // a point on face f adds s_j (kappa - gamma_f) c (over fx: unit form)
                             double d = 0.0;
 #pragma unroll
                             for (int f = 0; f < 6; ++f)
-                                if (fb & (1u << f)) d += a.kmg[f];
-                            w = fma(sj * d, cc[u], w);
+                                if (fb & (1u << f)) d += UNIT ? a.kmgx[f] : a.kmg[f];
+                            w = fma(UNIT ? d : sj * d, cc[u], w);
                         }
                     }
                     wv[u] = (pin && yin[h] && xin[u]) ? w : 0.0;
@@ -294,8 +331,8 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const double2 v2 = *reinterpret_cast<const double2*>(Wq + r * DWC + 64 * k + 2 * lane);
-                    cur[2 * k] = split3(v2.x, a.sh);
-                    cur[2 * k + 1] = split3(v2.y, a.sh);
+                    cur[2 * k] = split3(v2.x, sh);
+                    cur[2 * k + 1] = split3(v2.y, sh);
                 }
                 if (qz >= z0 && yint[h]) {
                     // x-1: column 2l-1 is lane l-1's second point, column 63+2l
@@ -320,8 +357,8 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
                         for (int k = 0; k < 2; ++k) {
                             const double2 v2 =
                                 *reinterpret_cast<const double2*>(Wq + (r - 1) * DWC + 64 * k + 2 * lane);
-                            up[2 * k] = split3(v2.x, a.sh);
-                            up[2 * k + 1] = split3(v2.y, a.sh);
+                            up[2 * k] = split3(v2.x, sh);
+                            up[2 * k + 1] = split3(v2.y, sh);
                         }
                     }
 #pragma unroll
@@ -404,7 +441,7 @@ __device__ __forceinline__ bool fused64_tile(const CUtensorMap* mB, const CUtens
         __syncthreads();
         return false;
     }
-    const double s2 = ldexp(1.0, 2 * a.sh);
+    const double s2 = ldexp(1.0, 2 * sh);
     sum_n = acc_n.value() * s2;
     double e = g.kx * acc_x.value() + g.ky * acc_y.value() + g.kz * acc_z.value();
     if (FACES) e += acc_g.value();
@@ -427,8 +464,12 @@ __global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constan
     const int per_z = a.nbx * a.nby;
     const int tz = bid / per_z, q = bid - tz * per_z;
     double sum_n, sum_e;
-    if (!fused64_tile<FIRST, FACES>(&mapB, &mapS, a, q % a.nbx, q / a.nbx, tz, sm, abort_flag, sum_n, sum_e))
-        return;
+    const bool unit = fused64_unit(a);
+    const bool ran = unit ? fused64_tile<FIRST, FACES, true>(&mapB, &mapS, a, q % a.nbx, q / a.nbx, tz, sm, abort_flag,
+                                                             sum_n, sum_e)
+                          : fused64_tile<FIRST, FACES, false>(&mapB, &mapS, a, q % a.nbx, q / a.nbx, tz, sm,
+                                                              abort_flag, sum_n, sum_e);
+    if (!ran) return;
     const double alpha = a.H[(int64_t)a.j * a.m + a.j];
 
     // ---- deterministic grid reduction of (w.w, -w.Aw)
@@ -444,7 +485,9 @@ __global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constan
     __shared__ int cont;
     if (t == 0) {
         const int j = a.j, m = a.m;
-        const double beta = sqrt(nw2);
+        // nw2 and edg: w.w and -w.A w for the stored vector (w, or w / fx)
+        const double nrm = sqrt(nw2);
+        const double beta = unit ? a.st->s[j] * a.g.kx * nrm : nrm;  // ||w||
         a.H[(int64_t)(j + 1) * m + j] = beta;
         const double bj = FIRST ? 0.0 : a.H[(int64_t)j * m + (j - 1)];
         const double nav = sqrt(alpha * alpha + bj * bj + beta * beta);  // ||A v_j||
@@ -454,8 +497,8 @@ __global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constan
             a.st->m_used = j + 1;
             cont = 0;
         } else {
-            a.st->s[j + 1] = 1.0 / beta;
-            snext = 1.0 / beta;
+            a.st->s[j + 1] = 1.0 / nrm;  // v_{j+1} = stored / ||stored||
+            snext = 1.0 / nrm;
             if (j + 1 < m) {
                 a.H[(int64_t)j * m + (j + 1)] = beta;
                 a.H[(int64_t)(j + 1) * m + (j + 1)] = -edg / nw2;  // alpha_{j+1}
@@ -476,10 +519,20 @@ __global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constan
 
 // ---------------------------------------------------------------- host side
 // Whether the single-pass FP64 iteration applies: FP64 grid, rows a multiple
-// of 16 bytes (TMA stride rule: nx even), extents that fit int coordinates.
+// of 16 bytes (TMA stride rule: nx even), extents that fit int coordinates,
+// and at least FUSED64_MIN_POINTS points.  Its float-split sums keep about 47
+// bits a term, so alpha and beta carry relative errors near 1e-14 at any
+// size; plain FP64 dot products (the two-pass kernels) are more accurate
+// below a few thousand points, and on such small grids an exhausted Krylov
+// space (beta at rounding level, Alg. 3's breakdown) is told apart from a
+// continuing one only at that accuracy.  The fused kernel gains nothing
+// there: a grid that small is one partial wave of tiles.
+constexpr int64_t FUSED64_MIN_POINTS = 4096;
+
 bool fused64_supported(const Prob* p) {
     const Sys* s = p->sys;
     if (s->kind != 0 || p->prec != KV_FP64) return false;
+    if (s->n < FUSED64_MIN_POINTS) return false;
     const int64_t nx = s->dims[0], ny = s->ndim >= 2 ? s->dims[1] : 1, nz = s->ndim >= 3 ? s->dims[2] : 1;
     if (nx % 2 != 0 || nx >= ((int64_t)1 << 30) || ny >= ((int64_t)1 << 30) || nz >= ((int64_t)1 << 30))
         return false;
@@ -566,12 +619,22 @@ int fused64_blocks(const Prob* p) { return (int)fused64_grid(p->sys, device_sms(
 
 // The split scale: 2^sh above the largest |w| (|w_p| <= ||w|| <= ||A v_j||
 // <= the Gershgorin bound of A, since v_j has unit norm).
-static int split_shift(const StencilGeom& g, const double* gface) {
-    double bound = 4.0 * (g.kx + g.ky + g.kz);
-    for (int f = 0; f < 6; ++f) bound += gface[f];
-    int e = 0;
-    frexp(bound > 0.0 ? bound : 1.0, &e);  // bound < 2^e
-    return e + 1;
+// |w_i| <= ||w||_2 <= ||A v_j||_2 <= ||A||_2 for a unit v_j; Gershgorin
+// (with every face term added) bounds ||A||_2.
+static double w_bound(const StencilGeom& g, const double* gface) {
+    double bound = 4.0 * (fabs(g.kx) + fabs(g.ky) + fabs(g.kz));
+    for (int f = 0; f < 6; ++f) bound += fabs(gface[f]);
+    return bound > 0.0 ? bound : 1.0;
+}
+
+// KV_FUSED64_UNIT=0 in the environment keeps every iteration in the plain
+// form (w stored as such): the two forms give the same results to rounding.
+static bool unit_form_allowed() {
+    static const bool on = [] {
+        const char* e = getenv("KV_FUSED64_UNIT");
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 int launch_lanczos_fused64(Prob* p, int j, int it, const void* B, const void* Aprev, void* Wout) {
@@ -603,11 +666,17 @@ int launch_lanczos_fused64(Prob* p, int j, int it, const void* B, const void* Ap
         a.gfl[q] = (float)(s->face[q] - (double)a.gfh[q]);
         const double kap = q < 2 ? g.kx : (q < 4 ? g.ky : g.kz);
         a.kmg[q] = kap - s->face[q];
+        a.kmgx[q] = g.kx > 0.0 ? a.kmg[q] / g.kx : 0.0;
     }
+    a.wbound = w_bound(g, s->face);
+    // the unit form: kappa_x > 0 and at most 64 bits of drift an iteration
+    a.unit_ok = g.kx > 0.0 && 3.0 * a.wbound / g.kx < 0x1p64 && unit_form_allowed();
+    a.ry = a.unit_ok ? g.ky / g.kx : 0.0;
+    a.rz = a.unit_ok ? g.kz / g.kx : 0.0;
+    a.ikx = a.unit_ok ? 1.0 / g.kx : 0.0;
     a.zc = f.zc;
     a.nbx = f.nbx;
     a.nby = f.nby;
-    a.sh = split_shift(g, s->face);
     a.st = p->d_state + j;
     a.H = p->d_H + (int64_t)j * (p->m + 1) * p->m;
     a.P = p->d_P + (int64_t)j * p->o * p->m;

@@ -271,10 +271,14 @@ int kv_system_grid(kv_ctx* c, kv_sys** out, int ndim, const int64_t dims[3], dou
         n *= dims[a];
     }
     if (!isfinite(coef)) return fail(KV_EINVAL, "kv_system_stencil: coef");
-    if (face)
+    if (face) {
         for (int f = 0; f < 2 * ndim; ++f)
             if (!isfinite(face[f]) || face[f] < 0.0)
                 return fail(KV_EINVAL, "kv_system_grid: face[%d] must be finite and >= 0", f);
+        // the grid kernels hold a face as its share gamma / kappa of the
+        // coupling it replaces, which needs kappa > 0
+        if (!(coef > 0.0)) return fail(KV_EINVAL, "kv_system_grid: face coefficients need coef > 0");
+    }
     // launch-shape limits of the grid kernels: ceil(ny/8) and ceil(nz/8) blocks
     if (dims[1] > 524280 || (ndim == 3 && dims[2] > 524280))
         return fail(KV_EINVAL, "kv_system_stencil: ny and nz must be <= 524280");

@@ -137,3 +137,26 @@ def test_lanczos_far_above_the_shared_memory_exponential(ctx):
     S = np.max(np.abs(ref["basis"][0]))
     assert np.max(np.abs(got["basis"][0] - ref["basis"][0])) <= 1e-9 * S
     assert bound_error(got, ref) <= 1e-9
+
+
+def test_grid_without_coupling(ctx):
+    """coef = 0: A = 0 and the outputs stay C E z at every step (the Krylov
+    space breaks down after one vector), against the oracle; the grid runs
+    the single-pass FP64 kernel in its plain form (the unit form divides by
+    kappa_x = 0).  Face coefficients with coef = 0 are refused: the kernels
+    hold a face as its share of the coupling it replaces."""
+    dims = (16, 16, 20)
+    sysm = W.GridSystem(dims=dims, coef=0.0, h=(0.1, 0.1, 0.1))
+    base = W.heat(dims, block=(6, 4, 3), output="centre", dt=0.05, steps=20, m=8)
+    cell = W.grid_index(dims, (dims[0] - 1, 2, 1))
+    rp, cc, cv = W._c_rows([([cell, W.grid_index(dims, (3, 2, 1))], [1.0, 1.0])])
+    col = W.Column(kind="box", zlo=0.5, zhi=1.5, box_lo=(2, 0, 0), box_hi=(dims[0], 6, 4), value=1.0)
+    p = W.Problem(**{**base.__dict__, "system": sysm, "columns": [col], "C_row_ptr": rp, "C_col": cc,
+                     "C_val": cv, "theta": np.array([np.inf])})
+    got = run_gpu(ctx, p)
+    assert bound_error(got, oracle.run(p)) <= 1e-9
+    assert np.allclose(got["hi"], 3.0) and np.allclose(got["lo"], 1.0)
+    faced = W.GridSystem(dims=dims, coef=0.0, h=(0.1, 0.1, 0.1), face=(0.0, 3.0, 0.0, 0.0, 0.0, 0.0))
+    with pytest.raises(kv.KvError) as ei:
+        kv.System(ctx, faced)
+    assert ei.value.code == kv.KV_EINVAL and "coef > 0" in str(ei.value)

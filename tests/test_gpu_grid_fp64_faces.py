@@ -65,7 +65,8 @@ def big_block(dims):
                                   (128, 16, 9),     # one tile + 2 columns, one row over
                                   (130, 31, 5),     # two x tiles (the second 4 wide), 3 y tiles
                                   (254, 30, 20),    # 3 x tiles, the last 2 columns wide
-                                  (2, 3, 2),        # tiny: 2 columns in a 128-column region
+                                  (2, 3, 2),        # below 4096 points: the two-pass kernels
+                                  (2, 40, 60),      # 2 columns in a 128-column region
                                   (20, 20, 200),    # many z chunks of one tile each
                                   (1000, 40)])      # 2-D, 8 x tiles
 @pytest.mark.parametrize("flags", [0, TWO_PASS])
@@ -252,3 +253,64 @@ def test_faces_fp32_tile_shapes(ctx, dims, flags):
     eh, _ = krylov_error(got, ref, 0)
     assert eh <= 1e-5, eh
     assert bound_error(got, ref) <= 1e-6
+
+
+def test_small_grids_take_the_two_pass_kernels(ctx):
+    """Below 4096 points the FP64 grid iteration runs the two-pass kernels
+    (FP64 dot products, more accurate than the float-split sums at that
+    size); from 4096 points on, the single-pass kernel."""
+    for dims, fused in (((2, 3, 2), False), ((16, 16, 15), False), ((16, 16, 16), True)):
+        p = W.heat(dims, block=big_block(dims), output="centre8", dt=1e-4, steps=10, m=8)
+        ctx.profile_enable(True)
+        run_gpu(ctx, p)
+        launches, _ = ctx.profile_read("lanczos_fused64")
+        ctx.profile_enable(False)
+        assert (launches > 0) == fused, (dims, launches)
+
+
+_UNIT_CHILD = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import workloads as W
+import paper_1804_01583_gb300 as kv
+ctx = kv.Context(1 << 30)
+out = {}
+for name, p in (("paper", W.paper_heat_grid(32, dt=0.05, steps=100, m=300)),
+                ("dirichlet", W.heat((40, 30, 20), block=(9, 7, 5), output="edge", dt=0.01, steps=80, m=200))):
+    got = kv.solve(p, ctx, expm_mode="propagate")
+    out[name] = {"lo": got["lo"].tolist(), "hi": got["hi"].tolist(), "H": got["H"][0].tolist(),
+                 "m_used": int(got["m_used"][0])}
+print("RESULT " + json.dumps(out))
+"""
+
+
+def test_unit_form_matches_the_plain_form(ctx):
+    """The single-pass FP64 kernel stores w divided by s_j kappa_x (one FP64
+    instruction a point fewer) and stores w itself for one iteration whenever
+    the buffers' scale has drifted by 2^250 (here after about 150 of 300
+    iterations).  Against every iteration in the plain form
+    (KV_FUSED64_UNIT=0): the same Krylov dimension, H to rounding over the
+    first 100 iterations, the same bounds; and the paper's heat model against
+    the oracle."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for unit in ("1", "0"):
+        r = subprocess.run([sys.executable, "-c", _UNIT_CHILD, root], cwd=root,
+                           env=dict(os.environ, KV_FUSED64_UNIT=unit), capture_output=True, text=True, timeout=900)
+        assert r.returncode == 0, r.stdout + r.stderr
+        outs.append(json.loads(next(s for s in r.stdout.splitlines() if s.startswith("RESULT "))[7:]))
+    for name in ("paper", "dirichlet"):
+        a = {k: np.array(v) for k, v in outs[0][name].items()}
+        b = {k: np.array(v) for k, v in outs[1][name].items()}
+        assert int(a["m_used"]) == int(b["m_used"]), name
+        # later entries of a recurrence without reorthogonalisation amplify
+        # rounding differences; the first 100 iterations agree to rounding
+        assert np.max(np.abs(a["H"][:101, :100] - b["H"][:101, :100])) <= 1e-9 * np.max(np.abs(b["H"])), name
+        assert bound_error(a, b) <= 1e-9, name
+    ref = oracle.run(W.paper_heat(32, dt=0.05, steps=100, m=300))
+    got = {k: np.array(v) for k, v in outs[0]["paper"].items()}
+    assert bound_error(got, ref) <= 1e-9
