@@ -930,7 +930,7 @@ def main():
     ap.add_argument("--pool-gb", type=int, default=0,
                     help="device pool of the --csr-only and --paper-heat-only cases (GB; profiling runs keep it small)")
     ap.add_argument("--serve-queries", type=int, default=512)
-    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-pool-gb", type=int, default=160)
     args = ap.parse_args()
 
