@@ -184,6 +184,16 @@ typedef struct {
    ceil(run / G) * G * N * element size bytes to kv_problem_bytes (run = the
    longest run of Arnoldi columns). */
 
+/* Other environment variables the library reads (once per process):
+   KV_AUTOTUNE_CACHE  path of the SpMM autotuner's cache file (default
+                      $HOME/.cache/kv_autotune.txt);
+   KV_PDL=0           launches the CSR Lanczos pair without programmatic
+                      dependent launch (the results are bit-identical);
+   KV_FUSED64_UNIT=0  keeps every single-pass FP64 grid iteration in the plain
+                      form, w stored as such, instead of the unit form that
+                      stores w / (s_j coef/h_x^2) with one FP64 instruction a
+                      point fewer (the results agree to rounding). */
+
 #define KV_MAX_M 256           /* largest krylov_m when any column runs Arnoldi */
 #define KV_MAX_M_LANCZOS 4096  /* largest krylov_m when every column runs Lanczos
                                   (above 64 the exponential runs in global memory) */
