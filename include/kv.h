@@ -187,8 +187,9 @@ typedef struct {
 /* Other environment variables the library reads (once per process):
    KV_AUTOTUNE_CACHE  path of the SpMM autotuner's cache file (default
                       $HOME/.cache/kv_autotune.txt);
-   KV_PDL=0           launches the CSR Lanczos pair without programmatic
-                      dependent launch (the results are bit-identical);
+   KV_PDL=0           launches the CSR Lanczos pair and the single-pass FP64
+                      grid iteration without programmatic dependent launch
+                      (the results are bit-identical);
    KV_FUSED64_UNIT=0  keeps every single-pass FP64 grid iteration in the plain
                       form, w stored as such, instead of the unit form that
                       stores w / (s_j coef/h_x^2) with one FP64 instruction a

@@ -453,6 +453,7 @@ template <bool FIRST, bool FACES>
 __global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constant__ CUtensorMap mapB,
                                                            const __grid_constant__ CUtensorMap mapS,
                                                            Fused64Args a) {
+    dep_wait();  // the previous iteration's w, scalars and state are complete
     if (a.st->done) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -479,6 +480,9 @@ __global__ void __launch_bounds__(DNT, 2) k_lanczos_fused64(const __grid_constan
     const int64_t slot = bid;
     if (t == 0) a.red.partials[nb + slot] = d_edg;
     if (!grid_arrive(d_nrm, a.red.partials, a.red.counter, slot, nb, &flag)) return;
+    // the last CTA: every other CTA has finished, so the next launch may be
+    // scheduled (its CTAs wait in dep_wait until this grid has completed)
+    dep_release();
     const double nw2 = grid_finish<DNT>(a.red.partials, nb, a.red.counter, shred);
     const double edg = grid_finish<DNT>(a.red.partials + nb, nb, a.red.counter, shred);
     __shared__ double snext;
@@ -617,8 +621,6 @@ static int device_sms(int device) {
 
 int fused64_blocks(const Prob* p) { return (int)fused64_grid(p->sys, device_sms(p->ctx->device)).blocks; }
 
-// The split scale: 2^sh above the largest |w| (|w_p| <= ||w|| <= ||A v_j||
-// <= the Gershgorin bound of A, since v_j has unit norm).
 // |w_i| <= ||w||_2 <= ||A v_j||_2 <= ||A||_2 for a unit v_j; Gershgorin
 // (with every face term added) bounds ||A||_2.
 static double w_bound(const StencilGeom& g, const double* gface) {
@@ -689,14 +691,12 @@ int launch_lanczos_fused64(Prob* p, int j, int it, const void* B, const void* Ap
     LaunchScope ls(p->ctx, "lanczos_fused64");
     cudaStream_t st = p->ctx->stream;
     const dim3 grd((unsigned)f.blocks);
-    if (s->faces) {
-        if (it == 0) k_lanczos_fused64<true, true><<<grd, DNT, DSMEM_TOTAL, st>>>(mB, mS, a);
-        else k_lanczos_fused64<false, true><<<grd, DNT, DSMEM_TOTAL, st>>>(mB, mS, a);
-    } else {
-        if (it == 0) k_lanczos_fused64<true, false><<<grd, DNT, DSMEM_TOTAL, st>>>(mB, mS, a);
-        else k_lanczos_fused64<false, false><<<grd, DNT, DSMEM_TOTAL, st>>>(mB, mS, a);
-    }
-    KV_CHECK_CUDA(cudaGetLastError());
+    // programmatic dependent launch: the launch and the CTAs' start overlap
+    // the previous kernel's last CTA (the grid reduction and the projection)
+    const bool pdl = dep_launch_ok(p->ctx);
+    auto kern = s->faces ? (it == 0 ? k_lanczos_fused64<true, true> : k_lanczos_fused64<false, true>)
+                         : (it == 0 ? k_lanczos_fused64<true, false> : k_lanczos_fused64<false, false>);
+    KV_CHECK_CUDA(launch_dep(pdl, kern, grd, dim3(DNT), (size_t)DSMEM_TOTAL, st, mB, mS, a));
     return KV_OK;
 }
 
