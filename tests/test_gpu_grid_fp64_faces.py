@@ -314,3 +314,31 @@ def test_unit_form_matches_the_plain_form(ctx):
     ref = oracle.run(W.paper_heat(32, dt=0.05, steps=100, m=300))
     got = {k: np.array(v) for k, v in outs[0]["paper"].items()}
     assert bound_error(got, ref) <= 1e-9
+
+
+_PDL_GRID_CHILD = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import workloads as W
+import paper_1804_01583_gb300 as kv
+p = W.paper_heat_grid(32, dt=0.05, steps=60, m=60)
+got = kv.solve(p, kv.Context(1 << 30), expm_mode="propagate")
+print("RESULT " + json.dumps({"lo": got["lo"].tolist(), "hi": got["hi"].tolist(), "H": got["H"][0].tolist()}))
+"""
+
+
+def test_grid_dependent_launches_change_no_result(ctx):
+    """The single-pass FP64 grid iteration runs as a programmatic dependent
+    chain (KV_PDL=0 turns it off): bit-identical results either way."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for pdl in ("1", "0"):
+        r = subprocess.run([sys.executable, "-c", _PDL_GRID_CHILD, root], cwd=root,
+                           env=dict(os.environ, KV_PDL=pdl), capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        outs.append(json.loads(next(s for s in r.stdout.splitlines() if s.startswith("RESULT "))[7:]))
+    assert outs[0] == outs[1]
