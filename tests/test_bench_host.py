@@ -97,3 +97,13 @@ def test_reference_arm_line_on_small_workload():
     assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_fp64_roofline_counts_the_unit_form():
+    """The FP64 roofline's algorithmic work: 7 FP64 instructions a grid point
+    (3 pair sums, 4 FMAs; w stored divided by s_j kappa_x), 6 in the first
+    iteration, averaged over the m launches of a query."""
+    import workloads as W
+    p = W.heat((40, 30, 20), block=(4, 4, 4), output="centre", dt=0.1, steps=5, m=30)
+    n = 40 * 30 * 20
+    assert bench.fp64_instr_per_launch(p) == pytest.approx(n * (6 + 7 * 29) / 30)
