@@ -50,3 +50,17 @@ def test_create_without_gpu_fails_cleanly(lib):
     with pytest.raises(kv.KvError) as ei:
         kv.Context(1 << 20)
     assert ei.value.code in (kv.KV_ECUDA, kv.KV_EINVAL)
+
+
+@pytest.mark.parametrize("std", [["gcc", "-std=c11", "-x", "c"], ["g++", "-std=c++17", "-x", "c++"]])
+def test_header_compiles_standalone(std):
+    """include/kv.h on its own, as C11 and as C++17, pedantic, warnings as
+    errors: the boundary needs no CUDA or torch header."""
+    import shutil
+    import subprocess
+    if not shutil.which(std[0]):
+        pytest.skip(f"{std[0]} not found")
+    hdr = os.path.join(ROOT, "include", "kv.h")
+    r = subprocess.run([std[0], std[1], "-pedantic", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", *std[2:], hdr],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
